@@ -1,0 +1,446 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the
+mathematics: closed forms, invariants, textbook special cases, brute force.
+None of these tests re-types an oracle formula; each would fail on a
+plausible mistake (sign, index, dropped term, transposed operand)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+from oracle import (BC, Fluid, Grid, Options, Problem, assemble, basis_operator,
+                    build_wirebasket, cams_iteration, coarse_operator, ilu0, ilu_apply,
+                    prolongation, prolongation_global, restriction, run)
+from oracle.basis import PRows
+from oracle.coarse import coarse_factor, coarse_solve
+from oracle.problem import accumulation_coefficient, residual, epsilon
+from oracle.solver import BasisState, solve_step
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(nx, ny, nz):
+    h = 1.0 / nx
+    return Grid(nx, ny, nz, h, h, h)
+
+
+def _lognormal(N, rng, s=1.5):
+    k = np.exp(s * rng.standard_normal(N))
+    return k, k.copy(), k.copy()
+
+
+def _problem(g, k, law=0, c=0.1, dirichlet=True, src=None):
+    fl = Fluid(law, c, 1.0, 1.0, 0.1)
+    bc = BC(dirichlet, 1.0, 0.0) if src is None else BC(dirichlet, 1.0, 0.0, *src)
+    return Problem.build(g, fl, bc, *k)
+
+
+# ---------------------------------------------------------------- Sec. 2 --
+
+def test_tpfa_series_resistance(rng):
+    """1D incompressible steady flow through layers: the flux equals
+    Delta p / sum_i (h / (A k_i)) (resistances in series) on every face."""
+    n = 17
+    g = Grid(n, 1, 1, 0.3, 2.0, 0.5)
+    k = np.exp(2.0 * rng.standard_normal(n))
+    pb = _problem(g, (k, k, k), law=1, c=0.0)        # rho = 1: incompressible
+    lin = assemble(pb, np.zeros(n), np.zeros(n), 1.0)
+    p = spl.spsolve(lin.A.tocsc(), lin.f)
+    area = g.dy * g.dz
+    q_exact = (1.0 - 0.0) / np.sum(g.dx / (area * k))
+    fc = pb.faces
+    q = fc.T * (p[fc.lo] - p[fc.hi])
+    np.testing.assert_allclose(q, q_exact, rtol=1e-12)
+
+
+@pytest.mark.parametrize("shape,coarse", [((12, 1, 1), (4, 1, 1)), ((10, 10, 1), (5, 5, 1)),
+                                          ((8, 6, 4), (4, 3, 2))])
+def test_linear_pressure_closed_form(shape, coarse):
+    """Homogeneous k, incompressible, Dirichlet 1/0 on west/east: TPFA
+    reproduces p_i = 1 - (x_i + 1/2)/nx exactly, and C-AMS converges to it."""
+    g = _grid(*shape)
+    one = np.ones(g.N)
+    pb = _problem(g, (one, one, one), law=1, c=0.0)
+    opt = Options(coarse=coarse, basis=4, n_post=2, nl_tol=1e-13, max_newton=20)
+    p, st = run(pb, opt, np.zeros(g.N), 1e-3, 1)
+    x, _, _ = g.coords()
+    np.testing.assert_allclose(p, 1.0 - (x + 0.5) / g.nx, atol=1e-12)
+    assert st[0].converged
+
+
+def test_epsilon_matches_linear_residual(rng):
+    """Eq. 19 and Eqs. 3-6 are two statements of one balance: at p^nu,
+    f - A p^nu = V rho eps = -F(p^nu)."""
+    g = _grid(6, 5, 4)
+    k = _lognormal(g.N, rng)
+    src = (np.array([3, 50]), np.array([0.7, -0.4]))
+    for law, c in ((0, 0.3), (1, 0.8)):
+        pb = _problem(g, k, law=law, c=c, src=src)
+        p = rng.uniform(-0.5, 1.5, g.N)
+        pn = rng.uniform(-0.5, 1.5, g.N)
+        lin = assemble(pb, p, pn, 0.01)
+        r = lin.f - lin.A @ p
+        np.testing.assert_allclose(r, g.V * lin.rho * lin.eps, rtol=1e-10, atol=1e-12 * np.abs(r).max())
+        np.testing.assert_allclose(r, -residual(pb, p, pn, 0.01), rtol=1e-10, atol=1e-12 * np.abs(r).max())
+
+
+@pytest.mark.parametrize("law,c", [(0, 0.2), (1, 1.0)])
+def test_accumulation_coefficient_is_derivative(law, c):
+    """Eq. 4: c = d/dp [ phi/dt - phi rho^n / (dt rho(p)) ] (complex step)."""
+    fl = Fluid(law, c, 1.3, 1.0, 0.1)
+    p = np.linspace(-0.4, 1.2, 9)
+    pn = np.linspace(0.3, -0.2, 9)
+    dt = 0.02
+    hstep = 1e-30
+    pz = p + 1j * hstep
+    rho_z = fl.rho0 * (np.exp(c * pz) if law == 0 else (1 + c * pz))
+    g = -fl.phi * fl.rho(pn) / (dt * rho_z)
+    np.testing.assert_allclose(accumulation_coefficient(fl, p, pn, dt), g.imag / hstep, rtol=1e-13)
+
+
+def test_global_mass_balance(rng):
+    """Internal fluxes cancel: sum_i F_i = accumulation + Dirichlet boundary
+    flux - sources, for any p."""
+    g = _grid(7, 5, 3)
+    k = _lognormal(g.N, rng)
+    src = (np.array([0, 100]), np.array([0.5, -0.25]))
+    pb = _problem(g, k, c=0.4, src=src)
+    p = rng.uniform(0, 1, g.N)
+    pn = rng.uniform(0, 1, g.N)
+    F = residual(pb, p, pn, 0.05)
+    fl, fc = pb.fluid, pb.faces
+    acc = g.V * fl.phi * np.sum(fl.rho(p) - fl.rho(pn)) / 0.05
+    bnd = np.sum(fc.b_T * fl.rho(fc.b_p) * (p[fc.b_cell] - fc.b_p))
+    srcs = np.sum(fl.rho(p)[src[0]] * src[1])
+    assert abs(F.sum() - (acc + bnd - srcs)) < 1e-11 * (abs(acc) + abs(bnd) + 1)
+
+
+def test_flux_divergence_second_order():
+    """Consistency with Eq. 1: for homogeneous k and a smooth pressure the
+    cell-averaged flux divergence of Eq. 19 tends to div(rho lambda grad p)
+    at second order in h."""
+    def err(n):
+        g = Grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n)
+        one = np.ones(g.N)
+        fl = Fluid(0, 0.5, 1.0, 1.0, 0.1)
+        pb = Problem.build(g, fl, BC(False), one, one, one)
+        x, y, z = [(c + 0.5) / n for c in g.coords()]
+        P = lambda x, y, z: np.sin(np.pi * x) * np.cos(np.pi * y) * np.cos(np.pi * z)
+        p = P(x, y, z)
+        # interior cells only (the no-flow boundary is not consistent with P)
+        inner = (g.coords()[0] > 0) & (g.coords()[0] < n - 1) & (g.coords()[1] > 0) & \
+                (g.coords()[1] < n - 1) & (g.coords()[2] > 0) & (g.coords()[2] < n - 1)
+        dt = 1.0
+        eps = epsilon(pb, p, p, dt)          # accumulation cancels with p_n = p
+        rho = fl.rho(p)
+        num = eps * rho                      # = div(rho lambda grad p), q = 0
+        # exact: div(exp(c p) grad p) = exp(c p) (c |grad p|^2 + lap p)
+        c, pi = 0.5, np.pi
+        px = pi * np.cos(pi * x) * np.cos(pi * y) * np.cos(pi * z)
+        py = -pi * np.sin(pi * x) * np.sin(pi * y) * np.cos(pi * z)
+        pz = -pi * np.sin(pi * x) * np.cos(pi * y) * np.sin(pi * z)
+        lap = -3 * pi ** 2 * p
+        exact = np.exp(c * p) * (c * (px ** 2 + py ** 2 + pz ** 2) + lap)
+        return np.max(np.abs(num - exact)[inner])
+    e1, e2 = err(24), err(48)
+    assert 3.4 < e1 / e2 < 4.6
+
+
+def test_dense_direct_newton(rng):
+    """O-exact: the C-AMS solution is the root of the nonlinear residual, as
+    found by a plain Newton iteration with a finite-difference Jacobian and
+    dense LU (tiny grid, compressible, heterogeneous, wells)."""
+    g = _grid(6, 6, 4)
+    k = _lognormal(g.N, rng, 1.0)
+    src = (np.array([0, g.N - 1]), np.array([0.02, -0.02]))
+    for dirichlet in (True, False):
+        pb = _problem(g, k, c=0.5, dirichlet=dirichlet, src=src)
+        pn = np.zeros(g.N)
+        dt = 0.005
+        p = pn.copy()
+        for _ in range(30):
+            F = residual(pb, p, pn, dt)
+            J = np.zeros((g.N, g.N))
+            for j in range(g.N):
+                e = np.zeros(g.N); e[j] = 1e-7
+                J[:, j] = (residual(pb, p + e, pn, dt) - residual(pb, p - e, pn, dt)) / 2e-7
+            p = p - np.linalg.solve(J, F)
+            if np.linalg.norm(F) < 1e-15:
+                break
+        for R in (0, 1):
+            opt = Options(coarse=(3, 3, 2), basis=4, restriction=R, n_post=3, nl_tol=1e-12)
+            q, st = run(pb, opt, pn, dt, 1)
+            assert st[0].converged
+            np.testing.assert_allclose(q, p, rtol=0, atol=1e-10 * np.abs(p).max())
+
+
+# ---------------------------------------------------------------- Sec. 3 --
+
+def test_wirebasket_golden_2d():
+    rows = [l.strip() for l in open(os.path.join(GOLDEN, "wirebasket_10x10_b5x5.txt"))
+            if l.strip() and not l.startswith("#")]
+    want = np.array([[{"V": 0, "E": 1, "I": 2}[ch] for ch in r] for r in rows])
+    wb = build_wirebasket(_grid(10, 10, 1), (5, 5, 1))
+    np.testing.assert_array_equal(wb.level.reshape(10, 10), want)
+    assert wb.Nc == 4
+
+
+def test_wirebasket_counts_3d():
+    """Level counts of a 6x6x4 grid with 3x3x2 blocks follow from the number
+    of vertex coordinates per direction (2, 2, 2) and non-vertex ones (4, 4, 2)."""
+    wb = build_wirebasket(_grid(6, 6, 4), (3, 3, 2))
+    counts = np.bincount(wb.level, minlength=4)
+    np.testing.assert_array_equal(counts, [8, 16 + 16 + 8, 32 + 16 + 16, 32])
+    # every entity's corners are vertices; each non-vertex cell is in one entity
+    assert np.all((wb.entity >= 0) == (wb.level > 0))
+    assert sum(len(e.cells) for e in wb.entities) == np.count_nonzero(wb.level)
+
+
+def _P(g, k, coarse, basis, pb=None, p=None):
+    pb = pb or _problem(g, k)
+    p = np.zeros(g.N) if p is None else p
+    lin = assemble(pb, p, np.zeros(g.N), 0.01)
+    Ab = basis_operator(pb, basis, lin.rho, lin.c, np.zeros(g.N), 0.01)
+    wb = build_wirebasket(g, coarse)
+    return prolongation(Ab, wb).to_csr(wb.Nc), wb, Ab, lin
+
+
+@pytest.mark.parametrize("basis", [4, 2])
+def test_partition_of_unity(rng, basis):
+    g = _grid(12, 10, 6)
+    P, wb, _, _ = _P(g, _lognormal(g.N, rng, 2.0), (4, 5, 3), basis,
+                     p=None)
+    s = np.asarray(P.sum(axis=1)).ravel()
+    np.testing.assert_allclose(s, 1.0, atol=1e-13)
+    assert P.data.min() >= -1e-14 and P.data.max() <= 1 + 1e-14
+
+
+@pytest.mark.parametrize("basis", [1, 3])
+def test_compressible_basis_not_unity(rng, basis):
+    """Fig. 2: with the accumulation term the basis functions decay and do
+    not sum to one (but stay non-negative)."""
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 1.0)
+    pb = _problem(g, k, c=2.0)
+    P, wb, _, _ = _P(g, k, (4, 5, 3), basis, pb=pb, p=np.full(g.N, 0.3))
+    s = np.asarray(P.sum(axis=1)).ravel()
+    nv = wb.level > 0
+    assert np.all(s[nv] < 1.0) and np.all(s[~nv] == 1.0)
+    assert P.data.min() >= 0.0
+
+
+def _hat(n, b, x):
+    """1D basis values of every coarse node at fine coordinate x for
+    homogeneous coefficients: linear between neighbouring nodes, constant
+    beyond the first/last node."""
+    nc = n // b
+    v = np.arange(nc) * b + b // 2
+    out = np.zeros(nc)
+    if x <= v[0]:
+        out[0] = 1.0
+    elif x >= v[-1]:
+        out[-1] = 1.0
+    else:
+        J = np.searchsorted(v, x, side="right") - 1
+        t = (x - v[J]) / b
+        out[J] = 1 - t
+        out[J + 1] = t
+    return out
+
+
+@pytest.mark.parametrize("shape,coarse", [((15, 1, 1), (5, 1, 1)), ((12, 8, 1), (4, 4, 1)),
+                                          ((8, 9, 6), (4, 3, 3))])
+def test_homogeneous_basis_is_multilinear(shape, coarse):
+    """For homogeneous k and (B4) the reduced-problem basis functions are the
+    tensor products of 1D linear hats (bilinear/trilinear are discrete
+    harmonic for the 5-/7-point stencil)."""
+    g = _grid(*shape)
+    one = np.ones(g.N)
+    P, wb, _, _ = _P(g, (one, one, one), coarse, 4)
+    P = P.toarray()
+    x, y, z = g.coords()
+    for i in range(g.N):
+        hx = _hat(g.nx, coarse[0], x[i]) if g.nx > 1 else np.ones(1)
+        hy = _hat(g.ny, coarse[1], y[i]) if g.ny > 1 else np.ones(1)
+        hz = _hat(g.nz, coarse[2], z[i]) if g.nz > 1 else np.ones(1)
+        want = np.einsum("k,j,i->kji", hz, hy, hx).ravel()
+        np.testing.assert_allclose(P[i], want, atol=1e-13)
+
+
+@pytest.mark.parametrize("basis", [1, 4])
+def test_staged_basis_equals_global_reduced_solve(rng, basis):
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 2.0)
+    pb = _problem(g, k, c=1.0)
+    P, wb, Ab, _ = _P(g, k, (4, 5, 3), basis, pb=pb, p=np.full(g.N, 0.2))
+    Pg = prolongation_global(Ab, wb)
+    np.testing.assert_allclose(P.toarray(), Pg.toarray(), atol=1e-12)
+
+
+def test_msfe_coarse_matrix_symmetric_spd(rng):
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 2.0)
+    P, wb, _, lin = _P(g, k, (4, 5, 3), 4)
+    Ac = coarse_operator(restriction(0, P, wb), lin.A, P)
+    assert np.abs(Ac - Ac.T).max() <= 1e-14 * np.abs(Ac).max()
+    np.linalg.cholesky(Ac)
+
+
+@pytest.mark.parametrize("R", [0, 1])
+def test_multiscale_stage_exact_on_coarse_space(rng, R):
+    """If the solution lies in range(P), one multiscale stage (Eq. 14)
+    recovers it from any start."""
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 2.0)
+    P, wb, _, lin = _P(g, k, (4, 5, 3), 4)
+    Rm = restriction(R, P, wb)
+    pc = rng.standard_normal(wb.Nc)
+    pstar = P @ pc
+    f = lin.A @ pstar
+    lu = coarse_factor(coarse_operator(Rm, lin.A, P))
+    LU = ilu0(lin.A)
+    p = cams_iteration(lin.A, f, np.zeros(g.N), P, Rm, lu, LU, 0, 0)
+    np.testing.assert_allclose(p, pstar, atol=1e-11 * np.abs(pstar).max())
+
+
+def test_msfv_local_conservation(rng):
+    """After an MSFV stage the restricted residual vanishes block by block
+    (locally conservative, Sec. 4)."""
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 2.0)
+    P, wb, _, lin = _P(g, k, (4, 5, 3), 4)
+    Rm = restriction(1, P, wb)
+    lu = coarse_factor(coarse_operator(Rm, lin.A, P))
+    p0 = rng.standard_normal(g.N)
+    r = lin.f - lin.A @ p0
+    p1 = p0 + P @ coarse_solve(lu, Rm @ r)
+    blk = Rm @ (lin.f - lin.A @ p1)
+    scale = np.abs(Rm @ np.abs(lin.f - lin.A @ p0)).max()
+    assert np.abs(blk).max() <= 1e-12 * scale
+
+
+def test_msfe_1d_homogeneous_coarse_laplacian():
+    """1D homogeneous, incompressible, (B4) + MSFE: the Galerkin coarse matrix
+    is the 3-point Laplacian of the coarse grid, coarse transmissibility
+    T / b, on rows away from the boundary."""
+    n, b = 30, 5
+    g = Grid(n, 1, 1, 1.0, 1.0, 1.0)
+    one = np.ones(n)
+    pb = _problem(g, (one, one, one), law=1, c=0.0)
+    P, wb, _, lin = _P(g, (one, one, one), (b, 1, 1), 4, pb=pb)
+    Ac = coarse_operator(restriction(0, P, wb), lin.A, P)
+    T = 1.0
+    for J in range(1, wb.Nc - 1):
+        np.testing.assert_allclose(Ac[J, J - 1:J + 2], [-T / b, 2 * T / b, -T / b], atol=1e-14)
+
+
+def _dense_ilu_check(A, L, U):
+    A = A.toarray(); LU = (L @ U).toarray()
+    mask = A != 0
+    np.testing.assert_allclose(LU[mask], A[mask], atol=1e-13 * np.abs(A).max())
+    assert np.all(L.toarray()[np.triu_indices(A.shape[0], 1)] == 0)
+    assert np.all(U.toarray()[np.tril_indices(A.shape[0], -1)] == 0)
+    # the factors keep the pattern of A (no fill)
+    Lm, Um = L.toarray(), U.toarray()
+    off = ~mask & ~np.eye(A.shape[0], dtype=bool)
+    assert np.all(Lm[off] == 0) and np.all(Um[off] == 0)
+
+
+def test_ilu0_reproduces_A_on_its_pattern(rng):
+    g = _grid(5, 4, 3)
+    pb = _problem(g, _lognormal(g.N, rng), c=0.3)
+    lin = assemble(pb, rng.uniform(0, 1, g.N), np.zeros(g.N), 0.02)
+    L, U = ilu0(lin.A)
+    _dense_ilu_check(lin.A, L, U)
+    # a non-symmetric matrix with the same pattern
+    B = lin.A.copy(); B.data = B.data * rng.uniform(0.5, 1.5, B.data.size)
+    B = B + sp.diags(np.abs(B).sum(axis=1).A1)
+    L, U = ilu0(B.tocsr())
+    _dense_ilu_check(B.tocsr(), L, U)
+
+
+def test_ilu0_tridiagonal_is_exact(rng):
+    """No fill for a tridiagonal matrix: ILU(0) = LU and one smoothing step
+    solves the 1D system."""
+    g = Grid(20, 1, 1, 1.0, 1.0, 1.0)
+    pb = _problem(g, _lognormal(20, rng), c=0.2)
+    lin = assemble(pb, np.zeros(20), np.zeros(20), 0.1)
+    LU = ilu0(lin.A)
+    p = ilu_apply(LU, lin.f)
+    np.testing.assert_allclose(lin.A @ p, lin.f, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(p, sla.solve(lin.A.toarray(), lin.f), rtol=1e-12, atol=1e-15)
+
+
+def test_ilu0_diagonal_recursion_7point(rng):
+    """For a 7-point stencil in natural order ILU(0) only changes the
+    diagonal: d_i = a_ii - sum_{j lower nbr} a_ij a_ji / d_j."""
+    g = _grid(6, 5, 4)
+    pb = _problem(g, _lognormal(g.N, rng), c=0.3)
+    A = assemble(pb, rng.uniform(0, 1, g.N), np.zeros(g.N), 0.02).A.toarray()
+    d = np.zeros(g.N)
+    for i in range(g.N):
+        d[i] = A[i, i]
+        for j in (i - 1, i - g.nx, i - g.nx * g.ny):
+            if j >= 0 and A[i, j] != 0:
+                d[i] -= A[i, j] * A[j, i] / d[j]
+    L, U = ilu0(sp.csr_matrix(A))
+    np.testing.assert_allclose(U.diagonal(), d, rtol=1e-14)
+    np.testing.assert_array_equal(sp.triu(U, 1).toarray(), np.triu(A, 1))
+
+
+# ------------------------------------------------------- Sec. 4.1.1/4.1.2 --
+
+def test_adaptive_basis_updates(rng):
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 1.5)
+    pb = _problem(g, k, c=1.0)
+    wb = build_wirebasket(g, (4, 5, 3))
+    ne = len(wb.entities)
+    pn = np.zeros(g.N)
+
+    def Ab(kind, p):
+        lin = assemble(pb, p, pn, 0.01)
+        return basis_operator(pb, kind, lin.rho, lin.c, pn, 0.01)
+
+    # (B4) is pressure independent: built once, never again (Sec. 3)
+    st = BasisState(wb)
+    assert st.update(Ab(4, pn), 0.1) == ne
+    assert st.update(Ab(4, rng.uniform(0, 1, g.N)), 0.1) == 0
+    # theta < 0: no adaptivity, everything is rebuilt
+    assert st.update(Ab(4, pn), -1.0) == ne
+    # (B1): a huge threshold keeps the first build
+    st1 = BasisState(wb)
+    st1.update(Ab(1, pn), 1e30)
+    assert st1.update(Ab(1, rng.uniform(0, 1, g.N)), 1e30) == 0
+    # a change confined to one edge segment rebuilds it and everything above
+    # it that depends on it, and nothing else
+    st2 = BasisState(wb)
+    A0 = Ab(4, pn)
+    st2.update(A0, 0.1)
+    edge = next(i for i, e in enumerate(wb.entities) if e.level == 1 and len(e.cells) > 1)
+    A1 = A0.copy().tolil()
+    c0 = wb.entities[edge].cells[0]
+    A1[c0, c0] = A1[c0, c0] * 1.5
+    n = st2.update(A1.tocsr(), 0.1)
+    deps = st2._deps
+    faces = {i for i, e in enumerate(wb.entities) if e.level == 2 and edge in deps[i]}
+    inter = {i for i, e in enumerate(wb.entities) if e.level == 3 and deps[i] & faces}
+    assert n == 1 + len(faces) + len(inter)
+    # the adaptive result equals a full rebuild with the same operator
+    full = prolongation(A1.tocsr(), wb).to_csr(wb.Nc)
+    np.testing.assert_allclose(st2.matrix().toarray(), full.toarray(), atol=1e-14)
+
+
+def test_newton_control_counts(rng):
+    """Every linearisation runs at least one C-AMS iteration; the stopping
+    test is on ||eps||_2 relative to the start of the step (Reading R13)."""
+    g = _grid(10, 10, 1)
+    pb = _problem(g, _lognormal(g.N, rng), c=0.5)
+    opt = Options(coarse=(5, 5, 1), basis=4, n_post=1, nl_tol=1e-8)
+    p, st = run(pb, opt, np.zeros(g.N), 0.002, 2)
+    for s in st:
+        assert s.converged and s.newton_its == len(s.cams_per_newton)
+        assert all(c >= 1 for c in s.cams_per_newton)
+        assert s.eps_hist[-1] < 1e-8 * s.eps_hist[0] <= s.eps_hist[-2]

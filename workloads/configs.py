@@ -1,0 +1,139 @@
+"""Workload definitions: grids, coarsening, fluid, boundary conditions, time
+step and solver options of the synthetic cases, and the recipe that turns
+one into concrete input arrays.
+
+Non-dimensionalisation follows Sec. 4 of the paper: the domain has unit
+length in x (cells are cubes of side h = 1/nx), Delta p = p_west - p_east = 1,
+mu = 1, phi = 0.1, and the time step is Delta t = Delta t* . tau with
+tau = mu phi L^2 / (K_bar Delta p), K_bar the geometric mean of k (Eq. 18).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+import math
+
+import numpy as np
+
+from .fields import lognormal_permeability
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    coarse: tuple            # primal block size (bx, by, bz)
+    sigma: float             # standard deviation of ln k
+    corr: tuple              # correlation lengths / L along (x, y, z)
+    kz_ratio: float = 1.0
+    cov: str = "exponential"
+    angle_deg: float = 0.0
+    law: int = 0             # 0: rho = rho0 exp(c p); 1: rho = rho0 (1 + eta p)
+    c_or_eta: float = 0.1
+    rho0: float = 1.0
+    mu: float = 1.0
+    phi: float = 0.1
+    bc: str = "dirichlet_we"  # or "wells"
+    p_west: float = 1.0
+    p_east: float = 0.0
+    well_rate: float = 0.02   # drawdown scale of the well rates (wells only)
+    steps: int = 1
+    dt_star: float = 0.01
+    basis: int = 4            # 1..4 = Eqs. (B1)..(B4)
+    restriction: int = 0      # 0 = MSFE, 1 = MSFV
+    n_pre: int = 0
+    n_post: int = 1
+    lin_rtol: float = 0.1
+    nl_tol: float = 1e-6
+    adapt_theta: float = 0.1
+    max_newton: int = 50
+    max_cams: int = 200
+    seeds: tuple = (0,)
+
+    @property
+    def n_cells(self):
+        return self.nx * self.ny * self.nz
+
+    def with_(self, **kw):
+        return replace(self, **kw)
+
+
+WORKLOADS = {
+    # 2D 40x40 unit square, 8x8 coarse, exponential rho with c dp = 0.1,
+    # Dirichlet west/east, 5 steps of dt* = 0.01, (B4), MSFE, 1 ILU(0) post step.
+    "2d-40x40": Workload(
+        name="2d-40x40", nx=40, ny=40, nz=1, coarse=(5, 5, 1), sigma=2.0,
+        corr=(0.1, 0.1, 0.1), c_or_eta=0.1, steps=5, basis=4, restriction=0,
+        n_post=1, nl_tol=1e-6, seeds=tuple(range(20))),
+    # 3D 100x100x50 layered field, kz = 0.1 k, c dp = 0.2, two wells in
+    # opposite corners, 10 steps, 10x10x5 coarse, (B1) adaptive at 0.1.
+    "3d-100x100x50-wells": Workload(
+        name="3d-100x100x50-wells", nx=100, ny=100, nz=50, coarse=(10, 10, 5),
+        sigma=3.0, corr=(0.2, 0.2, 0.02), kz_ratio=0.1, c_or_eta=0.2,
+        bc="wells", steps=10, basis=1, restriction=0, n_post=5,
+        nl_tol=1e-6, adapt_theta=0.1, seeds=(0, 1, 2, 3, 4)),
+    # 3D 200x200x100 (4M cells), sigma 3, corr 0.1 L, 20x20x10 coarse,
+    # Dirichlet west/east, (B4), MSFE, 5 ILU(0) post steps, tolerance 1e-8.
+    "3d-200x200x100": Workload(
+        name="3d-200x200x100", nx=200, ny=200, nz=100, coarse=(10, 10, 10),
+        sigma=3.0, corr=(0.1, 0.1, 0.1), c_or_eta=0.1, steps=1, basis=4,
+        restriction=0, n_post=5, nl_tol=1e-8, seeds=(0,)),
+}
+
+
+def _cell_transmissibility_sum(w: Workload, kx, ky, kz, h):
+    """Sum over the internal faces of each cell of A_f / (h/(2k_a) + h/(2k_b))
+    (cubic cells, mu = 1); only used to size the well rates."""
+    shp = (w.nz, w.ny, w.nx)
+    out = np.zeros(shp)
+    for k, ax in ((kx, 2), (ky, 1), (kz, 0)):
+        kk = np.asarray(k).reshape(shp)
+        if kk.shape[ax] < 2:
+            continue
+        a = np.take(kk, np.arange(kk.shape[ax] - 1), axis=ax)
+        b = np.take(kk, np.arange(1, kk.shape[ax]), axis=ax)
+        t = (h * h) / (h / (2 * a) + h / (2 * b))
+        lo = [slice(None)] * 3; lo[ax] = slice(0, kk.shape[ax] - 1)
+        hi = [slice(None)] * 3; hi[ax] = slice(1, kk.shape[ax])
+        out[tuple(lo)] += t
+        out[tuple(hi)] += t
+    return out.ravel()
+
+
+def make_inputs(w: Workload, seed: int | None = None):
+    """Concrete arrays and scalars for one realisation of workload w.
+
+    Returns a dict with grid spacing, kx/ky/kz (float64, length N, index
+    x + nx*(y + ny*z)), the time step dt, the initial pressure p0 (zero, as
+    in Sec. 4.1.3) and the source list (cell ids and volumetric rates q_i dV_i).
+    """
+    seed = w.seeds[0] if seed is None else seed
+    kx, ky, kz = lognormal_permeability(
+        w.nx, w.ny, w.nz, w.sigma, w.corr, seed, kind=w.cov,
+        kz_ratio=w.kz_ratio, angle_deg=w.angle_deg)
+    h = 1.0 / w.nx
+    k_bar = math.exp(float(np.mean(np.log(kx))))
+    dp = 1.0
+    tau = w.mu * w.phi * 1.0 ** 2 / (k_bar * dp)
+    dt = w.dt_star * tau
+    src_cell = np.zeros(0, dtype=np.int32)
+    src_rate = np.zeros(0, dtype=np.float64)
+    if w.bc == "wells":
+        # Vertical line wells through all layers at columns (0,0) (injector)
+        # and (nx-1, ny-1) (producer).  Rates are fixed for the whole run.
+        # Each perforated cell gets the rate that a pressure difference of
+        # well_rate across all of its internal faces would drive,
+        # q_i dV_i = +-well_rate * sum_faces T (TPFA, harmonic k average), so
+        # that pressures stay O(well_rate) whatever the realisation.
+        inj = np.array([0 + w.nx * (0 + w.ny * z) for z in range(w.nz)], np.int64)
+        prod = np.array([(w.nx - 1) + w.nx * ((w.ny - 1) + w.ny * z) for z in range(w.nz)], np.int64)
+        src_cell = np.concatenate([inj, prod]).astype(np.int32)
+        tsum = _cell_transmissibility_sum(w, kx, ky, kz, h)
+        src_rate = np.concatenate([w.well_rate * tsum[inj], -w.well_rate * tsum[prod]])
+    return dict(
+        nx=w.nx, ny=w.ny, nz=w.nz, dx=h, dy=h, dz=h,
+        kx=kx, ky=ky, kz=kz, dt=dt, tau=tau, k_bar=k_bar,
+        p0=np.zeros(w.n_cells), src_cell=src_cell, src_rate=src_rate,
+        dirichlet=(w.bc == "dirichlet_we"), p_west=w.p_west, p_east=w.p_east,
+    )
