@@ -1,0 +1,186 @@
+/*
+ * cams.h -- C-ABI of the GB300 (sm_103a) C-AMS pressure solver.
+ *
+ * The library solves one implicit time step of single-phase compressible
+ * flow in heterogeneous porous media (Sec. 2, Eqs. 1-6) with the adaptive
+ * algebraic multiscale solver C-AMS (Sec. 3, Table 1) inside a Newton loop
+ * with linear-system update adaptivity (Sec. 4.1.1) and adaptive multiscale
+ * operator updates (Sec. 4.1.2).  Every step runs in the library's own CUDA
+ * kernels on one GPU; there is no CPU fallback: without a usable CUDA device
+ * every entry point that needs one returns CAMS_ECUDA.
+ *
+ * Conventions shared by all entry points
+ *   - Cartesian grid of nx*ny*nz cells, cell index i = x + nx*(y + ny*z),
+ *     x fastest.  All fields are float64 arrays of N = nx*ny*nz entries in
+ *     that order.  A direction with one cell is inactive (2D: nz = 1).
+ *   - Pointers given to the library are HOST pointers when
+ *     cams_options.memspace == CAMS_HOST and DEVICE pointers (on the
+ *     handle's device) when memspace == CAMS_DEVICE.  The caller keeps
+ *     ownership of every buffer it passes; inputs are copied at the call
+ *     and never retained.  Outputs are written before the call returns.
+ *   - The handle owns all device memory it allocates (cudaMalloc at
+ *     cams_setup and at the first use of an optional feature).
+ *   - Every entry point returns CAMS_OK (0) or a negative CAMS_E* code and
+ *     never aborts the process or throws; the message of the last failure
+ *     is returned by cams_last_error.  A handle is not thread-safe.
+ *   - Work is issued on the handle's stream (default stream unless set with
+ *     cams_set_stream) and completed before the call returns.
+ */
+#ifndef CAMS_H
+#define CAMS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CAMS_OK          0
+#define CAMS_EINVAL     -1  /* bad argument: sizes, coarse size not dividing the grid, k/phi/dt <= 0 */
+#define CAMS_ENOMEM     -2  /* device or host allocation failed */
+#define CAMS_ECUDA      -3  /* CUDA runtime error (message carries cudaGetErrorString) */
+#define CAMS_ENOCONV    -4  /* max_newton reached; p_inout holds the last iterate */
+#define CAMS_ESINGULAR  -5  /* zero or non-finite pivot in a local or coarse factorisation */
+#define CAMS_ETIMEOUT   -6  /* a device-side wait exceeded its iteration limit */
+#define CAMS_ENAN       -7  /* a non-finite value appeared in a norm */
+
+/* memory spaces */
+#define CAMS_HOST   0
+#define CAMS_DEVICE 1
+
+/* density laws (Sec. 4): rho = rho0 exp(c p)  or  rho = rho0 (1 + eta p) */
+#define CAMS_RHO_EXP    0
+#define CAMS_RHO_LINEAR 1
+
+typedef struct cams_handle cams_handle;
+
+/* Fine grid (Sec. 4: Delta x / alpha = Delta y = Delta z). */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+} cams_grid;
+
+/* Fluid and rock: density law and its coefficient (c or eta), rho0,
+ * viscosity mu, porosity phi (constant, d phi/dp = 0). */
+typedef struct {
+  int law;
+  double c_or_eta;
+  double rho0;
+  double mu;
+  double phi;
+} cams_fluid;
+
+/* Boundary conditions and sources.  dirichlet != 0 fixes p = p_west on the
+ * west faces (x = 0) and p = p_east on the east faces (x = nx-1); every
+ * other face is no-flow.  n_src point sources: src_cell[k] is a cell index,
+ * src_rate[k] the integrated volumetric rate q_i dV_i of Eq. 6 (positive =
+ * injection).  src_cell/src_rate follow cams_options.memspace and may be
+ * NULL when n_src == 0.  Repeated cells add up. */
+typedef struct {
+  int dirichlet;
+  double p_west, p_east;
+  int n_src;
+  const int* src_cell;
+  const double* src_rate;
+} cams_bc;
+
+/* Solver options (Table 1 and Sec. 4.1). */
+typedef struct {
+  int coarse[3];       /* primal-coarse block size per direction; must divide
+                          the grid; >= 2 on active directions, 1 on inactive */
+  int basis;           /* 1..4: basis equation (B1)..(B4) (Eqs. 8-11) */
+  int restriction;     /* 0 = MSFE (R = P^T), 1 = MSFV (Eq. 7) */
+  int n_pre, n_post;   /* ILU(0) pre- / post-smoothing steps per iteration */
+  double lin_rtol;     /* inner stop: ||r^i|| / ||r^0|| < lin_rtol (0.1 in Sec. 4.1.1) */
+  double nl_tol;       /* outer stop: ||eps|| < nl_tol * ||eps at p^n|| (or absolute) */
+  int tol_abs;         /* nonzero: ||eps|| < nl_tol (the paper's absolute test) */
+  double adapt_theta;  /* relative-change threshold of the adaptive basis update;
+                          < 0 rebuilds every entity at every linearisation */
+  int max_newton;      /* linearisations per time step (<= 64) */
+  int max_cams;        /* C-AMS iterations per linearisation */
+  int memspace;        /* CAMS_HOST or CAMS_DEVICE for every pointer argument */
+} cams_options;
+
+/* Per-step statistics filled by cams_solve. */
+typedef struct {
+  int newton_its;           /* linearisations performed */
+  int cams_its;             /* C-AMS iterations, all linearisations */
+  int basis_rebuilt;        /* local entities rebuilt, all linearisations */
+  int converged;            /* 1 if the outer stopping test was met */
+  int cams_per_newton[64];
+  double eps_hist[65];      /* ||eps||_2 at each linearisation point */
+  double res_final;         /* ||f - A p||_2 after the last inner loop */
+  double t_assemble, t_precond, t_iterate, t_total;   /* milliseconds */
+} cams_stats;
+
+/* Quantities readable with cams_get / cams_get_int (debug and tests). */
+#define CAMS_Q_TRANS      1  /* double 3N: Tx, Ty, Tz; T_d[i] couples i and i - stride_d (0 on the low face) */
+#define CAMS_Q_MATRIX     2  /* double 4N: diag, then the couplings a_{i,i-1}, a_{i,i-nx}, a_{i,i-nx*ny} (0 when absent); A is symmetric */
+#define CAMS_Q_RHS        3  /* double N: f of Eq. 6 (rows scaled by V rho) */
+#define CAMS_Q_EPS        4  /* double N: nonlinear error of Eq. 19 at the linearisation point */
+#define CAMS_Q_PRESSURE   5  /* double N: the handle's current iterate p */
+#define CAMS_Q_PROLONG    6  /* double 8N: P values, slot-major (slot s, cell i at s*N + i) */
+#define CAMS_Q_PROLONG_J  7  /* int 8N: coarse column of each P slot, -1 where the slot is unused */
+#define CAMS_Q_COARSE     8  /* double 27*Nc: R A P as a 27-point coarse stencil, row I at 27*I,
+                                neighbour (dx,dy,dz) in {-1,0,1}^3 at (dx+1) + 3(dy+1) + 9(dz+1) */
+#define CAMS_Q_ILU_DIAG   9  /* double N: ILU(0) pivots d~_i (the only entries ILU(0) changes) */
+#define CAMS_Q_RESIDUAL  10  /* double N: f - A p for the current p */
+#define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, edges+faces+interiors rebuilt last, 0 */
+
+/* (a1) Set up a solver for one grid and permeability field.
+ * kx, ky, kz: permeability per cell (> 0, finite); ky and kz may alias kx.
+ * Computes the static TPFA transmissibilities (harmonic average of the
+ * half-cell conductances; half-cell distance to Dirichlet faces), the
+ * primal/dual-coarse wirebasket tables (Sec. 3, Fig. 1; coarse nodes at
+ * offset floor(b/2) in each primal block) and allocates every buffer.
+ * On success *out receives a handle to release with cams_destroy; on failure
+ * *out is NULL and the status tells why (cams_last_error(NULL) gives the
+ * message). */
+int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_options* opt,
+               const double* kx, const double* ky, const double* kz, cams_handle** out);
+
+/* Run the handle's work on the given cudaStream_t (passed as void*; NULL =
+ * default stream).  The stream must belong to the handle's device. */
+int cams_set_stream(cams_handle* h, void* stream);
+
+/* (a2) Linear-system population (Table 1, step 1): from p_nu (iterate) and
+ * p_n (previous time level) build A = C + A~ and f (Eq. 6, Eqs. 3-5, rows
+ * scaled by V rho^nu), the error eps of Eq. 19 and its 2-norm.  The handle's
+ * current iterate becomes p_nu.  eps_norm_out may be NULL. */
+int cams_assemble(cams_handle* h, const double* p_nu, const double* p_n, double dt,
+                  const cams_bc* bc, double* eps_norm_out);
+
+/* (a3-a10) Update the operators of the two-stage preconditioner for the
+ * system of the last cams_assemble: adaptively rebuild the basis functions
+ * (Sec. 4.1.2; force != 0 rebuilds all), form R A P (Eq. 13, MSFE or MSFV)
+ * and factorise it, and factorise ILU(0).  *n_rebuilt_out (may be NULL)
+ * receives the number of local entities rebuilt. */
+int cams_update_basis(cams_handle* h, int force, int* n_rebuilt_out);
+
+/* (a11) Run n C-AMS iterations (Table 1 steps 4-7) on the current system
+ * from the handle's current iterate.  res_norms (may be NULL; n+1 doubles,
+ * host memory always) receives ||f - A p||_2 before and after each one. */
+int cams_iterate(cams_handle* h, int n, double* res_norms);
+
+/* (a2-a12) One implicit time step from p_n: Newton loop of Sec. 4.1.1 with
+ * the C-AMS inner loop, adaptive basis updates and the stopping tests of
+ * cams_options.  p_inout: initial guess on entry (normally p_n), p^{n+1} on
+ * return (also when CAMS_ENOCONV is returned).  stats may be NULL (host). */
+int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc,
+               double* p_inout, cams_stats* stats);
+
+/* Copy an internal quantity (CAMS_Q_*) to dst (memspace of the handle, except
+ * CAMS_Q_SIZES which is always host).  dst must hold the documented size. */
+int cams_get(cams_handle* h, int what, double* dst);
+int cams_get_int(cams_handle* h, int what, int* dst);
+
+/* Message of the last failure on h (or of the last failed cams_setup when h
+ * is NULL).  Never NULL; owned by the library. */
+const char* cams_last_error(cams_handle* h);
+
+/* Release every resource of h.  NULL is ignored. */
+void cams_destroy(cams_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAMS_H */

@@ -44,7 +44,7 @@ def basis_operator(pb: Problem, kind: int, rho_nu, c_nu, p_n, dt) -> sp.csr_matr
     g, fc, fl = pb.grid, pb.faces, pb.fluid
     N, V = g.N, g.V
     if kind in (1, 2):
-        w = fc.T * 0.5 * (rho_nu[fc.lo] + rho_nu[fc.hi])
+        w = fc.T * (0.5 * (rho_nu[fc.lo] + rho_nu[fc.hi]))
     elif kind in (3, 4):
         w = fc.T.copy()
     else:

@@ -1,0 +1,191 @@
+"""Thin ctypes binding of include/cams.h (argument marshalling only).
+
+Each function has the name of the C entry point it calls.  Arrays are
+passed as numpy float64/int32 arrays (memspace CAMS_HOST) or as CUDA torch
+tensors (memspace CAMS_DEVICE); nothing here computes any part of the
+method.  Importing this module loads the in-tree libcams.so and fails loudly
+when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcams.so")
+
+CAMS_OK, CAMS_EINVAL, CAMS_ENOMEM, CAMS_ECUDA = 0, -1, -2, -3
+CAMS_ENOCONV, CAMS_ESINGULAR, CAMS_ETIMEOUT, CAMS_ENAN = -4, -5, -6, -7
+CAMS_HOST, CAMS_DEVICE = 0, 1
+CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 4, 5
+CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
+CAMS_Q_SIZES = 11
+
+EXPORTS = ("cams_setup", "cams_set_stream", "cams_assemble", "cams_update_basis",
+           "cams_iterate", "cams_solve", "cams_get", "cams_get_int", "cams_last_error",
+           "cams_destroy")
+
+
+class CamsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cams error {code}: {msg}")
+        self.code = code
+
+
+class cams_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class cams_fluid(C.Structure):
+    _fields_ = [("law", C.c_int), ("c_or_eta", C.c_double), ("rho0", C.c_double),
+                ("mu", C.c_double), ("phi", C.c_double)]
+
+
+class cams_bc(C.Structure):
+    _fields_ = [("dirichlet", C.c_int), ("p_west", C.c_double), ("p_east", C.c_double),
+                ("n_src", C.c_int), ("src_cell", C.c_void_p), ("src_rate", C.c_void_p)]
+
+
+class cams_options(C.Structure):
+    _fields_ = [("coarse", C.c_int * 3), ("basis", C.c_int), ("restriction", C.c_int),
+                ("n_pre", C.c_int), ("n_post", C.c_int), ("lin_rtol", C.c_double),
+                ("nl_tol", C.c_double), ("tol_abs", C.c_int), ("adapt_theta", C.c_double),
+                ("max_newton", C.c_int), ("max_cams", C.c_int), ("memspace", C.c_int)]
+
+
+class cams_stats(C.Structure):
+    _fields_ = [("newton_its", C.c_int), ("cams_its", C.c_int), ("basis_rebuilt", C.c_int),
+                ("converged", C.c_int), ("cams_per_newton", C.c_int * 64),
+                ("eps_hist", C.c_double * 65), ("res_final", C.c_double),
+                ("t_assemble", C.c_double), ("t_precond", C.c_double),
+                ("t_iterate", C.c_double), ("t_total", C.c_double)]
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libcams.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "cams_setup": (C.c_int, [C.POINTER(cams_grid), C.POINTER(cams_fluid),
+                                 C.POINTER(cams_options), P, P, P, C.POINTER(P)]),
+        "cams_set_stream": (C.c_int, [P, P]),
+        "cams_assemble": (C.c_int, [P, P, P, C.c_double, C.POINTER(cams_bc),
+                                    C.POINTER(C.c_double)]),
+        "cams_update_basis": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
+        "cams_iterate": (C.c_int, [P, C.c_int, P]),
+        "cams_solve": (C.c_int, [P, P, C.c_double, C.POINTER(cams_bc), P,
+                                 C.POINTER(cams_stats)]),
+        "cams_get": (C.c_int, [P, C.c_int, P]),
+        "cams_get_int": (C.c_int, [P, C.c_int, P]),
+        "cams_last_error": (C.c_char_p, [P]),
+        "cams_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    """Address of a numpy array (host) or a CUDA tensor (device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _check(code, h=None):
+    if code != CAMS_OK:
+        raise CamsError(code, _lib.cams_last_error(h).decode())
+
+
+def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None):
+    """cams_bc plus the arrays it points to (kept alive by the returned tuple)."""
+    keep = []
+    n = 0 if src_cell is None else len(src_cell)
+    bc = cams_bc(int(bool(dirichlet)), float(p_west), float(p_east), n, None, None)
+    if n:
+        if isinstance(src_cell, np.ndarray):
+            src_cell = np.ascontiguousarray(src_cell, dtype=np.int32)
+            src_rate = np.ascontiguousarray(src_rate, dtype=np.float64)
+        keep += [src_cell, src_rate]
+        bc.src_cell = _ptr(src_cell)
+        bc.src_rate = _ptr(src_rate)
+    return bc, keep
+
+
+def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1,
+                 nl_tol=1e-6, tol_abs=False, adapt_theta=0.1, max_newton=50, max_cams=200,
+                 memspace=CAMS_HOST):
+    o = cams_options()
+    o.coarse[:] = [int(v) for v in coarse]
+    o.basis, o.restriction, o.n_pre, o.n_post = int(basis), int(restriction), int(n_pre), int(n_post)
+    o.lin_rtol, o.nl_tol, o.tol_abs = float(lin_rtol), float(nl_tol), int(bool(tol_abs))
+    o.adapt_theta, o.max_newton, o.max_cams = float(adapt_theta), int(max_newton), int(max_cams)
+    o.memspace = int(memspace)
+    return o
+
+
+def cams_setup(grid: cams_grid, fluid: cams_fluid, opt: cams_options, kx, ky=None, kz=None):
+    h = C.c_void_p()
+    code = _lib.cams_setup(C.byref(grid), C.byref(fluid), C.byref(opt), _ptr(kx), _ptr(ky),
+                           _ptr(kz), C.byref(h))
+    _check(code, None)
+    return h
+
+
+def cams_set_stream(h, stream_ptr: int):
+    _check(_lib.cams_set_stream(h, C.c_void_p(stream_ptr)), h)
+
+
+def cams_assemble(h, p_nu, p_n, dt, bc):
+    e = C.c_double()
+    _check(_lib.cams_assemble(h, _ptr(p_nu), _ptr(p_n), float(dt), C.byref(bc), C.byref(e)), h)
+    return e.value
+
+
+def cams_update_basis(h, force=False):
+    n = C.c_int()
+    _check(_lib.cams_update_basis(h, int(bool(force)), C.byref(n)), h)
+    return n.value
+
+
+def cams_iterate(h, n):
+    out = np.zeros(n + 1)
+    _check(_lib.cams_iterate(h, int(n), out.ctypes.data), h)
+    return out
+
+
+def cams_solve(h, p_n, dt, bc, p_inout, allow_noconv=False):
+    st = cams_stats()
+    code = _lib.cams_solve(h, _ptr(p_n), float(dt), C.byref(bc), _ptr(p_inout), C.byref(st))
+    if not (allow_noconv and code == CAMS_ENOCONV):
+        _check(code, h)
+    return st
+
+
+def cams_get(h, what, dst):
+    _check(_lib.cams_get(h, int(what), _ptr(dst)), h)
+    return dst
+
+
+def cams_get_int(h, what, dst):
+    _check(_lib.cams_get_int(h, int(what), _ptr(dst)), h)
+    return dst
+
+
+def cams_last_error(h=None) -> str:
+    return _lib.cams_last_error(h).decode()
+
+
+def cams_destroy(h):
+    _lib.cams_destroy(h)

@@ -1,0 +1,715 @@
+// C-ABI and host-side control of the C-AMS engine: setup (static
+// transmissibilities and wirebasket tables), linear-system population, the
+// adaptive operator update, the C-AMS iteration of Table 1 and the Newton
+// loop of Sec. 4.1.1.  Every numerical step is a kernel of this library; the
+// host only sequences launches and reads back one scalar per stopping test.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cams_internal.h"
+
+using namespace cams;
+
+struct cams_handle {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  cams_grid grid{};
+  cams_fluid fluid{};
+  cams_options opt{};
+  Geo g{};
+  CGeo c{};
+  FluidK fl{};
+  Buffers b{};
+  // wirebasket
+  std::vector<Entity> ents;
+  int lev_first[4] = {0, 0, 0, 0}, lev_count[4] = {0, 0, 0, 0}, lev_smem[4] = {0, 0, 0, 0};
+  int lev_grid[4] = {0, 0, 0, 0};
+  long long lev_lstride[4] = {0, 0, 0, 0};
+  long long lscratch_len = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int d_active = 0;
+  int n_dual = 0;
+  // coarse band
+  int mc = 0;
+  // state
+  bool built = false;
+  bool assembled = false;
+  bool have_src = false;
+  double dt = 0.0;
+  int dirichlet = 0;
+  double pw = 0.0, pe = 0.0, rhow = 1.0, rhoe = 1.0;
+  int last_rebuilt = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_setup_error = "no error";
+
+int fail(cams_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_setup_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, CAMS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <typename T>
+int dalloc(cams_handle* h, T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, CAMS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return CAMS_OK;
+}
+
+cudaMemcpyKind kind_in(const cams_handle* h) {
+  return h->opt.memspace == CAMS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_out(const cams_handle* h) {
+  return h->opt.memspace == CAMS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+double rho_host(const FluidK& f, double p) {
+  return f.law == 0 ? f.rho0 * std::exp(f.c * p) : f.rho0 * (1.0 + f.c * p);
+}
+
+// device status word -> status code (and reset)
+int check_status(cams_handle* h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->b.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st) CK(cudaMemsetAsync(h->b.status, 0, sizeof(int), h->stream));
+  if (st & kStatTimeout) return fail(h, CAMS_ETIMEOUT, "a device-side wait exceeded its limit");
+  if (st & kStatSingular) return fail(h, CAMS_ESINGULAR, "zero or non-finite pivot in a local or coarse factorisation");
+  if (st & kStatNan) return fail(h, CAMS_ENAN, "non-finite value");
+  return CAMS_OK;
+}
+
+int read_scalar(cams_handle* h, double* out) {
+  CK(cudaMemcpyAsync(out, h->b.scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAMS_OK;
+}
+
+// ---------------------------------------------------------------- tables --
+
+void build_entities(cams_handle* h, std::vector<int>& ent_of_cell) {
+  const Geo& g = h->g;
+  const CGeo& c = h->c;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  bool active[3];
+  h->d_active = 0;
+  for (int d = 0; d < 3; ++d) {
+    active[d] = n[d] > 1;
+    h->d_active += active[d];
+  }
+  // per direction: list of (org, L, is_free)
+  struct Choice { int org, L, free_; };
+  std::vector<Choice> ch[3];
+  for (int d = 0; d < 3; ++d) {
+    if (!active[d]) { ch[d].push_back({0, 1, 0}); continue; }
+    for (int I = 0; I < c.nc[d]; ++I) ch[d].push_back({I * c.b[d] + c.o[d], 1, 0});
+    for (int j = 0; j <= c.nc[d]; ++j) {
+      const int lo = j == 0 ? 0 : (j - 1) * c.b[d] + c.o[d] + 1;
+      const int hi = j == c.nc[d] ? n[d] - 1 : j * c.b[d] + c.o[d] - 1;
+      if (lo <= hi) ch[d].push_back({lo, hi - lo + 1, 1});
+    }
+  }
+  h->ents.clear();
+  for (int lev = 1; lev <= 3; ++lev) {
+    h->lev_first[lev] = (int)h->ents.size();
+    for (const Choice& cz : ch[2])
+      for (const Choice& cy : ch[1])
+        for (const Choice& cx : ch[0]) {
+          if (cx.free_ + cy.free_ + cz.free_ != lev) continue;
+          Entity E{};
+          E.org[0] = cx.org; E.org[1] = cy.org; E.org[2] = cz.org;
+          E.L[0] = cx.L; E.L[1] = cy.L; E.L[2] = cz.L;
+          E.level = lev;
+          E.free_mask = cx.free_ | (cy.free_ << 1) | (cz.free_ << 2);
+          int ord[3] = {0, 1, 2};
+          std::stable_sort(ord, ord + 3, [&](int a, int b2) { return E.L[a] < E.L[b2]; });
+          for (int k = 0; k < 3; ++k) E.ord[k] = ord[k];
+          E.n = E.L[0] * E.L[1] * E.L[2];
+          const int st[3] = {1, E.L[ord[0]], E.L[ord[0]] * E.L[ord[1]]};
+          E.m = 0;
+          for (int k = 0; k < 3; ++k)
+            if (E.L[ord[k]] > 1) E.m = std::max(E.m, st[k]);
+          E.nrhs = 1 << (cx.free_ + cy.free_ + cz.free_);
+          const int id = (int)h->ents.size();
+          for (int z = 0; z < E.L[2]; ++z)
+            for (int y = 0; y < E.L[1]; ++y)
+              for (int x = 0; x < E.L[0]; ++x)
+                ent_of_cell[(E.org[0] + x) + g.sy * (E.org[1] + y) + g.sz * (E.org[2] + z)] = id;
+          h->ents.push_back(E);
+        }
+    h->lev_count[lev] = (int)h->ents.size() - h->lev_first[lev];
+  }
+}
+
+int alloc_all(cams_handle* h) {
+  const long long N = h->g.N;
+  Buffers& b = h->b;
+  int rc;
+#define AL(ptr, n) if ((rc = dalloc(h, &(ptr), (size_t)(n))) != CAMS_OK) return rc
+  AL(b.Tx, N); AL(b.Ty, N); AL(b.Tz, N);
+  AL(b.Tbw, (long long)h->g.ny * h->g.nz); AL(b.Tbe, (long long)h->g.ny * h->g.nz);
+  AL(b.p, N); AL(b.pn, N); AL(b.rho, N); AL(b.rhon, N);
+  AL(b.Ad, N); AL(b.Ax, N); AL(b.Ay, N); AL(b.Az, N); AL(b.Cacc, N);
+  AL(b.f, N); AL(b.eps, N);
+  AL(b.Abd, N); AL(b.Abx, N); AL(b.Aby, N); AL(b.Abz, N);
+  if (h->opt.basis != 4) AL(b.snap, 7 * N);
+  AL(b.P, 8 * N);
+  AL(b.ent_of_cell, N);
+  AL(b.ents, h->ents.size());
+  AL(b.flag, h->ents.size());
+  AL(b.lscratch, (size_t)h->lscratch_len);
+  AL(b.loc, (size_t)h->n_dual * 36);
+  AL(b.Acs, 27LL * h->c.Nc);
+  AL(b.band, (size_t)h->c.Nc * (2 * h->mc + 1));
+  AL(b.perm, h->c.Nc);
+  AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc);
+  AL(b.dinv, N);
+  AL(b.r, N); AL(b.w, N);
+  AL(b.red, kRedBlocks);
+  AL(b.scal, 8);
+  AL(b.status, 1);
+#undef AL
+  return CAMS_OK;
+}
+
+void free_all(cams_handle* h) {
+  Buffers& b = h->b;
+  void* ptrs[] = {b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe, b.p, b.pn, b.rho, b.rhon, b.Ad, b.Ax, b.Ay,
+                  b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
+                  b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
+                  b.pc, b.dinv, b.r, b.w, b.red, b.scal, b.status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->b = Buffers{};
+}
+
+int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
+  if (!gr || !fl || !o) return fail(nullptr, CAMS_EINVAL, "null argument");
+  if (gr->nx < 1 || gr->ny < 1 || gr->nz < 1) return fail(nullptr, CAMS_EINVAL, "grid sizes must be >= 1");
+  if (!(gr->dx > 0 && gr->dy > 0 && gr->dz > 0)) return fail(nullptr, CAMS_EINVAL, "cell sizes must be > 0");
+  if (!(fl->phi > 0 && fl->mu > 0 && fl->rho0 > 0)) return fail(nullptr, CAMS_EINVAL, "phi, mu, rho0 must be > 0");
+  if (fl->law != CAMS_RHO_EXP && fl->law != CAMS_RHO_LINEAR) return fail(nullptr, CAMS_EINVAL, "unknown density law");
+  const int n[3] = {gr->nx, gr->ny, gr->nz};
+  for (int d = 0; d < 3; ++d) {
+    const int b = o->coarse[d];
+    if (n[d] == 1) {
+      if (b != 1) return fail(nullptr, CAMS_EINVAL, "an inactive direction needs coarse size 1");
+    } else if (b < 2 || n[d] % b != 0) {
+      return fail(nullptr, CAMS_EINVAL, "coarse size must be >= 2 and divide the grid size");
+    }
+  }
+  if (o->basis < 1 || o->basis > 4) return fail(nullptr, CAMS_EINVAL, "basis must be 1..4");
+  if (o->restriction != 0 && o->restriction != 1) return fail(nullptr, CAMS_EINVAL, "restriction must be 0 or 1");
+  if (o->n_pre < 0 || o->n_post < 0) return fail(nullptr, CAMS_EINVAL, "smoothing counts must be >= 0");
+  if (o->max_newton < 1 || o->max_newton > kMaxNewton) return fail(nullptr, CAMS_EINVAL, "max_newton must be 1..64");
+  if (o->max_cams < 1) return fail(nullptr, CAMS_EINVAL, "max_cams must be >= 1");
+  if (o->memspace != CAMS_HOST && o->memspace != CAMS_DEVICE) return fail(nullptr, CAMS_EINVAL, "bad memspace");
+  if ((long long)gr->nx * gr->ny * gr->nz > (1LL << 31) - 1) return fail(nullptr, CAMS_EINVAL, "grid too large");
+  return CAMS_OK;
+}
+
+// ----------------------------------------------------------- operations --
+
+int set_sources(cams_handle* h, const cams_bc* bc) {
+  h->dirichlet = bc ? bc->dirichlet : 0;
+  h->pw = bc ? bc->p_west : 0.0;
+  h->pe = bc ? bc->p_east : 0.0;
+  h->rhow = rho_host(h->fl, h->pw);
+  h->rhoe = rho_host(h->fl, h->pe);
+  const int n = bc ? bc->n_src : 0;
+  if (n < 0) return fail(h, CAMS_EINVAL, "n_src < 0");
+  if (n == 0) { h->have_src = false; return CAMS_OK; }
+  if (!bc->src_cell || !bc->src_rate) return fail(h, CAMS_EINVAL, "null source arrays");
+  if (!h->b.src) {
+    int rc = dalloc(h, &h->b.src, (size_t)h->g.N);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(h->b.src, 0, sizeof(double) * h->g.N, h->stream));
+  int* dcell = nullptr;
+  double* drate = nullptr;
+  if (h->opt.memspace == CAMS_HOST) {
+    for (int k = 0; k < n; ++k)
+      if (bc->src_cell[k] < 0 || bc->src_cell[k] >= h->g.N) return fail(h, CAMS_EINVAL, "source cell out of range");
+    int rc = dalloc(h, &dcell, n);
+    if (rc) return rc;
+    rc = dalloc(h, &drate, n);
+    if (rc) { cudaFree(dcell); return rc; }
+    cudaMemcpyAsync(dcell, bc->src_cell, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(drate, bc->src_rate, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+  }
+  cudaError_t e = launch_add_sources(n, dcell ? dcell : bc->src_cell, drate ? drate : bc->src_rate,
+                                     h->b.src, h->g.N, h->stream);
+  if (dcell) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(dcell);
+    cudaFree(drate);
+  }
+  CK(e);
+  h->have_src = true;
+  return CAMS_OK;
+}
+
+int assemble(cams_handle* h, double* eps_norm) {
+  Buffers& b = h->b;
+  double* src_saved = b.src;
+  if (!h->have_src) b.src = nullptr;
+  CK(launch_density(h->g, h->fl, b.p, b.rho, h->stream));
+  cudaError_t e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe, b, h->stream);
+  b.src = src_saved;
+  CK(e);
+  double s2;
+  int rc = read_scalar(h, &s2);
+  if (rc) return rc;
+  if (!std::isfinite(s2)) return fail(h, CAMS_ENAN, "non-finite nonlinear error norm");
+  if (eps_norm) *eps_norm = std::sqrt(s2);
+  h->assembled = true;
+  return CAMS_OK;
+}
+
+int update_operators(cams_handle* h, int force, int* n_rebuilt) {
+  if (!h->assembled) return fail(h, CAMS_EINVAL, "cams_assemble must come first");
+  Buffers& b = h->b;
+  const cams_options& o = h->opt;
+  const int ne = (int)h->ents.size();
+  CK(launch_basis_operator(h->g, h->fl, o.basis, h->dt, b, h->stream));
+  const bool adaptive = o.basis != 4;
+  int rebuilt = 0;
+  if (!h->built || force || o.adapt_theta < 0) {
+    CK(cudaMemsetAsync(b.flag, 1, ne, h->stream));
+    rebuilt = ne;
+  } else if (o.basis == 4) {
+    // (B4) depends on the transmissibilities only: its operator cannot
+    // change, so the relative-change test of Sec. 4.1.2 flags nothing.
+    rebuilt = 0;
+  } else {
+    CK(launch_adapt_flags(h->g, b.ents, ne, o.adapt_theta, b, b.flag, h->stream));
+    for (int lev = 2; lev <= 3; ++lev)
+      CK(launch_adapt_propagate(h->g, h->lev_first[lev], h->lev_count[lev], b, h->stream));
+    CK(launch_count_flags(ne, b.flag, b.scal, h->stream));
+    double cnt;
+    int rc = read_scalar(h, &cnt);
+    if (rc) return rc;
+    rebuilt = (int)cnt;
+  }
+  if (rebuilt > 0) {
+    if (!h->built) CK(launch_vertices(h->g, h->c, b.P, h->stream));
+    for (int lev = 1; lev <= 3; ++lev) {
+      const int f = h->lev_first[lev];
+      CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
+                             h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, b, h->stream));
+    }
+  }
+  h->built = true;
+  h->last_rebuilt = rebuilt;
+  if (n_rebuilt) *n_rebuilt = rebuilt;
+  // Galerkin coarse operator and its factorisation
+  if (o.restriction == 0)
+    CK(launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+  else
+    CK(launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+  CK(launch_band_fill(h->c, h->mc, b, h->stream));
+  CK(launch_band_factor(h->c.Nc, h->mc, b, h->stream));
+  CK(launch_ilu_factor(h->g, b, h->stream));
+  return check_status(h);
+}
+
+int residual_norm(cams_handle* h, double* out) {
+  CK(launch_residual(h->g, h->b, h->b.p, h->b.r, h->b.red, h->b.scal, h->stream));
+  double s2;
+  int rc = read_scalar(h, &s2);
+  if (rc) return rc;
+  if (!std::isfinite(s2)) return fail(h, CAMS_ENAN, "non-finite residual norm");
+  *out = std::sqrt(s2);
+  return CAMS_OK;
+}
+
+// One C-AMS iteration (Table 1 steps 4-7 with ILU(0) smoothing).
+int cams_step(cams_handle* h) {
+  Buffers& b = h->b;
+  for (int k = 0; k < h->opt.n_pre; ++k) CK(launch_ilu_smooth(h->g, b, h->stream));
+  CK(launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
+  CK(launch_restrict(h->g, h->c, h->opt.restriction, b.r, b, h->stream));
+  CK(launch_band_solve(h->c.Nc, h->mc, b, h->stream));
+  CK(launch_prolong_add(h->g, h->c, b, h->stream));
+  for (int k = 0; k < h->opt.n_post; ++k) CK(launch_ilu_smooth(h->g, b, h->stream));
+  return CAMS_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+// =================================================================== ABI ==
+
+extern "C" {
+
+int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_options* opt,
+               const double* kx, const double* ky, const double* kz, cams_handle** out) {
+  if (!out) return fail(nullptr, CAMS_EINVAL, "out is null");
+  *out = nullptr;
+  int rc = validate(grid, fluid, opt);
+  if (rc) return rc;
+  if (!kx) return fail(nullptr, CAMS_EINVAL, "kx is null");
+  if (!ky) ky = kx;
+  if (!kz) kz = kx;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(nullptr, CAMS_ECUDA, "no CUDA device available");
+  cams_handle* h = new (std::nothrow) cams_handle();
+  if (!h) return fail(nullptr, CAMS_ENOMEM, "host allocation failed");
+  h->grid = *grid;
+  h->fluid = *fluid;
+  h->opt = *opt;
+  cudaGetDevice(&h->dev);
+  Geo& g = h->g;
+  g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
+  g.N = (long long)g.nx * g.ny * g.nz;
+  g.sy = g.nx; g.sz = (long long)g.nx * g.ny;
+  g.dx = grid->dx; g.dy = grid->dy; g.dz = grid->dz;
+  g.V = grid->dx * grid->dy * grid->dz;
+  h->fl = FluidK{fluid->law, fluid->c_or_eta, fluid->rho0, fluid->mu, fluid->phi};
+  CGeo& c = h->c;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  c.Nc = 1;
+  for (int d = 0; d < 3; ++d) {
+    c.b[d] = opt->coarse[d];
+    c.o[d] = opt->coarse[d] / 2;
+    c.nc[d] = n[d] / opt->coarse[d];
+    c.Nc *= c.nc[d];
+  }
+  h->n_dual = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
+  // wirebasket entity tables
+  std::vector<int> eoc((size_t)g.N, -1);
+  build_entities(h, eoc);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->dev) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, CAMS_ECUDA, "cudaGetDeviceProperties failed");
+  }
+  int smem_max = 0;
+  for (int lev = 1; lev <= 3; ++lev) {
+    int sm = 0;
+    long long ls = 0;
+    for (int e = h->lev_first[lev]; e < h->lev_first[lev] + h->lev_count[lev]; ++e) {
+      const Entity& E = h->ents[e];
+      const int mp = E.m + 1;
+      sm = std::max(sm, (int)sizeof(double) * (mp * mp + E.n * E.nrhs + 2 * mp));
+      ls = std::max(ls, (long long)E.n * mp);
+    }
+    h->lev_smem[lev] = sm;
+    h->lev_lstride[lev] = ls;
+    smem_max = std::max(smem_max, sm);
+  }
+  if (smem_max > (int)prop.sharedMemPerBlockOptin) {
+    delete h;
+    return fail(nullptr, CAMS_EINVAL, "dual-coarse blocks too large for the shared-memory local solver");
+  }
+  if (set_entity_smem(std::max(smem_max, 1)) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, CAMS_ECUDA, "cudaFuncSetAttribute failed");
+  }
+  for (int lev = 1; lev <= 3; ++lev) {
+    const int per_sm = std::max(1, (int)(prop.sharedMemPerMultiprocessor / std::max(h->lev_smem[lev] + 1024, 1)));
+    h->lev_grid[lev] = std::min(h->lev_count[lev], prop.multiProcessorCount * std::min(per_sm, 8));
+    h->lscratch_len = std::max(h->lscratch_len, (long long)h->lev_grid[lev] * h->lev_lstride[lev]);
+  }
+  // coarse ordering: fastest = fewest coarse cells
+  int ordc[3] = {0, 1, 2};
+  std::stable_sort(ordc, ordc + 3, [&](int a, int b2) { return c.nc[a] < c.nc[b2]; });
+  const int na = c.nc[ordc[0]], nb = c.nc[ordc[1]], ncc = c.nc[ordc[2]];
+  h->mc = (na > 1 ? 1 : 0) + (nb > 1 ? na : 0) + (ncc > 1 ? na * nb : 0);
+  std::vector<int> perm(c.Nc);
+  for (int I = 0; I < c.Nc; ++I) {
+    const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+    perm[I] = Ic[ordc[0]] + na * (Ic[ordc[1]] + nb * Ic[ordc[2]]);
+  }
+  rc = alloc_all(h);
+  if (rc) {
+    const std::string msg = h->err;
+    free_all(h);
+    delete h;
+    return fail(nullptr, rc, msg);
+  }
+  for (auto& x : h->ev) cudaEventCreate(&x);
+  // copy tables and compute transmissibilities
+  cudaStream_t s = h->stream;
+  cudaMemcpyAsync(h->b.ents, h->ents.data(), sizeof(Entity) * h->ents.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->b.ent_of_cell, eoc.data(), sizeof(int) * g.N, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(h->b.perm, perm.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(h->b.status, 0, sizeof(int), s);
+  cudaMemsetAsync(h->b.Tbw, 0, sizeof(double) * g.ny * g.nz, s);
+  cudaMemsetAsync(h->b.Tbe, 0, sizeof(double) * g.ny * g.nz, s);
+  const double* k3[3] = {kx, ky, kz};
+  double* dk[3] = {nullptr, nullptr, nullptr};
+  if (opt->memspace == CAMS_HOST) {
+    for (int d = 0; d < 3; ++d)
+      for (long long i = 0; i < g.N; ++i)
+        if (!(k3[d][i] > 0.0) || !std::isfinite(k3[d][i])) {
+          free_all(h);
+          delete h;
+          return fail(nullptr, CAMS_EINVAL, "permeability must be positive and finite");
+        }
+    // stage through the (not yet used) work vectors r, w, eps
+    double* stage[3] = {h->b.r, h->b.w, h->b.eps};
+    for (int d = 0; d < 3; ++d) {
+      cudaMemcpyAsync(stage[d], k3[d], sizeof(double) * g.N, cudaMemcpyHostToDevice, s);
+      dk[d] = stage[d];
+    }
+  } else {
+    for (int d = 0; d < 3; ++d) dk[d] = const_cast<double*>(k3[d]);
+  }
+  cudaError_t e = launch_transmissibility(g, fluid->mu, dk[0], dk[1], dk[2], 1, h->b, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("setup: ") + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return fail(nullptr, CAMS_ECUDA, msg);
+  }
+  *out = h;
+  return CAMS_OK;
+}
+
+int cams_set_stream(cams_handle* h, void* stream) {
+  if (!h) return CAMS_EINVAL;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return CAMS_OK;
+}
+
+int cams_assemble(cams_handle* h, const double* p_nu, const double* p_n, double dt,
+                  const cams_bc* bc, double* eps_norm_out) {
+  if (!h) return CAMS_EINVAL;
+  if (!p_nu || !p_n) return fail(h, CAMS_EINVAL, "null pressure");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, CAMS_EINVAL, "dt must be > 0");
+  h->dt = dt;
+  CK(cudaMemcpyAsync(h->b.p, p_nu, sizeof(double) * h->g.N, kind_in(h), h->stream));
+  CK(cudaMemcpyAsync(h->b.pn, p_n, sizeof(double) * h->g.N, kind_in(h), h->stream));
+  int rc = set_sources(h, bc);
+  if (rc) return rc;
+  CK(launch_density(h->g, h->fl, h->b.pn, h->b.rhon, h->stream));
+  double en = 0.0;
+  rc = assemble(h, &en);
+  if (rc) return rc;
+  if (eps_norm_out) *eps_norm_out = en;
+  return CAMS_OK;
+}
+
+int cams_update_basis(cams_handle* h, int force, int* n_rebuilt_out) {
+  if (!h) return CAMS_EINVAL;
+  return update_operators(h, force, n_rebuilt_out);
+}
+
+int cams_iterate(cams_handle* h, int n, double* res_norms) {
+  if (!h) return CAMS_EINVAL;
+  if (!h->built) return fail(h, CAMS_EINVAL, "cams_update_basis must come first");
+  double rn;
+  int rc = residual_norm(h, &rn);
+  if (rc) return rc;
+  if (res_norms) res_norms[0] = rn;
+  for (int k = 0; k < n; ++k) {
+    rc = cams_step(h);
+    if (rc) return rc;
+    rc = residual_norm(h, &rn);
+    if (rc) return rc;
+    if (res_norms) res_norms[k + 1] = rn;
+  }
+  return check_status(h);
+}
+
+int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc, double* p_inout,
+               cams_stats* stats) {
+  if (!h) return CAMS_EINVAL;
+  if (!p_n || !p_inout) return fail(h, CAMS_EINVAL, "null pressure");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, CAMS_EINVAL, "dt must be > 0");
+  cams_stats st;
+  std::memset(&st, 0, sizeof(st));
+  cudaEvent_t* ev = h->ev;
+  float t_asm = 0, t_pre = 0, t_it = 0;
+  cudaEventRecord(ev[0], h->stream);
+  h->dt = dt;
+  CK(cudaMemcpyAsync(h->b.pn, p_n, sizeof(double) * h->g.N, kind_in(h), h->stream));
+  CK(cudaMemcpyAsync(h->b.p, p_inout, sizeof(double) * h->g.N, kind_in(h), h->stream));
+  int rc = set_sources(h, bc);
+  if (rc) return rc;
+  CK(launch_density(h->g, h->fl, h->b.pn, h->b.rhon, h->stream));
+  const cams_options& o = h->opt;
+  double e0 = 0.0;
+  int result = CAMS_ENOCONV;
+  for (int nu = 0; nu <= o.max_newton; ++nu) {
+    cudaEventRecord(ev[1], h->stream);
+    double en;
+    rc = assemble(h, &en);
+    if (rc) return rc;
+    cudaEventRecord(ev[2], h->stream);
+    cudaEventSynchronize(ev[2]);
+    t_asm += elapsed(ev[1], ev[2]);
+    if (nu == 0) e0 = en;
+    if (nu < 65) st.eps_hist[nu] = en;
+    const double ref = o.tol_abs ? 1.0 : e0;
+    if (en == 0.0 || en < o.nl_tol * ref) {
+      st.converged = 1;
+      result = CAMS_OK;
+      break;
+    }
+    if (nu == o.max_newton) break;
+    int nb = 0;
+    cudaEventRecord(ev[1], h->stream);
+    rc = update_operators(h, 0, &nb);
+    if (rc) return rc;
+    cudaEventRecord(ev[2], h->stream);
+    cudaEventSynchronize(ev[2]);
+    t_pre += elapsed(ev[1], ev[2]);
+    st.basis_rebuilt += nb;
+    double r0, rn = 0.0;
+    rc = residual_norm(h, &r0);
+    if (rc) return rc;
+    int its = 0;
+    while (its < o.max_cams) {
+      rc = cams_step(h);
+      if (rc) return rc;
+      ++its;
+      rc = residual_norm(h, &rn);
+      if (rc) return rc;
+      if (rn < o.lin_rtol * r0) break;
+    }
+    cudaEventRecord(ev[3], h->stream);
+    cudaEventSynchronize(ev[3]);
+    t_it += elapsed(ev[2], ev[3]);
+    st.res_final = rn;
+    st.cams_its += its;
+    if (st.newton_its < 64) st.cams_per_newton[st.newton_its] = its;
+    st.newton_its += 1;
+  }
+  rc = check_status(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(p_inout, h->b.p, sizeof(double) * h->g.N, kind_out(h), h->stream));
+  cudaEventRecord(ev[3], h->stream);
+  CK(cudaStreamSynchronize(h->stream));
+  st.t_assemble = t_asm;
+  st.t_precond = t_pre;
+  st.t_iterate = t_it;
+  st.t_total = elapsed(ev[0], ev[3]);
+  if (stats) *stats = st;
+  if (result == CAMS_ENOCONV) fail(h, CAMS_ENOCONV, "max_newton reached without convergence");
+  return result;
+}
+
+int cams_get(cams_handle* h, int what, double* dst) {
+  if (!h || !dst) return CAMS_EINVAL;
+  const long long N = h->g.N;
+  Buffers& b = h->b;
+  const cudaMemcpyKind k = kind_out(h);
+  cudaStream_t s = h->stream;
+  switch (what) {
+    case CAMS_Q_TRANS:
+      CK(cudaMemcpyAsync(dst, b.Tx, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + N, b.Ty, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + 2 * N, b.Tz, sizeof(double) * N, k, s));
+      break;
+    case CAMS_Q_MATRIX:
+      CK(cudaMemcpyAsync(dst, b.Ad, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + N, b.Ax, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + 2 * N, b.Ay, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + 3 * N, b.Az, sizeof(double) * N, k, s));
+      break;
+    case CAMS_Q_RHS: CK(cudaMemcpyAsync(dst, b.f, sizeof(double) * N, k, s)); break;
+    case CAMS_Q_EPS: CK(cudaMemcpyAsync(dst, b.eps, sizeof(double) * N, k, s)); break;
+    case CAMS_Q_PRESSURE: CK(cudaMemcpyAsync(dst, b.p, sizeof(double) * N, k, s)); break;
+    case CAMS_Q_PROLONG: CK(cudaMemcpyAsync(dst, b.P, sizeof(double) * 8 * N, k, s)); break;
+    case CAMS_Q_COARSE: CK(cudaMemcpyAsync(dst, b.Acs, sizeof(double) * 27 * h->c.Nc, k, s)); break;
+    case CAMS_Q_ILU_DIAG: {
+      // d_i = 1 / dinv_i, formed in the residual work vector
+      std::vector<double> tmp(N);
+      CK(cudaMemcpyAsync(tmp.data(), b.dinv, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (long long i = 0; i < N; ++i) tmp[i] = 1.0 / tmp[i];
+      CK(cudaMemcpyAsync(dst, tmp.data(), sizeof(double) * N,
+                         h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      break;
+    }
+    case CAMS_Q_RESIDUAL: {
+      CK(launch_residual(h->g, b, b.p, b.r, b.red, b.scal, s));
+      CK(cudaMemcpyAsync(dst, b.r, sizeof(double) * N, k, s));
+      break;
+    }
+    default: return fail(h, CAMS_EINVAL, "unknown quantity");
+  }
+  CK(cudaStreamSynchronize(s));
+  return CAMS_OK;
+}
+
+int cams_get_int(cams_handle* h, int what, int* dst) {
+  if (!h || !dst) return CAMS_EINVAL;
+  const long long N = h->g.N;
+  if (what == CAMS_Q_SIZES) {
+    dst[0] = (int)N; dst[1] = h->c.Nc; dst[2] = h->c.nc[0]; dst[3] = h->c.nc[1]; dst[4] = h->c.nc[2];
+    dst[5] = (int)h->ents.size(); dst[6] = h->last_rebuilt; dst[7] = 0;
+    return CAMS_OK;
+  }
+  if (what != CAMS_Q_PROLONG_J) return fail(h, CAMS_EINVAL, "unknown integer quantity");
+  // coarse column of every slot, from the geometry (host computation)
+  std::vector<int> J((size_t)8 * N);
+  const CGeo& c = h->c;
+  const int n[3] = {h->g.nx, h->g.ny, h->g.nz};
+  for (long long i = 0; i < N; ++i) {
+    const int xc[3] = {(int)(i % n[0]), (int)((i / n[0]) % n[1]), (int)(i / ((long long)n[0] * n[1]))};
+    int cj[3][2];
+    for (int d = 0; d < 3; ++d)
+      for (int bit = 0; bit < 2; ++bit) {
+        const int sft = xc[d] - c.o[d];
+        int v;
+        if (sft >= 0 && sft % c.b[d] == 0) v = bit ? -1 : sft / c.b[d];
+        else {
+          const int j = sft >= 0 ? sft / c.b[d] + 1 : 0;
+          v = bit ? j : j - 1;
+        }
+        cj[d][bit] = (v >= 0 && v < c.nc[d]) ? v : -1;
+      }
+    for (int s = 0; s < 8; ++s) {
+      const int a = cj[0][s & 1], b2 = cj[1][(s >> 1) & 1], z = cj[2][(s >> 2) & 1];
+      J[(size_t)s * N + i] = (a < 0 || b2 < 0 || z < 0) ? -1 : a + c.nc[0] * (b2 + c.nc[1] * z);
+    }
+  }
+  CK(cudaMemcpyAsync(dst, J.data(), sizeof(int) * 8 * N,
+                     h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAMS_OK;
+}
+
+const char* cams_last_error(cams_handle* h) {
+  return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+void cams_destroy(cams_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& x : h->ev)
+    if (x) cudaEventDestroy(x);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations of the C-AMS engine: handle layout, entity tables
+// and the launchers of every kernel.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cams.h"
+
+namespace cams {
+
+constexpr int kMaxNewton = 64;
+
+// Grid geometry as seen by the kernels.
+struct Geo {
+  int nx, ny, nz;
+  long long N;
+  long long sy, sz;    // strides of y and z (nx, nx*ny)
+  double dx, dy, dz, V;
+};
+
+// Coarse-grid geometry: primal block size b, coarse-node offset o = b/2,
+// number of coarse cells nc per direction (inactive directions: b = 1,
+// o = 0, nc = 1).
+struct CGeo {
+  int b[3], o[3], nc[3];
+  int Nc;
+};
+
+// One local entity of the wirebasket: an edge segment (level 1), face patch
+// (level 2) or dual-block interior (level 3).  It is the box of cells
+// [org, org + L) where every lattice (non-free) direction has L = 1.
+// The local solve orders the cells with dimension ord[0] fastest and ord[2]
+// slowest (ascending extent) so that the band half-width m is minimal.
+struct Entity {
+  int org[3];
+  int L[3];
+  int level;
+  int free_mask;    // bit d set when direction d is free
+  int ord[3];
+  int n;            // cells
+  int m;            // band half-width of the local matrix
+  int nrhs;         // 2^(number of free directions)
+};
+
+// Fluid parameters passed by value to kernels.
+struct FluidK {
+  int law;
+  double c, rho0, mu, phi;
+};
+
+__host__ __device__ inline double rho_of(const FluidK& f, double p) {
+#ifdef __CUDA_ARCH__
+  return f.law == 0 ? f.rho0 * exp(f.c * p) : f.rho0 * (1.0 + f.c * p);
+#else
+  return 0.0;
+#endif
+}
+
+// Device buffers, one allocation each, owned by the handle.
+struct Buffers {
+  double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr;     // transmissibilities (lower faces)
+  double *Tbw = nullptr, *Tbe = nullptr;                  // Dirichlet faces (ny*nz)
+  double *p = nullptr, *pn = nullptr;                     // iterate, previous time level
+  double *rho = nullptr, *rhon = nullptr;
+  double *Ad = nullptr, *Ax = nullptr, *Ay = nullptr, *Az = nullptr;  // A = C + A~
+  double *Cacc = nullptr;                                 // V rho c (diagonal of C)
+  double *f = nullptr, *eps = nullptr;
+  double *src = nullptr;                                  // dense Q_i (N) or null
+  double *Abd = nullptr, *Abx = nullptr, *Aby = nullptr, *Abz = nullptr;  // basis operator
+  double *snap = nullptr;                                 // 7N snapshot (adaptive)
+  double *P = nullptr;                                    // 8N, slot-major
+  int* ent_of_cell = nullptr;                             // N, -1 on vertices
+  Entity* ents = nullptr;                                 // all entities, level-sorted
+  unsigned char* flag = nullptr;                          // per entity
+  double* lscratch = nullptr;                             // local L factors, per resident CTA
+  double* loc = nullptr;                                  // FE local 8x8 blocks per dual block (64 each)
+  double* Acs = nullptr;                                  // 27*Nc coarse stencil
+  double* band = nullptr;                                 // Nc*(2m+1) band LU
+  int* perm = nullptr;                                    // coarse natural -> band order
+  double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
+  double* dinv = nullptr;                                 // 1 / ILU(0) pivots
+  double *r = nullptr, *w = nullptr;                      // work vectors
+  double* red = nullptr;                                  // reduction partials
+  double* scal = nullptr;                                 // reduced scalars (device)
+  int* status = nullptr;                                  // device status word
+};
+
+// Bits of the device status word (set by kernels, read by the host).
+enum : int { kStatSingular = 1, kStatNan = 2, kStatTimeout = 4, kStatBounds = 8 };
+
+// Reductions use a fixed grid so results are bit-reproducible.
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+// ---- launchers (each returns the launch error) ----
+cudaError_t launch_transmissibility(const Geo& g, double mu, const double* kx, const double* ky,
+                                    const double* kz, int dirichlet, Buffers& b, cudaStream_t s);
+cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, double* rho,
+                           cudaStream_t s);
+cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int dirichlet, double pw,
+                            double pe, Buffers& b, cudaStream_t s);
+cudaError_t launch_add_sources(int n, const int* cell, const double* rate, double* src,
+                               long long N, cudaStream_t s);
+cudaError_t launch_sumsq(const double* x, long long N, double* red, double* out, cudaStream_t s);
+cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, double* r,
+                            double* red, double* out, cudaStream_t s);
+cudaError_t launch_basis_operator(const Geo& g, const FluidK& fl, int kind, double dt,
+                                  Buffers& b, cudaStream_t s);
+cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,
+                               Buffers& b, unsigned char* flag, cudaStream_t s);
+cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& b,
+                                   cudaStream_t s);
+cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out, cudaStream_t s);
+cudaError_t launch_vertices(const Geo& g, const CGeo& c, double* P, cudaStream_t s);
+cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
+                                int count, int smem, int grid, long long lstride, int adaptive,
+                                Buffers& b, cudaStream_t s);
+cudaError_t set_entity_smem(int smem);
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
+                               double rhoe, Buffers& b, cudaStream_t s);
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
+                               double rhoe, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_fill(const CGeo& c, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_factor(int Nc, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
+                            cudaStream_t s);
+cudaError_t launch_band_solve(int Nc, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s);
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, cudaStream_t s);
+cudaError_t launch_ilu_smooth(const Geo& g, Buffers& b, cudaStream_t s);
+
+}  // namespace cams

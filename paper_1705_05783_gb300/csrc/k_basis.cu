@@ -1,0 +1,337 @@
+// Multiscale basis construction (Sec. 3, Eqs. 8-12) with the wirebasket
+// reduced-problem conditions, and the adaptive-update flags of Sec. 4.1.2.
+//
+// Every edge segment, face patch and dual-block interior is one local SPD
+// problem  M_e P_e = -A_b[e, lower] P[lower]  (level-(k+1) neighbours lumped
+// onto the diagonal).  One CTA solves one entity: it orders the entity's
+// cells with the shortest direction fastest, which makes M_e banded with
+// half-width m = product of the two shortest extents, and runs a
+// right-looking banded LDL^T whose active (m+1)x(m+1) window lives in shared
+// memory as a ring of rows.  All right-hand sides (one per corner vertex,
+// 2^free) are carried through the forward elimination in shared memory; the
+// finished rows of L stream to a per-CTA scratch slice (L2-resident) for the
+// backward substitution.  FP64; no atomics, so the result is deterministic.
+#include "cams_internal.h"
+
+namespace cams {
+
+namespace {
+
+__device__ __forceinline__ double coupling(const Geo& g, const double* Abx, const double* Aby,
+                                           const double* Abz, int d, long long i) {
+  // A_b entry between i and i - e_d (stored at the upper cell)
+  return d == 0 ? Abx[i] : (d == 1 ? Aby[i] : Abz[i]);
+}
+
+__device__ __forceinline__ long long gstride(const Geo& g, int d) {
+  return d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+}
+
+__device__ __forceinline__ int gextent(const Geo& g, int d) {
+  return d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+}
+
+// global slot (bits over x,y,z) of the entity's r-th right-hand side
+__device__ __forceinline__ int slot_of(int r, int free_mask) {
+  int s = 0, k = 0;
+  for (int d = 0; d < 3; ++d)
+    if (free_mask & (1 << d)) {
+      if (r & (1 << k)) s |= 1 << d;
+      ++k;
+    }
+  return s;
+}
+
+struct Local {
+  int c[3];        // coordinates
+  long long i;     // global cell
+};
+
+__device__ __forceinline__ Local local_cell(const Entity& E, int l) {
+  Local L;
+  const int L0 = E.L[E.ord[0]], L1 = E.L[E.ord[1]];
+  int t[3];
+  t[0] = l % L0;
+  t[1] = (l / L0) % L1;
+  t[2] = l / (L0 * L1);
+  for (int k = 0; k < 3; ++k) L.c[E.ord[k]] = E.org[E.ord[k]] + t[k];
+  return L;
+}
+
+__device__ __forceinline__ int local_stride(const Entity& E, int d) {
+  const int L0 = E.L[E.ord[0]], L1 = E.L[E.ord[1]];
+  return d == E.ord[0] ? 1 : (d == E.ord[1] ? L0 : L0 * L1);
+}
+
+// Build row l of M (lower band, ring slot) and the right-hand sides of row l.
+__device__ void build_row(const Geo& g, const Entity& E, int l, double* Wrow, double* Yrow,
+                          const double* Abd, const double* Abx, const double* Aby,
+                          const double* Abz, const double* P) {
+  Local c = local_cell(E, l);
+  const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+  for (int dd = 0; dd <= E.m; ++dd) Wrow[dd] = 0.0;
+  for (int r = 0; r < E.nrhs; ++r) Yrow[r] = 0.0;
+  double diag = Abd[i];
+  for (int d = 0; d < 3; ++d) {
+    const int n_d = gextent(g, d);
+    if (n_d == 1) continue;
+    const long long sd = gstride(g, d);
+    const double lo = c.c[d] > 0 ? coupling(g, Abx, Aby, Abz, d, i) : 0.0;          // to i - e_d
+    const double up = c.c[d] < n_d - 1 ? coupling(g, Abx, Aby, Abz, d, i + sd) : 0.0; // to i + e_d
+    if (!(E.free_mask & (1 << d))) {
+      // lattice direction: neighbours are one level higher -> lumped
+      diag += lo;
+      diag += up;
+      continue;
+    }
+    // free direction: inside the box -> band entry; outside -> known data
+    if (c.c[d] > E.org[d]) {
+      Wrow[local_stride(E, d)] = lo;
+    } else if (c.c[d] > 0) {
+      const long long j = i - sd;
+      for (int r = 0; r < E.nrhs; ++r) {
+        const int s = slot_of(r, E.free_mask);
+        if (!(s & (1 << d))) Yrow[r] -= lo * P[(long long)s * g.N + j];
+      }
+    }
+    if (c.c[d] < E.org[d] + E.L[d] - 1) {
+      // upper in-box neighbour: its entry is stored in the neighbour's row
+    } else if (c.c[d] < n_d - 1) {
+      const long long j = i + sd;
+      for (int r = 0; r < E.nrhs; ++r) {
+        const int s = slot_of(r, E.free_mask);
+        if (s & (1 << d)) Yrow[r] -= up * P[(long long)(s & ~(1 << d)) * g.N + j];
+      }
+    }
+  }
+  Wrow[0] = diag;
+}
+
+__global__ void k_vertices(Geo g, CGeo c, double* P) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= c.Nc) return;
+  const int Jx = J % c.nc[0], Jy = (J / c.nc[0]) % c.nc[1], Jz = J / (c.nc[0] * c.nc[1]);
+  const long long v = (Jx * c.b[0] + c.o[0]) + g.sy * (Jy * c.b[1] + c.o[1]) +
+                      g.sz * (Jz * c.b[2] + c.o[2]);
+  for (int s = 0; s < 8; ++s) P[(long long)s * g.N + v] = (s == 0) ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_entity_solve(
+    Geo g, const Entity* __restrict__ ents, int count, const unsigned char* __restrict__ flag,
+    int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
+    const double* __restrict__ Aby, const double* __restrict__ Abz, double* P, double* snap,
+    double* lscratch, long long lstride, int* status) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* Lg = lscratch + (long long)blockIdx.x * lstride;
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    if (flag && !flag[e]) continue;
+    const Entity E = ents[e];
+    const int n = E.n, m = E.m, nr = E.nrhs, mp = m + 1;
+    double* W = sm;                 // mp * mp ring
+    double* Y = W + mp * mp;        // n * nr
+    double* lcol = Y + n * nr;      // mp
+    double* ucol = lcol + mp;       // mp
+    // rows 0..m go to the ring; rows beyond the first window are staged in
+    // the scratch slice (row l at l*mp) until they enter the ring
+    for (int l = tid; l < n; l += nt) {
+      double* row = (l <= m) ? W + l * mp : Lg + (long long)l * mp;
+      build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
+    }
+    __syncthreads();
+    // banded LDL^T with forward elimination of the right-hand sides
+    for (int k = 0; k < n; ++k) {
+      const int amax = min(m, n - 1 - k);
+      double dk = W[(k % mp) * mp];
+      if (!(dk > 0.0) || !isfinite(dk)) {
+        if (tid == 0) atomicOr(status, kStatSingular);
+        dk = 1.0;
+      }
+      const double inv = 1.0 / dk;
+      for (int a = 1 + tid; a <= amax; a += nt) {
+        double* w = W + ((k + a) % mp) * mp + a;
+        const double u = *w;
+        ucol[a] = u;
+        lcol[a] = u * inv;
+        *w = u * inv;
+      }
+      // row k is final: store (d_k, l_{k,k-1}, ..., l_{k,k-m})
+      for (int dd = tid; dd <= m; dd += nt) Lg[(long long)k * mp + dd] = (dd == 0) ? dk : W[(k % mp) * mp + dd];
+      __syncthreads();
+      // rank-1 update of the trailing window and of the right-hand sides
+      const int npair = amax * amax;
+      for (int t = tid; t < npair; t += nt) {
+        const int a = t / amax + 1, bb = t % amax + 1;
+        if (bb <= a) W[((k + a) % mp) * mp + (a - bb)] -= lcol[a] * ucol[bb];
+      }
+      for (int t = tid; t < amax * nr; t += nt) {
+        const int a = t / nr + 1, r = t % nr;
+        Y[(k + a) * nr + r] -= lcol[a] * Y[k * nr + r];
+      }
+      // the slot of row k receives row k + m + 1
+      const int nxt = k + m + 1;
+      if (nxt < n) {
+        double* dst = W + (k % mp) * mp;
+        // copy the band part that was prepared in the scratch row
+        for (int dd = tid; dd <= m; dd += nt) dst[dd] = Lg[(long long)nxt * mp + dd];
+      }
+      __syncthreads();
+    }
+    // D^{-1}
+    for (int t = tid; t < n * nr; t += nt) Y[t] /= Lg[(long long)(t / nr) * mp];
+    __syncthreads();
+    // backward substitution with L^T
+    for (int k = n - 1; k > 0; --k) {
+      const int amax = min(m, k);
+      for (int t = tid; t < amax * nr; t += nt) {
+        const int dd = t / nr + 1, r = t % nr;
+        Y[(k - dd) * nr + r] -= Lg[(long long)k * mp + dd] * Y[k * nr + r];
+      }
+      __syncthreads();
+    }
+    // write the basis values (slots on lattice bits stay zero)
+    for (int l = tid; l < n; l += nt) {
+      Local c = local_cell(E, l);
+      const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = 0.0;
+      for (int r = 0; r < nr; ++r) P[(long long)slot_of(r, E.free_mask) * g.N + i] = Y[l * nr + r];
+      if (adaptive) {
+        snap[0 * g.N + i] = Abd[i];
+        snap[1 * g.N + i] = c.c[0] > 0 ? Abx[i] : 0.0;
+        snap[2 * g.N + i] = c.c[0] < g.nx - 1 ? Abx[i + 1] : 0.0;
+        snap[3 * g.N + i] = c.c[1] > 0 ? Aby[i] : 0.0;
+        snap[4 * g.N + i] = c.c[1] < g.ny - 1 ? Aby[i + g.sy] : 0.0;
+        snap[5 * g.N + i] = c.c[2] > 0 ? Abz[i] : 0.0;
+        snap[6 * g.N + i] = c.c[2] < g.nz - 1 ? Abz[i + g.sz] : 0.0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ double block_max(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ double rel_change(double a, double s) {
+  if (s != 0.0) return fabs(a - s) / fabs(s);
+  return a != 0.0 ? INFINITY : 0.0;
+}
+
+// Sec. 4.1.2 (Reading R15): largest relative change of the A_b rows of the
+// entity's cells since its last build.
+__global__ void k_adapt_flags(Geo g, const Entity* __restrict__ ents, int count, double theta,
+                              const double* __restrict__ Abd, const double* __restrict__ Abx,
+                              const double* __restrict__ Aby, const double* __restrict__ Abz,
+                              const double* __restrict__ snap, unsigned char* flag) {
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    const Entity E = ents[e];
+    double mx = 0.0;
+    for (int l = threadIdx.x; l < E.n; l += blockDim.x) {
+      Local c = local_cell(E, l);
+      const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      const double a[7] = {Abd[i],
+                           c.c[0] > 0 ? Abx[i] : 0.0, c.c[0] < g.nx - 1 ? Abx[i + 1] : 0.0,
+                           c.c[1] > 0 ? Aby[i] : 0.0, c.c[1] < g.ny - 1 ? Aby[i + g.sy] : 0.0,
+                           c.c[2] > 0 ? Abz[i] : 0.0, c.c[2] < g.nz - 1 ? Abz[i + g.sz] : 0.0};
+      for (int q = 0; q < 7; ++q) mx = fmax(mx, rel_change(a[q], snap[q * g.N + i]));
+    }
+    mx = block_max(mx);
+    if (threadIdx.x == 0) flag[e] = (mx > theta) ? 1 : 0;
+  }
+}
+
+// An entity is also rebuilt when a lower-level entity it touches was.
+__global__ void k_adapt_propagate(Geo g, const Entity* __restrict__ ents, int first, int count,
+                                  const int* __restrict__ ent_of_cell, unsigned char* flag) {
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    const Entity E = ents[first + e];
+    int hit = 0;
+    for (int l = threadIdx.x; l < E.n; l += blockDim.x) {
+      Local c = local_cell(E, l);
+      const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      for (int d = 0; d < 3; ++d) {
+        if (!(E.free_mask & (1 << d))) continue;
+        const long long sd = gstride(g, d);
+        if (c.c[d] == E.org[d] && c.c[d] > 0) {
+          const int o = ent_of_cell[i - sd];
+          if (o >= 0 && flag[o]) hit = 1;
+        }
+        if (c.c[d] == E.org[d] + E.L[d] - 1 && c.c[d] < gextent(g, d) - 1) {
+          const int o = ent_of_cell[i + sd];
+          if (o >= 0 && flag[o]) hit = 1;
+        }
+      }
+    }
+    hit = __syncthreads_or(hit);
+    if (threadIdx.x == 0 && hit) flag[first + e] = 1;
+  }
+}
+
+__global__ void k_count_flags(int count, const unsigned char* __restrict__ flag, double* out) {
+  __shared__ int sh[32];
+  int c = 0;
+  for (int e = threadIdx.x; e < count; e += blockDim.x) c += flag[e];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    out[0] = (double)t;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_vertices(const Geo& g, const CGeo& c, double* P, cudaStream_t s) {
+  k_vertices<<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
+                                int count, int smem, int grid, long long lstride, int adaptive,
+                                Buffers& b, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (grid > count) grid = count;
+  k_entity_solve<<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby,
+                                         b.Abz, b.P, b.snap, b.lscratch, lstride, b.status);
+  return cudaGetLastError();
+}
+
+cudaError_t set_entity_smem(int smem) {
+  return cudaFuncSetAttribute(k_entity_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,
+                               Buffers& b, unsigned char* flag, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_adapt_flags<<<count < 4096 ? count : 4096, 256, 0, s>>>(g, ents, count, theta, b.Abd, b.Abx,
+                                                           b.Aby, b.Abz, b.snap, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& b,
+                                   cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_adapt_propagate<<<count < 4096 ? count : 4096, 256, 0, s>>>(g, b.ents, first, count,
+                                                               b.ent_of_cell, b.flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out, cudaStream_t s) {
+  k_count_flags<<<1, 1024, 0, s>>>(count, flag, out);
+  return cudaGetLastError();
+}
+
+}  // namespace cams

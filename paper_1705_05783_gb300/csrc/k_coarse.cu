@@ -1,0 +1,430 @@
+// Coarse-scale kernels of Sec. 3: Galerkin operator R A P (Eq. 13) for MSFE
+// (R = P^T) and MSFV (Eq. 7), restriction R r, coarse direct solve and
+// prolongation P p_c (Eqs. 12, 15).
+//
+// P is stored per fine cell as 8 slots (slot-major arrays); slot bit d says
+// whether the coarse node is the lower (0) or upper (1) one along d among the
+// nodes spanning the cell's dual block (a cell on a vertex plane of d uses
+// bit 0 for that plane's node and never bit 1).
+//
+// Deterministic reductions only: every sum over fine cells is a fixed-shape
+// block tree, and every sum over blocks runs in a fixed block order, so the
+// MSFE matrix is bitwise symmetric.
+#include "cams_internal.h"
+
+namespace cams {
+
+namespace {
+
+__device__ __forceinline__ int nd_of(const Geo& g, int d) { return d == 0 ? g.nx : (d == 1 ? g.ny : g.nz); }
+__device__ __forceinline__ long long sd_of(const Geo& g, int d) { return d == 0 ? 1 : (d == 1 ? g.sy : g.sz); }
+
+// Coarse node index along d of the cell coordinate x for slot bit `bit`
+// (-1 when that node does not exist).
+__device__ __forceinline__ int corner_d(const CGeo& c, int d, int x, int bit) {
+  const int b = c.b[d], o = c.o[d], s = x - o;
+  int J;
+  if (s >= 0 && s % b == 0) J = bit ? -1 : s / b;          // on a vertex plane
+  else {
+    const int j = s >= 0 ? s / b + 1 : 0;                   // interval index
+    J = bit ? j : j - 1;
+  }
+  return (J >= 0 && J < c.nc[d]) ? J : -1;
+}
+
+// Cell range [lo, hi] along d of dual block index j (0..nc): the cells from
+// the lower vertex plane (inclusive) to the upper one (exclusive).
+__device__ __forceinline__ void dual_range(const CGeo& c, const Geo& g, int d, int j, int& lo, int& hi) {
+  const int n = nd_of(g, d);
+  lo = j == 0 ? 0 : (j - 1) * c.b[d] + c.o[d];
+  hi = j == c.nc[d] ? n - 1 : j * c.b[d] + c.o[d] - 1;
+}
+
+template <int K>
+__device__ void block_sum_k(double (&v)[K], double* sh /* K*32 */, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double t = v[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k * 32 + wid] = t;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[k * 32 + w];
+    out[k] = t;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int sym_idx(int s, int t) {   // upper triangle of 8x8, s <= t
+  return s * 8 - (s * (s - 1)) / 2 + (t - s);
+}
+
+// MSFE: per dual block, the 8x8 block sum over its cells and its low-side
+// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T  (A = sum of face
+// terms + diagonal D = C + Dirichlet terms).
+__global__ void __launch_bounds__(256) k_galerkin_fe_local(
+    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const double* __restrict__ P,
+    const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
+    const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
+    double* loc) {
+  __shared__ double sh[36 * 32];
+  const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
+  const int D = blockIdx.x;
+  const int j[3] = {D % ndx, (D / ndx) % ndy, D / (ndx * ndy)};
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
+  const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+  const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+  double acc[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
+    const int x = lo[0] + l % ex, y = lo[1] + (l / ex) % ey, z = lo[2] + l / (ex * ey);
+    const long long i = x + g.sy * y + g.sz * z;
+    double pi[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) pi[s] = P[(long long)s * g.N + i];
+    double Dd = Cacc[i];
+    if (dirichlet) {
+      if (x == 0) Dd += Tbw[y + (long long)g.ny * z] * rhow;
+      if (x == g.nx - 1) Dd += Tbe[y + (long long)g.ny * z] * rhoe;
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const double a = Dd * pi[s];
+#pragma unroll
+      for (int t = s; t < 8; ++t) acc[sym_idx(s, t)] += a * pi[t];
+    }
+    const int xc[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (xc[d] >= nd_of(g, d) - 1) continue;
+      const long long jn = i + sd_of(g, d);
+      const double w = -(d == 0 ? Ax[jn] : (d == 1 ? Ay[jn] : Az[jn]));
+      const bool inside = xc[d] + 1 <= hi[d];
+      double dv[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        double pj;
+        if (inside) pj = P[(long long)s * g.N + jn];
+        else pj = (s & (1 << d)) ? P[(long long)(s & ~(1 << d)) * g.N + jn] : 0.0;
+        dv[s] = pi[s] - pj;
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const double a = w * dv[s];
+#pragma unroll
+        for (int t = s; t < 8; ++t) acc[sym_idx(s, t)] += a * dv[t];
+      }
+    }
+  }
+  block_sum_k<36>(acc, sh, loc + (long long)D * 36);
+}
+
+// Gather the dual-block blocks into the 27-point coarse stencil, in a fixed
+// block order (so entry (I,J) and (J,I) add identical terms in one order).
+__global__ void k_galerkin_fe_gather(CGeo c, const double* __restrict__ loc, double* Acs) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= 27LL * c.Nc) return;
+  const int I = (int)(q / 27), t = (int)(q % 27);
+  const int off[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+  const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+  int Jc[3];
+  for (int d = 0; d < 3; ++d) {
+    Jc[d] = Ic[d] + off[d];
+    if (Jc[d] < 0 || Jc[d] >= c.nc[d]) { Acs[q] = 0.0; return; }
+  }
+  const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
+  double sum = 0.0;
+  // dual blocks having I and J as corners: along d, j in {I, I+1} and {J, J+1}
+  for (int jz = Ic[2]; jz <= Ic[2] + 1; ++jz)
+    for (int jy = Ic[1]; jy <= Ic[1] + 1; ++jy)
+      for (int jx = Ic[0]; jx <= Ic[0] + 1; ++jx) {
+        const int jj[3] = {jx, jy, jz};
+        int sI = 0, sJ = 0;
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+          // corner bit of node K along d in dual block j: upper if j == K, lower if j == K + 1
+          if (jj[d] == Ic[d]) sI |= 1 << d;
+          else if (jj[d] != Ic[d] + 1) ok = false;
+          if (jj[d] == Jc[d]) sJ |= 1 << d;
+          else if (jj[d] != Jc[d] + 1) ok = false;
+        }
+        if (!ok) continue;
+        const int D = jx + ndx * (jy + ndy * jz);
+        const int a = sI < sJ ? sI : sJ, b = sI < sJ ? sJ : sI;
+        sum += loc[(long long)D * 36 + sym_idx(a, b)];
+      }
+  Acs[q] = sum;
+}
+
+// MSFV: row I of R A P = sum over the cells of primal block I of (A P)_i,
+// i.e. D_i P_i plus the fluxes w (P_i - P_j) through the block's faces.
+__global__ void __launch_bounds__(256) k_galerkin_fv(
+    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const double* __restrict__ P,
+    const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
+    const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
+    double* Acs) {
+  extern __shared__ double acc[];   // 27 * blockDim
+  const int I = blockIdx.x;
+  const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+  const int bx = c.b[0], by = c.b[1], bz = c.b[2];
+  const int nb = bx * by * bz;
+  const int T = blockDim.x, tid = threadIdx.x;
+  for (int k = 0; k < 27; ++k) acc[k * T + tid] = 0.0;
+  auto add_cell = [&](long long cell, const int* xc, double scale) {
+    for (int s = 0; s < 8; ++s) {
+      const double v = P[(long long)s * g.N + cell];
+      if (v == 0.0) continue;
+      int t = 0, mul = 1;
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        const int J = corner_d(c, d, xc[d], (s >> d) & 1);
+        if (J < 0) { ok = false; break; }
+        t += (J - Ic[d] + 1) * mul;
+        mul *= 3;
+      }
+      if (ok) acc[t * T + tid] += scale * v;
+    }
+  };
+  for (int l = tid; l < nb; l += T) {
+    const int x = Ic[0] * bx + l % bx, y = Ic[1] * by + (l / bx) % by, z = Ic[2] * bz + l / (bx * by);
+    const long long i = x + g.sy * y + g.sz * z;
+    const int xc[3] = {x, y, z};
+    double Dd = Cacc[i];
+    if (dirichlet) {
+      if (x == 0) Dd += Tbw[y + (long long)g.ny * z] * rhow;
+      if (x == g.nx - 1) Dd += Tbe[y + (long long)g.ny * z] * rhoe;
+    }
+    add_cell(i, xc, Dd);
+    for (int d = 0; d < 3; ++d) {
+      const int bd = c.b[d];
+      for (int side = 0; side < 2; ++side) {
+        const bool onface = side == 0 ? (xc[d] == Ic[d] * bd) : (xc[d] == Ic[d] * bd + bd - 1);
+        if (!onface) continue;
+        const int xn = xc[d] + (side == 0 ? -1 : 1);
+        if (xn < 0 || xn >= nd_of(g, d)) continue;
+        const long long jn = side == 0 ? i - sd_of(g, d) : i + sd_of(g, d);
+        const long long up = side == 0 ? i : jn;      // coupling stored at the upper cell
+        const double w = -(d == 0 ? Ax[up] : (d == 1 ? Ay[up] : Az[up]));
+        add_cell(i, xc, w);
+        int xcn[3] = {xc[0], xc[1], xc[2]};
+        xcn[d] = xn;
+        add_cell(jn, xcn, -w);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < 27; k += T) {
+    double s = 0.0;
+    for (int q = 0; q < T; ++q) s += acc[k * T + q];
+    Acs[(long long)I * 27 + k] = s;
+  }
+}
+
+// Natural-order 27-point stencil -> band storage in the reordered index.
+__global__ void k_band_fill(CGeo c, int m, const double* __restrict__ Acs, const int* __restrict__ perm,
+                            double* band) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= 27LL * c.Nc) return;
+  const int I = (int)(q / 27), t = (int)(q % 27);
+  const int off[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+  const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+  int J = 0, mul = 1;
+  for (int d = 0; d < 3; ++d) {
+    const int v = Ic[d] + off[d];
+    if (v < 0 || v >= c.nc[d]) return;
+    J += v * mul;
+    mul *= c.nc[d];
+  }
+  const int pi = perm[I], pj = perm[J];
+  const int w = 2 * m + 1;
+  band[(long long)pi * w + (pj - pi + m)] = Acs[q];
+}
+
+// Right-looking band LU without pivoting, one CTA (row k of U and column k
+// of L are final after step k).
+__global__ void __launch_bounds__(1024) k_band_lu(int Nc, int m, double* band, int* status) {
+  const int w = 2 * m + 1;
+  for (int k = 0; k < Nc; ++k) {
+    const int amax = min(m, Nc - 1 - k);
+    double piv = band[(long long)k * w + m];
+    if (!(piv != 0.0) || !isfinite(piv)) {
+      if (threadIdx.x == 0) atomicOr(status, kStatSingular);
+      piv = 1.0;
+    }
+    const double inv = 1.0 / piv;
+    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
+      band[(long long)(k + a) * w + (m - a)] *= inv;      // l_{k+a,k}
+    __syncthreads();
+    const int np = amax * amax;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+      const int a = t / amax + 1, bb = t % amax + 1;      // row k+a, column k+bb
+      band[(long long)(k + a) * w + (bb - a + m)] -=
+          band[(long long)(k + a) * w + (m - a)] * band[(long long)k * w + (m + bb)];
+    }
+    __syncthreads();
+  }
+}
+
+// Forward (unit L) and backward (U) substitution, one CTA, vector in smem.
+__global__ void __launch_bounds__(1024) k_band_solve(int Nc, int m, const double* __restrict__ band,
+                                                     double* rc, double* pc) {
+  extern __shared__ double y[];
+  const int w = 2 * m + 1;
+  for (int i = threadIdx.x; i < Nc; i += blockDim.x) y[i] = rc[i];
+  __syncthreads();
+  for (int k = 0; k < Nc; ++k) {
+    const int amax = min(m, Nc - 1 - k);
+    const double yk = y[k];
+    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
+      y[k + a] -= band[(long long)(k + a) * w + (m - a)] * yk;
+    __syncthreads();
+  }
+  for (int k = Nc - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) y[k] /= band[(long long)k * w + m];
+    __syncthreads();
+    const double xk = y[k];
+    const int amax = min(m, k);
+    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
+      y[k - a] -= band[(long long)(k - a) * w + (m + a)] * xk;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < Nc; i += blockDim.x) pc[i] = y[i];
+}
+
+// MSFE restriction, part 1: per dual block the 8 sums  sum_i P_i[s] r_i.
+__global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const double* __restrict__ P,
+                                                           const double* __restrict__ r, double* part) {
+  __shared__ double sh[8 * 32];
+  const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
+  const int D = blockIdx.x;
+  const int j[3] = {D % ndx, (D / ndx) % ndy, D / (ndx * ndy)};
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
+  const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+  const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
+    const long long i = (lo[0] + l % ex) + g.sy * (lo[1] + (l / ex) % ey) + g.sz * (lo[2] + l / (ex * ey));
+    const double ri = r[i];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[s] += P[(long long)s * g.N + i] * ri;
+  }
+  block_sum_k<8>(acc, sh, part + (long long)D * 8);
+}
+
+// MSFE restriction, part 2: coarse node J sums its (up to 8) dual blocks.
+__global__ void k_restrict_fe_gather(CGeo c, const double* __restrict__ part, const int* __restrict__ perm,
+                                     double* rc) {
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= c.Nc) return;
+  const int Jc[3] = {J % c.nc[0], (J / c.nc[0]) % c.nc[1], J / (c.nc[0] * c.nc[1])};
+  const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
+  double s = 0.0;
+  for (int bz = 0; bz < 2; ++bz)
+    for (int by = 0; by < 2; ++by)
+      for (int bx = 0; bx < 2; ++bx) {
+        // dual block j = J + bit: J is its lower corner (slot bit 0) when bit = 1
+        const int jx = Jc[0] + bx, jy = Jc[1] + by, jz = Jc[2] + bz;
+        const int slot = (bx ? 0 : 1) | (by ? 0 : 2) | (bz ? 0 : 4);
+        const int D = jx + ndx * (jy + ndy * jz);
+        s += part[(long long)D * 8 + slot];
+      }
+  rc[perm[J]] = s;
+}
+
+// MSFV restriction: block sums of r.
+__global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double* __restrict__ r,
+                                                     const int* __restrict__ perm, double* rc) {
+  __shared__ double sh[32];
+  const int I = blockIdx.x;
+  const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+  const int bx = c.b[0], by = c.b[1], bz = c.b[2];
+  double acc[1] = {0.0};
+  for (int l = threadIdx.x; l < bx * by * bz; l += blockDim.x)
+    acc[0] += r[(Ic[0] * bx + l % bx) + g.sy * (Ic[1] * by + (l / bx) % by) + g.sz * (Ic[2] * bz + l / (bx * by))];
+  double out;
+  block_sum_k<1>(acc, sh, &out);
+  // block_sum_k writes through thread 0 only when K == 1
+  if (threadIdx.x == 0) rc[perm[I]] = out;
+}
+
+// p += P p_c
+__global__ void k_prolong_add(Geo g, CGeo c, const double* __restrict__ P, const double* __restrict__ pc,
+                              const int* __restrict__ perm, double* p) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const int xc[3] = {(int)(i % g.nx), (int)((i / g.nx) % g.ny), (int)(i / ((long long)g.nx * g.ny))};
+  int Jl[3][2];
+  for (int d = 0; d < 3; ++d) {
+    Jl[d][0] = corner_d(c, d, xc[d], 0);
+    Jl[d][1] = corner_d(c, d, xc[d], 1);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 8; ++sl) {
+    const int jx = Jl[0][sl & 1], jy = Jl[1][(sl >> 1) & 1], jz = Jl[2][(sl >> 2) & 1];
+    if (jx < 0 || jy < 0 || jz < 0) continue;
+    s += P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
+  }
+  p[i] += s;
+}
+
+}  // namespace
+
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
+                               double rhoe, Buffers& b, cudaStream_t s) {
+  const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
+  k_galerkin_fe_local<<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay, b.Az,
+                                         b.Cacc, b.Tbw, b.Tbe, b.loc);
+  k_galerkin_fe_gather<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, b.loc, b.Acs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
+                               double rhoe, Buffers& b, cudaStream_t s) {
+  const int T = 128;
+  k_galerkin_fv<<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax,
+                                                          b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_fill(const CGeo& c, int m, Buffers& b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.band, 0, sizeof(double) * (size_t)c.Nc * (2 * m + 1), s);
+  if (e != cudaSuccess) return e;
+  k_band_fill<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, m, b.Acs, b.perm, b.band);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_factor(int Nc, int m, Buffers& b, cudaStream_t s) {
+  k_band_lu<<<1, 1024, 0, s>>>(Nc, m, b.band, b.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
+                            cudaStream_t s) {
+  if (kind == 0) {
+    const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
+    k_restrict_fe_local<<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc);
+    k_restrict_fe_gather<<<(c.Nc + 127) / 128, 128, 0, s>>>(c, b.loc, b.perm, b.rc);
+  } else {
+    k_restrict_fv<<<c.Nc, 256, 0, s>>>(g, c, r, b.perm, b.rc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_solve(int Nc, int m, Buffers& b, cudaStream_t s) {
+  k_band_solve<<<1, 1024, Nc * sizeof(double), s>>>(Nc, m, b.band, b.rc, b.pc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s) {
+  k_prolong_add<<<(int)((g.N + 255) / 256), 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+  return cudaGetLastError();
+}
+
+}  // namespace cams

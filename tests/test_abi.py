@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads, exports every entry point of
+include/cams.h, and refuses bad arguments without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cams.h")
+LIB = os.path.join(ROOT, "paper_1705_05783_gb300", "_lib", "libcams.so")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(cams_\w+)\s*\(", txt, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_1705_05783_gb300 import build
+        build.build()
+    return ctypes.CDLL(LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    from paper_1705_05783_gb300 import cams
+    assert sorted(cams.EXPORTS) == _declared()
+    for n in cams.EXPORTS:
+        assert callable(getattr(cams, n))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every field offset of the ctypes mirrors equals the C compiler's
+    offsetof for include/cams.h."""
+    import subprocess
+    from paper_1705_05783_gb300 import cams
+    structs = [cams.cams_grid, cams.cams_fluid, cams.cams_bc, cams.cams_options, cams.cams_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cams.h"', 'int main(void){']
+    for s in structs:
+        lines.append(f'printf("{s.__name__} %zu\\n", sizeof({s.__name__}));')
+        for name, _ in s._fields_:
+            lines.append(f'printf("{s.__name__}.{name} %zu\\n", offsetof({s.__name__}, {name}));')
+    lines.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split("\n") if l)
+    for s in structs:
+        assert int(out[s.__name__]) == ctypes.sizeof(s), s.__name__
+        for name, _ in s._fields_:
+            assert int(out[f"{s.__name__}.{name}"]) == getattr(s, name).offset, (s.__name__, name)
+
+
+def test_setup_rejects_bad_arguments_before_touching_the_gpu():
+    from paper_1705_05783_gb300 import cams
+    g = cams.cams_grid(10, 10, 1, 0.1, 0.1, 0.1)
+    f = cams.cams_fluid(0, 0.1, 1.0, 1.0, 0.1)
+    k = np.ones(100)
+    for bad in ((3, 5, 1), (5, 5, 2), (1, 5, 1)):      # not dividing / inactive z / b < 2
+        o = cams.make_options(bad)
+        with pytest.raises(cams.CamsError) as e:
+            cams.cams_setup(g, f, o, k)
+        assert e.value.code == cams.CAMS_EINVAL
+    o = cams.make_options((5, 5, 1), basis=7)
+    with pytest.raises(cams.CamsError) as e:
+        cams.cams_setup(g, f, o, k)
+    assert e.value.code == cams.CAMS_EINVAL
+    assert "basis" in cams.cams_last_error()

@@ -1,0 +1,212 @@
+"""GPU path vs the CPU oracle, element by element, on shared seeded inputs.
+
+Every call goes through the C-ABI (libcams.so) via the ctypes binding.
+Tolerances are relative to the largest magnitude of the compared quantity:
+1e-12 for single-pass arithmetic (assembly, transmissibilities, ILU pivots),
+1e-10 for quantities that pass through a local direct solve (P) or a sum of
+many products (R A P), and 1e-9 relative L_inf for converged pressures with
+iteration counts within +-1 (the agreement FP64 rounding-order differences
+allow when both sides follow the same algorithm).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle.basis import basis_operator, prolongation
+from oracle.coarse import coarse_factor, coarse_operator, restriction
+from oracle.ilu import ilu0
+from oracle.solver import cams_iteration
+from oracle.wirebasket import build_wirebasket
+
+from _cases import coarse_from_gpu, gpu_handle, make_case, matrix_from_gpu, p_from_gpu
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "2d-40x40": dict(name="2d-40x40"),
+    "3d-wells-40x40x20": dict(name="3d-100x100x50-wells", nx=40, ny=40, nz=20),
+    "3d-30x30x20-b10": dict(name="3d-200x200x100", nx=30, ny=30, nz=20),
+    "3d-12x8x6-b2x4x3": dict(name="3d-200x200x100", nx=12, ny=8, nz=6, coarse=(2, 4, 3)),
+    "linear-law-16x12x8": dict(name="3d-200x200x100", nx=16, ny=12, nz=8, coarse=(4, 4, 4),
+                               law=1, c_or_eta=1.0),
+}
+
+
+def _rel(a, b):
+    s = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / s)
+
+
+def _pressures(case, seed=7):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-0.2, 1.1, case.N), rng.uniform(-0.2, 1.1, case.N)
+
+
+@pytest.fixture(scope="module")
+def cams():
+    from paper_1705_05783_gb300 import cams
+    return cams
+
+
+@pytest.mark.parametrize("cname", list(CASES))
+def test_transmissibility_and_assembly(cams, cname):
+    case = make_case(**CASES[cname])
+    h, bc, keep = gpu_handle(case)
+    try:
+        N = case.N
+        # static transmissibilities
+        T = cams.cams_get(h, cams.CAMS_Q_TRANS, np.zeros(3 * N))
+        fc = case.pb.faces
+        want = np.zeros(3 * N)
+        d = np.select([fc.hi - fc.lo == 1, fc.hi - fc.lo == case.w.nx], [0, 1], 2)
+        want[d * N + fc.hi] = fc.T
+        assert _rel(T, want) < 1e-14
+        # linear-system population at arbitrary p^nu, p^n
+        p_nu, p_n = _pressures(case)
+        dt = case.inp["dt"]
+        en = cams.cams_assemble(h, p_nu, p_n, dt, bc)
+        lin = oracle.assemble(case.pb, p_nu, p_n, dt)
+        Ad, Ax, Ay, Az = matrix_from_gpu(h, N)
+        A = lin.A
+        assert _rel(Ad, A.diagonal()) < 1e-13
+        i = np.arange(N)
+        for arr, off, ok in ((Ax, 1, i % case.w.nx > 0), (Ay, case.w.nx, (i // case.w.nx) % case.w.ny > 0),
+                             (Az, case.w.nx * case.w.ny, i // (case.w.nx * case.w.ny) > 0)):
+            ref = np.zeros(N)
+            ref[ok] = np.asarray(A[i[ok], i[ok] - off]).ravel()
+            assert _rel(arr, ref) < 1e-13
+        f = cams.cams_get(h, cams.CAMS_Q_RHS, np.zeros(N))
+        assert _rel(f, lin.f) < 1e-12
+        eps = cams.cams_get(h, cams.CAMS_Q_EPS, np.zeros(N))
+        assert _rel(eps, lin.eps) < 1e-11
+        assert abs(en - np.linalg.norm(lin.eps)) < 1e-11 * np.linalg.norm(lin.eps)
+    finally:
+        cams.cams_destroy(h)
+
+
+@pytest.mark.parametrize("basis", [1, 2, 3, 4])
+@pytest.mark.parametrize("cname", ["2d-40x40", "3d-wells-40x40x20", "3d-12x8x6-b2x4x3"])
+def test_prolongation(cams, cname, basis):
+    case = make_case(**CASES[cname], basis=basis)
+    h, bc, keep = gpu_handle(case)
+    try:
+        N = case.N
+        p_nu, p_n = _pressures(case)
+        dt = case.inp["dt"]
+        cams.cams_assemble(h, p_nu, p_n, dt, bc)
+        n = cams.cams_update_basis(h, True)
+        wb = build_wirebasket(case.pb.grid, case.w.coarse)
+        assert n == len(wb.entities)
+        lin = oracle.assemble(case.pb, p_nu, p_n, dt)
+        Ab = basis_operator(case.pb, basis, lin.rho, lin.c, p_n, dt)
+        Po = prolongation(Ab, wb).to_csr(wb.Nc)
+        Pg, vals, cols = p_from_gpu(h, N, wb.Nc)
+        assert np.abs((Pg - Po).toarray()).max() < 1e-11
+        # unused slots hold exact zeros
+        assert np.all(vals[cols < 0] == 0.0)
+    finally:
+        cams.cams_destroy(h)
+
+
+@pytest.mark.parametrize("R", [0, 1])
+@pytest.mark.parametrize("cname", ["2d-40x40", "3d-wells-40x40x20", "3d-30x30x20-b10",
+                                   "3d-12x8x6-b2x4x3"])
+def test_coarse_operator_and_ilu(cams, cname, R):
+    case = make_case(**CASES[cname], restriction=R, basis=4)
+    h, bc, keep = gpu_handle(case)
+    try:
+        N = case.N
+        p_nu, p_n = _pressures(case)
+        dt = case.inp["dt"]
+        cams.cams_assemble(h, p_nu, p_n, dt, bc)
+        cams.cams_update_basis(h, True)
+        wb = build_wirebasket(case.pb.grid, case.w.coarse)
+        lin = oracle.assemble(case.pb, p_nu, p_n, dt)
+        Ab = basis_operator(case.pb, 4, lin.rho, lin.c, p_n, dt)
+        P = prolongation(Ab, wb).to_csr(wb.Nc)
+        Ac = coarse_operator(restriction(R, P, wb), lin.A, P)
+        G, st = coarse_from_gpu(h, wb.nc)
+        assert _rel(G, Ac) < 1e-11
+        if R == 0:
+            assert np.array_equal(G, G.T)          # bitwise symmetric
+        L, U = ilu0(lin.A)
+        d = cams.cams_get(h, cams.CAMS_Q_ILU_DIAG, np.zeros(N))
+        assert _rel(d, U.diagonal()) < 1e-12
+    finally:
+        cams.cams_destroy(h)
+
+
+@pytest.mark.parametrize("n_pre,n_post", [(0, 1), (1, 2), (0, 5)])
+@pytest.mark.parametrize("R", [0, 1])
+@pytest.mark.parametrize("cname", ["2d-40x40", "3d-30x30x20-b10", "3d-12x8x6-b2x4x3"])
+def test_cams_iterations(cams, cname, R, n_pre, n_post):
+    case = make_case(**CASES[cname], restriction=R, n_pre=n_pre, n_post=n_post)
+    h, bc, keep = gpu_handle(case)
+    try:
+        N = case.N
+        p_nu, p_n = _pressures(case)
+        dt = case.inp["dt"]
+        cams.cams_assemble(h, p_nu, p_n, dt, bc)
+        cams.cams_update_basis(h, True)
+        res = cams.cams_iterate(h, 4)
+        pg = cams.cams_get(h, cams.CAMS_Q_PRESSURE, np.zeros(N))
+        wb = build_wirebasket(case.pb.grid, case.w.coarse)
+        lin = oracle.assemble(case.pb, p_nu, p_n, dt)
+        Ab = basis_operator(case.pb, case.w.basis, lin.rho, lin.c, p_n, dt)
+        P = prolongation(Ab, wb).to_csr(wb.Nc)
+        Rm = restriction(R, P, wb)
+        lu = coarse_factor(coarse_operator(Rm, lin.A, P))
+        LU = ilu0(lin.A)
+        p = p_nu.copy()
+        ro = [np.linalg.norm(lin.f - lin.A @ p)]
+        for _ in range(4):
+            p = cams_iteration(lin.A, lin.f, p, P, Rm, lu, LU, n_pre, n_post)
+            ro.append(np.linalg.norm(lin.f - lin.A @ p))
+        assert _rel(pg, p) < 1e-10
+        np.testing.assert_allclose(res, ro, rtol=1e-7)
+    finally:
+        cams.cams_destroy(h)
+
+
+def _run_both(cams, case, steps):
+    h, bc, keep = gpu_handle(case)
+    try:
+        p = case.inp["p0"].copy()
+        out = []
+        for _ in range(steps):
+            pn = p.copy()
+            st = cams.cams_solve(h, pn, case.inp["dt"], bc, p)
+            out.append((p.copy(), st.newton_its, st.cams_its, st.basis_rebuilt,
+                        list(st.cams_per_newton[:st.newton_its])))
+    finally:
+        cams.cams_destroy(h)
+    q, sto = oracle.run(case.pb, case.opt, case.inp["p0"], case.inp["dt"], steps)
+    return out, q, sto
+
+
+@pytest.mark.parametrize("nl_tol", [1e-8, 1e-10])
+def test_solve_2d_five_steps(cams, nl_tol):
+    """The 2D 40x40 workload, five implicit steps."""
+    case = make_case("2d-40x40", nl_tol=nl_tol, steps=5)
+    steps = 5 if nl_tol == 1e-8 else 1
+    out, q, sto = _run_both(cams, case, steps)
+    pg, nwt, cit, rb, per = out[-1]
+    assert _rel(pg, q) < 1e-9
+    for (p, n, c, r, per), so in zip(out, sto):
+        assert abs(n - so.newton_its) <= 1
+        assert abs(c - so.cams_its) <= max(1, n)
+        assert r == so.basis_rebuilt
+
+
+@pytest.mark.parametrize("R", [0, 1])
+def test_solve_3d_wells_adaptive(cams, R):
+    """Scaled-down 3D wells workload: (B1) basis with adaptive updates at
+    theta = 0.1, MSFE and MSFV, 5 ILU(0) post-smoothing steps, two steps."""
+    case = make_case("3d-100x100x50-wells", nx=40, ny=40, nz=20, restriction=R, steps=2,
+                     nl_tol=1e-6, max_cams=40)
+    out, q, sto = _run_both(cams, case, 2)
+    assert _rel(out[-1][0], q) < 1e-8
+    for (p, n, c, r, per), so in zip(out, sto):
+        assert abs(n - so.newton_its) <= 1
+        assert r == so.basis_rebuilt
