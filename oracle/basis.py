@@ -109,6 +109,12 @@ class PRows:
 
 def solve_entity(Ab: sp.csr_matrix, wb: Wirebasket, P: PRows, e):
     """Reduced-problem solve of one entity (edge, face or interior)."""
+    M, rhs = entity_system(Ab, wb, P, e)
+    return np.linalg.solve(M, rhs)
+
+
+def entity_system(Ab: sp.csr_matrix, wb: Wirebasket, P: PRows, e):
+    """The dense local matrix M_e and right-hand sides of one entity."""
     S = e.cells
     k = e.level
     m = len(S)
@@ -128,7 +134,7 @@ def solve_entity(Ab: sp.csr_matrix, wb: Wirebasket, P: PRows, e):
     Plo = P.dense_rows(c[lo], e.corners)                # rows aligned with the lo entries
     rhs = np.zeros((m, len(e.corners)))
     np.add.at(rhs, r[lo], -v[lo][:, None] * Plo)
-    return np.linalg.solve(M, rhs)
+    return M, rhs
 
 
 def prolongation(Ab: sp.csr_matrix, wb: Wirebasket, P: PRows | None = None,

@@ -2,11 +2,13 @@
 
 Every call goes through the C-ABI (libcams.so) via the ctypes binding.
 Tolerances are relative to the largest magnitude of the compared quantity:
-1e-12 for single-pass arithmetic (assembly, transmissibilities, ILU pivots),
-1e-10 for quantities that pass through a local direct solve (P) or a sum of
-many products (R A P), and 1e-9 relative L_inf for converged pressures with
-iteration counts within +-1 (the agreement FP64 rounding-order differences
-allow when both sides follow the same algorithm).
+1e-14..1e-11 for single-pass arithmetic (transmissibilities, assembly, ILU
+pivots; the looser end for eps, which divides a flux sum by V rho), a bound
+derived from the local condition numbers for the basis values P and for
+R A P (see p_tolerance), 1e-10 for pressures after a few C-AMS iterations,
+and 1e-9 relative L_inf for converged pressures with Newton counts within
++-1 and C-AMS counts within one per linearisation (the agreement that FP64
+rounding-order differences allow when both sides follow the same steps).
 """
 import numpy as np
 import pytest
@@ -36,6 +38,23 @@ CASES = {
 def _rel(a, b):
     s = max(np.abs(b).max(), 1e-300)
     return float(np.abs(a - b).max() / s)
+
+
+def p_tolerance(Ab, wb):
+    """Forward-error bound of the basis values.  Both sides solve every local
+    SPD system with a backward-stable direct method (dense pivoted LU on the
+    CPU, banded LDL^T on the GPU), so their results differ by at most about
+    n * eps * cond(M_e) per entity, and errors pass on through the stages
+    (edge -> face -> interior).  The bound below takes the largest local
+    condition number (2-norm) times 64 * eps (float64), floored at 1e-12."""
+    from oracle.basis import PRows, entity_system
+    P = PRows(wb.grid.N)
+    kmax = 1.0
+    for e in wb.entities:
+        M, _ = entity_system(Ab, wb, P, e)
+        if M.shape[0] > 1:
+            kmax = max(kmax, np.linalg.cond(M))
+    return max(1e-12, 64 * np.finfo(float).eps * kmax)
 
 
 def _pressures(case, seed=7):
@@ -102,7 +121,7 @@ def test_prolongation(cams, cname, basis):
         Ab = basis_operator(case.pb, basis, lin.rho, lin.c, p_n, dt)
         Po = prolongation(Ab, wb).to_csr(wb.Nc)
         Pg, vals, cols = p_from_gpu(h, N, wb.Nc)
-        assert np.abs((Pg - Po).toarray()).max() < 1e-11
+        assert np.abs((Pg - Po).toarray()).max() < p_tolerance(Ab, wb)
         # unused slots hold exact zeros
         assert np.all(vals[cols < 0] == 0.0)
     finally:
@@ -127,7 +146,7 @@ def test_coarse_operator_and_ilu(cams, cname, R):
         P = prolongation(Ab, wb).to_csr(wb.Nc)
         Ac = coarse_operator(restriction(R, P, wb), lin.A, P)
         G, st = coarse_from_gpu(h, wb.nc)
-        assert _rel(G, Ac) < 1e-11
+        assert _rel(G, Ac) < 1e-13 + 4 * p_tolerance(Ab, wb)
         if R == 0:
             assert np.array_equal(G, G.T)          # bitwise symmetric
         L, U = ilu0(lin.A)
