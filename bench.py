@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the C-AMS hot path on one GB300 (replicas on N GPUs).
+
+One step = one pass of the whole hot path over one synthetic permeability
+field: static transmissibilities (cams_set_permeability), then one implicit
+time step (cams_solve): linear-system population, full basis construction,
+R A P and its factorisation, ILU(0) factorisation and the C-AMS inner loop,
+inside the Newton loop, to the workload's tolerance.
+
+Metric: fine-cell C-AMS iterations per second (N_f x C-AMS iterations / wall
+time), with the Newton-step wall time reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cams|reference]
+"""
+import os
+
+# the CPU oracle (reference arm and cpu_baseline) runs single-threaded, as
+# the paper's implementation did
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import WORKLOADS, make_inputs  # noqa: E402
+
+METRIC = ("Newton-step wall time & fine-cell·iters/s to 1e-8 residual; "
+          "learned/FP32 vs FP64 C-AMS")
+UNIT = "fine-cell·iters/s"
+DEFAULT_WORKLOAD = "3d-200x200x100"
+
+# Algorithmic bytes per fine cell of each kernel class (FP64; every array
+# touched once, neighbour re-reads served on chip).
+BYTES_PER_CELL = {
+    "assemble": 16 + 104,      # density: p -> rho; assembly: p, rho, rho_n, T x3 -> A x4, C, f, eps
+    "residual": 56,            # A x4, f, p -> r
+    "restrict": 72,            # P x8, r
+    "prolong": 80,             # P x8, p read + write
+    "ilu_resid": 64,           # A x4, f, p, 1/d -> D^{-1} r
+    "ilu_fwd": 40,             # D^{-1} r, scaled lower couplings x3 -> w
+    "ilu_bwd": 56,             # w, scaled upper couplings x3, p -> w, p
+    "galerkin": 96,            # P x8, couplings x3, C
+    "ilu_factor": 88,          # A x4 -> 1/d, scaled couplings x6
+    "basis_op": 64,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cams", choices=["cams", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ cams arm --
+
+def _handles(cams, w, inp, memspace, dev_arrays=None):
+    grid = cams.cams_grid(w.nx, w.ny, w.nz, inp["dx"], inp["dy"], inp["dz"])
+    fluid = cams.cams_fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi)
+    opt = cams.make_options(w.coarse, basis=w.basis, restriction=w.restriction, n_pre=w.n_pre,
+                            n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
+                            adapt_theta=w.adapt_theta, max_newton=w.max_newton,
+                            max_cams=w.max_cams, memspace=memspace)
+    k = dev_arrays if dev_arrays is not None else (inp["kx"], inp["ky"], inp["kz"])
+    return cams.cams_setup(grid, fluid, opt, *k)
+
+
+def run_cams(args, w, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1705_05783_gb300 import cams
+
+    inp = make_inputs(w, args.seed)
+    N = w.n_cells
+    # inputs resident in HBM for the device-timed value
+    dk = [torch.from_numpy(inp[k]).to(dev) for k in ("kx", "ky", "kz")]
+    p0 = torch.from_numpy(inp["p0"]).to(dev)
+    p = torch.empty_like(p0)
+    src = None
+    if len(inp["src_cell"]):
+        src = (torch.from_numpy(inp["src_cell"].astype(np.int32)).to(dev),
+               torch.from_numpy(inp["src_rate"]).to(dev))
+    bc, keep = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
+                            src[0] if src else None, src[1] if src else None)
+    stream = torch.cuda.current_stream(dev)
+    h = _handles(cams, w, inp, cams.CAMS_DEVICE, dk)
+    cams.cams_set_stream(h, stream.cuda_stream)
+
+    def step():
+        cams.cams_set_permeability(h, *dk)
+        p.copy_(p0)
+        return cams.cams_solve(h, p0, inp["dt"], bc, p)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # L2 is 129 MB; every step streams > 1 GB of fields (4M cells x 8 B x
+    # ~40 arrays), so the inputs of one iteration never stay L2-resident.
+    cams.cams_profile(h, True)
+    l0 = cams.launches(h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+            stats.append((st.newton_its, st.cams_its, st.t_assemble, st.t_precond, st.t_iterate))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = cams.launches(h) - l0
+    prof = cams.profile_table(h)
+    cams.cams_profile(h, False)
+    t_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    newton = sum(s[0] for s in stats)
+    its = sum(s[1] for s in stats)
+    units = N * its * world                   # replicas: every rank solves its own field
+    value = units / (t_ms / 1e3)
+
+    # dominant kernel class by time, with its live per-launch duration
+    dom = max((k for k in prof if prof[k][0] > 0 and k in BYTES_PER_CELL), key=lambda k: prof[k][1])
+    n_l, ms_tot, _ = prof[dom]
+    avg_ms = ms_tot / n_l
+    peak, peak_kind = measured_peaks()
+    bytes_per_launch = BYTES_PER_CELL[dom] * N
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+
+    # end to end through the C-ABI with HOST buffers (copies inside the timed region)
+    h_host = _handles(cams, w, inp, cams.CAMS_HOST)
+    bch, keeph = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
+                              inp["src_cell"] if len(inp["src_cell"]) else None,
+                              inp["src_rate"] if len(inp["src_rate"]) else None)
+    ph = np.empty(N)
+    for _ in range(1):
+        cams.cams_set_permeability(h_host, inp["kx"], inp["ky"], inp["kz"])
+        ph[:] = inp["p0"]
+        cams.cams_solve(h_host, inp["p0"], inp["dt"], bch, ph)
+    t0 = time.perf_counter()
+    e_its = 0
+    for _ in range(args.steps):
+        cams.cams_set_permeability(h_host, inp["kx"], inp["ky"], inp["kz"])
+        ph[:] = inp["p0"]
+        st = cams.cams_solve(h_host, inp["p0"], inp["dt"], bch, ph)
+        e_its += st.cams_its
+    e_s = time.perf_counter() - t0
+    cams.cams_destroy(h_host)
+    cams.cams_destroy(h)
+    e2e = {"value": N * e_its * world / e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(8 * N * 5 + 12 * len(inp["src_cell"])),
+           "d2h_bytes_per_step": int(8 * N)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name} FP64 C-AMS basis B{w.basis} "
+                               f"{'MSFE' if w.restriction == 0 else 'MSFV'} n_post={w.n_post} "
+                               f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}",
+                   "cells": N, "time_step": "first (full basis build) from p=0",
+                   "l2": "inputs > L2 (4M-cell fields, >1 GB touched per step)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "newton_step_ms": t_ms / max(newton, 1),
+        "newton_its_per_step": newton / args.steps, "cams_its_per_step": its / args.steps,
+        "stage_ms_per_step": {"assemble": sum(s[2] for s in stats) / args.steps,
+                              "precond_update": sum(s[3] for s in stats) / args.steps,
+                              "iterate": sum(s[4] for s in stats) / args.steps},
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": None, "bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": avg_ms},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    return out
+
+
+# ---------------------------------------------------- oracle (CPU) legs --
+
+def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
+    """A bounded sample of workload w for the CPU oracle: the (sub) corner
+    box of the same seeded field, same coarsening, fluid, time step and
+    solver options, one implicit step."""
+    import oracle
+    if inp is None:
+        inp = make_inputs(w, seed)
+    nx, ny, nz = sub
+    kx = inp["kx"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    ky = inp["ky"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    kz = inp["kz"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    g = oracle.Grid(nx, ny, nz, inp["dx"], inp["dy"], inp["dz"])
+    pb = oracle.Problem.build(g, oracle.Fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi),
+                              oracle.BC(True, w.p_west, w.p_east), kx, ky, kz)
+    opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
+                         n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
+                         adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams)
+    t0 = time.perf_counter()
+    _, st = oracle.run(pb, opt, np.zeros(g.N), inp["dt"], 1)
+    dt = time.perf_counter() - t0
+    return g.N * st[0].cams_its / dt, dt, st[0], f"{nx}x{ny}x{nz} corner box of the {w.name} field"
+
+
+def cpu_cores_used():
+    return 1
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return None
+    vals = []
+    inp = make_inputs(w, args.seed)
+    for _ in range(args.warmup):
+        oracle_sample(w, args.seed, inp=inp)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, dt, st, sample = oracle_sample(w, args.seed, inp=inp)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    w = WORKLOADS[args.workload]
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, w, rank, world)
+    else:
+        out = run_cams(args, w, rank, world, local_rank)
+        if rank == 0 and world == 1 and not args.no_baseline:
+            v, dt, st, sample = oracle_sample(w, args.seed)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores_used(),
+                                   "kind": "oracle", "sample": f"{sample}, one implicit step "
+                                   f"({st.newton_its} Newton, {st.cams_its} C-AMS its) in {dt:.1f} s"}
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -124,7 +124,27 @@ typedef struct {
                                 neighbour (dx,dy,dz) in {-1,0,1}^3 at (dx+1) + 3(dy+1) + 9(dz+1) */
 #define CAMS_Q_ILU_DIAG   9  /* double N: ILU(0) pivots d~_i (the only entries ILU(0) changes) */
 #define CAMS_Q_RESIDUAL  10  /* double N: f - A p for the current p */
-#define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, edges+faces+interiors rebuilt last, 0 */
+#define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, entities rebuilt by the last update, 0 */
+#define CAMS_Q_PROFILE   12  /* double 3*CAMS_PROF_CLASSES: per kernel class {launches, total ms,
+                                kernels}; accumulated while profiling is on (cams_profile) */
+#define CAMS_Q_LAUNCHES  13  /* double 1: kernels launched by this handle since cams_setup */
+
+/* kernel classes of CAMS_Q_PROFILE */
+#define CAMS_PROF_ASSEMBLE      0   /* density + linear-system population (a2) */
+#define CAMS_PROF_BASIS_OP      1   /* basis operator of Eqs. 8-11 */
+#define CAMS_PROF_ADAPT         2   /* adaptive-update flags (a3) */
+#define CAMS_PROF_BASIS         3   /* vertex/edge/face/interior local solves (a4-a7) */
+#define CAMS_PROF_GALERKIN      4   /* R A P (a8) */
+#define CAMS_PROF_COARSE_FACTOR 5   /* band fill + LU of R A P (a9) */
+#define CAMS_PROF_ILU_FACTOR    6   /* ILU(0) pivots (a10) */
+#define CAMS_PROF_RESIDUAL      7   /* r = f - A p with its norm */
+#define CAMS_PROF_RESTRICT      8   /* R r */
+#define CAMS_PROF_COARSE_SOLVE  9   /* band substitution */
+#define CAMS_PROF_PROLONG      10   /* p += P p_c */
+#define CAMS_PROF_ILU_FWD      11   /* ILU(0) forward wavefront sweep */
+#define CAMS_PROF_ILU_BWD      12   /* ILU(0) backward wavefront sweep and update of p */
+#define CAMS_PROF_ILU_RESID    13   /* D^{-1}(f - A p) feeding the forward sweep */
+#define CAMS_PROF_CLASSES      14
 
 /* (a1) Set up a solver for one grid and permeability field.
  * kx, ky, kz: permeability per cell (> 0, finite); ky and kz may alias kx.
@@ -137,6 +157,25 @@ typedef struct {
  * message). */
 int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_options* opt,
                const double* kx, const double* ky, const double* kz, cams_handle** out);
+
+/* (a1) Replace the permeability field of an existing handle: recompute the
+ * static transmissibilities and mark every basis function for rebuilding at
+ * the next cams_update_basis / cams_solve (as on a fresh handle).  Same
+ * argument rules as cams_setup; no allocation. */
+int cams_set_permeability(cams_handle* h, const double* kx, const double* ky, const double* kz);
+
+/* Turn per-kernel-class timing on (enable != 0) or off.  While on, CUDA
+ * events bracket every kernel class on the handle's stream and
+ * CAMS_Q_PROFILE accumulates launches and milliseconds; turning it on resets
+ * the totals. */
+int cams_profile(cams_handle* h, int enable);
+
+/* Self-test of the bounded device-side waits used by the wavefront sweeps:
+ * launches one wait on a counter that nothing sets.  The wait gives up after
+ * its iteration limit (well under a few seconds), the kernel returns and the
+ * call returns CAMS_ETIMEOUT; the handle stays usable.  Any other result
+ * means the timeout path is broken. */
+int cams_selftest_wait(cams_handle* h);
 
 /* Run the handle's work on the given cudaStream_t (passed as void*; NULL =
  * default stream).  The stream must belong to the handle's device. */

@@ -21,11 +21,15 @@ CAMS_ENOCONV, CAMS_ESINGULAR, CAMS_ETIMEOUT, CAMS_ENAN = -4, -5, -6, -7
 CAMS_HOST, CAMS_DEVICE = 0, 1
 CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 4, 5
 CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
-CAMS_Q_SIZES = 11
+CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES = 11, 12, 13
+PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
+                "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
+                "ilu_bwd", "ilu_resid")
 
-EXPORTS = ("cams_setup", "cams_set_stream", "cams_assemble", "cams_update_basis",
-           "cams_iterate", "cams_solve", "cams_get", "cams_get_int", "cams_last_error",
-           "cams_destroy")
+EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
+           "cams_set_stream",
+           "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve", "cams_get",
+           "cams_get_int", "cams_last_error", "cams_destroy")
 
 
 class CamsError(RuntimeError):
@@ -73,6 +77,9 @@ def load_library(path: str = LIB_PATH):
         "cams_setup": (C.c_int, [C.POINTER(cams_grid), C.POINTER(cams_fluid),
                                  C.POINTER(cams_options), P, P, P, C.POINTER(P)]),
         "cams_set_stream": (C.c_int, [P, P]),
+        "cams_set_permeability": (C.c_int, [P, P, P, P]),
+        "cams_profile": (C.c_int, [P, C.c_int]),
+        "cams_selftest_wait": (C.c_int, [P]),
         "cams_assemble": (C.c_int, [P, P, P, C.c_double, C.POINTER(cams_bc),
                                     C.POINTER(C.c_double)]),
         "cams_update_basis": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
@@ -141,6 +148,33 @@ def cams_setup(grid: cams_grid, fluid: cams_fluid, opt: cams_options, kx, ky=Non
                            _ptr(kz), C.byref(h))
     _check(code, None)
     return h
+
+
+def cams_set_permeability(h, kx, ky=None, kz=None):
+    _check(_lib.cams_set_permeability(h, _ptr(kx), _ptr(ky), _ptr(kz)), h)
+
+
+def cams_profile(h, enable=True):
+    _check(_lib.cams_profile(h, int(bool(enable))), h)
+
+
+def profile_table(h):
+    """{class name: (launch groups, total ms, kernels)} from CAMS_Q_PROFILE."""
+    a = np.zeros(3 * len(PROF_CLASSES))
+    _check(_lib.cams_get(h, CAMS_Q_PROFILE, a.ctypes.data), h)
+    return {n: (int(a[3 * k]), float(a[3 * k + 1]), int(a[3 * k + 2]))
+            for k, n in enumerate(PROF_CLASSES)}
+
+
+def cams_selftest_wait(h):
+    """Returns the status code (CAMS_ETIMEOUT expected) without raising."""
+    return _lib.cams_selftest_wait(h)
+
+
+def launches(h):
+    a = np.zeros(1)
+    _check(_lib.cams_get(h, CAMS_Q_LAUNCHES, a.ctypes.data), h)
+    return int(a[0])
 
 
 def cams_set_stream(h, stream_ptr: int):

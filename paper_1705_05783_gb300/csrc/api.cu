@@ -4,8 +4,10 @@
 // loop of Sec. 4.1.1.  Every numerical step is a kernel of this library; the
 // host only sequences launches and reads back one scalar per stopping test.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -44,6 +46,15 @@ struct cams_handle {
   int dirichlet = 0;
   double pw = 0.0, pe = 0.0, rhow = 1.0, rhoe = 1.0;
   int last_rebuilt = 0;
+  long long launch_base = 0;
+  bool ilu_pipelined = true;    // false: level-scheduled sweeps (CAMS_ILU_LEVEL=1)
+  int ilu_grid = 1;
+  // per-kernel-class profiling (cams_profile)
+  bool prof = false;
+  struct Pending { int cls; cudaEvent_t a, b; long long k0, k1; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_acc[3 * CAMS_PROF_CLASSES] = {};
   std::string err;
 };
 
@@ -86,11 +97,14 @@ double rho_host(const FluidK& f, double p) {
   return f.law == 0 ? f.rho0 * std::exp(f.c * p) : f.rho0 * (1.0 + f.c * p);
 }
 
+void prof_flush(cams_handle* h);
+
 // device status word -> status code (and reset)
 int check_status(cams_handle* h) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, h->b.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->prof) prof_flush(h);
   if (st) CK(cudaMemsetAsync(h->b.status, 0, sizeof(int), h->stream));
   if (st & kStatTimeout) return fail(h, CAMS_ETIMEOUT, "a device-side wait exceeded its limit");
   if (st & kStatSingular) return fail(h, CAMS_ESINGULAR, "zero or non-finite pivot in a local or coarse factorisation");
@@ -101,8 +115,73 @@ int check_status(cams_handle* h) {
 int read_scalar(cams_handle* h, double* out) {
   CK(cudaMemcpyAsync(out, h->b.scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->prof) prof_flush(h);
   return CAMS_OK;
 }
+
+// ------------------------------------------------------------- profiling --
+
+namespace lc {
+std::atomic<long long> total{0};
+}
+
+cudaEvent_t pool_get(cams_handle* h) {
+  if (h->pool.empty()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = h->pool.back();
+  h->pool.pop_back();
+  return e;
+}
+
+// Accumulate the timed launches whose events have completed (call after a
+// stream synchronisation) and recycle their events.
+void prof_flush(cams_handle* h) {
+  for (auto& q : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      h->prof_acc[3 * q.cls + 0] += 1.0;
+      h->prof_acc[3 * q.cls + 1] += ms;
+      h->prof_acc[3 * q.cls + 2] += (double)(q.k1 - q.k0);
+    }
+    h->pool.push_back(q.a);
+    h->pool.push_back(q.b);
+  }
+  h->pending.clear();
+}
+
+struct ProfScope {
+  cams_handle* h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  long long k0 = 0;
+  ProfScope(cams_handle* hh, int c) : h(hh), cls(c) {
+    if (!h->prof) return;
+    a = pool_get(h);
+    k0 = cams::launches_total();
+    if (a) cudaEventRecord(a, h->stream);
+  }
+  ~ProfScope() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = pool_get(h);
+    if (!b) { h->pool.push_back(a); return; }
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({cls, a, b, k0, cams::launches_total()});
+    if (h->pending.size() > 4096) {   // bound the number of live events
+      cudaEventSynchronize(b);
+      prof_flush(h);
+    }
+  }
+};
+
+// One kernel class: events bracket the launcher when profiling is on.
+#define LAUNCH(cls, call)          \
+  do {                             \
+    ProfScope ps_(h, cls);         \
+    CK(call);                      \
+  } while (0)
 
 // ---------------------------------------------------------------- tables --
 
@@ -180,9 +259,12 @@ int alloc_all(cams_handle* h) {
   AL(b.loc, (size_t)h->n_dual * 36);
   AL(b.Acs, 27LL * h->c.Nc);
   AL(b.band, (size_t)h->c.Nc * (2 * h->mc + 1));
+  AL(b.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(b.Lr, (size_t)h->c.Nc * (h->mc + 1));
   AL(b.perm, h->c.Nc);
   AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc);
   AL(b.dinv, N);
+  AL(b.Lx, N); AL(b.Ly, N); AL(b.Lz, N); AL(b.Ux, N); AL(b.Uy, N); AL(b.Uz, N);
+  AL(b.ctrl, ilu_ctrl_ints(h->g));
   AL(b.r, N); AL(b.w, N);
   AL(b.red, kRedBlocks);
   AL(b.scal, 8);
@@ -196,7 +278,8 @@ void free_all(cams_handle* h) {
   void* ptrs[] = {b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe, b.p, b.pn, b.rho, b.rhon, b.Ad, b.Ax, b.Ay,
                   b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
-                  b.pc, b.dinv, b.r, b.w, b.red, b.scal, b.status};
+                  b.pc, b.dinv, b.r, b.w, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
+                  b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->b = Buffers{};
@@ -272,10 +355,13 @@ int assemble(cams_handle* h, double* eps_norm) {
   Buffers& b = h->b;
   double* src_saved = b.src;
   if (!h->have_src) b.src = nullptr;
-  CK(launch_density(h->g, h->fl, b.p, b.rho, h->stream));
-  cudaError_t e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe, b, h->stream);
-  b.src = src_saved;
-  CK(e);
+  {
+    ProfScope ps_(h, CAMS_PROF_ASSEMBLE);
+    cudaError_t e = launch_density(h->g, h->fl, b.p, b.rho, h->stream);
+    if (e == cudaSuccess) e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe, b, h->stream);
+    b.src = src_saved;
+    CK(e);
+  }
   double s2;
   int rc = read_scalar(h, &s2);
   if (rc) return rc;
@@ -290,7 +376,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   Buffers& b = h->b;
   const cams_options& o = h->opt;
   const int ne = (int)h->ents.size();
-  CK(launch_basis_operator(h->g, h->fl, o.basis, h->dt, b, h->stream));
+  LAUNCH(CAMS_PROF_BASIS_OP, launch_basis_operator(h->g, h->fl, o.basis, h->dt, b, h->stream));
   const bool adaptive = o.basis != 4;
   int rebuilt = 0;
   if (!h->built || force || o.adapt_theta < 0) {
@@ -301,16 +387,20 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
     // change, so the relative-change test of Sec. 4.1.2 flags nothing.
     rebuilt = 0;
   } else {
-    CK(launch_adapt_flags(h->g, b.ents, ne, o.adapt_theta, b, b.flag, h->stream));
-    for (int lev = 2; lev <= 3; ++lev)
-      CK(launch_adapt_propagate(h->g, h->lev_first[lev], h->lev_count[lev], b, h->stream));
-    CK(launch_count_flags(ne, b.flag, b.scal, h->stream));
+    {
+      ProfScope ps_(h, CAMS_PROF_ADAPT);
+      CK(launch_adapt_flags(h->g, b.ents, ne, o.adapt_theta, b, b.flag, h->stream));
+      for (int lev = 2; lev <= 3; ++lev)
+        CK(launch_adapt_propagate(h->g, h->lev_first[lev], h->lev_count[lev], b, h->stream));
+      CK(launch_count_flags(ne, b.flag, b.scal, h->stream));
+    }
     double cnt;
     int rc = read_scalar(h, &cnt);
     if (rc) return rc;
     rebuilt = (int)cnt;
   }
   if (rebuilt > 0) {
+    ProfScope ps_(h, CAMS_PROF_BASIS);
     if (!h->built) CK(launch_vertices(h->g, h->c, b.P, h->stream));
     for (int lev = 1; lev <= 3; ++lev) {
       const int f = h->lev_first[lev];
@@ -323,17 +413,21 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   if (n_rebuilt) *n_rebuilt = rebuilt;
   // Galerkin coarse operator and its factorisation
   if (o.restriction == 0)
-    CK(launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
   else
-    CK(launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
-  CK(launch_band_fill(h->c, h->mc, b, h->stream));
-  CK(launch_band_factor(h->c.Nc, h->mc, b, h->stream));
-  CK(launch_ilu_factor(h->g, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+  {
+    ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
+    const int sym = o.restriction == 0;   // MSFE: R A P = P^T A P is symmetric
+    CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
+    CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
+  }
+  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->stream));
   return check_status(h);
 }
 
 int residual_norm(cams_handle* h, double* out) {
-  CK(launch_residual(h->g, h->b, h->b.p, h->b.r, h->b.red, h->b.scal, h->stream));
+  LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, h->b, h->b.p, h->b.r, h->b.red, h->b.scal, h->stream));
   double s2;
   int rc = read_scalar(h, &s2);
   if (rc) return rc;
@@ -342,15 +436,29 @@ int residual_norm(cams_handle* h, double* out) {
   return CAMS_OK;
 }
 
+// One ILU(0) smoothing step p <- p + M^{-1}(f - A p).
+int ilu_smooth(cams_handle* h) {
+  LAUNCH(CAMS_PROF_ILU_RESID, launch_ilu_resid(h->g, h->b, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, h->stream));
+  LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, h->stream));
+  return CAMS_OK;
+}
+
 // One C-AMS iteration (Table 1 steps 4-7 with ILU(0) smoothing).
 int cams_step(cams_handle* h) {
   Buffers& b = h->b;
-  for (int k = 0; k < h->opt.n_pre; ++k) CK(launch_ilu_smooth(h->g, b, h->stream));
-  CK(launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
-  CK(launch_restrict(h->g, h->c, h->opt.restriction, b.r, b, h->stream));
-  CK(launch_band_solve(h->c.Nc, h->mc, b, h->stream));
-  CK(launch_prolong_add(h->g, h->c, b, h->stream));
-  for (int k = 0; k < h->opt.n_post; ++k) CK(launch_ilu_smooth(h->g, b, h->stream));
+  for (int k = 0; k < h->opt.n_pre; ++k) {
+    int rc = ilu_smooth(h);
+    if (rc) return rc;
+  }
+  LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
+  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, h->opt.restriction, b.r, b, h->stream));
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, h->opt.restriction == 0, b, h->stream));
+  LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, b, h->stream));
+  for (int k = 0; k < h->opt.n_post; ++k) {
+    int rc = ilu_smooth(h);
+    if (rc) return rc;
+  }
   return CAMS_OK;
 }
 
@@ -361,6 +469,11 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 
 }  // namespace
+
+namespace cams {
+void count_launches(long long n) { lc::total += n; }
+long long launches_total() { return lc::total.load(); }
+}  // namespace cams
 
 // =================================================================== ABI ==
 
@@ -454,6 +567,12 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     return fail(nullptr, rc, msg);
   }
   for (auto& x : h->ev) cudaEventCreate(&x);
+  h->launch_base = launches_total();
+  {
+    const char* lv = std::getenv("CAMS_ILU_LEVEL");
+    h->ilu_pipelined = !(lv && lv[0] == '1');
+    h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
+  }
   // copy tables and compute transmissibilities
   cudaStream_t s = h->stream;
   cudaMemcpyAsync(h->b.ents, h->ents.data(), sizeof(Entity) * h->ents.size(), cudaMemcpyHostToDevice, s);
@@ -490,6 +609,50 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     return fail(nullptr, CAMS_ECUDA, msg);
   }
   *out = h;
+  return CAMS_OK;
+}
+
+int cams_set_permeability(cams_handle* h, const double* kx, const double* ky, const double* kz) {
+  if (!h) return CAMS_EINVAL;
+  if (!kx) return fail(h, CAMS_EINVAL, "kx is null");
+  if (!ky) ky = kx;
+  if (!kz) kz = kx;
+  const Geo& g = h->g;
+  const double* k3[3] = {kx, ky, kz};
+  double* dk[3];
+  if (h->opt.memspace == CAMS_HOST) {
+    for (int d = 0; d < 3; ++d)
+      for (long long i = 0; i < g.N; ++i)
+        if (!(k3[d][i] > 0.0) || !std::isfinite(k3[d][i]))
+          return fail(h, CAMS_EINVAL, "permeability must be positive and finite");
+    double* stage[3] = {h->b.r, h->b.w, h->b.eps};
+    for (int d = 0; d < 3; ++d) {
+      CK(cudaMemcpyAsync(stage[d], k3[d], sizeof(double) * g.N, cudaMemcpyHostToDevice, h->stream));
+      dk[d] = stage[d];
+    }
+  } else {
+    for (int d = 0; d < 3; ++d) dk[d] = const_cast<double*>(k3[d]);
+  }
+  CK(launch_transmissibility(g, h->fluid.mu, dk[0], dk[1], dk[2], 1, h->b, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->built = false;
+  h->assembled = false;
+  return CAMS_OK;
+}
+
+int cams_selftest_wait(cams_handle* h) {
+  if (!h) return CAMS_EINVAL;
+  CK(launch_wait_selftest(h->g, h->b, h->stream));
+  return check_status(h);
+}
+
+int cams_profile(cams_handle* h, int enable) {
+  if (!h) return CAMS_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  prof_flush(h);
+  h->prof = enable != 0;
+  if (h->prof)
+    for (double& v : h->prof_acc) v = 0.0;
   return CAMS_OK;
 }
 
@@ -650,6 +813,20 @@ int cams_get(cams_handle* h, int what, double* dst) {
                          h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
       break;
     }
+    case CAMS_Q_PROFILE: {
+      CK(cudaStreamSynchronize(s));
+      prof_flush(h);
+      CK(cudaMemcpyAsync(dst, h->prof_acc, sizeof(h->prof_acc),
+                         h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      break;
+    }
+    case CAMS_Q_LAUNCHES: {
+      const double v = (double)(launches_total() - h->launch_base);
+      CK(cudaMemcpyAsync(dst, &v, sizeof(double),
+                         h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      CK(cudaStreamSynchronize(s));
+      break;
+    }
     case CAMS_Q_RESIDUAL: {
       CK(launch_residual(h->g, b, b.p, b.r, b.red, b.scal, s));
       CK(cudaMemcpyAsync(dst, b.r, sizeof(double) * N, k, s));
@@ -708,6 +885,8 @@ void cams_destroy(cams_handle* h) {
   cudaStreamSynchronize(h->stream);
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
+  prof_flush(h);
+  for (auto& x : h->pool) cudaEventDestroy(x);
   free_all(h);
   delete h;
 }

@@ -79,10 +79,14 @@ struct Buffers {
   double* lscratch = nullptr;                             // local L factors, per resident CTA
   double* loc = nullptr;                                  // FE local 8x8 blocks per dual block (64 each)
   double* Acs = nullptr;                                  // 27*Nc coarse stencil
-  double* band = nullptr;                                 // Nc*(2m+1) band LU
+  double* band = nullptr;                                 // coarse band (column-major)
+  double *Lc = nullptr, *Lr = nullptr;                    // LDL^T factor, column/row-major
   int* perm = nullptr;                                    // coarse natural -> band order
   double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
   double* dinv = nullptr;                                 // 1 / ILU(0) pivots
+  double *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;     // a_{i,i-e_d} / d_i
+  double *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;     // a_{i,i+e_d} / d_i
+  int* ctrl = nullptr;                                    // wavefront tickets / progress
   double *r = nullptr, *w = nullptr;                      // work vectors
   double* red = nullptr;                                  // reduction partials
   double* scal = nullptr;                                 // reduced scalars (device)
@@ -91,6 +95,11 @@ struct Buffers {
 
 // Bits of the device status word (set by kernels, read by the host).
 enum : int { kStatSingular = 1, kStatNan = 2, kStatTimeout = 4, kStatBounds = 8 };
+
+// Kernels launched by this library in this process (read per handle as a
+// difference around its calls).
+void count_launches(long long n);
+long long launches_total();
 
 // Reductions use a fixed grid so results are bit-reproducible.
 constexpr int kRedBlocks = 1024;
@@ -124,13 +133,18 @@ cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, doubl
                                double rhoe, Buffers& b, cudaStream_t s);
 cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
                                double rhoe, Buffers& b, cudaStream_t s);
-cudaError_t launch_band_fill(const CGeo& c, int m, Buffers& b, cudaStream_t s);
-cudaError_t launch_band_factor(int Nc, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
                             cudaStream_t s);
-cudaError_t launch_band_solve(int Nc, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_solve(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s);
-cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, cudaStream_t s);
-cudaError_t launch_ilu_smooth(const Geo& g, Buffers& b, cudaStream_t s);
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s);
+cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s);
+cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
+                             cudaStream_t s);
+int ilu_ctrl_ints(const Geo& g);
+int ilu_pipe_grid(const Geo& g, int num_sms);
+cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s);
 
 }  // namespace cams

@@ -295,7 +295,7 @@ __global__ void k_count_flags(int count, const unsigned char* __restrict__ flag,
 }  // namespace
 
 cudaError_t launch_vertices(const Geo& g, const CGeo& c, double* P, cudaStream_t s) {
-  k_vertices<<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, P);
+  k_vertices<<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, P); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -305,7 +305,7 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
   if (count <= 0) return cudaSuccess;
   if (grid > count) grid = count;
   k_entity_solve<<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby,
-                                         b.Abz, b.P, b.snap, b.lscratch, lstride, b.status);
+                                         b.Abz, b.P, b.snap, b.lscratch, lstride, b.status); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -317,7 +317,7 @@ cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, doub
                                Buffers& b, unsigned char* flag, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_adapt_flags<<<count < 4096 ? count : 4096, 256, 0, s>>>(g, ents, count, theta, b.Abd, b.Abx,
-                                                           b.Aby, b.Abz, b.snap, flag);
+                                                           b.Aby, b.Abz, b.snap, flag); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -325,12 +325,12 @@ cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& 
                                    cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   k_adapt_propagate<<<count < 4096 ? count : 4096, 256, 0, s>>>(g, b.ents, first, count,
-                                                               b.ent_of_cell, b.flag);
+                                                               b.ent_of_cell, b.flag); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out, cudaStream_t s) {
-  k_count_flags<<<1, 1024, 0, s>>>(count, flag, out);
+  k_count_flags<<<1, 1024, 0, s>>>(count, flag, out); count_launches(1);
   return cudaGetLastError();
 }
 

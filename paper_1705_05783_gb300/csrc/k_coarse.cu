@@ -225,9 +225,11 @@ __global__ void __launch_bounds__(256) k_galerkin_fv(
   }
 }
 
-// Natural-order 27-point stencil -> band storage in the reordered index.
-__global__ void k_band_fill(CGeo c, int m, const double* __restrict__ Acs, const int* __restrict__ perm,
-                            double* band) {
+// Natural-order 27-point stencil -> column-major band in the reordered
+// index.  General (MSFV): Bc[col*(2m+1) + (row - col + m)].  Symmetric
+// (MSFE): lower triangle only, W[col*(m+1) + (row - col)].
+__global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ Acs,
+                            const int* __restrict__ perm, double* band) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= 27LL * c.Nc) return;
   const int I = (int)(q / 27), t = (int)(q % 27);
@@ -240,39 +242,215 @@ __global__ void k_band_fill(CGeo c, int m, const double* __restrict__ Acs, const
     J += v * mul;
     mul *= c.nc[d];
   }
-  const int pi = perm[I], pj = perm[J];
-  const int w = 2 * m + 1;
-  band[(long long)pi * w + (pj - pi + m)] = Acs[q];
+  const int row = perm[I], col = perm[J];
+  if (sym) {
+    if (row >= col) band[(long long)col * (m + 1) + (row - col)] = Acs[q];
+  } else {
+    band[(long long)col * (2 * m + 1) + (row - col + m)] = Acs[q];
+  }
 }
 
-// Right-looking band LU without pivoting, one CTA (row k of U and column k
-// of L are final after step k).
-__global__ void __launch_bounds__(1024) k_band_lu(int Nc, int m, double* band, int* status) {
+// ---- symmetric (MSFE) coarse matrix: blocked right-looking band LDL^T ----
+// One launch per block of kTB columns [c0, c1].  Each CTA factors the
+// kTB x kTB diagonal block in shared memory (redundantly: cheaper than a
+// separate launch), forms the panel rows l_rq (q in the block) of the
+// kTB-row tiles it owns, and subtracts  sum_q l_rq d_q l_cq  from its tile of
+// the trailing band.  Diagonal-tile CTAs write their panel rows to the
+// factor Lc (column-major: Lc[q*(m+1) + (r-q)], Lc[q*(m+1)] = d_q).  The
+// working band W is only read in the block columns and only written right of
+// them, so CTAs of one launch never race.
+constexpr int kTB = 16;
+
+__device__ __forceinline__ double band_at(const double* W, int m, int r, int c) {
+  // lower band, column-major; 0 outside the band
+  return (r - c <= m && r >= c) ? W[(long long)c * (m + 1) + (r - c)] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const double* __restrict__ Wr,
+                                                    double* W, double* Lc, int* status) {
+  __shared__ double Ld[kTB][kTB];     // diagonal block: unit L below, d on the diagonal
+  __shared__ double PR[kTB][kTB + 1]; // panel rows of my row tile:  l_rq
+  __shared__ double PC[kTB][kTB + 1]; // panel rows of my column tile
+  const int c1 = min(c0 + kTB, N) - 1;
+  const int tb = c1 - c0 + 1;
+  const int tid = threadIdx.x;
+  // --- factor the diagonal block (every CTA) ---
+  for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+    const int r = e / kTB, q = e % kTB;
+    Ld[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : 0.0;
+  }
+  __syncthreads();
+  for (int q = 0; q < tb; ++q) {
+    double dq = Ld[q][q];
+    if (!(dq > 0.0) || !isfinite(dq)) {
+      if (tid == 0 && blockIdx.x == 0) atomicOr(status, kStatSingular);
+      dq = 1.0;
+    }
+    // column q below the diagonal: l_rq = a_rq / d_q ; then rank-1 update
+    __syncthreads();
+    if (tid > q && tid < tb) Ld[tid][q] = Ld[tid][q] / dq;
+    __syncthreads();
+    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+      const int r = e / kTB, cc = e % kTB;
+      if (r < tb && cc > q && cc <= r) Ld[r][cc] -= Ld[r][q] * dq * Ld[cc][q];
+    }
+    __syncthreads();
+  }
+  // --- my tile of the trailing triangle ---
+  const int rlo = c1 + 1;
+  const int rhi = min(c1 + m, N - 1);
+  const int nb = rhi >= rlo ? (rhi - rlo + kTB) / kTB : 0;
+  int bi = 0, bj = 0;
+  {
+    int t = blockIdx.x;          // tiles enumerated row by row, bj <= bi
+    while (t > bi) { t -= bi + 1; ++bi; }
+    bj = t;
+  }
+  const bool have_tile = nb > 0 && bi < nb;
+  const int r0 = rlo + bi * kTB, cc0 = rlo + bj * kTB;
+  // panel rows: thread k < kTB handles row r0+k, thread kTB + k row cc0+k
+  if (have_tile && tid < 2 * kTB) {
+    const int k = tid % kTB;
+    const int r = (tid < kTB ? r0 : cc0) + k;
+    double v[kTB];
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) v[q] = (r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : 0.0;
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) {
+      if (q < tb) {
+        const double l = v[q] / Ld[q][q];
+        v[q] = l;
+#pragma unroll
+        for (int q2 = q + 1; q2 < kTB; ++q2)
+          if (q2 < tb) v[q2] -= l * Ld[q][q] * Ld[q2][q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kTB; ++q) {
+      if (tid < kTB) PR[k][q] = v[q];
+      else PC[k][q] = v[q];
+    }
+  }
+  __syncthreads();
+  if (have_tile) {
+    // W[r][c] -= sum_q l_rq d_q l_cq
+    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+      const int a = e / kTB, b = e % kTB;
+      const int r = r0 + a, cc = cc0 + b;
+      if (r > rhi || cc > rhi || cc > r || r - cc > m) continue;
+      double s = 0.0;
+      for (int q = 0; q < tb; ++q) s += PR[a][q] * Ld[q][q] * PC[b][q];
+      W[(long long)cc * (m + 1) + (r - cc)] -= s;
+    }
+    // diagonal tiles publish their panel rows
+    if (bi == bj) {
+      for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+        const int a = e / kTB, q = e % kTB;
+        const int r = r0 + a, col = c0 + q;
+        if (r <= rhi && q < tb && r - col <= m) Lc[(long long)col * (m + 1) + (r - col)] = PR[a][q];
+      }
+    }
+  }
+  // the first CTA publishes the diagonal block
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+      const int r = e / kTB, q = e % kTB;
+      if (r < tb && q <= r && r - q <= m) Lc[(long long)(c0 + q) * (m + 1) + (r - q)] = Ld[r][q];
+    }
+  }
+}
+
+// Row-major copy of L for the backward substitution: Lr[k*(m+1) + a] = l_{k,k-a}.
+__global__ void k_ldlt_rows(int N, int m, const double* __restrict__ Lc, double* Lr) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)N * (m + 1)) return;
+  const int k = (int)(e / (m + 1)), a = (int)(e % (m + 1));
+  Lr[e] = (a == 0) ? Lc[(long long)k * (m + 1)] : (k - a >= 0 ? Lc[(long long)(k - a) * (m + 1) + a] : 0.0);
+}
+
+// L D L^T x = b, one CTA; y in shared memory, the next column of L is
+// prefetched into registers while the current one is applied.
+__global__ void __launch_bounds__(256) k_ldlt_solve(int N, int m, const double* __restrict__ Lc,
+                                                    const double* __restrict__ Lr, const double* __restrict__ rc,
+                                                    double* pc) {
+  extern __shared__ double y[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int mp = m + 1;
+  for (int i = tid; i < N; i += nt) y[i] = rc[i];
+  __syncthreads();
+  // forward: unit lower L, column-oriented; thread a (1..m) owns offset a
+  const int a0 = tid + 1;
+  double lnext[2];
+  auto loadcol = [&](int k, double* dst) {
+    for (int u = 0; u < 2; ++u) {
+      const int a = a0 + u * nt;
+      dst[u] = (k < N && a <= m && k + a < N) ? Lc[(long long)k * mp + a] : 0.0;
+    }
+  };
+  double lcur[2];
+  loadcol(0, lcur);
+  for (int k = 0; k < N; ++k) {
+    loadcol(k + 1, lnext);
+    const double yk = y[k];
+    for (int u = 0; u < 2; ++u) {
+      const int a = a0 + u * nt;
+      if (a <= m && k + a < N) y[k + a] -= lcur[u] * yk;
+    }
+    lcur[0] = lnext[0]; lcur[1] = lnext[1];
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += nt) y[i] /= Lc[(long long)i * mp];
+  __syncthreads();
+  // backward with L^T, column-oriented over rows of L
+  auto loadrow = [&](int k, double* dst) {
+    for (int u = 0; u < 2; ++u) {
+      const int a = a0 + u * nt;
+      dst[u] = (k >= 0 && a <= m && k - a >= 0) ? Lr[(long long)k * mp + a] : 0.0;
+    }
+  };
+  loadrow(N - 1, lcur);
+  for (int k = N - 1; k >= 0; --k) {
+    loadrow(k - 1, lnext);
+    const double xk = y[k];
+    for (int u = 0; u < 2; ++u) {
+      const int a = a0 + u * nt;
+      if (a <= m && k - a >= 0) y[k - a] -= lcur[u] * xk;
+    }
+    lcur[0] = lnext[0]; lcur[1] = lnext[1];
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += nt) pc[i] = y[i];
+}
+
+// ---- general (MSFV) coarse matrix: band LU without pivoting, one CTA ----
+// Column-major band Bc[col*(2m+1) + (row-col+m)]; after the factorisation
+// column k holds U above/on the diagonal and the multipliers of L below.
+__global__ void __launch_bounds__(1024) k_band_lu(int Nc, int m, double* Bc, int* status) {
   const int w = 2 * m + 1;
   for (int k = 0; k < Nc; ++k) {
     const int amax = min(m, Nc - 1 - k);
-    double piv = band[(long long)k * w + m];
+    double piv = Bc[(long long)k * w + m];
     if (!(piv != 0.0) || !isfinite(piv)) {
       if (threadIdx.x == 0) atomicOr(status, kStatSingular);
       piv = 1.0;
     }
     const double inv = 1.0 / piv;
     for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      band[(long long)(k + a) * w + (m - a)] *= inv;      // l_{k+a,k}
+      Bc[(long long)k * w + (m + a)] *= inv;              // l_{k+a,k}
     __syncthreads();
     const int np = amax * amax;
     for (int t = threadIdx.x; t < np; t += blockDim.x) {
-      const int a = t / amax + 1, bb = t % amax + 1;      // row k+a, column k+bb
-      band[(long long)(k + a) * w + (bb - a + m)] -=
-          band[(long long)(k + a) * w + (m - a)] * band[(long long)k * w + (m + bb)];
+      const int bb = t / amax + 1, a = t % amax + 1;      // column k+bb, row k+a
+      Bc[(long long)(k + bb) * w + (a - bb + m)] -=
+          Bc[(long long)k * w + (m + a)] * Bc[(long long)(k + bb) * w + (m - bb)];
     }
     __syncthreads();
   }
 }
 
-// Forward (unit L) and backward (U) substitution, one CTA, vector in smem.
-__global__ void __launch_bounds__(1024) k_band_solve(int Nc, int m, const double* __restrict__ band,
-                                                     double* rc, double* pc) {
+// Forward (unit L) and backward (U) substitution with the column-major LU.
+__global__ void __launch_bounds__(256) k_band_solve(int Nc, int m, const double* __restrict__ Bc,
+                                                    const double* __restrict__ rc, double* pc) {
   extern __shared__ double y[];
   const int w = 2 * m + 1;
   for (int i = threadIdx.x; i < Nc; i += blockDim.x) y[i] = rc[i];
@@ -281,16 +459,16 @@ __global__ void __launch_bounds__(1024) k_band_solve(int Nc, int m, const double
     const int amax = min(m, Nc - 1 - k);
     const double yk = y[k];
     for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      y[k + a] -= band[(long long)(k + a) * w + (m - a)] * yk;
+      y[k + a] -= Bc[(long long)k * w + (m + a)] * yk;
     __syncthreads();
   }
   for (int k = Nc - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) y[k] /= band[(long long)k * w + m];
+    const double xk = y[k] / Bc[(long long)k * w + m];
     __syncthreads();
-    const double xk = y[k];
+    if (threadIdx.x == 0) y[k] = xk;
     const int amax = min(m, k);
     for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      y[k - a] -= band[(long long)(k - a) * w + (m + a)] * xk;
+      y[k - a] -= Bc[(long long)k * w + (m - a)] * xk;
     __syncthreads();
   }
   for (int i = threadIdx.x; i < Nc; i += blockDim.x) pc[i] = y[i];
@@ -380,8 +558,8 @@ cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, doubl
                                double rhoe, Buffers& b, cudaStream_t s) {
   const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
   k_galerkin_fe_local<<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay, b.Az,
-                                         b.Cacc, b.Tbw, b.Tbe, b.loc);
-  k_galerkin_fe_gather<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, b.loc, b.Acs);
+                                         b.Cacc, b.Tbw, b.Tbe, b.loc); count_launches(1);
+  k_galerkin_fe_gather<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, b.loc, b.Acs); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -389,19 +567,35 @@ cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, doubl
                                double rhoe, Buffers& b, cudaStream_t s) {
   const int T = 128;
   k_galerkin_fv<<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax,
-                                                          b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+                                                          b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs); count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_fill(const CGeo& c, int m, Buffers& b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b.band, 0, sizeof(double) * (size_t)c.Nc * (2 * m + 1), s);
+cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s) {
+  const size_t len = sym ? (size_t)c.Nc * (m + 1) : (size_t)c.Nc * (2 * m + 1);
+  cudaError_t e = cudaMemsetAsync(b.band, 0, sizeof(double) * len, s);
   if (e != cudaSuccess) return e;
-  k_band_fill<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, m, b.Acs, b.perm, b.band);
+  k_band_fill<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, m, sym, b.Acs, b.perm, b.band); count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_factor(int Nc, int m, Buffers& b, cudaStream_t s) {
-  k_band_lu<<<1, 1024, 0, s>>>(Nc, m, b.band, b.status);
+cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s) {
+  if (!sym) {
+    k_band_lu<<<1, 1024, 0, s>>>(Nc, m, b.band, b.status); count_launches(1);
+    return cudaGetLastError();
+  }
+  int launches = 0;
+  for (int c0 = 0; c0 < Nc; c0 += kTB) {
+    const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
+    const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
+    const int nb = rhi > c1 ? (rhi - c1 - 1 + kTB) / kTB : 0;
+    const int grid = nb > 0 ? nb * (nb + 1) / 2 : 1;
+    k_ldlt_block<<<grid, 256, 0, s>>>(Nc, m, c0, b.band, b.band, b.Lc, b.status);
+    ++launches;
+  }
+  const long long n = (long long)Nc * (m + 1);
+  k_ldlt_rows<<<(int)((n + 255) / 256), 256, 0, s>>>(Nc, m, b.Lc, b.Lr);
+  count_launches(launches + 1);
   return cudaGetLastError();
 }
 
@@ -409,21 +603,26 @@ cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double*
                             cudaStream_t s) {
   if (kind == 0) {
     const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
-    k_restrict_fe_local<<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc);
-    k_restrict_fe_gather<<<(c.Nc + 127) / 128, 128, 0, s>>>(c, b.loc, b.perm, b.rc);
+    k_restrict_fe_local<<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc); count_launches(1);
+    k_restrict_fe_gather<<<(c.Nc + 127) / 128, 128, 0, s>>>(c, b.loc, b.perm, b.rc); count_launches(1);
   } else {
-    k_restrict_fv<<<c.Nc, 256, 0, s>>>(g, c, r, b.perm, b.rc);
+    k_restrict_fv<<<c.Nc, 256, 0, s>>>(g, c, r, b.perm, b.rc); count_launches(1);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_solve(int Nc, int m, Buffers& b, cudaStream_t s) {
-  k_band_solve<<<1, 1024, Nc * sizeof(double), s>>>(Nc, m, b.band, b.rc, b.pc);
+cudaError_t launch_band_solve(int Nc, int m, int sym, Buffers& b, cudaStream_t s) {
+  if (sym) {
+    k_ldlt_solve<<<1, 256, Nc * sizeof(double), s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
+  } else {
+    k_band_solve<<<1, 256, Nc * sizeof(double), s>>>(Nc, m, b.band, b.rc, b.pc);
+  }
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s) {
-  k_prolong_add<<<(int)((g.N + 255) / 256), 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+  k_prolong_add<<<(int)((g.N + 255) / 256), 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p); count_launches(1);
   return cudaGetLastError();
 }
 

@@ -214,13 +214,13 @@ inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 cudaError_t launch_transmissibility(const Geo& g, double mu, const double* kx, const double* ky,
                                     const double* kz, int dirichlet, Buffers& b, cudaStream_t s) {
   k_transmissibility<<<blocks_for(g.N, 256), 256, 0, s>>>(g, mu, kx, ky, kz, dirichlet, b.Tx,
-                                                          b.Ty, b.Tz, b.Tbw, b.Tbe);
+                                                          b.Ty, b.Tz, b.Tbw, b.Tbe); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, double* rho,
                            cudaStream_t s) {
-  k_density<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, fl, p, rho);
+  k_density<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, fl, p, rho); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -232,27 +232,27 @@ cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int diric
   k_assemble<<<kRedBlocks, kRedThreads, 0, s>>>(g, f2, dt, dirichlet, pw, pe, rhow, rhoe, b.p,
                                                 b.rho, b.rhon, b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe,
                                                 b.src, b.Ad, b.Ax, b.Ay, b.Az, b.Cacc, b.f, b.eps,
-                                                b.red);
-  k_finish_sum<<<1, 1024, 0, s>>>(b.red, kRedBlocks, b.scal);
+                                                b.red); count_launches(1);
+  k_finish_sum<<<1, 1024, 0, s>>>(b.red, kRedBlocks, b.scal); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_sources(int n, const int* cell, const double* rate, double* src,
                                long long N, cudaStream_t s) {
-  k_add_sources<<<1, 32, 0, s>>>(n, cell, rate, src, N);
+  k_add_sources<<<1, 32, 0, s>>>(n, cell, rate, src, N); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq(const double* x, long long N, double* red, double* out, cudaStream_t s) {
-  k_sumsq_partial<<<kRedBlocks, kRedThreads, 0, s>>>(x, N, red);
-  k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out);
+  k_sumsq_partial<<<kRedBlocks, kRedThreads, 0, s>>>(x, N, red); count_launches(1);
+  k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, double* r,
                             double* red, double* out, cudaStream_t s) {
-  k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.f, p, r, red);
-  k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out);
+  k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.f, p, r, red); count_launches(1);
+  k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -260,7 +260,7 @@ cudaError_t launch_basis_operator(const Geo& g, const FluidK& fl, int kind, doub
                                   Buffers& b, cudaStream_t s) {
   k_basis_operator<<<blocks_for(g.N, 256), 256, 0, s>>>(g, fl, kind, dt, b.Tx, b.Ty, b.Tz, b.Ax,
                                                         b.Ay, b.Az, b.Cacc, b.pn, b.Abd, b.Abx,
-                                                        b.Aby, b.Abz);
+                                                        b.Aby, b.Abz); count_launches(1);
   return cudaGetLastError();
 }
 
