@@ -29,7 +29,7 @@ PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_fa
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
            "cams_set_stream",
            "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve", "cams_get",
-           "cams_get_int", "cams_last_error", "cams_destroy")
+           "cams_get_int", "cams_last_error", "cams_destroy", "cams_residual_norm_noalloc")
 
 
 class CamsError(RuntimeError):
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "cams_get_int": (C.c_int, [P, C.c_int, P]),
         "cams_last_error": (C.c_char_p, [P]),
         "cams_destroy": (None, [P]),
+        "cams_residual_norm_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P,
+                                                 C.POINTER(C.c_double), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -105,6 +107,8 @@ def _ptr(a):
     """Address of a numpy array (host) or a CUDA tensor (device)."""
     if a is None:
         return None
+    if isinstance(a, int):
+        return a
     if isinstance(a, np.ndarray):
         return a.ctypes.data
     return a.data_ptr()
@@ -219,6 +223,16 @@ def cams_get_int(h, what, dst):
 
 def cams_last_error(h=None) -> str:
     return _lib.cams_last_error(h).decode()
+
+
+def cams_residual_norm_noalloc(nx, ny, nz, diag, ax, ay, az, f, p, r=None, stream_ptr=0):
+    """||f - A p||_2 (and r, if given) with no device allocation; device
+    tensors in, Python float out.  Returns (status, norm)."""
+    out = C.c_double(0.0)
+    code = _lib.cams_residual_norm_noalloc(int(nx), int(ny), int(nz), _ptr(diag), _ptr(ax),
+                                           _ptr(ay), _ptr(az), _ptr(f), _ptr(p), _ptr(r),
+                                           C.byref(out), C.c_void_p(stream_ptr))
+    return code, out.value
 
 
 def cams_destroy(h):

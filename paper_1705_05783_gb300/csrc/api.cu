@@ -471,6 +471,7 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }  // namespace
 
 namespace cams {
+void set_global_error(const std::string& msg) { g_setup_error = msg; }
 void count_launches(long long n) { lc::total += n; }
 long long launches_total() { return lc::total.load(); }
 }  // namespace cams

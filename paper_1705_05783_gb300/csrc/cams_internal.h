@@ -96,6 +96,9 @@ struct Buffers {
 // Bits of the device status word (set by kernels, read by the host).
 enum : int { kStatSingular = 1, kStatNan = 2, kStatTimeout = 4, kStatBounds = 8 };
 
+// Message returned by cams_last_error(NULL).
+void set_global_error(const std::string& msg);
+
 // Kernels launched by this library in this process (read per handle as a
 // difference around its calls).
 void count_launches(long long n);
