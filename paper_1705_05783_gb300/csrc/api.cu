@@ -555,6 +555,10 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   std::stable_sort(ordc, ordc + 3, [&](int a, int b2) { return c.nc[a] < c.nc[b2]; });
   const int na = c.nc[ordc[0]], nb = c.nc[ordc[1]], ncc = c.nc[ordc[2]];
   h->mc = (na > 1 ? 1 : 0) + (nb > 1 ? na : 0) + (ncc > 1 ? na * nb : 0);
+  // an odd half-width makes m + 1 even, so every band column starts on a
+  // 16-byte boundary (the substitution streams columns with 16-byte copies);
+  // the extra diagonal is structurally zero
+  if (h->mc % 2 == 0) h->mc += 1;
   std::vector<int> perm(c.Nc);
   for (int I = 0; I < c.Nc; ++I) {
     const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};

@@ -296,6 +296,15 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
     }
     __syncthreads();
   }
+  // reciprocal pivots and d-scaled columns of the diagonal block
+  __shared__ double rinv[kTB];
+  __shared__ double LdD[kTB][kTB];    // LdD[r][q] = l_rq d_q
+  if (tid < kTB) rinv[tid] = tid < tb ? 1.0 / Ld[tid][tid] : 0.0;
+  for (int e = tid; e < kTB * kTB; e += blockDim.x) {
+    const int r = e / kTB, q = e % kTB;
+    LdD[r][q] = (r < tb && q < r) ? Ld[r][q] * Ld[q][q] : 0.0;
+  }
+  __syncthreads();
   // --- my tile of the trailing triangle ---
   const int rlo = c1 + 1;
   const int rhi = min(c1 + m, N - 1);
@@ -318,11 +327,11 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
       if (q < tb) {
-        const double l = v[q] / Ld[q][q];
+        const double l = v[q] * rinv[q];
         v[q] = l;
 #pragma unroll
         for (int q2 = q + 1; q2 < kTB; ++q2)
-          if (q2 < tb) v[q2] -= l * Ld[q][q] * Ld[q2][q];
+          if (q2 < tb) v[q2] -= l * LdD[q2][q];
       }
     }
 #pragma unroll
@@ -368,57 +377,80 @@ __global__ void k_ldlt_rows(int N, int m, const double* __restrict__ Lc, double*
   Lr[e] = (a == 0) ? Lc[(long long)k * (m + 1)] : (k - a >= 0 ? Lc[(long long)(k - a) * (m + 1) + a] : 0.0);
 }
 
-// L D L^T x = b, one CTA; y in shared memory, the next column of L is
-// prefetched into registers while the current one is applied.
+// L D L^T x = b, one CTA.  y lives in shared memory; the factor is streamed
+// through shared memory in chunks of kSC consecutive columns (forward, from
+// the column-major Lc) or rows (backward, from the row-major Lr), each chunk
+// a contiguous run copied with cp.async while the previous one is applied.
+constexpr int kSC = 16;
+
+__device__ __forceinline__ void cp_async16(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// copy `n` doubles (n even, both addresses 16-byte aligned) into shared memory
+__device__ __forceinline__ void stage(double* dst, const double* src, int n) {
+  for (int e = 2 * threadIdx.x; e < n; e += 2 * blockDim.x) cp_async16(dst + e, src + e);
+  cp_async_commit();
+}
+
 __global__ void __launch_bounds__(256) k_ldlt_solve(int N, int m, const double* __restrict__ Lc,
                                                     const double* __restrict__ Lr, const double* __restrict__ rc,
                                                     double* pc) {
-  extern __shared__ double y[];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  extern __shared__ __align__(16) double sm[];
   const int mp = m + 1;
+  const int chunk = kSC * mp;                  // even: mp is even by construction
+  double* buf0 = sm;
+  double* buf1 = sm + chunk;
+  double* y = sm + 2 * chunk;
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < N; i += nt) y[i] = rc[i];
-  __syncthreads();
-  // forward: unit lower L, column-oriented; thread a (1..m) owns offset a
-  const int a0 = tid + 1;
-  double lnext[2];
-  auto loadcol = [&](int k, double* dst) {
-    for (int u = 0; u < 2; ++u) {
-      const int a = a0 + u * nt;
-      dst[u] = (k < N && a <= m && k + a < N) ? Lc[(long long)k * mp + a] : 0.0;
-    }
-  };
-  double lcur[2];
-  loadcol(0, lcur);
-  for (int k = 0; k < N; ++k) {
-    loadcol(k + 1, lnext);
-    const double yk = y[k];
-    for (int u = 0; u < 2; ++u) {
-      const int a = a0 + u * nt;
-      if (a <= m && k + a < N) y[k + a] -= lcur[u] * yk;
-    }
-    lcur[0] = lnext[0]; lcur[1] = lnext[1];
+  const int nchunks = (N + kSC - 1) / kSC;
+  // forward with the unit lower factor, column by column
+  stage(buf0, Lc, min(kSC, N) * mp);
+  for (int ck = 0; ck < nchunks; ++ck) {
+    double* cur = (ck & 1) ? buf1 : buf0;
+    double* nxt = (ck & 1) ? buf0 : buf1;
+    cp_async_wait_all();
     __syncthreads();
+    if (ck + 1 < nchunks) {
+      const int k1 = (ck + 1) * kSC;
+      stage(nxt, Lc + (long long)k1 * mp, min(kSC, N - k1) * mp);
+    }
+    const int k0 = ck * kSC;
+    for (int c = 0; c < kSC && k0 + c < N; ++c) {
+      const int k = k0 + c;
+      const double yk = y[k];
+      const int amax = min(m, N - 1 - k);
+      for (int a = 1 + tid; a <= amax; a += nt) y[k + a] -= cur[c * mp + a] * yk;
+      __syncthreads();
+    }
   }
+  cp_async_wait_all();
+  __syncthreads();
   for (int i = tid; i < N; i += nt) y[i] /= Lc[(long long)i * mp];
-  __syncthreads();
-  // backward with L^T, column-oriented over rows of L
-  auto loadrow = [&](int k, double* dst) {
-    for (int u = 0; u < 2; ++u) {
-      const int a = a0 + u * nt;
-      dst[u] = (k >= 0 && a <= m && k - a >= 0) ? Lr[(long long)k * mp + a] : 0.0;
-    }
-  };
-  loadrow(N - 1, lcur);
-  for (int k = N - 1; k >= 0; --k) {
-    loadrow(k - 1, lnext);
-    const double xk = y[k];
-    for (int u = 0; u < 2; ++u) {
-      const int a = a0 + u * nt;
-      if (a <= m && k - a >= 0) y[k - a] -= lcur[u] * xk;
-    }
-    lcur[0] = lnext[0]; lcur[1] = lnext[1];
+  // backward with L^T: rows of L from the last chunk down
+  const int last0 = (nchunks - 1) * kSC;
+  stage(buf0, Lr + (long long)last0 * mp, (N - last0) * mp);
+  for (int ck = nchunks - 1, it = 0; ck >= 0; --ck, ++it) {
+    double* cur = (it & 1) ? buf1 : buf0;
+    double* nxt = (it & 1) ? buf0 : buf1;
+    cp_async_wait_all();
     __syncthreads();
+    if (ck > 0) stage(nxt, Lr + (long long)(ck - 1) * kSC * mp, kSC * mp);
+    const int k0 = ck * kSC;
+    for (int c = min(kSC, N - k0) - 1; c >= 0; --c) {
+      const int k = k0 + c;
+      const double xk = y[k];
+      const int amax = min(m, k);
+      for (int a = 1 + tid; a <= amax; a += nt) y[k - a] -= cur[c * mp + a] * xk;
+      __syncthreads();
+    }
   }
+  cp_async_wait_all();
+  __syncthreads();
   for (int i = tid; i < N; i += nt) pc[i] = y[i];
 }
 
@@ -613,7 +645,10 @@ cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double*
 
 cudaError_t launch_band_solve(int Nc, int m, int sym, Buffers& b, cudaStream_t s) {
   if (sym) {
-    k_ldlt_solve<<<1, 256, Nc * sizeof(double), s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
+    const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
+    cudaError_t e = cudaFuncSetAttribute(k_ldlt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_ldlt_solve<<<1, 256, smem, s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
   } else {
     k_band_solve<<<1, 256, Nc * sizeof(double), s>>>(Nc, m, b.band, b.rc, b.pc);
   }

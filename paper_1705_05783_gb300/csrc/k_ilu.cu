@@ -19,7 +19,8 @@
 //    and are exchanged in shared memory.  Row blocks that border other CTAs
 //    read those CTAs' boundary rows from global memory (L2, bypassing L1)
 //    after an acquire-poll of the producer's progress counter, which the
-//    producer publishes with release semantics every kPublish steps.  Tiles
+//    producer publishes with release semantics every kBatch steps; a row
+//    that borders another tile fetches kBatch boundary values per poll.  Tiles
 //    are claimed through an atomic ticket in anti-diagonal order, so a CTA
 //    only ever waits on tiles already claimed by running CTAs: no
 //    co-residency assumption, no deadlock.  Every wait has an iteration
@@ -33,7 +34,7 @@ namespace cams {
 
 namespace {
 
-constexpr int kPublish = 4;                  // steps between progress publications
+constexpr int kBatch = 8;                    // steps per batch of cross-tile loads / publications
 constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ seconds)
 
 // ----------------------------------------------------------- factor ---
@@ -223,11 +224,17 @@ __device__ __forceinline__ bool wait_at_least(int* ctr, int need, int* abort_fla
 
 // ctrl: [0] ticket, [1] abort flag, [2 + tile] progress (steps completed).
 // The backward sweep runs the same schedule on the mirrored grid
-// (x -> nx-1-x, y -> ny-1-y, z -> nz-1-z).
+// (x -> nx-1-x, y -> ny-1-y, z -> nz-1-z).  Steps are grouped in batches of
+// kBatch: a row that borders an upstream tile waits once per batch for the
+// producer to be a whole batch ahead and then loads that batch's kBatch
+// boundary values with independent L2 loads, so one L2 round trip is paid
+// per batch instead of per step; producers publish at the end of each batch.
 template <int TY, int TZ, class Op, bool kBackward>
-__global__ void __launch_bounds__(TY* TZ) k_sweep_pipe(Geo g, Op op, const double* vals, int* ctrl,
+__global__ void __launch_bounds__(TY* TZ, 1) k_sweep_pipe(Geo g, Op op, const double* vals, int* ctrl,
                                                        int* status) {
   __shared__ double buf[2][TZ][TY];
+  __shared__ double yin[TZ][kBatch];   // boundary values from the tile below in y (ty == 0 rows)
+  __shared__ double zin[TY][kBatch];   // boundary values from the tile below in z (tz == 0 rows)
   __shared__ int s_tile;
   const int ty = threadIdx.x % TY, tz = threadIdx.x / TY;
   const int nty = (g.ny + TY - 1) / TY, ntz = (g.nz + TZ - 1) / TZ;
@@ -249,13 +256,43 @@ __global__ void __launch_bounds__(TY* TZ) k_sweep_pipe(Geo g, Op op, const doubl
     const long long row = (long long)y * g.sy + (long long)z * g.sz;
     const long long sy = kBackward ? -g.sy : g.sy, sz = kBackward ? -g.sz : g.sz;
     const bool hy = ym > 0, hz = zm > 0;       // upstream neighbours exist
-    int* dep_y = (ty == 0 && hy) ? &progress[(Y - 1) + nty * Z] : nullptr;
-    int* dep_z = (tz == 0 && hz) ? &progress[Y + nty * (Z - 1)] : nullptr;
+    const bool ext_y = valid && ty == 0 && hy; // my y-neighbour lives in another tile
+    const bool ext_z = valid && tz == 0 && hz;
+    int* dep_y = ext_y ? &progress[(Y - 1) + nty * Z] : nullptr;
+    int* dep_z = ext_z ? &progress[Y + nty * (Z - 1)] : nullptr;
     const bool boundary = (ty == TY - 1) || (tz == TZ - 1);
-    int seen_y = 0, seen_z = 0;
     double vprev = 0.0;
     bool fail = false;
     for (int s = 0; s < nsteps; ++s) {
+      const int j = s % kBatch;
+      if (j == 0 && (ext_y || ext_z)) {
+        // one wait and kBatch independent loads per batch
+        const int last = min(s + kBatch - 1, nsteps - 1);
+        if (ext_y && !fail) {
+          if (!wait_at_least(dep_y, min(last + TY, nsteps), ctrl + 1, status)) fail = true;
+          for (int u = 0; u < kBatch && !fail; ++u) {
+            const int k = s + u - ty - tz;
+            double v = 0.0;
+            if (k >= 0 && k < g.nx) {
+              const int x = kBackward ? g.nx - 1 - k : k;
+              v = __ldcg(vals + (row + x - sy));
+            }
+            yin[tz][u] = v;
+          }
+        }
+        if (ext_z && !fail) {
+          if (!wait_at_least(dep_z, min(last + TZ, nsteps), ctrl + 1, status)) fail = true;
+          for (int u = 0; u < kBatch && !fail; ++u) {
+            const int k = s + u - ty - tz;
+            double v = 0.0;
+            if (k >= 0 && k < g.nx) {
+              const int x = kBackward ? g.nx - 1 - k : k;
+              v = __ldcg(vals + (row + x - sz));
+            }
+            zin[ty][u] = v;
+          }
+        }
+      }
       const int k = s - ty - tz;               // cell of my row at this step
       double v = 0.0;
       if (valid && k >= 0 && k < g.nx && !fail) {
@@ -266,37 +303,13 @@ __global__ void __launch_bounds__(TY* TZ) k_sweep_pipe(Geo g, Op op, const doubl
           if (kk < g.nx) op.prefetch(row + (kBackward ? g.nx - 1 - kk : kk));
         }
         double vy = 0.0, vz = 0.0;
-        if (hy) {
-          if (ty > 0) {
-            vy = buf[(s - 1) & 1][tz][ty - 1];
-          } else {
-            const int need = min(s + TY, nsteps);
-            if (seen_y < need) {
-              if (wait_at_least(dep_y, need, ctrl + 1, status)) seen_y = need;
-              else fail = true;
-            }
-            if (!fail) vy = __ldcg(vals + (i - sy));
-          }
-        }
-        if (hz && !fail) {
-          if (tz > 0) {
-            vz = buf[(s - 1) & 1][tz - 1][ty];
-          } else {
-            const int need = min(s + TZ, nsteps);
-            if (seen_z < need) {
-              if (wait_at_least(dep_z, need, ctrl + 1, status)) seen_z = need;
-              else fail = true;
-            }
-            if (!fail) vz = __ldcg(vals + (i - sz));
-          }
-        }
-        if (!fail) {
-          v = op(i, k > 0, vprev, hy, vy, hz, vz);
-          vprev = v;
-        }
+        if (hy) vy = (ty > 0) ? buf[(s - 1) & 1][tz][ty - 1] : yin[tz][j];
+        if (hz) vz = (tz > 0) ? buf[(s - 1) & 1][tz - 1][ty] : zin[ty][j];
+        v = op(i, k > 0, vprev, hy, vy, hz, vz);
+        vprev = v;
       }
       buf[s & 1][tz][ty] = v;
-      const bool publish = ((s + 1) % kPublish == 0) || (s + 1 == nsteps);
+      const bool publish = (j == kBatch - 1) || (s + 1 == nsteps);
       if (publish && boundary) __threadfence();
       if (__syncthreads_or(fail)) {
         if (threadIdx.x == 0) {
@@ -306,7 +319,6 @@ __global__ void __launch_bounds__(TY* TZ) k_sweep_pipe(Geo g, Op op, const doubl
         return;
       }
       if (publish && threadIdx.x == 0) {
-        __threadfence();
         cuda::atomic_ref<int, cuda::thread_scope_device> pr(progress[Y + nty * Z]);
         pr.store(s + 1, cuda::memory_order_release);
       }
