@@ -133,6 +133,22 @@ def measured_peaks():
 
 # ------------------------------------------------------------ cams arm --
 
+def aggregate_replicas(t_ms, units, world, device=None):
+    """Replicas only: every rank solves its own field with no data exchange.
+    The job's time is the slowest rank's and its work is the sum over ranks
+    (the one collective here is for the measurement, not the data path)."""
+    if world <= 1:
+        return float(t_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+
 def _handles(cams, w, inp, memspace, dev_arrays=None):
     grid = cams.cams_grid(w.nx, w.ny, w.nz, inp["dx"], inp["dy"], inp["dz"])
     fluid = cams.cams_fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi)
@@ -194,14 +210,9 @@ def run_cams(args, w, rank, world, local_rank):
     launches = cams.launches(h) - l0
     prof = cams.profile_table(h)
     cams.cams_profile(h, False)
-    t_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
     newton = sum(s[0] for s in stats)
     its = sum(s[1] for s in stats)
-    units = N * its * world                   # replicas: every rank solves its own field
+    t_ms, units = aggregate_replicas(ev0.elapsed_time(ev1), N * its, world, dev)
     value = units / (t_ms / 1e3)
 
     # dominant kernel class by time, with its live per-launch duration

@@ -19,8 +19,10 @@
 //    and are exchanged in shared memory.  Row blocks that border other CTAs
 //    read those CTAs' boundary rows from global memory (L2, bypassing L1)
 //    after an acquire-poll of the producer's progress counter, which the
-//    producer publishes with release semantics every kBatch steps; a row
-//    that borders another tile fetches kBatch boundary values per poll.  Tiles
+//    producer publishes with release semantics every kBatch steps; every
+//    row loads the operands of its next kBatch cells with independent loads
+//    at the start of a batch, and a row that borders another tile fetches
+//    kBatch boundary values per poll.  Tiles
 //    are claimed through an atomic ticket in anti-diagonal order, so a CTA
 //    only ever waits on tiles already claimed by running CTAs: no
 //    co-residency assumption, no deadlock.  Every wait has an iteration
@@ -99,46 +101,43 @@ __global__ void k_resid_scaled(Geo g, const double* __restrict__ Ad, const doubl
 
 // ------------------------------------------------- per-cell operators ---
 // Each sweep is "value_i = op(i, values of the three upstream neighbours)".
+// load() fetches the operands of one cell (issued a batch ahead, so the
+// loads overlap); apply() combines them with the upstream values.
 
 struct FwdSolve {   // w_i = rd_i - Lz w_{z-1} - Ly w_{y-1} - Lx w_{x-1}
   const double *rd, *Lx, *Ly, *Lz;
   double* w;
-  __device__ __forceinline__ double operator()(long long i, bool hx, double vx, bool hy, double vy,
-                                               bool hz, double vz) const {
-    double v = rd[i];
-    if (hz) v = fma(-Lz[i], vz, v);
-    if (hy) v = fma(-Ly[i], vy, v);
-    if (hx) v = fma(-Lx[i], vx, v);
+  struct In { double rd, lx, ly, lz; };
+  __device__ __forceinline__ In load(long long i) const {
+    return In{__ldg(rd + i), __ldg(Lx + i), __ldg(Ly + i), __ldg(Lz + i)};
+  }
+  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
+                                          double vy, bool hz, double vz) const {
+    double v = a.rd;
+    if (hz) v = fma(-a.lz, vz, v);
+    if (hy) v = fma(-a.ly, vy, v);
+    if (hx) v = fma(-a.lx, vx, v);
     w[i] = v;
     return v;
-  }
-  __device__ __forceinline__ void prefetch(long long i) const {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(rd + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Lx + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Ly + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Lz + i));
   }
 };
 
 struct BwdSolve {   // z_i = w_i - Uz z_{z+1} - Uy z_{y+1} - Ux z_{x+1};  p_i += z_i
   const double *Ux, *Uy, *Uz;
   double *w, *p;
-  __device__ __forceinline__ double operator()(long long i, bool hx, double vx, bool hy, double vy,
-                                               bool hz, double vz) const {
-    double v = w[i];
-    if (hz) v = fma(-Uz[i], vz, v);
-    if (hy) v = fma(-Uy[i], vy, v);
-    if (hx) v = fma(-Ux[i], vx, v);
-    w[i] = v;
-    p[i] += v;
-    return v;
+  struct In { double w, ux, uy, uz, p; };
+  __device__ __forceinline__ In load(long long i) const {
+    return In{w[i], __ldg(Ux + i), __ldg(Uy + i), __ldg(Uz + i), p[i]};
   }
-  __device__ __forceinline__ void prefetch(long long i) const {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(w + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Ux + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Uy + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Uz + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + i));
+  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
+                                          double vy, bool hz, double vz) const {
+    double v = a.w;
+    if (hz) v = fma(-a.uz, vz, v);
+    if (hy) v = fma(-a.uy, vy, v);
+    if (hx) v = fma(-a.ux, vx, v);
+    w[i] = v;
+    p[i] = a.p + v;
+    return v;
   }
 };
 
@@ -146,12 +145,16 @@ struct Factor {     // d_i = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1
   const double *Ad, *Ax, *Ay, *Az;
   double* dinv;
   int* status;
-  __device__ __forceinline__ double operator()(long long i, bool hx, double vx, bool hy, double vy,
-                                               bool hz, double vz) const {
-    double d = Ad[i];
-    if (hx) d -= Ax[i] * Ax[i] * vx;
-    if (hy) d -= Ay[i] * Ay[i] * vy;
-    if (hz) d -= Az[i] * Az[i] * vz;
+  struct In { double d, ax, ay, az; };
+  __device__ __forceinline__ In load(long long i) const {
+    return In{__ldg(Ad + i), __ldg(Ax + i), __ldg(Ay + i), __ldg(Az + i)};
+  }
+  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
+                                          double vy, bool hz, double vz) const {
+    double d = a.d;
+    if (hx) d -= a.ax * a.ax * vx;
+    if (hy) d -= a.ay * a.ay * vy;
+    if (hz) d -= a.az * a.az * vz;
     if (!(d != 0.0) || !isfinite(d)) {
       atomicOr(status, kStatSingular);
       d = 1.0;
@@ -159,12 +162,6 @@ struct Factor {     // d_i = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1
     const double v = 1.0 / d;
     dinv[i] = v;
     return v;
-  }
-  __device__ __forceinline__ void prefetch(long long i) const {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Ad + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Ax + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Ay + i));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(Az + i));
   }
 };
 
@@ -182,12 +179,15 @@ __global__ void k_sweep_level(Geo g, int L, Op op, const double* vals) {
   const int yy = kBackward ? g.ny - 1 - y : y;
   const int zz = kBackward ? g.nz - 1 - z : z;
   const long long i = x + g.sy * yy + g.sz * zz;
+  const typename Op::In in = op.load(i);
   if (!kBackward) {
     const bool hx = x > 0, hy = yy > 0, hz = zz > 0;
-    op(i, hx, hx ? vals[i - 1] : 0.0, hy, hy ? vals[i - g.sy] : 0.0, hz, hz ? vals[i - g.sz] : 0.0);
+    op.apply(in, i, hx, hx ? vals[i - 1] : 0.0, hy, hy ? vals[i - g.sy] : 0.0, hz,
+             hz ? vals[i - g.sz] : 0.0);
   } else {
     const bool hx = x < g.nx - 1, hy = yy < g.ny - 1, hz = zz < g.nz - 1;
-    op(i, hx, hx ? vals[i + 1] : 0.0, hy, hy ? vals[i + g.sy] : 0.0, hz, hz ? vals[i + g.sz] : 0.0);
+    op.apply(in, i, hx, hx ? vals[i + 1] : 0.0, hy, hy ? vals[i + g.sy] : 0.0, hz,
+             hz ? vals[i + g.sz] : 0.0);
   }
 }
 
@@ -225,13 +225,15 @@ __device__ __forceinline__ bool wait_at_least(int* ctr, int need, int* abort_fla
 // ctrl: [0] ticket, [1] abort flag, [2 + tile] progress (steps completed).
 // The backward sweep runs the same schedule on the mirrored grid
 // (x -> nx-1-x, y -> ny-1-y, z -> nz-1-z).  Steps are grouped in batches of
-// kBatch: a row that borders an upstream tile waits once per batch for the
-// producer to be a whole batch ahead and then loads that batch's kBatch
-// boundary values with independent L2 loads, so one L2 round trip is paid
-// per batch instead of per step; producers publish at the end of each batch.
+// kBatch.  At the start of a batch every row loads the operands of its
+// kBatch cells of that batch (independent loads: one memory round trip per
+// batch), and a row that borders an upstream tile waits once for the
+// producer to be a whole batch ahead and then fetches that batch's boundary
+// values with independent L2 loads; producers publish at the end of each
+// batch.
 template <int TY, int TZ, class Op, bool kBackward>
 __global__ void __launch_bounds__(TY* TZ, 1) k_sweep_pipe(Geo g, Op op, const double* vals, int* ctrl,
-                                                       int* status) {
+                                                          int* status) {
   __shared__ double buf[2][TZ][TY];
   __shared__ double yin[TZ][kBatch];   // boundary values from the tile below in y (ty == 0 rows)
   __shared__ double zin[TY][kBatch];   // boundary values from the tile below in z (tz == 0 rows)
@@ -263,64 +265,64 @@ __global__ void __launch_bounds__(TY* TZ, 1) k_sweep_pipe(Geo g, Op op, const do
     const bool boundary = (ty == TY - 1) || (tz == TZ - 1);
     double vprev = 0.0;
     bool fail = false;
-    for (int s = 0; s < nsteps; ++s) {
-      const int j = s % kBatch;
-      if (j == 0 && (ext_y || ext_z)) {
-        // one wait and kBatch independent loads per batch
-        const int last = min(s + kBatch - 1, nsteps - 1);
-        if (ext_y && !fail) {
-          if (!wait_at_least(dep_y, min(last + TY, nsteps), ctrl + 1, status)) fail = true;
-          for (int u = 0; u < kBatch && !fail; ++u) {
-            const int k = s + u - ty - tz;
-            double v = 0.0;
-            if (k >= 0 && k < g.nx) {
-              const int x = kBackward ? g.nx - 1 - k : k;
-              v = __ldcg(vals + (row + x - sy));
-            }
-            yin[tz][u] = v;
+    for (int s0 = 0; s0 < nsteps; s0 += kBatch) {
+      // operands of my cells in this batch
+      typename Op::In in[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int k = s0 + u - ty - tz;
+        if (valid && k >= 0 && k < g.nx) in[u] = op.load(row + (kBackward ? g.nx - 1 - k : k));
+      }
+      // boundary values from upstream tiles
+      const int last = min(s0 + kBatch - 1, nsteps - 1);
+      if (ext_y && !fail) {
+        if (!wait_at_least(dep_y, min(last + TY, nsteps), ctrl + 1, status)) fail = true;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int k = s0 + u - ty - tz;
+          double v = 0.0;
+          if (!fail && k >= 0 && k < g.nx) v = __ldcg(vals + (row + (kBackward ? g.nx - 1 - k : k) - sy));
+          yin[tz][u] = v;
+        }
+      }
+      if (ext_z && !fail) {
+        if (!wait_at_least(dep_z, min(last + TZ, nsteps), ctrl + 1, status)) fail = true;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const int k = s0 + u - ty - tz;
+          double v = 0.0;
+          if (!fail && k >= 0 && k < g.nx) v = __ldcg(vals + (row + (kBackward ? g.nx - 1 - k : k) - sz));
+          zin[ty][u] = v;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int s = s0 + u;
+        if (s >= nsteps) break;                // uniform over the CTA
+        const int k = s - ty - tz;             // cell of my row at this step
+        double v = 0.0;
+        if (valid && k >= 0 && k < g.nx && !fail) {
+          const int x = kBackward ? g.nx - 1 - k : k;
+          double vy = 0.0, vz = 0.0;
+          if (hy) vy = (ty > 0) ? buf[(s - 1) & 1][tz][ty - 1] : yin[tz][u];
+          if (hz) vz = (tz > 0) ? buf[(s - 1) & 1][tz - 1][ty] : zin[ty][u];
+          v = op.apply(in[u], row + x, k > 0, vprev, hy, vy, hz, vz);
+          vprev = v;
+        }
+        buf[s & 1][tz][ty] = v;
+        const bool publish = (u == kBatch - 1) || (s + 1 == nsteps);
+        if (publish && boundary) __threadfence();
+        if (__syncthreads_or(fail)) {
+          if (threadIdx.x == 0) {
+            cuda::atomic_ref<int, cuda::thread_scope_device> ab(ctrl[1]);
+            ab.store(1, cuda::memory_order_relaxed);
           }
+          return;
         }
-        if (ext_z && !fail) {
-          if (!wait_at_least(dep_z, min(last + TZ, nsteps), ctrl + 1, status)) fail = true;
-          for (int u = 0; u < kBatch && !fail; ++u) {
-            const int k = s + u - ty - tz;
-            double v = 0.0;
-            if (k >= 0 && k < g.nx) {
-              const int x = kBackward ? g.nx - 1 - k : k;
-              v = __ldcg(vals + (row + x - sz));
-            }
-            zin[ty][u] = v;
-          }
+        if (publish && threadIdx.x == 0) {
+          cuda::atomic_ref<int, cuda::thread_scope_device> pr(progress[Y + nty * Z]);
+          pr.store(s + 1, cuda::memory_order_release);
         }
-      }
-      const int k = s - ty - tz;               // cell of my row at this step
-      double v = 0.0;
-      if (valid && k >= 0 && k < g.nx && !fail) {
-        const int x = kBackward ? g.nx - 1 - k : k;
-        const long long i = row + x;
-        if ((k & 7) == 0) {
-          const int kk = k + 16;
-          if (kk < g.nx) op.prefetch(row + (kBackward ? g.nx - 1 - kk : kk));
-        }
-        double vy = 0.0, vz = 0.0;
-        if (hy) vy = (ty > 0) ? buf[(s - 1) & 1][tz][ty - 1] : yin[tz][j];
-        if (hz) vz = (tz > 0) ? buf[(s - 1) & 1][tz - 1][ty] : zin[ty][j];
-        v = op(i, k > 0, vprev, hy, vy, hz, vz);
-        vprev = v;
-      }
-      buf[s & 1][tz][ty] = v;
-      const bool publish = (j == kBatch - 1) || (s + 1 == nsteps);
-      if (publish && boundary) __threadfence();
-      if (__syncthreads_or(fail)) {
-        if (threadIdx.x == 0) {
-          cuda::atomic_ref<int, cuda::thread_scope_device> ab(ctrl[1]);
-          ab.store(1, cuda::memory_order_relaxed);
-        }
-        return;
-      }
-      if (publish && threadIdx.x == 0) {
-        cuda::atomic_ref<int, cuda::thread_scope_device> pr(progress[Y + nty * Z]);
-        pr.store(s + 1, cuda::memory_order_release);
       }
     }
   }
