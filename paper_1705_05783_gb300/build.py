@@ -22,6 +22,8 @@ LIB = os.path.join(LIBDIR, "libcams.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
+# compile-time tunables (e.g. CAMS_ILU_TY=16) may be given as -D flags in CAMS_NVCC_DEFINES
+EXTRA_DEFINES = [f"-D{d}" for d in os.environ.get("CAMS_NVCC_DEFINES", "").split() if d]
 
 
 def nvcc() -> str:
@@ -44,7 +46,7 @@ def build(verbose: bool = False, extra=()) -> str:
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA_DEFINES, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -263,9 +263,17 @@ int alloc_all(cams_handle* h) {
   AL(b.perm, h->c.Nc);
   AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc);
   AL(b.dinv, N);
-  AL(b.Lx, N); AL(b.Ly, N); AL(b.Lz, N); AL(b.Ux, N); AL(b.Uy, N); AL(b.Uz, N);
+  {
+    const long long S = ilu_skew_len(h->g);   // >= N
+    AL(b.Lx, S); AL(b.Ly, S); AL(b.Lz, S); AL(b.Ux, S); AL(b.Uy, S); AL(b.Uz, S);
+    AL(b.rds, S); AL(b.w, S); AL(b.z, S);
+    // slots that hold no cell must read as zero (the sweeps run branch-free over them)
+    for (double* v : {b.Lx, b.Ly, b.Lz, b.Ux, b.Uy, b.Uz, b.rds, b.w, b.z})
+      if (cudaMemset(v, 0, sizeof(double) * (size_t)S) != cudaSuccess)
+        return fail(h, CAMS_ECUDA, "cudaMemset failed");
+  }
   AL(b.ctrl, ilu_ctrl_ints(h->g));
-  AL(b.r, N); AL(b.w, N);
+  AL(b.r, N);
   AL(b.red, kRedBlocks);
   AL(b.scal, 8);
   AL(b.status, 1);
@@ -278,7 +286,7 @@ void free_all(cams_handle* h) {
   void* ptrs[] = {b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe, b.p, b.pn, b.rho, b.rhon, b.Ad, b.Ax, b.Ay,
                   b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
-                  b.pc, b.dinv, b.r, b.w, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
+                  b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr};
   for (void* p : ptrs)
     if (p) cudaFree(p);

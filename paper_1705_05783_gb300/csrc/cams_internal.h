@@ -84,10 +84,12 @@ struct Buffers {
   int* perm = nullptr;                                    // coarse natural -> band order
   double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
   double* dinv = nullptr;                                 // 1 / ILU(0) pivots
+  // ILU(0) sweep vectors, skewed tile-major (ilu_skew_len elements each)
   double *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;     // a_{i,i-e_d} / d_i
   double *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;     // a_{i,i+e_d} / d_i
-  int* ctrl = nullptr;                                    // wavefront tickets / progress
-  double *r = nullptr, *w = nullptr;                      // work vectors
+  double *rds = nullptr, *w = nullptr, *z = nullptr;      // D^{-1} r, forward / backward sweeps
+  int* ctrl = nullptr;                                    // wavefront tickets, abort flag
+  double* r = nullptr;                                    // residual (natural order)
   double* red = nullptr;                                  // reduction partials
   double* scal = nullptr;                                 // reduced scalars (device)
   int* status = nullptr;                                  // device status word
@@ -147,6 +149,9 @@ cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s);
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
                              cudaStream_t s);
 int ilu_ctrl_ints(const Geo& g);
+// Rows per wavefront tile (y, z) and the length of a skewed sweep vector.
+constexpr int kIluTY = 8, kIluTZ = 4, kIluR = kIluTY * kIluTZ;   // one warp per tile
+long long ilu_skew_len(const Geo& g);
 int ilu_pipe_grid(const Geo& g, int num_sms);
 cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s);
 

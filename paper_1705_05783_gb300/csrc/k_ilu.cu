@@ -10,85 +10,148 @@
 // with the couplings pre-scaled by the row pivot once per factorisation, so
 // every cell of a sweep is a chain of at most three FMAs.
 //
+// Layout.  The sweep vectors (rd, the scaled couplings, w, z) are stored
+// "skewed tile-major": the (y, z) cross-section is cut into tiles of
+// kIluTY x kIluTZ = 32 x-rows, one warp each, and cell (x, y, z) of tile T,
+// row (ty, tz) sits at record T * ns + x + ty + tz, slot ty + kIluTY * tz
+// (ns >= nx + kIluTY + kIluTZ - 2 records per tile, 32 doubles per record,
+// plus kPad spare records at both ends).  A tile advances one "step" s at a
+// time and row (ty, tz) works on x = s - ty - tz, so the 32 cells of one
+// step are one contiguous 256-byte record.  Slots that hold no cell (the
+// pipeline's fill and drain, rows beyond the grid) are zero in rd and in
+// the couplings, so every step runs the same branch-free arithmetic; the
+// values computed there are never read by a cell.  Pivots (dinv) stay in
+// natural order.
+//
 // Two schedules of the same arithmetic (bitwise identical results):
 //  * level-scheduled: one launch per hyperplane x+y+z = L (reference);
-//  * pipelined: one persistent launch per sweep.  A thread owns an x-row
-//    (y, z); a CTA owns a TY x TZ block of rows and steps through x in
-//    lockstep, row (ty, tz) lagging one cell per row hop (ty + tz), so the
-//    values it needs from rows y-1 and z-1 were produced one step earlier
-//    and are exchanged in shared memory.  Row blocks that border other CTAs
-//    read those CTAs' boundary rows from global memory (L2, bypassing L1)
-//    after an acquire-poll of the producer's progress counter, which the
-//    producer publishes with release semantics every kBatch steps; every
-//    row loads the operands of its next kBatch cells with independent loads
-//    at the start of a batch, and a row that borders another tile fetches
-//    kBatch boundary values per poll.  Tiles
-//    are claimed through an atomic ticket in anti-diagonal order, so a CTA
-//    only ever waits on tiles already claimed by running CTAs: no
-//    co-residency assumption, no deadlock.  Every wait has an iteration
-//    limit; on expiry the kernel sets an abort flag and the status word and
-//    all CTAs leave.
-#include <cuda/atomic>
-
+//  * pipelined: one persistent launch per sweep.  Each warp takes a whole
+//    tile and steps through it; the values a row needs from rows y-1 and
+//    z-1 of its own tile were produced by the neighbouring lanes one step
+//    earlier and arrive by warp shuffle.  Operands are staged into a
+//    per-lane shared-memory ring by cp.async two groups ahead.  Values from
+//    another tile are read from the sweep's output vector itself, which is
+//    pre-filled with a signalling-NaN sentinel that no arithmetic produces:
+//    a value is ready once it differs from the sentinel, so no flags or
+//    fences are needed (8-byte values are written and read with single-copy
+//    atomic relaxed accesses at device scope); they are fetched one group
+//    ahead and re-polled only when still unset.  Tiles are claimed through
+//    an atomic ticket in anti-diagonal order, so a warp only ever waits on
+//    tiles already claimed by running warps: no co-residency assumption, no
+//    deadlock.  Every wait has an iteration limit; on expiry the kernel sets
+//    an abort flag and the status word and all warps leave.  One CTA of
+//    four warps per SM keeps one sweeping warp per FP64 pipe.
+//  The backward sweep runs the same schedule on the mirrored grid; with the
+//  tiling fixed by the forward direction, its steps read the same records in
+//  reverse order.
 #include "cams_internal.h"
 
 namespace cams {
 
 namespace {
 
-constexpr int kBatch = 8;                    // steps per batch of cross-tile loads / publications
-constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ seconds)
+constexpr int kTY = kIluTY, kTZ = kIluTZ, kR = kIluR;
+static_assert(kR == 32, "a tile is one warp");
+constexpr int kWarps = 4;                    // tiles in flight per CTA (one per FP64 pipe)
+constexpr int kU = 4;                        // steps per group (straight-line code)
+constexpr int kG = 3;                        // operand groups in flight (staged 2 groups ahead)
+constexpr int kPad = kG * kU;                // spare records at both ends of a vector
+constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ a second)
+constexpr int kFastPolls = 64;               // polls before a wait starts to sleep
+
+// "Not computed yet": a signalling-NaN bit pattern.  IEEE arithmetic never
+// produces a signalling NaN, so no computed value carries this pattern.
+constexpr unsigned long long kNotReady = 0x7FF4DEADBEEF0001ull;
+
+struct Skew {
+  int nty, ntz, ns;   // tiles in y and z, records per tile (a multiple of kU)
+};
+
+inline Skew make_skew(const Geo& g) {
+  const int ns = g.nx + kTY + kTZ - 2;
+  return Skew{(g.ny + kTY - 1) / kTY, (g.nz + kTZ - 1) / kTZ, (ns + kU - 1) / kU * kU};
+}
+
+__device__ __forceinline__ long long skew_index(const Skew& k, int x, int y, int z) {
+  const int Y = y / kTY, ty = y - Y * kTY, Z = z / kTZ, tz = z - Z * kTZ;
+  return ((long long)(Y + k.nty * Z) * k.ns + x + ty + tz + kPad) * kR + ty + kTY * tz;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// ld_relaxed when `pred` holds, else 0 (a predicated load: no branch).
+__device__ __forceinline__ unsigned long long ld_relaxed_if(bool pred, const double* p) {
+  unsigned long long v = 0ull;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.relaxed.gpu.global.b64 %0, [%1];\n\t}"
+      : "+l"(v)
+      : "l"(p), "r"((unsigned)pred));
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void publish(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+
+__device__ __forceinline__ void cp_async8(double* smem_dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ----------------------------------------------------------- factor ---
 
-__global__ void k_ilu_factor_level(Geo g, int L, const double* __restrict__ Ad,
-                                   const double* __restrict__ Ax, const double* __restrict__ Ay,
-                                   const double* __restrict__ Az, double* dinv, int* status) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)g.ny * g.nz) return;
-  const int y = (int)(t % g.ny), z = (int)(t / g.ny);
-  const int x = L - y - z;
-  if (x < 0 || x >= g.nx) return;
-  const long long i = x + g.sy * y + g.sz * z;
-  double d = Ad[i];
-  if (x > 0) d -= Ax[i] * Ax[i] * dinv[i - 1];
-  if (y > 0) d -= Ay[i] * Ay[i] * dinv[i - g.sy];
-  if (z > 0) d -= Az[i] * Az[i] * dinv[i - g.sz];
-  if (!(d != 0.0) || !isfinite(d)) {
-    atomicOr(status, kStatSingular);
-    d = 1.0;
-  }
-  dinv[i] = 1.0 / d;
-}
-
-// Row-pivot-scaled couplings: L_d[i] = a_{i,i-e_d} / d_i, U_d[i] = a_{i,i+e_d} / d_i.
-__global__ void k_ilu_scale(Geo g, const double* __restrict__ Ax, const double* __restrict__ Ay,
-                            const double* __restrict__ Az, const double* __restrict__ dinv,
-                            double* Lx, double* Ly, double* Lz, double* Ux, double* Uy, double* Uz) {
+// Row-pivot-scaled couplings, stored skewed:
+// L_d = a_{i,i-e_d} / d_i, U_d = a_{i,i+e_d} / d_i.
+__global__ void k_ilu_scale(Geo g, Skew sk, const double* __restrict__ Ax,
+                            const double* __restrict__ Ay, const double* __restrict__ Az,
+                            const double* __restrict__ dinv, double* Lx, double* Ly, double* Lz,
+                            double* Ux, double* Uy, double* Uz) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
+  const long long j = skew_index(sk, x, y, z);
   const double di = dinv[i];
-  Lx[i] = Ax[i] * di;
-  Ly[i] = Ay[i] * di;
-  Lz[i] = Az[i] * di;
-  Ux[i] = x < g.nx - 1 ? Ax[i + 1] * di : 0.0;
-  Uy[i] = y < g.ny - 1 ? Ay[i + g.sy] * di : 0.0;
-  Uz[i] = z < g.nz - 1 ? Az[i + g.sz] * di : 0.0;
+  Lx[j] = Ax[i] * di;
+  Ly[j] = Ay[i] * di;
+  Lz[j] = Az[i] * di;
+  Ux[j] = x < g.nx - 1 ? Ax[i + 1] * di : 0.0;
+  Uy[j] = y < g.ny - 1 ? Ay[i + g.sy] * di : 0.0;
+  Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : 0.0;
 }
 
-// rd = D^{-1} (f - A p)
-__global__ void k_resid_scaled(Geo g, const double* __restrict__ Ad, const double* __restrict__ Ax,
-                               const double* __restrict__ Ay, const double* __restrict__ Az,
-                               const double* __restrict__ f, const double* __restrict__ p,
-                               const double* __restrict__ dinv, double* rd) {
+// rd = D^{-1} (f - A p), stored skewed; the outputs w, z of the two sweeps
+// that follow start as "not computed".
+__global__ void k_resid_scaled(Geo g, Skew sk, const double* __restrict__ Ad,
+                               const double* __restrict__ Ax, const double* __restrict__ Ay,
+                               const double* __restrict__ Az, const double* __restrict__ f,
+                               const double* __restrict__ p, const double* __restrict__ dinv,
+                               double* rd, double* w, double* zs) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
+  const long long j = skew_index(sk, x, y, z);
+  const double nr = __longlong_as_double((long long)kNotReady);
+  w[j] = nr;
+  zs[j] = nr;
   double a = f[i] - Ad[i] * p[i];
   if (x > 0) a -= Ax[i] * p[i - 1];
   if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
@@ -96,71 +159,73 @@ __global__ void k_resid_scaled(Geo g, const double* __restrict__ Ad, const doubl
   if (y < g.ny - 1) a -= Ay[i + g.sy] * p[i + g.sy];
   if (z > 0) a -= Az[i] * p[i - g.sz];
   if (z < g.nz - 1) a -= Az[i + g.sz] * p[i + g.sz];
-  rd[i] = a * dinv[i];
+  rd[j] = a * dinv[i];
 }
 
 // ------------------------------------------------- per-cell operators ---
-// Each sweep is "value_i = op(i, values of the three upstream neighbours)".
-// load() fetches the operands of one cell (issued a batch ahead, so the
-// loads overlap); apply() combines them with the upstream values.
+// Each sweep is "value = op(cell, operands, values of the three upstream
+// neighbours)", with 0 standing for a neighbour outside the grid (its
+// coupling is 0 as well).  src(a, i, j) is the address of operand a of the
+// cell with natural index i and skewed index j; apply() combines the
+// operands with the upstream values and publishes the result.  `cell` is
+// false on the pipeline's fill/drain slots and on rows beyond the grid:
+// there the result is discarded and nothing outside the slot is written.
 
-struct FwdSolve {   // w_i = rd_i - Lz w_{z-1} - Ly w_{y-1} - Lx w_{x-1}
+struct FwdSolve {   // w = rd - Lx w_{x-1} - Ly w_{y-1} - Lz w_{z-1}
+  static constexpr int kN = 4;
+  static constexpr bool kSkewIn = true, kSkewOut = true;
   const double *rd, *Lx, *Ly, *Lz;
   double* w;
-  struct In { double rd, lx, ly, lz; };
-  __device__ __forceinline__ In load(long long i) const {
-    return In{__ldg(rd + i), __ldg(Lx + i), __ldg(Ly + i), __ldg(Lz + i)};
+  __device__ __forceinline__ const double* src(int a, long long, long long j) const {
+    return (a == 0 ? rd : a == 1 ? Lx : a == 2 ? Ly : Lz) + j;
   }
-  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
-                                          double vy, bool hz, double vz) const {
-    double v = a.rd;
-    if (hz) v = fma(-a.lz, vz, v);
-    if (hy) v = fma(-a.ly, vy, v);
-    if (hx) v = fma(-a.lx, vx, v);
-    w[i] = v;
+  __device__ __forceinline__ double apply(const double* in, long long, long long j, bool,
+                                          double vx, double vy, double vz) const {
+    const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
+    publish(w + j, v);
     return v;
   }
 };
 
-struct BwdSolve {   // z_i = w_i - Uz z_{z+1} - Uy z_{y+1} - Ux z_{x+1};  p_i += z_i
+struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1};  p += z
+  static constexpr int kN = 5;
+  static constexpr bool kSkewIn = true, kSkewOut = true;
   const double *Ux, *Uy, *Uz;
-  double *w, *p;
-  struct In { double w, ux, uy, uz, p; };
-  __device__ __forceinline__ In load(long long i) const {
-    return In{w[i], __ldg(Ux + i), __ldg(Uy + i), __ldg(Uz + i), p[i]};
+  const double* w;
+  double *z, *p;
+  __device__ __forceinline__ const double* src(int a, long long i, long long j) const {
+    return a == 4 ? p + i : (a == 0 ? w : a == 1 ? Ux : a == 2 ? Uy : Uz) + j;
   }
-  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
-                                          double vy, bool hz, double vz) const {
-    double v = a.w;
-    if (hz) v = fma(-a.uz, vz, v);
-    if (hy) v = fma(-a.uy, vy, v);
-    if (hx) v = fma(-a.ux, vx, v);
-    w[i] = v;
-    p[i] = a.p + v;
+  __device__ __forceinline__ double apply(const double* in, long long i, long long j, bool cell,
+                                          double vx, double vy, double vz) const {
+    const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
+    publish(z + j, v);
+    if (cell) p[i] = in[4] + v;
     return v;
   }
 };
 
-struct Factor {     // d_i = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} - a_{i,z-1}^2 / d_{z-1}
+struct Factor {     // d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} - a_{i,z-1}^2 / d_{z-1}
+  static constexpr int kN = 4;
+  static constexpr bool kSkewIn = false, kSkewOut = false;
   const double *Ad, *Ax, *Ay, *Az;
   double* dinv;
   int* status;
-  struct In { double d, ax, ay, az; };
-  __device__ __forceinline__ In load(long long i) const {
-    return In{__ldg(Ad + i), __ldg(Ax + i), __ldg(Ay + i), __ldg(Az + i)};
+  __device__ __forceinline__ const double* src(int a, long long i, long long) const {
+    return (a == 0 ? Ad : a == 1 ? Ax : a == 2 ? Ay : Az) + i;
   }
-  __device__ __forceinline__ double apply(const In& a, long long i, bool hx, double vx, bool hy,
-                                          double vy, bool hz, double vz) const {
-    double d = a.d;
-    if (hx) d -= a.ax * a.ax * vx;
-    if (hy) d -= a.ay * a.ay * vy;
-    if (hz) d -= a.az * a.az * vz;
-    if (!(d != 0.0) || !isfinite(d)) {
+  __device__ __forceinline__ double apply(const double* in, long long i, long long, bool cell,
+                                          double vx, double vy, double vz) const {
+    double d = in[0];
+    d -= in[1] * in[1] * vx;
+    d -= in[2] * in[2] * vy;
+    d -= in[3] * in[3] * vz;
+    if (cell && (!(d != 0.0) || !isfinite(d))) {
       atomicOr(status, kStatSingular);
       d = 1.0;
     }
     const double v = 1.0 / d;
-    dinv[i] = v;
+    if (cell) publish(dinv + i, v);
     return v;
   }
 };
@@ -168,7 +233,7 @@ struct Factor {     // d_i = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1
 // ---------------------------------------------------- level schedule ---
 
 template <class Op, bool kBackward>
-__global__ void k_sweep_level(Geo g, int L, Op op, const double* vals) {
+__global__ void k_sweep_level(Geo g, Skew sk, int L, Op op, const double* vals) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)g.ny * g.nz) return;
   const int y = (int)(t % g.ny), z = (int)(t / g.ny);
@@ -179,16 +244,20 @@ __global__ void k_sweep_level(Geo g, int L, Op op, const double* vals) {
   const int yy = kBackward ? g.ny - 1 - y : y;
   const int zz = kBackward ? g.nz - 1 - z : z;
   const long long i = x + g.sy * yy + g.sz * zz;
-  const typename Op::In in = op.load(i);
-  if (!kBackward) {
-    const bool hx = x > 0, hy = yy > 0, hz = zz > 0;
-    op.apply(in, i, hx, hx ? vals[i - 1] : 0.0, hy, hy ? vals[i - g.sy] : 0.0, hz,
-             hz ? vals[i - g.sz] : 0.0);
-  } else {
-    const bool hx = x < g.nx - 1, hy = yy < g.ny - 1, hz = zz < g.nz - 1;
-    op.apply(in, i, hx, hx ? vals[i + 1] : 0.0, hy, hy ? vals[i + g.sy] : 0.0, hz,
-             hz ? vals[i + g.sz] : 0.0);
-  }
+  const long long j = skew_index(sk, x, yy, zz);
+  double in[Op::kN];
+#pragma unroll
+  for (int a = 0; a < Op::kN; ++a) in[a] = *op.src(a, i, j);
+  const int e = kBackward ? 1 : -1;
+  const bool hx = kBackward ? x < g.nx - 1 : x > 0;
+  const bool hy = kBackward ? yy < g.ny - 1 : yy > 0;
+  const bool hz = kBackward ? zz < g.nz - 1 : zz > 0;
+  auto at = [&](int dx, int dy, int dz) {
+    return Op::kSkewOut ? vals[skew_index(sk, x + dx, yy + dy, zz + dz)]
+                        : vals[i + dx + g.sy * dy + g.sz * dz];
+  };
+  op.apply(in, i, j, true, hx ? at(e, 0, 0) : 0.0, hy ? at(0, e, 0) : 0.0,
+           hz ? at(0, 0, e) : 0.0);
 }
 
 // ------------------------------------------------ pipelined schedule ---
@@ -208,189 +277,279 @@ __device__ __forceinline__ void tile_of_ticket(int t, int nty, int ntz, int& Y, 
   }
 }
 
-// Wait until *ctr >= need (acquire).  Returns false on abort or timeout.
+// ctrl: [0] ticket, [1] abort flag.  `out` is the vector the operator
+// publishes into (pre-filled with kNotReady on every cell).  Shared memory:
+// per warp, the operand ring [kG][kU][Op::kN][32].
+//
+// Steps run in groups of kU.  A group's prologue stages the operands of the
+// group two ahead (cp.async), fetches the cross-tile values of the next
+// group, and then waits, if need be, for its own cross-tile values; the kU
+// steps themselves are straight-line code (shuffles, three FMAs, stores).
+template <class Op, bool kBackward>
+__global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, Op op,
+                                                                const double* out, int* ctrl,
+                                                                int* status) {
+  constexpr unsigned kAll = 0xffffffffu;
+  constexpr int kN = Op::kN;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* ring = smem + warp * (kG * kU * kN * kR) + lane;
+  const int tym = lane % kTY, tzm = lane / kTY;   // row within the tile, sweep frame
+  const int ty = kBackward ? kTY - 1 - tym : tym, tz = kBackward ? kTZ - 1 - tzm : tzm;
+  const int slot = ty + kTY * tz;                 // my slot of a record
+  const int ntiles = sk.nty * sk.ntz;
+  int* abort_flag = ctrl + 1;
+  const long long rec = (long long)sk.ns * kR;    // one tile's records
+  const long long dj = kBackward ? -kR : kR;      // skewed index change per step
+  const long long di = kBackward ? -1 : 1;        // natural index change per step
+  // cross-tile neighbour of an edge row, relative to my own index
+  const long long offy_s = (kBackward ? 1 : -1) * (rec - (long long)(kTY - 1) * (kR + 1));
+  const long long offz_s =
+      (kBackward ? 1 : -1) * ((long long)sk.nty * rec - (long long)(kTZ - 1) * (kR + kTY));
+  const long long offy_n = kBackward ? g.sy : -g.sy, offz_n = kBackward ? g.sz : -g.sz;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&ctrl[0], 1);
+    t = __shfl_sync(kAll, t, 0);
+    if (t >= ntiles) return;
+    int Ym, Zm;
+    tile_of_ticket(t, sk.nty, sk.ntz, Ym, Zm);
+    const int Y = kBackward ? sk.nty - 1 - Ym : Ym, Z = kBackward ? sk.ntz - 1 - Zm : Zm;
+    const int y = Y * kTY + ty, z = Z * kTZ + tz;
+    const bool valid = y < g.ny && z < g.nz;
+    const bool hy = valid && (kBackward ? y < g.ny - 1 : y > 0);   // upstream rows exist
+    const bool hz = valid && (kBackward ? z < g.nz - 1 : z > 0);
+    const bool ext_y = hy && tym == 0;                              // ... in another tile
+    const bool ext_z = hz && tzm == 0;
+    // indices at sweep step 0.  x in the sweep frame is step - xoff; the
+    // backward sweep walks the tile's records from the last one down, and its
+    // first ns - (nx + kTY + kTZ - 2) steps are padding.
+    const int xoff = tym + tzm + (kBackward ? sk.ns - (g.nx + kTY + kTZ - 2) : 0);
+    const long long j0 =
+        ((long long)(Y + sk.nty * Z) * sk.ns + (kBackward ? sk.ns - 1 : 0) + kPad) * kR + slot;
+    const int yc = valid ? y : 0, zc = valid ? z : 0;               // rows beyond the grid read row 0
+    const long long row = (long long)yc * g.sy + (long long)zc * g.sz;
+    const long long i0 = row + (kBackward ? g.nx - 1 + xoff : -xoff);
+    const long long o0 = Op::kSkewOut ? j0 : i0;
+    const long long od = Op::kSkewOut ? dj : di;
+    const long long oy0 = o0 + (Op::kSkewOut ? offy_s : offy_n);
+    const long long oz0 = o0 + (Op::kSkewOut ? offz_s : offz_n);
+    // operands of steps gs .. gs+kU-1 into ring group q.  Skewed operands
+    // are always in range (spare records); natural ones are clamped to my
+    // row (read, then discarded).
+    auto stage = [&](int gs, int q) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        long long i = i0 + (gs + u) * di;
+        if (!Op::kSkewIn || kN > 4) {
+          i = i < row ? row : i;
+          i = i > row + g.nx - 1 ? row + g.nx - 1 : i;
+        }
+        const long long j = j0 + (gs + u) * dj;
+#pragma unroll
+        for (int a = 0; a < kN; ++a) cp_async8(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
+      }
+      cp_async_commit();
+    };
+    // cross-tile values of steps gs .. gs+kU-1 (0 where none is needed)
+    auto fetch = [&](int gs, unsigned long long* cy, unsigned long long* cz) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int xq = gs + u - xoff;
+        const bool in_row = xq >= 0 && xq < g.nx;
+        cy[u] = ld_relaxed_if(ext_y && in_row, out + oy0 + (gs + u) * od);
+        cz[u] = ld_relaxed_if(ext_z && in_row, out + oz0 + (gs + u) * od);
+      }
+    };
+    stage(0, 0);
+    stage(kU, 1);
+    unsigned long long cy[kU], cz[kU];
+    fetch(0, cy, cz);
+    double vprev = 0.0, from_y = 0.0, from_z = 0.0;
+    int q = 0;
+    for (int s0 = 0; s0 < sk.ns; s0 += kU) {
+      stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
+      unsigned long long ny_[kU], nz_[kU];
+      fetch(s0 + kU, ny_, nz_);
+      // wait for this group's cross-tile values: re-poll those still unset
+      bool pending = false;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) pending |= (cy[u] == kNotReady) | (cz[u] == kNotReady);
+      if (__any_sync(kAll, pending)) {
+        bool fail = false;
+        for (long long it = 0; pending && !fail; ++it) {
+          pending = false;
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (cy[u] == kNotReady) {
+              cy[u] = ld_relaxed(out + oy0 + (s0 + u) * od);
+              pending |= cy[u] == kNotReady;
+            }
+            if (cz[u] == kNotReady) {
+              cz[u] = ld_relaxed(out + oz0 + (s0 + u) * od);
+              pending |= cz[u] == kNotReady;
+            }
+          }
+          if (pending && it >= kFastPolls) {
+            if (it >= kSpinLimit) {
+              atomicOr(status, kStatTimeout);
+              atomicExch(abort_flag, 1);
+              fail = true;
+            } else if ((it & 15) == 0 && ld_relaxed_int(abort_flag)) {
+              fail = true;
+            } else {
+              __nanosleep(100);
+            }
+          }
+        }
+        if (__any_sync(kAll, fail)) {
+          cp_async_wait<0>();
+          return;
+        }
+      }
+      cp_async_wait<2>();
+      double in[kU][kN];
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+#pragma unroll
+        for (int a = 0; a < kN; ++a) in[u][a] = ring[((q * kU + u) * kN + a) * kR];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int s = s0 + u;
+        const int xs = s - xoff;
+        const bool cell = valid && xs >= 0 && xs < g.nx;
+        const double vy = hy ? (tym > 0 ? from_y : __longlong_as_double((long long)cy[u])) : 0.0;
+        const double vz = hz ? (tzm > 0 ? from_z : __longlong_as_double((long long)cz[u])) : 0.0;
+        const double vx = xs > 0 ? vprev : 0.0;
+        const double v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
+        // rows y-1 / z-1 of my tile computed my next neighbours just now
+        from_y = __shfl_up_sync(kAll, v, 1);
+        from_z = __shfl_up_sync(kAll, v, kTY);
+        vprev = v;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        cy[u] = ny_[u];
+        cz[u] = nz_[u];
+      }
+      q = q == kG - 1 ? 0 : q + 1;
+    }
+    cp_async_wait<0>();
+  }
+}
+
+__global__ void k_fill_not_ready(long long n, double* a) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  a[i] = __longlong_as_double((long long)kNotReady);
+}
+
+// Bounded wait used by the self-test: polls a counter that nothing sets.
 __device__ __forceinline__ bool wait_at_least(int* ctr, int need, int* abort_flag, int* status) {
-  cuda::atomic_ref<int, cuda::thread_scope_device> a(*ctr);
-  cuda::atomic_ref<int, cuda::thread_scope_device> ab(*abort_flag);
   for (long long it = 0; it < kSpinLimit; ++it) {
-    if (a.load(cuda::memory_order_acquire) >= need) return true;
-    if (ab.load(cuda::memory_order_relaxed)) return false;
+    if (ld_relaxed_int(ctr) >= need) return true;
+    if (ld_relaxed_int(abort_flag)) return false;
     __nanosleep(64);
   }
   atomicOr(status, kStatTimeout);
-  ab.store(1, cuda::memory_order_relaxed);
+  atomicExch(abort_flag, 1);
   return false;
 }
 
-// ctrl: [0] ticket, [1] abort flag, [2 + tile] progress (steps completed).
-// The backward sweep runs the same schedule on the mirrored grid
-// (x -> nx-1-x, y -> ny-1-y, z -> nz-1-z).  Steps are grouped in batches of
-// kBatch.  At the start of a batch every row loads the operands of its
-// kBatch cells of that batch (independent loads: one memory round trip per
-// batch), and a row that borders an upstream tile waits once for the
-// producer to be a whole batch ahead and then fetches that batch's boundary
-// values with independent L2 loads; producers publish at the end of each
-// batch.
-template <int TY, int TZ, class Op, bool kBackward>
-__global__ void __launch_bounds__(TY* TZ, 1) k_sweep_pipe(Geo g, Op op, const double* vals, int* ctrl,
-                                                          int* status) {
-  __shared__ double buf[2][TZ][TY];
-  __shared__ double yin[TZ][kBatch];   // boundary values from the tile below in y (ty == 0 rows)
-  __shared__ double zin[TY][kBatch];   // boundary values from the tile below in z (tz == 0 rows)
-  __shared__ int s_tile;
-  const int ty = threadIdx.x % TY, tz = threadIdx.x / TY;
-  const int nty = (g.ny + TY - 1) / TY, ntz = (g.nz + TZ - 1) / TZ;
-  const int ntiles = nty * ntz;
-  const int nsteps = g.nx + TY + TZ - 2;
-  int* progress = ctrl + 2;
-  for (;;) {
-    __syncthreads();                           // s_tile of the previous tile is consumed
-    if (threadIdx.x == 0) s_tile = atomicAdd(&ctrl[0], 1);
-    __syncthreads();
-    const int t = s_tile;
-    if (t >= ntiles) return;
-    int Y, Z;                                  // tile in mirrored coordinates
-    tile_of_ticket(t, nty, ntz, Y, Z);
-    const int ym = Y * TY + ty, zm = Z * TZ + tz;   // my row, mirrored coordinates
-    const bool valid = ym < g.ny && zm < g.nz;
-    const int y = kBackward ? g.ny - 1 - ym : ym;
-    const int z = kBackward ? g.nz - 1 - zm : zm;
-    const long long row = (long long)y * g.sy + (long long)z * g.sz;
-    const long long sy = kBackward ? -g.sy : g.sy, sz = kBackward ? -g.sz : g.sz;
-    const bool hy = ym > 0, hz = zm > 0;       // upstream neighbours exist
-    const bool ext_y = valid && ty == 0 && hy; // my y-neighbour lives in another tile
-    const bool ext_z = valid && tz == 0 && hz;
-    int* dep_y = ext_y ? &progress[(Y - 1) + nty * Z] : nullptr;
-    int* dep_z = ext_z ? &progress[Y + nty * (Z - 1)] : nullptr;
-    const bool boundary = (ty == TY - 1) || (tz == TZ - 1);
-    double vprev = 0.0;
-    bool fail = false;
-    for (int s0 = 0; s0 < nsteps; s0 += kBatch) {
-      // operands of my cells in this batch
-      typename Op::In in[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int k = s0 + u - ty - tz;
-        if (valid && k >= 0 && k < g.nx) in[u] = op.load(row + (kBackward ? g.nx - 1 - k : k));
-      }
-      // boundary values from upstream tiles
-      const int last = min(s0 + kBatch - 1, nsteps - 1);
-      if (ext_y && !fail) {
-        if (!wait_at_least(dep_y, min(last + TY, nsteps), ctrl + 1, status)) fail = true;
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int k = s0 + u - ty - tz;
-          double v = 0.0;
-          if (!fail && k >= 0 && k < g.nx) v = __ldcg(vals + (row + (kBackward ? g.nx - 1 - k : k) - sy));
-          yin[tz][u] = v;
-        }
-      }
-      if (ext_z && !fail) {
-        if (!wait_at_least(dep_z, min(last + TZ, nsteps), ctrl + 1, status)) fail = true;
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int k = s0 + u - ty - tz;
-          double v = 0.0;
-          if (!fail && k >= 0 && k < g.nx) v = __ldcg(vals + (row + (kBackward ? g.nx - 1 - k : k) - sz));
-          zin[ty][u] = v;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int s = s0 + u;
-        if (s >= nsteps) break;                // uniform over the CTA
-        const int k = s - ty - tz;             // cell of my row at this step
-        double v = 0.0;
-        if (valid && k >= 0 && k < g.nx && !fail) {
-          const int x = kBackward ? g.nx - 1 - k : k;
-          double vy = 0.0, vz = 0.0;
-          if (hy) vy = (ty > 0) ? buf[(s - 1) & 1][tz][ty - 1] : yin[tz][u];
-          if (hz) vz = (tz > 0) ? buf[(s - 1) & 1][tz - 1][ty] : zin[ty][u];
-          v = op.apply(in[u], row + x, k > 0, vprev, hy, vy, hz, vz);
-          vprev = v;
-        }
-        buf[s & 1][tz][ty] = v;
-        const bool publish = (u == kBatch - 1) || (s + 1 == nsteps);
-        if (publish && boundary) __threadfence();
-        if (__syncthreads_or(fail)) {
-          if (threadIdx.x == 0) {
-            cuda::atomic_ref<int, cuda::thread_scope_device> ab(ctrl[1]);
-            ab.store(1, cuda::memory_order_relaxed);
-          }
-          return;
-        }
-        if (publish && threadIdx.x == 0) {
-          cuda::atomic_ref<int, cuda::thread_scope_device> pr(progress[Y + nty * Z]);
-          pr.store(s + 1, cuda::memory_order_release);
-        }
-      }
-    }
-  }
-}
-
-// Self-test of the bounded wait: waits on a counter that nothing sets.
 __global__ void k_wait_selftest(int* ctrl, int* status) {
   if (threadIdx.x == 0) wait_at_least(&ctrl[2], 1, &ctrl[1], status);
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
-constexpr int kTY = 8, kTZ = 8;
+template <class Op>
+constexpr int warp_smem() {
+  return (int)sizeof(double) * kWarps * kG * kU * Op::kN * kR;
+}
+
+template <class Op, bool kBackward>
+cudaError_t launch_warp(const Geo& g, const Skew& sk, const Op& op, const double* out, int grid,
+                        Buffers& b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
+  if (e != cudaSuccess) return e;
+  k_sweep_warp<Op, kBackward><<<grid, 32 * kWarps, warp_smem<Op>(), s>>>(g, sk, op, out, b.ctrl,
+                                                                         b.status);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
+long long ilu_skew_len(const Geo& g) {
+  const Skew k = make_skew(g);
+  return ((long long)k.nty * k.ntz * k.ns + 2 * kPad) * kR;
+}
+
 int ilu_ctrl_ints(const Geo& g) {
-  return 2 + ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
+  (void)g;
+  return 4;                                    // ticket, abort flag, self-test counter
+}
+
+int ilu_pipe_grid(const Geo& g, int num_sms) {
+  const Skew k = make_skew(g);
+  const int ctas = (k.nty * k.ntz + kWarps - 1) / kWarps;
+  cudaFuncSetAttribute(k_sweep_warp<FwdSolve, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       warp_smem<FwdSolve>());
+  cudaFuncSetAttribute(k_sweep_warp<BwdSolve, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       warp_smem<BwdSolve>());
+  cudaFuncSetAttribute(k_sweep_warp<Factor, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       warp_smem<Factor>());
+  // one CTA per SM: more sweeping warps per SM would share the FP64 pipes
+  return ctas < num_sms ? ctas : num_sms;
 }
 
 cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s) {
-  const int levels = g.nx + g.ny + g.nz - 2;
+  const Skew sk = make_skew(g);
+  Factor fa{b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.status};
   int n = 1;
   if (!pipelined) {
     const int blocks = blocks_for((long long)g.ny * g.nz, 256);
+    const int levels = g.nx + g.ny + g.nz - 2;
     for (int L = 0; L < levels; ++L)
-      k_ilu_factor_level<<<blocks, 256, 0, s>>>(g, L, b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.status);
+      k_sweep_level<Factor, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, b.dinv);
     n += levels;
   } else {
-    cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
+    k_fill_not_ready<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.dinv);
+    cudaError_t e = launch_warp<Factor, false>(g, sk, fa, b.dinv, grid, b, s);
     if (e != cudaSuccess) return e;
-    Factor fa{b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.status};
-    k_sweep_pipe<kTY, kTZ, Factor, false><<<grid, kTY * kTZ, 0, s>>>(g, fa, b.dinv, b.ctrl, b.status);
-    n += 1;
+    n += 2;
   }
-  k_ilu_scale<<<blocks_for(g.N, 256), 256, 0, s>>>(g, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly, b.Lz,
-                                                   b.Ux, b.Uy, b.Uz);
+  k_ilu_scale<<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly,
+                                                   b.Lz, b.Ux, b.Uy, b.Uz);
   count_launches(n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s) {
-  k_resid_scaled<<<blocks_for(g.N, 256), 256, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.f, b.p, b.dinv,
-                                                      b.r);
+  k_resid_scaled<<<blocks_for(g.N, 256), 256, 0, s>>>(g, make_skew(g), b.Ad, b.Ax, b.Ay, b.Az,
+                                                      b.f, b.p, b.dinv, b.rds, b.w, b.z);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
                              cudaStream_t s) {
-  FwdSolve fw{b.r, b.Lx, b.Ly, b.Lz, b.w};
-  BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.p};
+  const Skew sk = make_skew(g);
+  FwdSolve fw{b.rds, b.Lx, b.Ly, b.Lz, b.w};
+  BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.z, b.p};
   if (!pipelined) {
     const int blocks = blocks_for((long long)g.ny * g.nz, 256);
     const int levels = g.nx + g.ny + g.nz - 2;
     for (int L = 0; L < levels; ++L) {
-      if (!backward) k_sweep_level<FwdSolve, false><<<blocks, 256, 0, s>>>(g, L, fw, b.w);
-      else k_sweep_level<BwdSolve, true><<<blocks, 256, 0, s>>>(g, L, bw, b.w);
+      if (!backward) k_sweep_level<FwdSolve, false><<<blocks, 256, 0, s>>>(g, sk, L, fw, b.w);
+      else k_sweep_level<BwdSolve, true><<<blocks, 256, 0, s>>>(g, sk, L, bw, b.z);
     }
     count_launches(levels);
     return cudaGetLastError();
   }
-  cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
-  if (e != cudaSuccess) return e;
-  if (!backward) k_sweep_pipe<kTY, kTZ, FwdSolve, false><<<grid, kTY * kTZ, 0, s>>>(g, fw, b.w, b.ctrl, b.status);
-  else k_sweep_pipe<kTY, kTZ, BwdSolve, true><<<grid, kTY * kTZ, 0, s>>>(g, bw, b.w, b.ctrl, b.status);
+  cudaError_t e = !backward ? launch_warp<FwdSolve, false>(g, sk, fw, b.w, grid, b, s)
+                            : launch_warp<BwdSolve, true>(g, sk, bw, b.z, grid, b, s);
   count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s) {
@@ -399,15 +558,6 @@ cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(b.ctrl, b.status);
   count_launches(1);
   return cudaGetLastError();
-}
-
-int ilu_pipe_grid(const Geo& g, int num_sms) {
-  const int ntiles = ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_pipe<kTY, kTZ, FwdSolve, false>,
-                                                kTY * kTZ, 0);
-  const int cap = num_sms * (per_sm > 0 ? per_sm : 1);
-  return ntiles < cap ? ntiles : cap;
 }
 
 }  // namespace cams
