@@ -604,8 +604,8 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
           delete h;
           return fail(nullptr, CAMS_EINVAL, "permeability must be positive and finite");
         }
-    // stage through the (not yet used) work vectors r, w, eps
-    double* stage[3] = {h->b.r, h->b.w, h->b.eps};
+    // stage through the work vectors r, f, eps (overwritten by the next assembly)
+    double* stage[3] = {h->b.r, h->b.f, h->b.eps};
     for (int d = 0; d < 3; ++d) {
       cudaMemcpyAsync(stage[d], k3[d], sizeof(double) * g.N, cudaMemcpyHostToDevice, s);
       dk[d] = stage[d];
@@ -638,7 +638,7 @@ int cams_set_permeability(cams_handle* h, const double* kx, const double* ky, co
       for (long long i = 0; i < g.N; ++i)
         if (!(k3[d][i] > 0.0) || !std::isfinite(k3[d][i]))
           return fail(h, CAMS_EINVAL, "permeability must be positive and finite");
-    double* stage[3] = {h->b.r, h->b.w, h->b.eps};
+    double* stage[3] = {h->b.r, h->b.f, h->b.eps};
     for (int d = 0; d < 3; ++d) {
       CK(cudaMemcpyAsync(stage[d], k3[d], sizeof(double) * g.N, cudaMemcpyHostToDevice, h->stream));
       dk[d] = stage[d];

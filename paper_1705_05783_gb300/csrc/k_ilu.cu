@@ -136,22 +136,18 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const double* __restrict__ Ax,
   Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : 0.0;
 }
 
-// rd = D^{-1} (f - A p), stored skewed; the outputs w, z of the two sweeps
-// that follow start as "not computed".
+// rd = D^{-1} (f - A p), stored skewed.
 __global__ void k_resid_scaled(Geo g, Skew sk, const double* __restrict__ Ad,
                                const double* __restrict__ Ax, const double* __restrict__ Ay,
                                const double* __restrict__ Az, const double* __restrict__ f,
                                const double* __restrict__ p, const double* __restrict__ dinv,
-                               double* rd, double* w, double* zs) {
+                               double* rd) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
   const long long j = skew_index(sk, x, y, z);
-  const double nr = __longlong_as_double((long long)kNotReady);
-  w[j] = nr;
-  zs[j] = nr;
   double a = f[i] - Ad[i] * p[i];
   if (x > 0) a -= Ax[i] * p[i - 1];
   if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
@@ -171,11 +167,15 @@ __global__ void k_resid_scaled(Geo g, Skew sk, const double* __restrict__ Ad,
 // false on the pipeline's fill/drain slots and on rows beyond the grid:
 // there the result is discarded and nothing outside the slot is written.
 
+// The two solves also keep the sentinels of the pipelined schedule: the
+// forward sweep marks z "not computed" as it passes (the backward sweep that
+// follows publishes into z), and the backward sweep does the same for w once
+// it has consumed it (the next forward sweep publishes into w).
 struct FwdSolve {   // w = rd - Lx w_{x-1} - Ly w_{y-1} - Lz w_{z-1}
   static constexpr int kN = 4;
   static constexpr bool kSkewIn = true, kSkewOut = true;
   const double *rd, *Lx, *Ly, *Lz;
-  double* w;
+  double *w, *z;
   __device__ __forceinline__ const double* src(int a, long long, long long j) const {
     return (a == 0 ? rd : a == 1 ? Lx : a == 2 ? Ly : Lz) + j;
   }
@@ -183,6 +183,7 @@ struct FwdSolve {   // w = rd - Lx w_{x-1} - Ly w_{y-1} - Lz w_{z-1}
                                           double vx, double vy, double vz) const {
     const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
     publish(w + j, v);
+    z[j] = __longlong_as_double((long long)kNotReady);
     return v;
   }
 };
@@ -200,6 +201,7 @@ struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1};  p += z
                                           double vx, double vy, double vz) const {
     const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
     publish(z + j, v);
+    const_cast<double*>(w)[j] = __longlong_as_double((long long)kNotReady);
     if (cell) p[i] = in[4] + v;
     return v;
   }
@@ -438,10 +440,11 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
   }
 }
 
-__global__ void k_fill_not_ready(long long n, double* a) {
+__global__ void k_fill_not_ready(long long n, double* a, double* b) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   a[i] = __longlong_as_double((long long)kNotReady);
+  if (b) b[i] = __longlong_as_double((long long)kNotReady);
 }
 
 // Bounded wait used by the self-test: polls a counter that nothing sets.
@@ -513,10 +516,13 @@ cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid
       k_sweep_level<Factor, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, b.dinv);
     n += levels;
   } else {
-    k_fill_not_ready<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.dinv);
+    k_fill_not_ready<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.dinv, nullptr);
     cudaError_t e = launch_warp<Factor, false>(g, sk, fa, b.dinv, grid, b, s);
     if (e != cudaSuccess) return e;
-    n += 2;
+    // sweep outputs start "not computed"; the sweeps keep it so from here on
+    const long long S = ilu_skew_len(g);
+    k_fill_not_ready<<<blocks_for(S, 256), 256, 0, s>>>(S, b.w, b.z);
+    n += 3;
   }
   k_ilu_scale<<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly,
                                                    b.Lz, b.Ux, b.Uy, b.Uz);
@@ -526,7 +532,7 @@ cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid
 
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s) {
   k_resid_scaled<<<blocks_for(g.N, 256), 256, 0, s>>>(g, make_skew(g), b.Ad, b.Ax, b.Ay, b.Az,
-                                                      b.f, b.p, b.dinv, b.rds, b.w, b.z);
+                                                      b.f, b.p, b.dinv, b.rds);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -534,7 +540,7 @@ cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s) {
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
                              cudaStream_t s) {
   const Skew sk = make_skew(g);
-  FwdSolve fw{b.rds, b.Lx, b.Ly, b.Lz, b.w};
+  FwdSolve fw{b.rds, b.Lx, b.Ly, b.Lz, b.w, b.z};
   BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.z, b.p};
   if (!pipelined) {
     const int blocks = blocks_for((long long)g.ny * g.nz, 256);
