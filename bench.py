@@ -47,7 +47,7 @@ BYTES_PER_CELL = {
     "prolong": 80,             # P x8, p read + write
     "ilu_resid": 64,           # A x4, f, p, 1/d -> D^{-1} r
     "ilu_fwd": 48,             # D^{-1} r, scaled lower couplings x3 -> w, z marked unset
-    "ilu_bwd": 64,             # w, scaled upper couplings x3, p -> z, p, w marked unset
+    "ilu_bwd": 72,             # w, scaled upper couplings x3 -> z, w marked unset; p += z
     "galerkin": 96,            # P x8, couplings x3, C
     "ilu_factor": 88,          # A x4 -> 1/d, scaled couplings x6
     "basis_op": 64,

@@ -57,7 +57,7 @@ constexpr int kU = 4;                        // steps per group (straight-line c
 constexpr int kG = 3;                        // operand groups in flight (staged 2 groups ahead)
 constexpr int kPad = kG * kU;                // spare records at both ends of a vector
 constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ a second)
-constexpr int kFastPolls = 64;               // polls before a wait starts to sleep
+constexpr int kFastPolls = 64;               // in-loop polls before a wait starts to sleep
 
 // "Not computed yet": a signalling-NaN bit pattern.  IEEE arithmetic never
 // produces a signalling NaN, so no computed value carries this pattern.
@@ -158,6 +158,16 @@ __global__ void k_resid_scaled(Geo g, Skew sk, const double* __restrict__ Ad,
   rd[j] = a * dinv[i];
 }
 
+// p += z (the correction of one smoothing step), z stored skewed.
+__global__ void k_apply_z(Geo g, Skew sk, const double* __restrict__ zs, double* p) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= g.N) return;
+  const int x = (int)(i % g.nx);
+  const int y = (int)((i / g.nx) % g.ny);
+  const int z = (int)(i / g.sz);
+  p[i] += zs[skew_index(sk, x, y, z)];
+}
+
 // ------------------------------------------------- per-cell operators ---
 // Each sweep is "value = op(cell, operands, values of the three upstream
 // neighbours)", with 0 standing for a neighbour outside the grid (its
@@ -188,21 +198,19 @@ struct FwdSolve {   // w = rd - Lx w_{x-1} - Ly w_{y-1} - Lz w_{z-1}
   }
 };
 
-struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1};  p += z
-  static constexpr int kN = 5;
+struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1}  (p += z follows)
+  static constexpr int kN = 4;
   static constexpr bool kSkewIn = true, kSkewOut = true;
   const double *Ux, *Uy, *Uz;
-  const double* w;
-  double *z, *p;
-  __device__ __forceinline__ const double* src(int a, long long i, long long j) const {
-    return a == 4 ? p + i : (a == 0 ? w : a == 1 ? Ux : a == 2 ? Uy : Uz) + j;
+  double *w, *z;
+  __device__ __forceinline__ const double* src(int a, long long, long long j) const {
+    return (a == 0 ? w : a == 1 ? Ux : a == 2 ? Uy : Uz) + j;
   }
-  __device__ __forceinline__ double apply(const double* in, long long i, long long j, bool cell,
+  __device__ __forceinline__ double apply(const double* in, long long, long long j, bool,
                                           double vx, double vy, double vz) const {
     const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
     publish(z + j, v);
-    const_cast<double*>(w)[j] = __longlong_as_double((long long)kNotReady);
-    if (cell) p[i] = in[4] + v;
+    w[j] = __longlong_as_double((long long)kNotReady);
     return v;
   }
 };
@@ -279,28 +287,42 @@ __device__ __forceinline__ void tile_of_ticket(int t, int nty, int ntz, int& Y, 
   }
 }
 
-// ctrl: [0] ticket, [1] abort flag.  `out` is the vector the operator
-// publishes into (pre-filled with kNotReady on every cell).  Shared memory:
-// per warp, the operand ring [kG][kU][Op::kN][32].
-//
-// Steps run in groups of kU.  A group's prologue stages the operands of the
-// group two ahead (cp.async), fetches the cross-tile values of the next
-// group, and then waits, if need be, for its own cross-tile values; the kU
-// steps themselves are straight-line code (shuffles, three FMAs, stores).
+// Polls *p until it holds a published value; returns its bits, or
+// kNotReady after an abort or a timeout (the status word and the abort flag
+// are then set).  A light loop (one address, a short sleep between polls)
+// for the long wait before a tile's first step: heavy polling there slows
+// the tile's first steps and every tile downstream of it.
+__device__ __forceinline__ unsigned long long wait_bits(const double* p, int* abort_flag,
+                                                        int* status) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    const unsigned long long b = ld_relaxed(p);
+    if (b != kNotReady) return b;
+    if ((it & 63) == 63 && ld_relaxed_int(abort_flag)) return kNotReady;
+    __nanosleep(32);
+  }
+  atomicOr(status, kStatTimeout);
+  atomicExch(abort_flag, 1);
+  return kNotReady;
+}
+
+// One tile of a sweep, run by one warp: the tile at (Ym, Zm) in the sweep
+// frame (mirrored for the backward sweep).  ring: this lane's operand ring.
+// Values from other tiles are read from `out`.  Before its first step the
+// tile waits (lightly) for the upstream values of its first group; steps
+// then run in groups of kU: a group's prologue stages the operands of the
+// group two ahead (cp.async) and prefetches the next group's cross-tile
+// values; values still unset are re-polled together; the kU steps
+// themselves are straight-line code.  Returns false after an abort
+// or a timeout (the warp's copies drained).
 template <class Op, bool kBackward>
-__global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, Op op,
-                                                                const double* out, int* ctrl,
-                                                                int* status) {
+__device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const Op& op,
+                                           const double* out, int* abort_flag, int* status,
+                                           double* ring, int lane, int Ym, int Zm) {
   constexpr unsigned kAll = 0xffffffffu;
   constexpr int kN = Op::kN;
-  extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* ring = smem + warp * (kG * kU * kN * kR) + lane;
   const int tym = lane % kTY, tzm = lane / kTY;   // row within the tile, sweep frame
   const int ty = kBackward ? kTY - 1 - tym : tym, tz = kBackward ? kTZ - 1 - tzm : tzm;
   const int slot = ty + kTY * tz;                 // my slot of a record
-  const int ntiles = sk.nty * sk.ntz;
-  int* abort_flag = ctrl + 1;
   const long long rec = (long long)sk.ns * kR;    // one tile's records
   const long long dj = kBackward ? -kR : kR;      // skewed index change per step
   const long long di = kBackward ? -1 : 1;        // natural index change per step
@@ -309,134 +331,158 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
   const long long offz_s =
       (kBackward ? 1 : -1) * ((long long)sk.nty * rec - (long long)(kTZ - 1) * (kR + kTY));
   const long long offy_n = kBackward ? g.sy : -g.sy, offz_n = kBackward ? g.sz : -g.sz;
+  const int Y = kBackward ? sk.nty - 1 - Ym : Ym, Z = kBackward ? sk.ntz - 1 - Zm : Zm;
+  const int y = Y * kTY + ty, z = Z * kTZ + tz;
+  const bool valid = y < g.ny && z < g.nz;
+  const bool hy = valid && (kBackward ? y < g.ny - 1 : y > 0);   // upstream rows exist
+  const bool hz = valid && (kBackward ? z < g.nz - 1 : z > 0);
+  const bool ext_y = hy && tym == 0;                              // ... in another tile
+  const bool ext_z = hz && tzm == 0;
+  // indices at sweep step 0.  x in the sweep frame is step - xoff; the
+  // backward sweep walks the tile's records from the last one down, and its
+  // first ns - (nx + kTY + kTZ - 2) steps are padding.
+  const int xoff = tym + tzm + (kBackward ? sk.ns - (g.nx + kTY + kTZ - 2) : 0);
+  const long long j0 =
+      ((long long)(Y + sk.nty * Z) * sk.ns + (kBackward ? sk.ns - 1 : 0) + kPad) * kR + slot;
+  const int yc = valid ? y : 0, zc = valid ? z : 0;               // rows beyond the grid read row 0
+  const long long row = (long long)yc * g.sy + (long long)zc * g.sz;
+  const long long i0 = row + (kBackward ? g.nx - 1 + xoff : -xoff);
+  const long long o0 = Op::kSkewOut ? j0 : i0;
+  const long long od = Op::kSkewOut ? dj : di;
+  const long long oy0 = o0 + (Op::kSkewOut ? offy_s : offy_n);
+  const long long oz0 = o0 + (Op::kSkewOut ? offz_s : offz_n);
+  // operands of steps gs .. gs+kU-1 into ring group q.  Skewed operands
+  // are always in range (spare records); natural ones (the factorisation's)
+  // are clamped to my row (read, then discarded).
+  auto stage = [&](int gs, int q) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      long long i = i0 + (gs + u) * di;
+      if (!Op::kSkewIn) {
+        i = i < row ? row : i;
+        i = i > row + g.nx - 1 ? row + g.nx - 1 : i;
+      }
+      const long long j = j0 + (gs + u) * dj;
+#pragma unroll
+      for (int a = 0; a < kN; ++a) cp_async8(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
+    }
+    cp_async_commit();
+  };
+  // values of steps gs .. gs+kU-1 read from `out` (0 where none is needed)
+  auto fetch = [&](int gs, unsigned long long* cy, unsigned long long* cz) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int xq = gs + u - xoff;
+      const bool in_row = xq >= 0 && xq < g.nx;
+      cy[u] = ld_relaxed_if(ext_y && in_row, out + oy0 + (gs + u) * od);
+      cz[u] = ld_relaxed_if(ext_z && in_row, out + oz0 + (gs + u) * od);
+    }
+  };
+  {
+    // the first group's last upstream values (the first wait is the long one)
+    const int xq = kU - 1 - xoff;
+    bool ok = true;
+    if (ext_y && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oy0 + (kU - 1) * od, abort_flag, status) != kNotReady;
+    if (ext_z && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oz0 + (kU - 1) * od, abort_flag, status) != kNotReady;
+    if (__any_sync(kAll, !ok)) return false;
+  }
+  stage(0, 0);
+  stage(kU, 1);
+  unsigned long long cy[kU], cz[kU];
+  fetch(0, cy, cz);
+  double vprev = 0.0, from_y = 0.0, from_z = 0.0;
+  int q = 0;
+  for (int s0 = 0; s0 < sk.ns; s0 += kU) {
+    stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
+    unsigned long long ny_[kU], nz_[kU];
+    fetch(s0 + kU, ny_, nz_);
+    // values still unset: re-poll them together (one round trip per poll)
+    bool pending = false;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) pending |= (cy[u] == kNotReady) | (cz[u] == kNotReady);
+    if (__any_sync(kAll, pending)) {
+      bool fail = false;
+      for (long long it = 0; pending && !fail; ++it) {
+        pending = false;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          if (cy[u] == kNotReady) {
+            cy[u] = ld_relaxed(out + oy0 + (s0 + u) * od);
+            pending |= cy[u] == kNotReady;
+          }
+          if (cz[u] == kNotReady) {
+            cz[u] = ld_relaxed(out + oz0 + (s0 + u) * od);
+            pending |= cz[u] == kNotReady;
+          }
+        }
+        if (pending && it >= kFastPolls) {
+          if (it >= kSpinLimit) {
+            atomicOr(status, kStatTimeout);
+            atomicExch(abort_flag, 1);
+            fail = true;
+          } else if ((it & 15) == 0 && ld_relaxed_int(abort_flag)) {
+            fail = true;
+          } else {
+            __nanosleep(100);
+          }
+        }
+      }
+      if (__any_sync(kAll, fail)) {
+        cp_async_wait<0>();
+        return false;
+      }
+    }
+    cp_async_wait<2>();
+    double in[kU][kN];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int a = 0; a < kN; ++a) in[u][a] = ring[((q * kU + u) * kN + a) * kR];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int s = s0 + u;
+      const int xs = s - xoff;
+      const bool cell = valid && xs >= 0 && xs < g.nx;
+      const double vy = hy ? (tym > 0 ? from_y : __longlong_as_double((long long)cy[u])) : 0.0;
+      const double vz = hz ? (tzm > 0 ? from_z : __longlong_as_double((long long)cz[u])) : 0.0;
+      const double vx = xs > 0 ? vprev : 0.0;
+      const double v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
+      // rows y-1 / z-1 of my tile computed my next neighbours just now
+      from_y = __shfl_up_sync(kAll, v, 1);
+      from_z = __shfl_up_sync(kAll, v, kTY);
+      vprev = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      cy[u] = ny_[u];
+      cz[u] = nz_[u];
+    }
+    q = q == kG - 1 ? 0 : q + 1;
+  }
+  cp_async_wait<0>();
+  return true;
+}
+
+// ctrl: [0] ticket, [1] abort flag.  `out` is the vector the operator
+// publishes into (pre-filled with kNotReady on every cell).  Shared memory:
+// per warp, the operand ring [kG][kU][Op::kN][32].  Each warp claims tiles
+// on its own; cross-tile values travel through L2.
+template <class Op, bool kBackward>
+__global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, Op op,
+                                                                const double* out, int* ctrl,
+                                                                int* status) {
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
+  const int ntiles = sk.nty * sk.ntz;
   for (;;) {
     int t = 0;
     if (lane == 0) t = atomicAdd(&ctrl[0], 1);
-    t = __shfl_sync(kAll, t, 0);
+    t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= ntiles) return;
     int Ym, Zm;
     tile_of_ticket(t, sk.nty, sk.ntz, Ym, Zm);
-    const int Y = kBackward ? sk.nty - 1 - Ym : Ym, Z = kBackward ? sk.ntz - 1 - Zm : Zm;
-    const int y = Y * kTY + ty, z = Z * kTZ + tz;
-    const bool valid = y < g.ny && z < g.nz;
-    const bool hy = valid && (kBackward ? y < g.ny - 1 : y > 0);   // upstream rows exist
-    const bool hz = valid && (kBackward ? z < g.nz - 1 : z > 0);
-    const bool ext_y = hy && tym == 0;                              // ... in another tile
-    const bool ext_z = hz && tzm == 0;
-    // indices at sweep step 0.  x in the sweep frame is step - xoff; the
-    // backward sweep walks the tile's records from the last one down, and its
-    // first ns - (nx + kTY + kTZ - 2) steps are padding.
-    const int xoff = tym + tzm + (kBackward ? sk.ns - (g.nx + kTY + kTZ - 2) : 0);
-    const long long j0 =
-        ((long long)(Y + sk.nty * Z) * sk.ns + (kBackward ? sk.ns - 1 : 0) + kPad) * kR + slot;
-    const int yc = valid ? y : 0, zc = valid ? z : 0;               // rows beyond the grid read row 0
-    const long long row = (long long)yc * g.sy + (long long)zc * g.sz;
-    const long long i0 = row + (kBackward ? g.nx - 1 + xoff : -xoff);
-    const long long o0 = Op::kSkewOut ? j0 : i0;
-    const long long od = Op::kSkewOut ? dj : di;
-    const long long oy0 = o0 + (Op::kSkewOut ? offy_s : offy_n);
-    const long long oz0 = o0 + (Op::kSkewOut ? offz_s : offz_n);
-    // operands of steps gs .. gs+kU-1 into ring group q.  Skewed operands
-    // are always in range (spare records); natural ones are clamped to my
-    // row (read, then discarded).
-    auto stage = [&](int gs, int q) {
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        long long i = i0 + (gs + u) * di;
-        if (!Op::kSkewIn || kN > 4) {
-          i = i < row ? row : i;
-          i = i > row + g.nx - 1 ? row + g.nx - 1 : i;
-        }
-        const long long j = j0 + (gs + u) * dj;
-#pragma unroll
-        for (int a = 0; a < kN; ++a) cp_async8(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
-      }
-      cp_async_commit();
-    };
-    // cross-tile values of steps gs .. gs+kU-1 (0 where none is needed)
-    auto fetch = [&](int gs, unsigned long long* cy, unsigned long long* cz) {
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int xq = gs + u - xoff;
-        const bool in_row = xq >= 0 && xq < g.nx;
-        cy[u] = ld_relaxed_if(ext_y && in_row, out + oy0 + (gs + u) * od);
-        cz[u] = ld_relaxed_if(ext_z && in_row, out + oz0 + (gs + u) * od);
-      }
-    };
-    stage(0, 0);
-    stage(kU, 1);
-    unsigned long long cy[kU], cz[kU];
-    fetch(0, cy, cz);
-    double vprev = 0.0, from_y = 0.0, from_z = 0.0;
-    int q = 0;
-    for (int s0 = 0; s0 < sk.ns; s0 += kU) {
-      stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
-      unsigned long long ny_[kU], nz_[kU];
-      fetch(s0 + kU, ny_, nz_);
-      // wait for this group's cross-tile values: re-poll those still unset
-      bool pending = false;
-#pragma unroll
-      for (int u = 0; u < kU; ++u) pending |= (cy[u] == kNotReady) | (cz[u] == kNotReady);
-      if (__any_sync(kAll, pending)) {
-        bool fail = false;
-        for (long long it = 0; pending && !fail; ++it) {
-          pending = false;
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            if (cy[u] == kNotReady) {
-              cy[u] = ld_relaxed(out + oy0 + (s0 + u) * od);
-              pending |= cy[u] == kNotReady;
-            }
-            if (cz[u] == kNotReady) {
-              cz[u] = ld_relaxed(out + oz0 + (s0 + u) * od);
-              pending |= cz[u] == kNotReady;
-            }
-          }
-          if (pending && it >= kFastPolls) {
-            if (it >= kSpinLimit) {
-              atomicOr(status, kStatTimeout);
-              atomicExch(abort_flag, 1);
-              fail = true;
-            } else if ((it & 15) == 0 && ld_relaxed_int(abort_flag)) {
-              fail = true;
-            } else {
-              __nanosleep(100);
-            }
-          }
-        }
-        if (__any_sync(kAll, fail)) {
-          cp_async_wait<0>();
-          return;
-        }
-      }
-      cp_async_wait<2>();
-      double in[kU][kN];
-#pragma unroll
-      for (int u = 0; u < kU; ++u)
-#pragma unroll
-        for (int a = 0; a < kN; ++a) in[u][a] = ring[((q * kU + u) * kN + a) * kR];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int s = s0 + u;
-        const int xs = s - xoff;
-        const bool cell = valid && xs >= 0 && xs < g.nx;
-        const double vy = hy ? (tym > 0 ? from_y : __longlong_as_double((long long)cy[u])) : 0.0;
-        const double vz = hz ? (tzm > 0 ? from_z : __longlong_as_double((long long)cz[u])) : 0.0;
-        const double vx = xs > 0 ? vprev : 0.0;
-        const double v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
-        // rows y-1 / z-1 of my tile computed my next neighbours just now
-        from_y = __shfl_up_sync(kAll, v, 1);
-        from_z = __shfl_up_sync(kAll, v, kTY);
-        vprev = v;
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        cy[u] = ny_[u];
-        cz[u] = nz_[u];
-      }
-      q = q == kG - 1 ? 0 : q + 1;
-    }
-    cp_async_wait<0>();
+    if (!sweep_tile<Op, kBackward>(g, sk, op, out, ctrl + 1, status, ring, lane, Ym, Zm)) return;
   }
 }
 
@@ -471,8 +517,8 @@ constexpr int warp_smem() {
 }
 
 template <class Op, bool kBackward>
-cudaError_t launch_warp(const Geo& g, const Skew& sk, const Op& op, const double* out, int grid,
-                        Buffers& b, cudaStream_t s) {
+cudaError_t launch_sweep(const Geo& g, const Skew& sk, int grid, const Op& op, const double* out,
+                         Buffers& b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
   if (e != cudaSuccess) return e;
   k_sweep_warp<Op, kBackward><<<grid, 32 * kWarps, warp_smem<Op>(), s>>>(g, sk, op, out, b.ctrl,
@@ -517,7 +563,7 @@ cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid
     n += levels;
   } else {
     k_fill_not_ready<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.dinv, nullptr);
-    cudaError_t e = launch_warp<Factor, false>(g, sk, fa, b.dinv, grid, b, s);
+    cudaError_t e = launch_sweep<Factor, false>(g, sk, grid, fa, b.dinv, b, s);
     if (e != cudaSuccess) return e;
     // sweep outputs start "not computed"; the sweeps keep it so from here on
     const long long S = ilu_skew_len(g);
@@ -541,7 +587,7 @@ cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipel
                              cudaStream_t s) {
   const Skew sk = make_skew(g);
   FwdSolve fw{b.rds, b.Lx, b.Ly, b.Lz, b.w, b.z};
-  BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.z, b.p};
+  BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.z};
   if (!pipelined) {
     const int blocks = blocks_for((long long)g.ny * g.nz, 256);
     const int levels = g.nx + g.ny + g.nz - 2;
@@ -550,12 +596,17 @@ cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipel
       else k_sweep_level<BwdSolve, true><<<blocks, 256, 0, s>>>(g, sk, L, bw, b.z);
     }
     count_launches(levels);
-    return cudaGetLastError();
+  } else {
+    cudaError_t e = !backward ? launch_sweep<FwdSolve, false>(g, sk, grid, fw, b.w, b, s)
+                              : launch_sweep<BwdSolve, true>(g, sk, grid, bw, b.z, b, s);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
   }
-  cudaError_t e = !backward ? launch_warp<FwdSolve, false>(g, sk, fw, b.w, grid, b, s)
-                            : launch_warp<BwdSolve, true>(g, sk, bw, b.z, grid, b, s);
-  count_launches(1);
-  return e;
+  if (backward) {
+    k_apply_z<<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, b.z, b.p);
+    count_launches(1);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s) {

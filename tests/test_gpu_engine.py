@@ -45,9 +45,10 @@ def _iterate(cams, case, n, level):
 
 @pytest.mark.parametrize("shape,coarse", [((40, 40, 1), (5, 5, 1)), ((30, 30, 20), (10, 10, 10)),
                                           ((24, 17, 13), (6, 17, 13)), ((64, 9, 33), (8, 3, 3)),
-                                          ((12, 8, 6), (2, 4, 3))])
+                                          ((12, 8, 6), (2, 4, 3)), ((20, 72, 40), (10, 8, 8))])
 def test_pipelined_sweeps_equal_level_schedule(cams, shape, coarse):
-    """Ragged tiles in y and z, 2D and 3D: same arithmetic, same bits."""
+    """Ragged tiles in y and z, 2D and 3D, a single tile and many: same
+    arithmetic, same bits."""
     case = make_case("3d-200x200x100", nx=shape[0], ny=shape[1], nz=shape[2], coarse=coarse,
                      n_post=3, n_pre=1)
     r1, p1, d1 = _iterate(cams, case, 3, level=False)
