@@ -48,6 +48,7 @@ struct cams_handle {
   int last_rebuilt = 0;
   long long launch_base = 0;
   bool ilu_pipelined = true;    // false: level-scheduled sweeps (CAMS_ILU_LEVEL=1)
+  bool coarse_cluster = false;  // MSFE coarse solve across a cluster (CAMS_COARSE_CLUSTER=0: one CTA)
   int ilu_grid = 1;
   // per-kernel-class profiling (cams_profile)
   bool prof = false;
@@ -260,6 +261,7 @@ int alloc_all(cams_handle* h) {
   AL(b.Acs, 27LL * h->c.Nc);
   AL(b.band, (size_t)h->c.Nc * (2 * h->mc + 1));
   AL(b.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(b.Lr, (size_t)h->c.Nc * (h->mc + 1));
+  AL(b.cblk, coarse_blocks_len(h->c.Nc)); AL(b.cdinv, h->c.Nc); AL(b.cabort, 1);
   AL(b.perm, h->c.Nc);
   AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc);
   AL(b.dinv, N);
@@ -287,7 +289,7 @@ void free_all(cams_handle* h) {
                   b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
-                  b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr};
+                  b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->b = Buffers{};
@@ -461,7 +463,8 @@ int cams_step(cams_handle* h) {
   }
   LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
   LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, h->opt.restriction, b.r, b, h->stream));
-  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, h->opt.restriction == 0, b, h->stream));
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, h->opt.restriction == 0,
+                                                   h->coarse_cluster, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
     int rc = ilu_smooth(h);
@@ -585,6 +588,9 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     const char* lv = std::getenv("CAMS_ILU_LEVEL");
     h->ilu_pipelined = !(lv && lv[0] == '1');
     h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
+    const char* cc = std::getenv("CAMS_COARSE_CLUSTER");
+    h->coarse_cluster = !(cc && cc[0] == '0') &&
+                        coarse_cluster_ok(h->c.Nc, (int)prop.sharedMemPerBlockOptin);
   }
   // copy tables and compute transmissibilities
   cudaStream_t s = h->stream;

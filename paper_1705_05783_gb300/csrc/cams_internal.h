@@ -81,6 +81,8 @@ struct Buffers {
   double* Acs = nullptr;                                  // 27*Nc coarse stencil
   double* band = nullptr;                                 // coarse band (column-major)
   double *Lc = nullptr, *Lr = nullptr;                    // LDL^T factor, column/row-major
+  double *cblk = nullptr, *cdinv = nullptr;               // block inverses / products, 1/d
+  int* cabort = nullptr;                                  // abort flag of the cluster solve
   int* perm = nullptr;                                    // coarse natural -> band order
   double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
   double* dinv = nullptr;                                 // 1 / ILU(0) pivots
@@ -142,7 +144,9 @@ cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStre
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
                             cudaStream_t s);
-cudaError_t launch_band_solve(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
+cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, cudaStream_t s);
+long long coarse_blocks_len(int Nc);
+bool coarse_cluster_ok(int Nc, int max_smem);
 cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s);
 cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s);
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s);

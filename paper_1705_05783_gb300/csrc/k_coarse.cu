@@ -454,6 +454,243 @@ __global__ void __launch_bounds__(256) k_ldlt_solve(int N, int m, const double* 
   for (int i = tid; i < N; i += nt) pc[i] = y[i];
 }
 
+// ---- L D L^T x = b across a thread-block cluster ----
+// The rows are cut into blocks of kCB.  With L_IJ the blocks of the unit
+// lower factor, the forward solve L y = b is, block by block,
+//   y_J = s_J - M_J y_{J-1},  s_J = L_JJ^{-1} (b_J - sum_{I <= J-2} L_JI y_I),
+//   M_J = L_JJ^{-1} L_{J,J-1},
+// so once y_{J-1} is known only one kCB x kCB product remains; s_J needs
+// y_{J-2} and is formed one block earlier.  The backward solve
+// L^T x = D^{-1} y is the same with the transposed blocks:
+//   x_I = s'_I - M'_I x_{I+1},  M'_I = L_II^{-T} L_{I+1,I}^T.
+// k_coarse_prep computes L_JJ^{-1}, M_J, M'_J and 1/d after each
+// factorisation.  k_coarse_solve_cluster deals the blocks round-robin to the
+// kCC CTAs of one cluster; each CTA keeps a copy of y and x in shared memory
+// (kNotReady until written) and the owner of a block stores its values into
+// every CTA's copy through distributed shared memory.
+constexpr int kCB = 32;                      // rows per block
+constexpr int kCC = 8;                       // CTAs per cluster
+constexpr unsigned long long kCNotReady = 0x7FF4DEADBEEF0002ull;   // signalling NaN
+constexpr long long kCSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ double lower_at(const double* Lc, int N, int m, int r, int c) {
+  // strictly lower entry of the unit factor (column-major band), 0 elsewhere
+  return (r < N && c >= 0 && r > c && r - c <= m) ? Lc[(long long)c * (m + 1) + (r - c)] : 0.0;
+}
+
+// One CTA per block J: blk[J] = { L_JJ^{-1}, M_J, M'_J } (kCB x kCB each,
+// row-major), dinv[i] = 1 / d_i.  Rows past N act as identity rows.
+__global__ void __launch_bounds__(256) k_coarse_prep(int N, int m, const double* __restrict__ Lc,
+                                                     double* blk, double* dinv) {
+  __shared__ double Lj[kCB][kCB + 1];
+  __shared__ double Li[kCB][kCB + 1];
+  __shared__ double Lo[kCB][kCB + 1];
+  const int J = blockIdx.x, NB = gridDim.x, base = J * kCB, tid = threadIdx.x;
+  double* out = blk + (long long)J * 3 * kCB * kCB;
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int r = e / kCB, q = e % kCB;
+    Lj[r][q] = q == r ? 1.0 : lower_at(Lc, N, m, base + r, base + q);
+  }
+  if (tid < kCB && base + tid < N) dinv[base + tid] = 1.0 / Lc[(long long)(base + tid) * (m + 1)];
+  __syncthreads();
+  // inverse of the unit lower block, one column per thread (forward substitution)
+  if (tid < kCB) {
+    const int c = tid;
+    for (int r = 0; r < kCB; ++r) {
+      double s = r == c ? 1.0 : 0.0;
+      if (r > c) {
+        for (int q = c; q < r; ++q) s -= Lj[r][q] * Li[q][c];
+      }
+      Li[r][c] = s;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) out[e] = Li[e / kCB][e % kCB];
+  // M_J = L_JJ^{-1} L_{J,J-1}
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int r = e / kCB, q = e % kCB;
+    Lo[r][q] = J > 0 ? lower_at(Lc, N, m, base + r, base - kCB + q) : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int r = e / kCB, q = e % kCB;
+    double s = 0.0;
+    for (int k = 0; k < kCB; ++k) s += Li[r][k] * Lo[k][q];
+    out[kCB * kCB + e] = s;
+  }
+  __syncthreads();
+  // M'_J = L_JJ^{-T} L_{J+1,J}^T :  M'[c][q] = sum_k Li[k][c] L[(J+1)B + q][JB + k]
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int q = e / kCB, kk = e % kCB;
+    Lo[q][kk] = J + 1 < NB ? lower_at(Lc, N, m, base + kCB + q, base + kk) : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < kCB * kCB; e += blockDim.x) {
+    const int c = e / kCB, q = e % kCB;
+    double s = 0.0;
+    for (int kk = 0; kk < kCB; ++kk) s += Li[kk][c] * Lo[q][kk];
+    out[2 * kCB * kCB + e] = s;
+  }
+}
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// store v into the same shared-memory location of every CTA of the cluster
+__device__ __forceinline__ void cl_broadcast(const double* local, double v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+#pragma unroll
+  for (int rk = 0; rk < kCC; ++rk) {
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rk));
+    asm volatile("st.relaxed.cluster.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+  }
+}
+__device__ __forceinline__ unsigned long long ld_cl(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.cluster.shared::cta.b64 %0, [%1];"
+               : "=l"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_abort(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+// Waits until the 4 values at p are written; false after an abort or a timeout.
+__device__ __forceinline__ bool wait4(const double* p, double* v, int* abort_flag, int* status) {
+  for (long long it = 0; it < kCSpinLimit; ++it) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned long long b = ld_cl(p + k);
+      v[k] = __longlong_as_double((long long)b);
+      ok &= b != kCNotReady;
+    }
+    if (ok) return true;
+    if ((it & 63) == 63) {
+      if (ld_abort(abort_flag)) return false;
+      __nanosleep(32);
+    }
+  }
+  atomicOr(status, kStatTimeout);
+  atomicExch(abort_flag, 1);
+  return false;
+}
+
+// sum over the 8 lanes of an aligned lane group (every lane gets the sum)
+__device__ __forceinline__ double sum8(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// 256 threads: thread (r = tid / 8, h = tid % 8) owns row r of a block and
+// the 4 columns 4h .. 4h+3 of every kCB x kCB product.
+__global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
+    int N, int m, const double* __restrict__ Lc, const double* __restrict__ Lr,
+    const double* __restrict__ blk, const double* __restrict__ dinv,
+    const double* __restrict__ rc, double* pc, int* abort_flag, int* status) {
+  extern __shared__ double sm[];
+  __shared__ double uv[kCB];
+  const int NB = (N + kCB - 1) / kCB, Np = NB * kCB;
+  double* y = sm;
+  double* x = sm + Np;
+  const int rank = (int)cl_rank();
+  const int tid = threadIdx.x, r = tid >> 3, h = tid & 7;
+  const int W = (m + kCB - 1) / kCB;           // blocks of the band left of a diagonal block
+  for (int i = tid; i < 2 * Np; i += blockDim.x) sm[i] = __longlong_as_double((long long)kCNotReady);
+  cl_sync();
+  bool ok = true;
+  // ---- forward: L y = b ----
+  for (int J = rank; J < NB; J += kCC) {
+    const int base = J * kCB, row = base + r;
+    double acc = (h == 0 && row < N) ? rc[row] : 0.0;
+    for (int I = J - W > 0 ? J - W : 0; I <= J - 2; ++I) {
+      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      ok = ok && wait4(y + I * kCB + 4 * h, yv, abort_flag, status);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = I * kCB + 4 * h + k;
+        const double l = (row < N && row - c <= m) ? Lr[(long long)row * (m + 1) + (row - c)] : 0.0;
+        acc -= l * yv[k];
+      }
+    }
+    acc = sum8(acc);
+    if (h == 0) uv[r] = acc;
+    __syncthreads();
+    const double* Li = blk + (long long)J * 3 * kCB * kCB;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += Li[r * kCB + 4 * h + k] * uv[4 * h + k];
+    s = sum8(s);
+    if (J > 0) {
+      const double* M = Li + kCB * kCB;
+      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      ok = ok && wait4(y + (J - 1) * kCB + 4 * h, yv, abort_flag, status);
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t += M[r * kCB + 4 * h + k] * yv[k];
+      s -= sum8(t);
+    }
+    __syncthreads();
+    if (h == 0) cl_broadcast(y + row, ok ? s : 0.0);
+  }
+  // ---- backward: L^T x = D^{-1} y ----
+  const int lastJ = NB - 1 - ((NB - 1 - rank) % kCC + kCC) % kCC;
+  for (int I = lastJ; I >= 0; I -= kCC) {
+    const int base = I * kCB, col = base + r;
+    double acc = 0.0;
+    if (h == 0) {
+      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      ok = ok && wait4(y + base + (r & ~3), yv, abort_flag, status);
+      acc = col < N ? yv[r & 3] * dinv[col] : 0.0;
+    }
+    for (int J = I + W < NB - 1 ? I + W : NB - 1; J >= I + 2; --J) {
+      double xv[4] = {0.0, 0.0, 0.0, 0.0};
+      ok = ok && wait4(x + J * kCB + 4 * h, xv, abort_flag, status);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int rw = J * kCB + 4 * h + k;
+        const double l = (rw < N && col < N && rw - col <= m) ? Lc[(long long)col * (m + 1) + (rw - col)] : 0.0;
+        acc -= l * xv[k];
+      }
+    }
+    acc = sum8(acc);
+    if (h == 0) uv[r] = acc;
+    __syncthreads();
+    const double* Li = blk + (long long)I * 3 * kCB * kCB;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += Li[(4 * h + k) * kCB + r] * uv[4 * h + k];
+    s = sum8(s);
+    if (I + 1 < NB) {
+      const double* Mt = Li + 2 * kCB * kCB;
+      double xv[4] = {0.0, 0.0, 0.0, 0.0};
+      ok = ok && wait4(x + (I + 1) * kCB + 4 * h, xv, abort_flag, status);
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t += Mt[r * kCB + 4 * h + k] * xv[k];
+      s -= sum8(t);
+    }
+    __syncthreads();
+    if (h == 0) {
+      cl_broadcast(x + col, ok ? s : 0.0);
+      if (col < N) pc[col] = s;
+    }
+  }
+  cl_sync();   // no CTA leaves while others may still store into its shared memory
+}
+
 // ---- general (MSFV) coarse matrix: band LU without pivoting, one CTA ----
 // Column-major band Bc[col*(2m+1) + (row-col+m)]; after the factorisation
 // column k holds U above/on the diagonal and the multipliers of L below.
@@ -627,7 +864,8 @@ cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t 
   }
   const long long n = (long long)Nc * (m + 1);
   k_ldlt_rows<<<(int)((n + 255) / 256), 256, 0, s>>>(Nc, m, b.Lc, b.Lr);
-  count_launches(launches + 1);
+  k_coarse_prep<<<(Nc + kCB - 1) / kCB, 256, 0, s>>>(Nc, m, b.Lc, b.cblk, b.cdinv);
+  count_launches(launches + 2);
   return cudaGetLastError();
 }
 
@@ -643,7 +881,61 @@ cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_solve(int Nc, int m, int sym, Buffers& b, cudaStream_t s) {
+long long coarse_blocks_len(int Nc) {
+  return (long long)((Nc + kCB - 1) / kCB) * 3 * kCB * kCB;
+}
+
+static int coarse_cluster_smem(int Nc) {
+  return (int)sizeof(double) * 2 * ((Nc + kCB - 1) / kCB) * kCB;
+}
+
+bool coarse_cluster_ok(int Nc, int max_smem) {
+  const int smem = coarse_cluster_smem(Nc);
+  if (smem > max_smem) return false;
+  if (cudaFuncSetAttribute(k_coarse_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCC);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_coarse_solve_cluster, &cfg) != cudaSuccess) n = 0;
+  cudaGetLastError();
+  return n > 0;
+}
+
+cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, cudaStream_t s) {
+  if (sym && cluster) {
+    cudaError_t e = cudaMemsetAsync(b.cabort, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCC);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)coarse_cluster_smem(Nc);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_coarse_solve_cluster, Nc, m, (const double*)b.Lc,
+                           (const double*)b.Lr, (const double*)b.cblk, (const double*)b.cdinv,
+                           (const double*)b.rc, b.pc, b.cabort, b.status);
+    count_launches(1);
+    return e;
+  }
   if (sym) {
     const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
     cudaError_t e = cudaFuncSetAttribute(k_ldlt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
