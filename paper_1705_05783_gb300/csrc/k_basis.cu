@@ -139,52 +139,74 @@ __global__ void __launch_bounds__(256) k_entity_solve(
       build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
     }
     __syncthreads();
-    // banded LDL^T with forward elimination of the right-hand sides
+    // banded LDL^T with forward elimination of the right-hand sides.  The
+    // reciprocal pivot 1/d_k is formed once, by the thread that completes
+    // d_k, and kept in the factor (slot 0 of row k) for the D^{-1} step.
+    __shared__ double s_inv;
+    const int lnr = __ffs(nr) - 1;                 // nr is a power of two
+    if (tid == 0) {
+      double d0 = W[0];
+      if (!(d0 > 0.0) || !isfinite(d0)) {
+        atomicOr(status, kStatSingular);
+        d0 = 1.0;
+      }
+      s_inv = 1.0 / d0;
+    }
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
       const int amax = min(m, n - 1 - k);
-      double dk = W[(k % mp) * mp];
-      if (!(dk > 0.0) || !isfinite(dk)) {
-        if (tid == 0) atomicOr(status, kStatSingular);
-        dk = 1.0;
-      }
-      const double inv = 1.0 / dk;
+      const int ks = k % mp;                       // ring slot of row k
+      const double inv = s_inv;
       for (int a = 1 + tid; a <= amax; a += nt) {
-        double* w = W + ((k + a) % mp) * mp + a;
+        int sl = ks + a;
+        if (sl >= mp) sl -= mp;
+        double* w = W + sl * mp + a;
         const double u = *w;
         ucol[a] = u;
         lcol[a] = u * inv;
         *w = u * inv;
       }
-      // row k is final: store (d_k, l_{k,k-1}, ..., l_{k,k-m})
-      for (int dd = tid; dd <= m; dd += nt) Lg[(long long)k * mp + dd] = (dd == 0) ? dk : W[(k % mp) * mp + dd];
+      // row k is final: store (1/d_k, l_{k,k-1}, ..., l_{k,k-m})
+      for (int dd = tid; dd <= m; dd += nt) Lg[(long long)k * mp + dd] = (dd == 0) ? inv : W[ks * mp + dd];
       __syncthreads();
-      // rank-1 update of the trailing window and of the right-hand sides
-      const int npair = amax * amax;
-      for (int t = tid; t < npair; t += nt) {
-        const int a = t / amax + 1, bb = t % amax + 1;
-        if (bb <= a) W[((k + a) % mp) * mp + (a - bb)] -= lcol[a] * ucol[bb];
+      // rank-1 update of the trailing window (lower triangle only): warp w
+      // takes rows a = 1 + w, 1 + w + nw, ..., its lanes the columns b <= a
+      for (int a = 1 + (tid >> 5); a <= amax; a += nt >> 5) {
+        int sl = ks + a;
+        if (sl >= mp) sl -= mp;
+        double* wr = W + sl * mp + a;              // wr[-b] = W(k+a, k+b)
+        const double la = lcol[a];
+        for (int bb = 1 + (tid & 31); bb <= a; bb += 32) wr[-bb] -= la * ucol[bb];
+        if (a == 1 && (tid & 31) == 0) {           // d_{k+1} is final: its reciprocal
+          double d1 = wr[-1];
+          if (!(d1 > 0.0) || !isfinite(d1)) {
+            atomicOr(status, kStatSingular);
+            d1 = 1.0;
+          }
+          s_inv = 1.0 / d1;
+        }
       }
-      for (int t = tid; t < amax * nr; t += nt) {
-        const int a = t / nr + 1, r = t % nr;
+      for (int t = tid; t < (amax << lnr); t += nt) {
+        const int a = (t >> lnr) + 1, r = t & (nr - 1);
         Y[(k + a) * nr + r] -= lcol[a] * Y[k * nr + r];
       }
       // the slot of row k receives row k + m + 1
       const int nxt = k + m + 1;
       if (nxt < n) {
-        double* dst = W + (k % mp) * mp;
+        double* dst = W + ks * mp;
         // copy the band part that was prepared in the scratch row
         for (int dd = tid; dd <= m; dd += nt) dst[dd] = Lg[(long long)nxt * mp + dd];
       }
       __syncthreads();
     }
     // D^{-1}
-    for (int t = tid; t < n * nr; t += nt) Y[t] /= Lg[(long long)(t / nr) * mp];
+    for (int t = tid; t < n * nr; t += nt) Y[t] *= Lg[(long long)(t >> lnr) * mp];
     __syncthreads();
     // backward substitution with L^T
     for (int k = n - 1; k > 0; --k) {
       const int amax = min(m, k);
-      for (int t = tid; t < amax * nr; t += nt) {
-        const int dd = t / nr + 1, r = t % nr;
+      for (int t = tid; t < (amax << lnr); t += nt) {
+        const int dd = (t >> lnr) + 1, r = t & (nr - 1);
         Y[(k - dd) * nr + r] -= Lg[(long long)k * mp + dd] * Y[k * nr + r];
       }
       __syncthreads();
