@@ -36,7 +36,7 @@ from workloads import WORKLOADS, make_inputs  # noqa: E402
 METRIC = ("Newton-step wall time & fine-cell·iters/s to 1e-8 residual; "
           "learned/FP32 vs FP64 C-AMS")
 UNIT = "fine-cell·iters/s"
-DEFAULT_WORKLOAD = "3d-200x200x100"
+DEFAULT_WORKLOAD = "3d-200x200x100-mixed"
 
 # Algorithmic bytes per fine cell of each kernel class (FP64; every array
 # touched once, neighbour re-reads served on chip).
@@ -52,6 +52,16 @@ BYTES_PER_CELL = {
     "ilu_factor": 88,          # A x4 -> 1/d, scaled couplings x6
     "basis_op": 64,
 }
+# the same classes with the FP32 preconditioner (4-byte operands; r stays FP64)
+BYTES_PER_CELL_MIXED = dict(BYTES_PER_CELL, **{
+    "restrict": 40,            # P x8 (FP32), r
+    "prolong": 36,             # P x8 -> delta (FP32)
+    "ilu_resid": 36,           # A x4, delta, 1/d (FP32), r (FP64) -> D^{-1}(r - A delta)
+    "ilu_fwd": 24,             # FP32 forward sweep
+    "ilu_bwd": 36,             # FP32 backward sweep; delta += z
+    "galerkin": 64,            # P x8 (FP32), couplings x3, C
+    "ilu_factor": 108,         # A (FP64) -> A (FP32); pivots and scaled couplings in FP32
+})
 
 
 def parse():
@@ -63,6 +73,8 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="mixed-precision workloads: skip the FP64 comparison run")
     return ap.parse_args()
 
 
@@ -155,12 +167,12 @@ def _handles(cams, w, inp, memspace, dev_arrays=None):
     opt = cams.make_options(w.coarse, basis=w.basis, restriction=w.restriction, n_pre=w.n_pre,
                             n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
                             adapt_theta=w.adapt_theta, max_newton=w.max_newton,
-                            max_cams=w.max_cams, memspace=memspace)
+                            max_cams=w.max_cams, memspace=memspace, precision=w.precision)
     k = dev_arrays if dev_arrays is not None else (inp["kx"], inp["ky"], inp["kz"])
     return cams.cams_setup(grid, fluid, opt, *k)
 
 
-def run_cams(args, w, rank, world, local_rank):
+def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
     import torch
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -220,8 +232,20 @@ def run_cams(args, w, rank, world, local_rank):
     n_l, ms_tot, _ = prof[dom]
     avg_ms = ms_tot / n_l
     peak, peak_kind = measured_peaks()
-    bytes_per_launch = BYTES_PER_CELL[dom] * N
+    bytes_per_launch = (BYTES_PER_CELL_MIXED if w.precision else BYTES_PER_CELL)[dom] * N
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+
+    p_final = p.cpu().numpy()
+    if not e2e_leg:
+        cams.cams_destroy(h)
+        return {"value": value, "unit": UNIT, "ms_per_step": t_ms / args.steps,
+                "dtype": "f32+f64" if w.precision else "f64",
+                "newton_its_per_step": newton / args.steps, "cams_its_per_step": its / args.steps,
+                "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                             "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms},
+                "_p": p_final}
 
     # end to end through the C-ABI with HOST buffers (copies inside the timed region)
     h_host = _handles(cams, w, inp, cams.CAMS_HOST)
@@ -250,8 +274,9 @@ def run_cams(args, w, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name} FP64 C-AMS basis B{w.basis} "
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.precision else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name} {'mixed FP32/FP64' if w.precision else 'FP64'} C-AMS basis B{w.basis} "
                                f"{'MSFE' if w.restriction == 0 else 'MSFV'} n_post={w.n_post} "
                                f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}",
                    "cells": N, "time_step": "first (full basis build) from p=0",
@@ -270,6 +295,7 @@ def run_cams(args, w, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "_p": p_final,
     }
     return out
 
@@ -338,6 +364,16 @@ def main():
         out = run_reference(args, w, rank, world)
     else:
         out = run_cams(args, w, rank, world, local_rank)
+        if w.precision and not args.no_fp64:
+            # the same step with every stage in FP64, measured the same way
+            ref = run_cams(args, w.with_(precision=0), rank, world, local_rank, e2e_leg=False)
+            p64 = ref.pop("_p")
+            out["fp64"] = ref
+            err = float(np.abs(out["_p"] - p64).max() / max(np.abs(p64).max(), 1e-300))
+            out["error_vs_fp64"] = {"rel_linf": err, "note": "final pressure of the mixed step "
+                                    "against the FP64 step (the FP64 engine is held to the "
+                                    "FP64 oracle by the parity tests)"}
+        out.pop("_p", None)
         if rank == 0 and world == 1 and not args.no_baseline:
             v, dt, st, sample = oracle_sample(w, args.seed)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores_used(),

@@ -98,7 +98,18 @@ typedef struct {
   int max_newton;      /* linearisations per time step (<= 64) */
   int max_cams;        /* C-AMS iterations per linearisation */
   int memspace;        /* CAMS_HOST or CAMS_DEVICE for every pointer argument */
+  int precision;       /* CAMS_PREC_FP64: every stage in FP64.  CAMS_PREC_MIXED: the
+                          multiscale preconditioner (basis solves and P, restriction and
+                          prolongation, ILU(0) factor and sweeps) runs in FP32 on the
+                          correction equation A delta = r inside FP64 iterative refinement;
+                          assembly, the residual r = f - A p, the update p += delta, the
+                          Galerkin product R A P and the coarse factorisation and solve stay
+                          FP64.  Converges to the same fixed point (the FP64 residual decides
+                          the stopping tests). */
 } cams_options;
+
+#define CAMS_PREC_FP64  0
+#define CAMS_PREC_MIXED 1
 
 /* Per-step statistics filled by cams_solve. */
 typedef struct {
@@ -118,11 +129,13 @@ typedef struct {
 #define CAMS_Q_RHS        3  /* double N: f of Eq. 6 (rows scaled by V rho) */
 #define CAMS_Q_EPS        4  /* double N: nonlinear error of Eq. 19 at the linearisation point */
 #define CAMS_Q_PRESSURE   5  /* double N: the handle's current iterate p */
-#define CAMS_Q_PROLONG    6  /* double 8N: P values, slot-major (slot s, cell i at s*N + i) */
+#define CAMS_Q_PROLONG    6  /* double 8N: P values, slot-major (slot s, cell i at s*N + i);
+                                the FP32 values widened in mixed precision */
 #define CAMS_Q_PROLONG_J  7  /* int 8N: coarse column of each P slot, -1 where the slot is unused */
 #define CAMS_Q_COARSE     8  /* double 27*Nc: R A P as a 27-point coarse stencil, row I at 27*I,
                                 neighbour (dx,dy,dz) in {-1,0,1}^3 at (dx+1) + 3(dy+1) + 9(dz+1) */
-#define CAMS_Q_ILU_DIAG   9  /* double N: ILU(0) pivots d~_i (the only entries ILU(0) changes) */
+#define CAMS_Q_ILU_DIAG   9  /* double N: ILU(0) pivots d~_i (the only entries ILU(0) changes);
+                                of the FP32 copy of A in mixed precision */
 #define CAMS_Q_RESIDUAL  10  /* double N: f - A p for the current p */
 #define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, entities rebuilt by the last update, 0 */
 #define CAMS_Q_PROFILE   12  /* double 3*CAMS_PROF_CLASSES: per kernel class {launches, total ms,

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcams.so")
 CAMS_OK, CAMS_EINVAL, CAMS_ENOMEM, CAMS_ECUDA = 0, -1, -2, -3
 CAMS_ENOCONV, CAMS_ESINGULAR, CAMS_ETIMEOUT, CAMS_ENAN = -4, -5, -6, -7
 CAMS_HOST, CAMS_DEVICE = 0, 1
+CAMS_PREC_FP64, CAMS_PREC_MIXED = 0, 1
 CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 4, 5
 CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
 CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES = 11, 12, 13
@@ -57,7 +58,8 @@ class cams_options(C.Structure):
     _fields_ = [("coarse", C.c_int * 3), ("basis", C.c_int), ("restriction", C.c_int),
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("lin_rtol", C.c_double),
                 ("nl_tol", C.c_double), ("tol_abs", C.c_int), ("adapt_theta", C.c_double),
-                ("max_newton", C.c_int), ("max_cams", C.c_int), ("memspace", C.c_int)]
+                ("max_newton", C.c_int), ("max_cams", C.c_int), ("memspace", C.c_int),
+                ("precision", C.c_int)]
 
 
 class cams_stats(C.Structure):
@@ -136,13 +138,14 @@ def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None
 
 def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1,
                  nl_tol=1e-6, tol_abs=False, adapt_theta=0.1, max_newton=50, max_cams=200,
-                 memspace=CAMS_HOST):
+                 memspace=CAMS_HOST, precision=CAMS_PREC_FP64):
     o = cams_options()
     o.coarse[:] = [int(v) for v in coarse]
     o.basis, o.restriction, o.n_pre, o.n_post = int(basis), int(restriction), int(n_pre), int(n_post)
     o.lin_rtol, o.nl_tol, o.tol_abs = float(lin_rtol), float(nl_tol), int(bool(tol_abs))
     o.adapt_theta, o.max_newton, o.max_cams = float(adapt_theta), int(max_newton), int(max_cams)
     o.memspace = int(memspace)
+    o.precision = int(precision)
     return o
 
 

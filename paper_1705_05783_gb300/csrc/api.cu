@@ -47,6 +47,7 @@ struct cams_handle {
   double pw = 0.0, pe = 0.0, rhow = 1.0, rhoe = 1.0;
   int last_rebuilt = 0;
   long long launch_base = 0;
+  bool single = false;          // mixed precision: FP32 preconditioner (b.f32)
   bool ilu_pipelined = true;    // false: level-scheduled sweeps (CAMS_ILU_LEVEL=1)
   bool coarse_cluster = false;  // MSFE coarse solve across a cluster (CAMS_COARSE_CLUSTER=0: one CTA)
   int ilu_grid = 1;
@@ -252,7 +253,19 @@ int alloc_all(cams_handle* h) {
   AL(b.f, N); AL(b.eps, N);
   AL(b.Abd, N); AL(b.Abx, N); AL(b.Aby, N); AL(b.Abz, N);
   if (h->opt.basis != 4) AL(b.snap, 7 * N);
-  AL(b.P, 8 * N);
+  if (!h->single) AL(b.P, 8 * N);
+  if (h->single) {
+    SingleBuffers& f = b.f32;
+    const long long S = ilu_skew_len(h->g);
+    AL(f.Ad, N); AL(f.Ax, N); AL(f.Ay, N); AL(f.Az, N); AL(f.dinv, N); AL(f.d, N);
+    AL(f.P, 8 * N); AL(f.pc, h->c.Nc);
+    AL(f.Lx, S); AL(f.Ly, S); AL(f.Lz, S); AL(f.Ux, S); AL(f.Uy, S); AL(f.Uz, S);
+    AL(f.rds, S); AL(f.w, S); AL(f.z, S);
+    // slots that hold no cell must read as zero (the sweeps run branch-free over them)
+    for (float* v : {f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz, f.rds, f.w, f.z})
+      if (cudaMemset(v, 0, sizeof(float) * (size_t)S) != cudaSuccess)
+        return fail(h, CAMS_ECUDA, "cudaMemset failed");
+  }
   AL(b.ent_of_cell, N);
   AL(b.ents, h->ents.size());
   AL(b.flag, h->ents.size());
@@ -292,6 +305,11 @@ void free_all(cams_handle* h) {
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  const SingleBuffers& f = b.f32;
+  void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
+                   f.rds, f.w, f.z, f.d, f.P, f.pc};
+  for (void* p : fptrs)
+    if (p) cudaFree(p);
   h->b = Buffers{};
 }
 
@@ -316,6 +334,8 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
   if (o->max_newton < 1 || o->max_newton > kMaxNewton) return fail(nullptr, CAMS_EINVAL, "max_newton must be 1..64");
   if (o->max_cams < 1) return fail(nullptr, CAMS_EINVAL, "max_cams must be >= 1");
   if (o->memspace != CAMS_HOST && o->memspace != CAMS_DEVICE) return fail(nullptr, CAMS_EINVAL, "bad memspace");
+  if (o->precision != CAMS_PREC_FP64 && o->precision != CAMS_PREC_MIXED)
+    return fail(nullptr, CAMS_EINVAL, "precision must be CAMS_PREC_FP64 or CAMS_PREC_MIXED");
   if ((long long)gr->nx * gr->ny * gr->nz > (1LL << 31) - 1) return fail(nullptr, CAMS_EINVAL, "grid too large");
   return CAMS_OK;
 }
@@ -411,11 +431,12 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   }
   if (rebuilt > 0) {
     ProfScope ps_(h, CAMS_PROF_BASIS);
-    if (!h->built) CK(launch_vertices(h->g, h->c, b.P, h->stream));
+    if (!h->built) CK(launch_vertices(h->g, h->c, b, h->single, h->stream));
     for (int lev = 1; lev <= 3; ++lev) {
       const int f = h->lev_first[lev];
       CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
-                             h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, b, h->stream));
+                             h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, h->single,
+                             b, h->stream));
     }
   }
   h->built = true;
@@ -423,16 +444,16 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   if (n_rebuilt) *n_rebuilt = rebuilt;
   // Galerkin coarse operator and its factorisation
   if (o.restriction == 0)
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
   else
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     const int sym = o.restriction == 0;   // MSFE: R A P = P^T A P is symmetric
     CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
     CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
   }
-  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->single, h->stream));
   return check_status(h);
 }
 
@@ -446,30 +467,46 @@ int residual_norm(cams_handle* h, double* out) {
   return CAMS_OK;
 }
 
-// One ILU(0) smoothing step p <- p + M^{-1}(f - A p).
+// One ILU(0) smoothing step: p <- p + M^{-1}(f - A p) in FP64, or in mixed
+// precision delta <- delta + M^{-1}(r - A delta) in FP32 (r the FP64
+// residual of the current p).
 int ilu_smooth(cams_handle* h) {
-  LAUNCH(CAMS_PROF_ILU_RESID, launch_ilu_resid(h->g, h->b, h->stream));
-  LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, h->stream));
-  LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, h->stream));
+  const bool s = h->single;
+  LAUNCH(CAMS_PROF_ILU_RESID, launch_ilu_resid(h->g, h->b, s, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, s, h->stream));
+  LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, s, h->stream));
   return CAMS_OK;
 }
 
-// One C-AMS iteration (Table 1 steps 4-7 with ILU(0) smoothing).
+// One C-AMS iteration (Table 1 steps 4-7 with ILU(0) smoothing).  On entry
+// b.r holds f - A p for the current p (residual_norm computed it).
+//
+// Mixed precision runs the same iteration on the correction: delta =
+// P (R A P)^{-1} R r, then n_post smoothing steps on A delta = r, then
+// p += delta; f - A(p + delta) = r - A delta, so this is the FP64
+// iteration with the preconditioner rounded to FP32.  Pre-smoothing steps
+// are applied the same way and added to p before the coarse correction.
 int cams_step(cams_handle* h) {
   Buffers& b = h->b;
-  for (int k = 0; k < h->opt.n_pre; ++k) {
-    int rc = ilu_smooth(h);
-    if (rc) return rc;
+  const bool s = h->single;
+  if (h->opt.n_pre > 0) {
+    if (s) CK(cudaMemsetAsync(b.f32.d, 0, sizeof(float) * h->g.N, h->stream));
+    for (int k = 0; k < h->opt.n_pre; ++k) {
+      int rc = ilu_smooth(h);
+      if (rc) return rc;
+    }
+    if (s) LAUNCH(CAMS_PROF_ILU_BWD, launch_add_correction(h->g, b, h->stream));
+    LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
   }
-  LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
-  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, h->opt.restriction, b.r, b, h->stream));
+  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, h->opt.restriction, b.r, s, b, h->stream));
   LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, h->opt.restriction == 0,
                                                    h->coarse_cluster, b, h->stream));
-  LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, b, h->stream));
+  LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, s, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
     int rc = ilu_smooth(h);
     if (rc) return rc;
   }
+  if (s) LAUNCH(CAMS_PROF_ILU_BWD, launch_add_correction(h->g, b, h->stream));
   return CAMS_OK;
 }
 
@@ -508,6 +545,7 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   h->grid = *grid;
   h->fluid = *fluid;
   h->opt = *opt;
+  h->single = opt->precision == CAMS_PREC_MIXED;
   cudaGetDevice(&h->dev);
   Geo& g = h->g;
   g.nx = grid->nx; g.ny = grid->ny; g.nz = grid->nz;
@@ -541,7 +579,7 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     for (int e = h->lev_first[lev]; e < h->lev_first[lev] + h->lev_count[lev]; ++e) {
       const Entity& E = h->ents[e];
       const int mp = E.m + 1;
-      sm = std::max(sm, (int)sizeof(double) * (mp * mp + E.n * E.nrhs + 2 * mp));
+      sm = std::max(sm, (int)(h->single ? sizeof(float) : sizeof(double)) * (mp * mp + E.n * E.nrhs + 2 * mp));
       ls = std::max(ls, (long long)E.n * mp);
     }
     h->lev_smem[lev] = sm;
@@ -820,14 +858,35 @@ int cams_get(cams_handle* h, int what, double* dst) {
     case CAMS_Q_RHS: CK(cudaMemcpyAsync(dst, b.f, sizeof(double) * N, k, s)); break;
     case CAMS_Q_EPS: CK(cudaMemcpyAsync(dst, b.eps, sizeof(double) * N, k, s)); break;
     case CAMS_Q_PRESSURE: CK(cudaMemcpyAsync(dst, b.p, sizeof(double) * N, k, s)); break;
-    case CAMS_Q_PROLONG: CK(cudaMemcpyAsync(dst, b.P, sizeof(double) * 8 * N, k, s)); break;
+    case CAMS_Q_PROLONG: {
+      if (!h->single) {
+        CK(cudaMemcpyAsync(dst, b.P, sizeof(double) * 8 * N, k, s));
+        break;
+      }
+      std::vector<float> tf(8 * N);
+      std::vector<double> td(8 * N);
+      CK(cudaMemcpyAsync(tf.data(), b.f32.P, sizeof(float) * 8 * N, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (long long i = 0; i < 8 * N; ++i) td[i] = tf[i];
+      CK(cudaMemcpyAsync(dst, td.data(), sizeof(double) * 8 * N,
+                         h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      CK(cudaStreamSynchronize(s));
+      break;
+    }
     case CAMS_Q_COARSE: CK(cudaMemcpyAsync(dst, b.Acs, sizeof(double) * 27 * h->c.Nc, k, s)); break;
     case CAMS_Q_ILU_DIAG: {
       // d_i = 1 / dinv_i, formed in the residual work vector
       std::vector<double> tmp(N);
-      CK(cudaMemcpyAsync(tmp.data(), b.dinv, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      for (long long i = 0; i < N; ++i) tmp[i] = 1.0 / tmp[i];
+      if (h->single) {
+        std::vector<float> tf(N);
+        CK(cudaMemcpyAsync(tf.data(), b.f32.dinv, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (long long i = 0; i < N; ++i) tmp[i] = 1.0 / (double)tf[i];
+      } else {
+        CK(cudaMemcpyAsync(tmp.data(), b.dinv, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (long long i = 0; i < N; ++i) tmp[i] = 1.0 / tmp[i];
+      }
       CK(cudaMemcpyAsync(dst, tmp.data(), sizeof(double) * N,
                          h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
       break;

@@ -60,6 +60,19 @@ __host__ __device__ inline double rho_of(const FluidK& f, double p) {
 #endif
 }
 
+// FP32 copies used by the mixed-precision preconditioner (allocated only
+// when cams_options.precision is CAMS_PREC_MIXED).
+struct SingleBuffers {
+  float *Ad = nullptr, *Ax = nullptr, *Ay = nullptr, *Az = nullptr;   // A in FP32
+  float* dinv = nullptr;                                  // 1 / ILU(0) pivots
+  float *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;      // scaled couplings, skewed
+  float *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;
+  float *rds = nullptr, *w = nullptr, *z = nullptr;       // smoother vectors, skewed
+  float* d = nullptr;                                     // the correction delta (N)
+  float* P = nullptr;                                     // 8N, slot-major
+  float* pc = nullptr;                                    // coarse solution (band order)
+};
+
 // Device buffers, one allocation each, owned by the handle.
 struct Buffers {
   double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr;     // transmissibilities (lower faces)
@@ -95,6 +108,7 @@ struct Buffers {
   double* red = nullptr;                                  // reduction partials
   double* scal = nullptr;                                 // reduced scalars (device)
   int* status = nullptr;                                  // device status word
+  SingleBuffers f32;                                      // mixed precision only
 };
 
 // Bits of the device status word (set by kernels, read by the host).
@@ -131,27 +145,34 @@ cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, doub
 cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& b,
                                    cudaStream_t s);
 cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out, cudaStream_t s);
-cudaError_t launch_vertices(const Geo& g, const CGeo& c, double* P, cudaStream_t s);
+// single: P and the local solves in FP32 (mixed precision), else FP64.
+cudaError_t launch_vertices(const Geo& g, const CGeo& c, Buffers& b, bool single, cudaStream_t s);
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                Buffers& b, cudaStream_t s);
+                                bool single, Buffers& b, cudaStream_t s);
 cudaError_t set_entity_smem(int smem);
 cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, Buffers& b, cudaStream_t s);
+                               double rhoe, bool single, Buffers& b, cudaStream_t s);
 cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, Buffers& b, cudaStream_t s);
+                               double rhoe, bool single, Buffers& b, cudaStream_t s);
 cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
-cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
-                            cudaStream_t s);
+cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, bool single,
+                            Buffers& b, cudaStream_t s);
 cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, cudaStream_t s);
 long long coarse_blocks_len(int Nc);
 bool coarse_cluster_ok(int Nc, int max_smem);
-cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s);
-cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s);
-cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s);
+// FP64: p += P p_c; single: delta = P p_c (FP32 P and delta)
+cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s);
+// single: the FP32 smoother of the mixed-precision preconditioner (on
+// A delta = r, vectors in b.f32); otherwise the FP64 smoother on A p = f.
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, bool single,
+                              cudaStream_t s);
+cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s);
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
-                             cudaStream_t s);
+                             bool single, cudaStream_t s);
+cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s);   // p += delta
 int ilu_ctrl_ints(const Geo& g);
 // Rows per wavefront tile (y, z) and the length of a skewed sweep vector.
 constexpr int kIluTY = 8, kIluTZ = 4, kIluR = kIluTY * kIluTZ;   // one warp per tile

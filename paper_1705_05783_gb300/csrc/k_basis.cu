@@ -10,7 +10,9 @@
 // memory as a ring of rows.  All right-hand sides (one per corner vertex,
 // 2^free) are carried through the forward elimination in shared memory; the
 // finished rows of L stream to a per-CTA scratch slice (L2-resident) for the
-// backward substitution.  FP64; no atomics, so the result is deterministic.
+// backward substitution.  No atomics, so the result is deterministic.  The
+// local solve and P are FP64, or FP32 for the mixed-precision preconditioner
+// (the basis operator is read in FP64 and rounded).
 #include "cams_internal.h"
 
 namespace cams {
@@ -64,13 +66,14 @@ __device__ __forceinline__ int local_stride(const Entity& E, int d) {
 }
 
 // Build row l of M (lower band, ring slot) and the right-hand sides of row l.
-__device__ void build_row(const Geo& g, const Entity& E, int l, double* Wrow, double* Yrow,
+template <class T>
+__device__ void build_row(const Geo& g, const Entity& E, int l, T* Wrow, T* Yrow,
                           const double* Abd, const double* Abx, const double* Aby,
-                          const double* Abz, const double* P) {
+                          const double* Abz, const T* P) {
   Local c = local_cell(E, l);
   const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
-  for (int dd = 0; dd <= E.m; ++dd) Wrow[dd] = 0.0;
-  for (int r = 0; r < E.nrhs; ++r) Yrow[r] = 0.0;
+  for (int dd = 0; dd <= E.m; ++dd) Wrow[dd] = T(0);
+  for (int r = 0; r < E.nrhs; ++r) Yrow[r] = T(0);
   double diag = Abd[i];
   for (int d = 0; d < 3; ++d) {
     const int n_d = gextent(g, d);
@@ -86,12 +89,12 @@ __device__ void build_row(const Geo& g, const Entity& E, int l, double* Wrow, do
     }
     // free direction: inside the box -> band entry; outside -> known data
     if (c.c[d] > E.org[d]) {
-      Wrow[local_stride(E, d)] = lo;
+      Wrow[local_stride(E, d)] = T(lo);
     } else if (c.c[d] > 0) {
       const long long j = i - sd;
       for (int r = 0; r < E.nrhs; ++r) {
         const int s = slot_of(r, E.free_mask);
-        if (!(s & (1 << d))) Yrow[r] -= lo * P[(long long)s * g.N + j];
+        if (!(s & (1 << d))) Yrow[r] -= T(lo) * P[(long long)s * g.N + j];
       }
     }
     if (c.c[d] < E.org[d] + E.L[d] - 1) {
@@ -100,68 +103,71 @@ __device__ void build_row(const Geo& g, const Entity& E, int l, double* Wrow, do
       const long long j = i + sd;
       for (int r = 0; r < E.nrhs; ++r) {
         const int s = slot_of(r, E.free_mask);
-        if (s & (1 << d)) Yrow[r] -= up * P[(long long)(s & ~(1 << d)) * g.N + j];
+        if (s & (1 << d)) Yrow[r] -= T(up) * P[(long long)(s & ~(1 << d)) * g.N + j];
       }
     }
   }
-  Wrow[0] = diag;
+  Wrow[0] = T(diag);
 }
 
-__global__ void k_vertices(Geo g, CGeo c, double* P) {
+template <class T>
+__global__ void k_vertices(Geo g, CGeo c, T* P) {
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (J >= c.Nc) return;
   const int Jx = J % c.nc[0], Jy = (J / c.nc[0]) % c.nc[1], Jz = J / (c.nc[0] * c.nc[1]);
   const long long v = (Jx * c.b[0] + c.o[0]) + g.sy * (Jy * c.b[1] + c.o[1]) +
                       g.sz * (Jz * c.b[2] + c.o[2]);
-  for (int s = 0; s < 8; ++s) P[(long long)s * g.N + v] = (s == 0) ? 1.0 : 0.0;
+  for (int s = 0; s < 8; ++s) P[(long long)s * g.N + v] = (s == 0) ? T(1) : T(0);
 }
 
+template <class T>
 __global__ void __launch_bounds__(256) k_entity_solve(
     Geo g, const Entity* __restrict__ ents, int count, const unsigned char* __restrict__ flag,
     int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
-    const double* __restrict__ Aby, const double* __restrict__ Abz, double* P, double* snap,
-    double* lscratch, long long lstride, int* status) {
-  extern __shared__ double sm[];
+    const double* __restrict__ Aby, const double* __restrict__ Abz, T* P, double* snap,
+    T* lscratch, long long lstride, int* status) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
-  double* Lg = lscratch + (long long)blockIdx.x * lstride;
+  T* Lg = lscratch + (long long)blockIdx.x * lstride;
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     if (flag && !flag[e]) continue;
     const Entity E = ents[e];
     const int n = E.n, m = E.m, nr = E.nrhs, mp = m + 1;
-    double* W = sm;                 // mp * mp ring
-    double* Y = W + mp * mp;        // n * nr
-    double* lcol = Y + n * nr;      // mp
-    double* ucol = lcol + mp;       // mp
+    T* W = sm;                      // mp * mp ring
+    T* Y = W + mp * mp;             // n * nr
+    T* lcol = Y + n * nr;           // mp
+    T* ucol = lcol + mp;            // mp
     // rows 0..m go to the ring; rows beyond the first window are staged in
     // the scratch slice (row l at l*mp) until they enter the ring
     for (int l = tid; l < n; l += nt) {
-      double* row = (l <= m) ? W + l * mp : Lg + (long long)l * mp;
+      T* row = (l <= m) ? W + l * mp : Lg + (long long)l * mp;
       build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
     }
     __syncthreads();
     // banded LDL^T with forward elimination of the right-hand sides.  The
     // reciprocal pivot 1/d_k is formed once, by the thread that completes
     // d_k, and kept in the factor (slot 0 of row k) for the D^{-1} step.
-    __shared__ double s_inv;
+    __shared__ T s_inv;
     const int lnr = __ffs(nr) - 1;                 // nr is a power of two
     if (tid == 0) {
-      double d0 = W[0];
-      if (!(d0 > 0.0) || !isfinite(d0)) {
+      T d0 = W[0];
+      if (!(d0 > T(0)) || !isfinite(d0)) {
         atomicOr(status, kStatSingular);
-        d0 = 1.0;
+        d0 = T(1);
       }
-      s_inv = 1.0 / d0;
+      s_inv = T(1) / d0;
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
       const int amax = min(m, n - 1 - k);
       const int ks = k % mp;                       // ring slot of row k
-      const double inv = s_inv;
+      const T inv = s_inv;
       for (int a = 1 + tid; a <= amax; a += nt) {
         int sl = ks + a;
         if (sl >= mp) sl -= mp;
-        double* w = W + sl * mp + a;
-        const double u = *w;
+        T* w = W + sl * mp + a;
+        const T u = *w;
         ucol[a] = u;
         lcol[a] = u * inv;
         *w = u * inv;
@@ -174,16 +180,16 @@ __global__ void __launch_bounds__(256) k_entity_solve(
       for (int a = 1 + (tid >> 5); a <= amax; a += nt >> 5) {
         int sl = ks + a;
         if (sl >= mp) sl -= mp;
-        double* wr = W + sl * mp + a;              // wr[-b] = W(k+a, k+b)
-        const double la = lcol[a];
+        T* wr = W + sl * mp + a;                   // wr[-b] = W(k+a, k+b)
+        const T la = lcol[a];
         for (int bb = 1 + (tid & 31); bb <= a; bb += 32) wr[-bb] -= la * ucol[bb];
         if (a == 1 && (tid & 31) == 0) {           // d_{k+1} is final: its reciprocal
-          double d1 = wr[-1];
-          if (!(d1 > 0.0) || !isfinite(d1)) {
+          T d1 = wr[-1];
+          if (!(d1 > T(0)) || !isfinite(d1)) {
             atomicOr(status, kStatSingular);
-            d1 = 1.0;
+            d1 = T(1);
           }
-          s_inv = 1.0 / d1;
+          s_inv = T(1) / d1;
         }
       }
       for (int t = tid; t < (amax << lnr); t += nt) {
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(256) k_entity_solve(
       // the slot of row k receives row k + m + 1
       const int nxt = k + m + 1;
       if (nxt < n) {
-        double* dst = W + ks * mp;
+        T* dst = W + ks * mp;
         // copy the band part that was prepared in the scratch row
         for (int dd = tid; dd <= m; dd += nt) dst[dd] = Lg[(long long)nxt * mp + dd];
       }
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256) k_entity_solve(
     for (int l = tid; l < n; l += nt) {
       Local c = local_cell(E, l);
       const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
-      for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = 0.0;
+      for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = T(0);
       for (int r = 0; r < nr; ++r) P[(long long)slot_of(r, E.free_mask) * g.N + i] = Y[l * nr + r];
       if (adaptive) {
         snap[0 * g.N + i] = Abd[i];
@@ -316,23 +322,37 @@ __global__ void k_count_flags(int count, const unsigned char* __restrict__ flag,
 
 }  // namespace
 
-cudaError_t launch_vertices(const Geo& g, const CGeo& c, double* P, cudaStream_t s) {
-  k_vertices<<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, P); count_launches(1);
+cudaError_t launch_vertices(const Geo& g, const CGeo& c, Buffers& b, bool single, cudaStream_t s) {
+  if (single) k_vertices<float><<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, b.f32.P);
+  else k_vertices<double><<<(c.Nc + 127) / 128, 128, 0, s>>>(g, c, b.P);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                Buffers& b, cudaStream_t s) {
+                                bool single, Buffers& b, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (grid > count) grid = count;
-  k_entity_solve<<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby,
-                                         b.Abz, b.P, b.snap, b.lscratch, lstride, b.status); count_launches(1);
+  if (single)
+    k_entity_solve<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
+                                                  b.Aby, b.Abz, b.f32.P, b.snap,
+                                                  reinterpret_cast<float*>(b.lscratch), lstride,
+                                                  b.status);
+  else
+    k_entity_solve<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
+                                                   b.Aby, b.Abz, b.P, b.snap, b.lscratch, lstride,
+                                                   b.status);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t set_entity_smem(int smem) {
-  return cudaFuncSetAttribute(k_entity_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_entity_solve<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_entity_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
 }
 
 cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,

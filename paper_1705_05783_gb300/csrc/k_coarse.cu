@@ -7,6 +7,9 @@
 // nodes spanning the cell's dual block (a cell on a vertex plane of d uses
 // bit 0 for that plane's node and never bit 1).
 //
+// P is FP64, or FP32 in the mixed-precision preconditioner; products with P
+// are formed and summed in FP64 either way.
+//
 // Deterministic reductions only: every sum over fine cells is a fixed-shape
 // block tree, and every sum over blocks runs in a fixed block order, so the
 // MSFE matrix is bitwise symmetric.
@@ -65,8 +68,9 @@ __device__ __forceinline__ int sym_idx(int s, int t) {   // upper triangle of 8x
 // MSFE: per dual block, the 8x8 block sum over its cells and its low-side
 // faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T  (A = sum of face
 // terms + diagonal D = C + Dirichlet terms).
+template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fe_local(
-    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const double* __restrict__ P,
+    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const TP* __restrict__ P,
     const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
     const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
     double* loc) {
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     const long long i = x + g.sy * y + g.sz * z;
     double pi[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) pi[s] = P[(long long)s * g.N + i];
+    for (int s = 0; s < 8; ++s) pi[s] = (double)P[(long long)s * g.N + i];
     double Dd = Cacc[i];
     if (dirichlet) {
       if (x == 0) Dd += Tbw[y + (long long)g.ny * z] * rhow;
@@ -109,8 +113,8 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         double pj;
-        if (inside) pj = P[(long long)s * g.N + jn];
-        else pj = (s & (1 << d)) ? P[(long long)(s & ~(1 << d)) * g.N + jn] : 0.0;
+        if (inside) pj = (double)P[(long long)s * g.N + jn];
+        else pj = (s & (1 << d)) ? (double)P[(long long)(s & ~(1 << d)) * g.N + jn] : 0.0;
         dv[s] = pi[s] - pj;
       }
 #pragma unroll
@@ -163,8 +167,9 @@ __global__ void k_galerkin_fe_gather(CGeo c, const double* __restrict__ loc, dou
 
 // MSFV: row I of R A P = sum over the cells of primal block I of (A P)_i,
 // i.e. D_i P_i plus the fluxes w (P_i - P_j) through the block's faces.
+template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fv(
-    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const double* __restrict__ P,
+    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const TP* __restrict__ P,
     const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
     const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
     double* Acs) {
@@ -177,7 +182,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fv(
   for (int k = 0; k < 27; ++k) acc[k * T + tid] = 0.0;
   auto add_cell = [&](long long cell, const int* xc, double scale) {
     for (int s = 0; s < 8; ++s) {
-      const double v = P[(long long)s * g.N + cell];
+      const double v = (double)P[(long long)s * g.N + cell];
       if (v == 0.0) continue;
       int t = 0, mul = 1;
       bool ok = true;
@@ -744,7 +749,8 @@ __global__ void __launch_bounds__(256) k_band_solve(int Nc, int m, const double*
 }
 
 // MSFE restriction, part 1: per dual block the 8 sums  sum_i P_i[s] r_i.
-__global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const double* __restrict__ P,
+template <class TP>
+__global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const TP* __restrict__ P,
                                                            const double* __restrict__ r, double* part) {
   __shared__ double sh[8 * 32];
   const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
@@ -754,13 +760,18 @@ __global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const 
   for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
   const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
   const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // products and each thread's partial sums in P's precision, the block
+  // tree in FP64 (with FP32 P this widens 8 values per thread, not per cell)
+  TP tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
     const long long i = (lo[0] + l % ex) + g.sy * (lo[1] + (l / ex) % ey) + g.sz * (lo[2] + l / (ex * ey));
-    const double ri = r[i];
+    const TP ri = (TP)r[i];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) acc[s] += P[(long long)s * g.N + i] * ri;
+    for (int s = 0; s < 8; ++s) tacc[s] += P[(long long)s * g.N + i] * ri;
   }
+  double acc[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) acc[s] = (double)tacc[s];
   block_sum_k<8>(acc, sh, part + (long long)D * 8);
 }
 
@@ -800,9 +811,11 @@ __global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double
   if (threadIdx.x == 0) rc[perm[I]] = out;
 }
 
-// p += P p_c
-__global__ void k_prolong_add(Geo g, CGeo c, const double* __restrict__ P, const double* __restrict__ pc,
-                              const int* __restrict__ perm, double* p) {
+// p += P p_c (FP64), or delta = P p_c (the mixed-precision preconditioner:
+// P, p_c and delta in FP32)
+template <class TP, class TO, bool kSet>
+__global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TP* __restrict__ pc,
+                          const int* __restrict__ perm, TO* p) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int xc[3] = {(int)(i % g.nx), (int)((i / g.nx) % g.ny), (int)(i / ((long long)g.nx * g.ny))};
@@ -811,32 +824,48 @@ __global__ void k_prolong_add(Geo g, CGeo c, const double* __restrict__ P, const
     Jl[d][0] = corner_d(c, d, xc[d], 0);
     Jl[d][1] = corner_d(c, d, xc[d], 1);
   }
-  double s = 0.0;
+  TP s = TP(0);
 #pragma unroll
   for (int sl = 0; sl < 8; ++sl) {
     const int jx = Jl[0][sl & 1], jy = Jl[1][(sl >> 1) & 1], jz = Jl[2][(sl >> 2) & 1];
     if (jx < 0 || jy < 0 || jz < 0) continue;
     s += P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
   }
-  p[i] += s;
+  if (kSet) p[i] = (TO)s;
+  else p[i] += (TO)s;
+}
+
+__global__ void k_to_single(int n, const double* __restrict__ a, float* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
 }
 
 }  // namespace
 
 cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, Buffers& b, cudaStream_t s) {
+                               double rhoe, bool single, Buffers& b, cudaStream_t s) {
   const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
-  k_galerkin_fe_local<<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay, b.Az,
-                                         b.Cacc, b.Tbw, b.Tbe, b.loc); count_launches(1);
+  if (single)
+    k_galerkin_fe_local<float><<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.f32.P, b.Ax, b.Ay,
+                                                  b.Az, b.Cacc, b.Tbw, b.Tbe, b.loc);
+  else
+    k_galerkin_fe_local<double><<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay,
+                                                   b.Az, b.Cacc, b.Tbw, b.Tbe, b.loc);
+  count_launches(1);
   k_galerkin_fe_gather<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, b.loc, b.Acs); count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, Buffers& b, cudaStream_t s) {
+                               double rhoe, bool single, Buffers& b, cudaStream_t s) {
   const int T = 128;
-  k_galerkin_fv<<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax,
-                                                          b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs); count_launches(1);
+  if (single)
+    k_galerkin_fv<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+        g, c, dirichlet, rhow, rhoe, b.f32.P, b.Ax, b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+  else
+    k_galerkin_fv<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+        g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -869,11 +898,13 @@ cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, Buffers& b,
-                            cudaStream_t s) {
+cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, bool single,
+                            Buffers& b, cudaStream_t s) {
   if (kind == 0) {
     const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
-    k_restrict_fe_local<<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc); count_launches(1);
+    if (single) k_restrict_fe_local<float><<<nd, 256, 0, s>>>(g, c, b.f32.P, r, b.loc);
+    else k_restrict_fe_local<double><<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc);
+    count_launches(1);
     k_restrict_fe_gather<<<(c.Nc + 127) / 128, 128, 0, s>>>(c, b.loc, b.perm, b.rc); count_launches(1);
   } else {
     k_restrict_fv<<<c.Nc, 256, 0, s>>>(g, c, r, b.perm, b.rc); count_launches(1);
@@ -948,8 +979,16 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, Buffers& b, cudaStream_t s) {
-  k_prolong_add<<<(int)((g.N + 255) / 256), 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p); count_launches(1);
+cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s) {
+  const int blocks = (int)((g.N + 255) / 256);
+  if (single) {
+    k_to_single<<<(c.Nc + 255) / 256, 256, 0, s>>>(c.Nc, b.pc, b.f32.pc);
+    k_prolong<float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm, b.f32.d);
+    count_launches(1);
+  } else
+    k_prolong<double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -2,26 +2,29 @@
 // matrix in natural order.  For this stencil ILU(0) only changes the
 // diagonal: d_i = a_ii - sum_{j in {i-1, i-nx, i-nx*ny}} a_ij a_ji / d_j, and
 // M = (D + L_A) D^{-1} (D + U_A) with L_A, U_A the strict triangles of A.
-// One smoothing step p <- p + M^{-1}(f - A p) is
-//   rd = D^{-1} (f - A p)                         (parallel)
+// One smoothing step x <- x + M^{-1}(b - A x) is
+//   rd = D^{-1} (b - A x)                         (parallel)
 //   w_i = rd_i - sum_{j<i} (a_ij / d_i) w_j       (forward wavefront)
 //   z_i = w_i  - sum_{j>i} (a_ij / d_i) z_j       (backward wavefront)
-//   p += z
+//   x += z
 // with the couplings pre-scaled by the row pivot once per factorisation, so
-// every cell of a sweep is a chain of at most three FMAs.
+// every cell of a sweep is a chain of at most three FMAs.  In FP64 (b, x) =
+// (f, p).  In the mixed-precision preconditioner the smoother runs in FP32
+// on the correction equation A delta = r, (b, x) = (r, delta), with an FP32
+// copy of A; r is the FP64 residual and p += delta is taken in FP64.
 //
 // Layout.  The sweep vectors (rd, the scaled couplings, w, z) are stored
 // "skewed tile-major": the (y, z) cross-section is cut into tiles of
 // kIluTY x kIluTZ = 32 x-rows, one warp each, and cell (x, y, z) of tile T,
 // row (ty, tz) sits at record T * ns + x + ty + tz, slot ty + kIluTY * tz
-// (ns >= nx + kIluTY + kIluTZ - 2 records per tile, 32 doubles per record,
+// (ns >= nx + kIluTY + kIluTZ - 2 records per tile, 32 values per record,
 // plus kPad spare records at both ends).  A tile advances one "step" s at a
 // time and row (ty, tz) works on x = s - ty - tz, so the 32 cells of one
-// step are one contiguous 256-byte record.  Slots that hold no cell (the
-// pipeline's fill and drain, rows beyond the grid) are zero in rd and in
-// the couplings, so every step runs the same branch-free arithmetic; the
-// values computed there are never read by a cell.  Pivots (dinv) stay in
-// natural order.
+// step are one contiguous record.  Slots that hold no cell (the pipeline's
+// fill and drain, rows beyond the grid) are zero in rd and in the
+// couplings, so every step runs the same branch-free arithmetic; the values
+// computed there are never read by a cell.  Pivots (dinv) stay in natural
+// order.
 //
 // Two schedules of the same arithmetic (bitwise identical results):
 //  * level-scheduled: one launch per hyperplane x+y+z = L (reference);
@@ -33,11 +36,11 @@
 //    another tile are read from the sweep's output vector itself, which is
 //    pre-filled with a signalling-NaN sentinel that no arithmetic produces:
 //    a value is ready once it differs from the sentinel, so no flags or
-//    fences are needed (8-byte values are written and read with single-copy
-//    atomic relaxed accesses at device scope); they are fetched one group
-//    ahead and re-polled only when still unset.  Tiles are claimed through
-//    an atomic ticket in anti-diagonal order, so a warp only ever waits on
-//    tiles already claimed by running warps: no co-residency assumption, no
+//    fences are needed (values are written and read with single-copy atomic
+//    relaxed accesses at device scope); they are fetched one group ahead and
+//    re-polled only when still unset.  Tiles are claimed through an atomic
+//    ticket in anti-diagonal order, so a warp only ever waits on tiles
+//    already claimed by running warps: no co-residency assumption, no
 //    deadlock.  Every wait has an iteration limit; on expiry the kernel sets
 //    an abort flag and the status word and all warps leave.  One CTA of
 //    four warps per SM keeps one sweeping warp per FP64 pipe.
@@ -59,9 +62,28 @@ constexpr int kPad = kG * kU;                // spare records at both ends of a 
 constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ a second)
 constexpr int kFastPolls = 64;               // in-loop polls before a wait starts to sleep
 
-// "Not computed yet": a signalling-NaN bit pattern.  IEEE arithmetic never
-// produces a signalling NaN, so no computed value carries this pattern.
-constexpr unsigned long long kNotReady = 0x7FF4DEADBEEF0001ull;
+// Bit pattern of a value and the "not computed yet" sentinel: a signalling
+// NaN.  IEEE arithmetic never produces a signalling NaN, so no computed
+// value carries this pattern.
+template <class T>
+struct Word;
+template <>
+struct Word<double> {
+  using U = unsigned long long;
+  static constexpr U kNotReady = 0x7FF4DEADBEEF0001ull;
+  static __device__ __forceinline__ double value(U u) { return __longlong_as_double((long long)u); }
+};
+template <>
+struct Word<float> {
+  using U = unsigned;
+  static constexpr U kNotReady = 0x7FA5A5A1u;
+  static __device__ __forceinline__ float value(U u) { return __uint_as_float(u); }
+};
+
+template <class T>
+__device__ __forceinline__ T not_ready() {
+  return Word<T>::value(Word<T>::kNotReady);
+}
 
 struct Skew {
   int nty, ntz, ns;   // tiles in y and z, records per tile (a multiple of kU)
@@ -77,9 +99,15 @@ __device__ __forceinline__ long long skew_index(const Skew& k, int x, int y, int
   return ((long long)(Y + k.nty * Z) * k.ns + x + ty + tz + kPad) * kR + ty + kTY * tz;
 }
 
+// ---- relaxed device-scope accesses, copies (8- or 4-byte values) ----
 __device__ __forceinline__ unsigned long long ld_relaxed(const double* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const float* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 
@@ -89,6 +117,14 @@ __device__ __forceinline__ unsigned long long ld_relaxed_if(bool pred, const dou
   asm volatile(
       "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.relaxed.gpu.global.b64 %0, [%1];\n\t}"
       : "+l"(v)
+      : "l"(p), "r"((unsigned)pred));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_if(bool pred, const float* p) {
+  unsigned v = 0u;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.relaxed.gpu.global.b32 %0, [%1];\n\t}"
+      : "+r"(v)
       : "l"(p), "r"((unsigned)pred));
   return v;
 }
@@ -102,10 +138,17 @@ __device__ __forceinline__ int ld_relaxed_int(const int* p) {
 __device__ __forceinline__ void publish(double* p, double v) {
   asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
+__device__ __forceinline__ void publish(float* p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
 
-__device__ __forceinline__ void cp_async8(double* smem_dst, const double* src) {
+__device__ __forceinline__ void cp_async(double* smem_dst, const double* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(float* smem_dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -113,59 +156,89 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// ----------------------------------------------------------- factor ---
+// ------------------------------------------------------ parallel parts ---
 
 // Row-pivot-scaled couplings, stored skewed:
 // L_d = a_{i,i-e_d} / d_i, U_d = a_{i,i+e_d} / d_i.
-__global__ void k_ilu_scale(Geo g, Skew sk, const double* __restrict__ Ax,
-                            const double* __restrict__ Ay, const double* __restrict__ Az,
-                            const double* __restrict__ dinv, double* Lx, double* Ly, double* Lz,
-                            double* Ux, double* Uy, double* Uz) {
+template <class T>
+__global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* __restrict__ Ay,
+                            const T* __restrict__ Az, const T* __restrict__ dinv, T* Lx, T* Ly,
+                            T* Lz, T* Ux, T* Uy, T* Uz) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
   const long long j = skew_index(sk, x, y, z);
-  const double di = dinv[i];
+  const T di = dinv[i];
   Lx[j] = Ax[i] * di;
   Ly[j] = Ay[i] * di;
   Lz[j] = Az[i] * di;
-  Ux[j] = x < g.nx - 1 ? Ax[i + 1] * di : 0.0;
-  Uy[j] = y < g.ny - 1 ? Ay[i + g.sy] * di : 0.0;
-  Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : 0.0;
+  Ux[j] = x < g.nx - 1 ? Ax[i + 1] * di : T(0);
+  Uy[j] = y < g.ny - 1 ? Ay[i + g.sy] * di : T(0);
+  Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : T(0);
 }
 
-// rd = D^{-1} (f - A p), stored skewed.
-__global__ void k_resid_scaled(Geo g, Skew sk, const double* __restrict__ Ad,
-                               const double* __restrict__ Ax, const double* __restrict__ Ay,
-                               const double* __restrict__ Az, const double* __restrict__ f,
-                               const double* __restrict__ p, const double* __restrict__ dinv,
-                               double* rd) {
+// rd = D^{-1} (b - A x), stored skewed; b is read in its own precision and
+// rounded to T.
+template <class B, class T>
+__global__ void k_resid_scaled(Geo g, Skew sk, const T* __restrict__ Ad, const T* __restrict__ Ax,
+                               const T* __restrict__ Ay, const T* __restrict__ Az,
+                               const B* __restrict__ bv, const T* __restrict__ xv,
+                               const T* __restrict__ dinv, T* rd) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
   const long long j = skew_index(sk, x, y, z);
-  double a = f[i] - Ad[i] * p[i];
-  if (x > 0) a -= Ax[i] * p[i - 1];
-  if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
-  if (y > 0) a -= Ay[i] * p[i - g.sy];
-  if (y < g.ny - 1) a -= Ay[i + g.sy] * p[i + g.sy];
-  if (z > 0) a -= Az[i] * p[i - g.sz];
-  if (z < g.nz - 1) a -= Az[i + g.sz] * p[i + g.sz];
+  T a = T(bv[i]) - Ad[i] * xv[i];
+  if (x > 0) a -= Ax[i] * xv[i - 1];
+  if (x < g.nx - 1) a -= Ax[i + 1] * xv[i + 1];
+  if (y > 0) a -= Ay[i] * xv[i - g.sy];
+  if (y < g.ny - 1) a -= Ay[i + g.sy] * xv[i + g.sy];
+  if (z > 0) a -= Az[i] * xv[i - g.sz];
+  if (z < g.nz - 1) a -= Az[i + g.sz] * xv[i + g.sz];
   rd[j] = a * dinv[i];
 }
 
-// p += z (the correction of one smoothing step), z stored skewed.
-__global__ void k_apply_z(Geo g, Skew sk, const double* __restrict__ zs, double* p) {
+// x += z (the correction of one smoothing step), z stored skewed.
+template <class T>
+__global__ void k_apply_z(Geo g, Skew sk, const T* __restrict__ zs, T* xv) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   const int x = (int)(i % g.nx);
   const int y = (int)((i / g.nx) % g.ny);
   const int z = (int)(i / g.sz);
-  p[i] += zs[skew_index(sk, x, y, z)];
+  xv[i] += zs[skew_index(sk, x, y, z)];
+}
+
+template <class T>
+__global__ void k_fill_not_ready(long long n, T* a, T* b) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  a[i] = not_ready<T>();
+  if (b) b[i] = not_ready<T>();
+}
+
+// FP32 copy of the 7-point matrix (mixed precision)
+__global__ void k_matrix_to_single(long long n, const double* __restrict__ Ad,
+                                   const double* __restrict__ Ax, const double* __restrict__ Ay,
+                                   const double* __restrict__ Az, float* sd, float* sx, float* sy,
+                                   float* sz) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  sd[i] = (float)Ad[i];
+  sx[i] = (float)Ax[i];
+  sy[i] = (float)Ay[i];
+  sz[i] = (float)Az[i];
+}
+
+// p += delta (mixed precision: the FP32 correction enters the FP64 iterate)
+__global__ void k_add_correction(long long n, const float* __restrict__ d, double* p) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] += (double)d[i];
 }
 
 // ------------------------------------------------- per-cell operators ---
@@ -176,65 +249,71 @@ __global__ void k_apply_z(Geo g, Skew sk, const double* __restrict__ zs, double*
 // operands with the upstream values and publishes the result.  `cell` is
 // false on the pipeline's fill/drain slots and on rows beyond the grid:
 // there the result is discarded and nothing outside the slot is written.
-
+//
 // The two solves also keep the sentinels of the pipelined schedule: the
 // forward sweep marks z "not computed" as it passes (the backward sweep that
 // follows publishes into z), and the backward sweep does the same for w once
 // it has consumed it (the next forward sweep publishes into w).
+template <class T>
 struct FwdSolve {   // w = rd - Lx w_{x-1} - Ly w_{y-1} - Lz w_{z-1}
+  using Scalar = T;
   static constexpr int kN = 4;
   static constexpr bool kSkewIn = true, kSkewOut = true;
-  const double *rd, *Lx, *Ly, *Lz;
-  double *w, *z;
-  __device__ __forceinline__ const double* src(int a, long long, long long j) const {
+  const T *rd, *Lx, *Ly, *Lz;
+  T *w, *z;
+  __device__ __forceinline__ const T* src(int a, long long, long long j) const {
     return (a == 0 ? rd : a == 1 ? Lx : a == 2 ? Ly : Lz) + j;
   }
-  __device__ __forceinline__ double apply(const double* in, long long, long long j, bool,
-                                          double vx, double vy, double vz) const {
-    const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
+  __device__ __forceinline__ T apply(const T* in, long long, long long j, bool, T vx, T vy,
+                                     T vz) const {
+    const T v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
     publish(w + j, v);
-    z[j] = __longlong_as_double((long long)kNotReady);
+    z[j] = not_ready<T>();
     return v;
   }
 };
 
-struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1}  (p += z follows)
+template <class T>
+struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1}  (x += z follows)
+  using Scalar = T;
   static constexpr int kN = 4;
   static constexpr bool kSkewIn = true, kSkewOut = true;
-  const double *Ux, *Uy, *Uz;
-  double *w, *z;
-  __device__ __forceinline__ const double* src(int a, long long, long long j) const {
+  const T *Ux, *Uy, *Uz;
+  T *w, *z;
+  __device__ __forceinline__ const T* src(int a, long long, long long j) const {
     return (a == 0 ? w : a == 1 ? Ux : a == 2 ? Uy : Uz) + j;
   }
-  __device__ __forceinline__ double apply(const double* in, long long, long long j, bool,
-                                          double vx, double vy, double vz) const {
-    const double v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
+  __device__ __forceinline__ T apply(const T* in, long long, long long j, bool, T vx, T vy,
+                                     T vz) const {
+    const T v = fma(-in[1], vx, fma(-in[2], vy, fma(-in[3], vz, in[0])));
     publish(z + j, v);
-    w[j] = __longlong_as_double((long long)kNotReady);
+    w[j] = not_ready<T>();
     return v;
   }
 };
 
+template <class T>
 struct Factor {     // d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} - a_{i,z-1}^2 / d_{z-1}
+  using Scalar = T;
   static constexpr int kN = 4;
   static constexpr bool kSkewIn = false, kSkewOut = false;
-  const double *Ad, *Ax, *Ay, *Az;
-  double* dinv;
+  const T *Ad, *Ax, *Ay, *Az;
+  T* dinv;
   int* status;
-  __device__ __forceinline__ const double* src(int a, long long i, long long) const {
+  __device__ __forceinline__ const T* src(int a, long long i, long long) const {
     return (a == 0 ? Ad : a == 1 ? Ax : a == 2 ? Ay : Az) + i;
   }
-  __device__ __forceinline__ double apply(const double* in, long long i, long long, bool cell,
-                                          double vx, double vy, double vz) const {
-    double d = in[0];
+  __device__ __forceinline__ T apply(const T* in, long long i, long long, bool cell, T vx, T vy,
+                                     T vz) const {
+    T d = in[0];
     d -= in[1] * in[1] * vx;
     d -= in[2] * in[2] * vy;
     d -= in[3] * in[3] * vz;
-    if (cell && (!(d != 0.0) || !isfinite(d))) {
+    if (cell && (!(d != T(0)) || !isfinite(d))) {
       atomicOr(status, kStatSingular);
-      d = 1.0;
+      d = T(1);
     }
-    const double v = 1.0 / d;
+    const T v = T(1) / d;
     if (cell) publish(dinv + i, v);
     return v;
   }
@@ -243,7 +322,8 @@ struct Factor {     // d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} 
 // ---------------------------------------------------- level schedule ---
 
 template <class Op, bool kBackward>
-__global__ void k_sweep_level(Geo g, Skew sk, int L, Op op, const double* vals) {
+__global__ void k_sweep_level(Geo g, Skew sk, int L, Op op, const typename Op::Scalar* vals) {
+  using T = typename Op::Scalar;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)g.ny * g.nz) return;
   const int y = (int)(t % g.ny), z = (int)(t / g.ny);
@@ -255,7 +335,7 @@ __global__ void k_sweep_level(Geo g, Skew sk, int L, Op op, const double* vals) 
   const int zz = kBackward ? g.nz - 1 - z : z;
   const long long i = x + g.sy * yy + g.sz * zz;
   const long long j = skew_index(sk, x, yy, zz);
-  double in[Op::kN];
+  T in[Op::kN];
 #pragma unroll
   for (int a = 0; a < Op::kN; ++a) in[a] = *op.src(a, i, j);
   const int e = kBackward ? 1 : -1;
@@ -266,8 +346,8 @@ __global__ void k_sweep_level(Geo g, Skew sk, int L, Op op, const double* vals) 
     return Op::kSkewOut ? vals[skew_index(sk, x + dx, yy + dy, zz + dz)]
                         : vals[i + dx + g.sy * dy + g.sz * dz];
   };
-  op.apply(in, i, j, true, hx ? at(e, 0, 0) : 0.0, hy ? at(0, e, 0) : 0.0,
-           hz ? at(0, 0, e) : 0.0);
+  op.apply(in, i, j, true, hx ? at(e, 0, 0) : T(0), hy ? at(0, e, 0) : T(0),
+           hz ? at(0, 0, e) : T(0));
 }
 
 // ------------------------------------------------ pipelined schedule ---
@@ -287,22 +367,22 @@ __device__ __forceinline__ void tile_of_ticket(int t, int nty, int ntz, int& Y, 
   }
 }
 
-// Polls *p until it holds a published value; returns its bits, or
-// kNotReady after an abort or a timeout (the status word and the abort flag
+// Polls *p until it holds a published value; returns its bits, or the
+// sentinel after an abort or a timeout (the status word and the abort flag
 // are then set).  A light loop (one address, a short sleep between polls)
 // for the long wait before a tile's first step: heavy polling there slows
 // the tile's first steps and every tile downstream of it.
-__device__ __forceinline__ unsigned long long wait_bits(const double* p, int* abort_flag,
-                                                        int* status) {
+template <class T>
+__device__ __forceinline__ typename Word<T>::U wait_bits(const T* p, int* abort_flag, int* status) {
   for (long long it = 0; it < kSpinLimit; ++it) {
-    const unsigned long long b = ld_relaxed(p);
-    if (b != kNotReady) return b;
-    if ((it & 63) == 63 && ld_relaxed_int(abort_flag)) return kNotReady;
+    const typename Word<T>::U b = ld_relaxed(p);
+    if (b != Word<T>::kNotReady) return b;
+    if ((it & 63) == 63 && ld_relaxed_int(abort_flag)) return Word<T>::kNotReady;
     __nanosleep(32);
   }
   atomicOr(status, kStatTimeout);
   atomicExch(abort_flag, 1);
-  return kNotReady;
+  return Word<T>::kNotReady;
 }
 
 // One tile of a sweep, run by one warp: the tile at (Ym, Zm) in the sweep
@@ -312,12 +392,16 @@ __device__ __forceinline__ unsigned long long wait_bits(const double* p, int* ab
 // then run in groups of kU: a group's prologue stages the operands of the
 // group two ahead (cp.async) and prefetches the next group's cross-tile
 // values; values still unset are re-polled together; the kU steps
-// themselves are straight-line code.  Returns false after an abort
-// or a timeout (the warp's copies drained).
+// themselves are straight-line code.  Returns false after an abort or a
+// timeout (the warp's copies drained).
 template <class Op, bool kBackward>
 __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const Op& op,
-                                           const double* out, int* abort_flag, int* status,
-                                           double* ring, int lane, int Ym, int Zm) {
+                                           const typename Op::Scalar* out, int* abort_flag,
+                                           int* status, typename Op::Scalar* ring, int lane, int Ym,
+                                           int Zm) {
+  using T = typename Op::Scalar;
+  using U = typename Word<T>::U;
+  constexpr U kNR = Word<T>::kNotReady;
   constexpr unsigned kAll = 0xffffffffu;
   constexpr int kN = Op::kN;
   const int tym = lane % kTY, tzm = lane / kTY;   // row within the tile, sweep frame
@@ -364,12 +448,12 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
       }
       const long long j = j0 + (gs + u) * dj;
 #pragma unroll
-      for (int a = 0; a < kN; ++a) cp_async8(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
+      for (int a = 0; a < kN; ++a) cp_async(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
     }
     cp_async_commit();
   };
   // values of steps gs .. gs+kU-1 read from `out` (0 where none is needed)
-  auto fetch = [&](int gs, unsigned long long* cy, unsigned long long* cz) {
+  auto fetch = [&](int gs, U* cy, U* cz) {
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int xq = gs + u - xoff;
@@ -382,37 +466,37 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
     // the first group's last upstream values (the first wait is the long one)
     const int xq = kU - 1 - xoff;
     bool ok = true;
-    if (ext_y && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oy0 + (kU - 1) * od, abort_flag, status) != kNotReady;
-    if (ext_z && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oz0 + (kU - 1) * od, abort_flag, status) != kNotReady;
+    if (ext_y && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oy0 + (kU - 1) * od, abort_flag, status) != kNR;
+    if (ext_z && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oz0 + (kU - 1) * od, abort_flag, status) != kNR;
     if (__any_sync(kAll, !ok)) return false;
   }
   stage(0, 0);
   stage(kU, 1);
-  unsigned long long cy[kU], cz[kU];
+  U cy[kU], cz[kU];
   fetch(0, cy, cz);
-  double vprev = 0.0, from_y = 0.0, from_z = 0.0;
+  T vprev = T(0), from_y = T(0), from_z = T(0);
   int q = 0;
   for (int s0 = 0; s0 < sk.ns; s0 += kU) {
     stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
-    unsigned long long ny_[kU], nz_[kU];
+    U ny_[kU], nz_[kU];
     fetch(s0 + kU, ny_, nz_);
     // values still unset: re-poll them together (one round trip per poll)
     bool pending = false;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) pending |= (cy[u] == kNotReady) | (cz[u] == kNotReady);
+    for (int u = 0; u < kU; ++u) pending |= (cy[u] == kNR) | (cz[u] == kNR);
     if (__any_sync(kAll, pending)) {
       bool fail = false;
       for (long long it = 0; pending && !fail; ++it) {
         pending = false;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-          if (cy[u] == kNotReady) {
+          if (cy[u] == kNR) {
             cy[u] = ld_relaxed(out + oy0 + (s0 + u) * od);
-            pending |= cy[u] == kNotReady;
+            pending |= cy[u] == kNR;
           }
-          if (cz[u] == kNotReady) {
+          if (cz[u] == kNR) {
             cz[u] = ld_relaxed(out + oz0 + (s0 + u) * od);
-            pending |= cz[u] == kNotReady;
+            pending |= cz[u] == kNR;
           }
         }
         if (pending && it >= kFastPolls) {
@@ -433,7 +517,7 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
       }
     }
     cp_async_wait<2>();
-    double in[kU][kN];
+    T in[kU][kN];
 #pragma unroll
     for (int u = 0; u < kU; ++u)
 #pragma unroll
@@ -443,10 +527,10 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
       const int s = s0 + u;
       const int xs = s - xoff;
       const bool cell = valid && xs >= 0 && xs < g.nx;
-      const double vy = hy ? (tym > 0 ? from_y : __longlong_as_double((long long)cy[u])) : 0.0;
-      const double vz = hz ? (tzm > 0 ? from_z : __longlong_as_double((long long)cz[u])) : 0.0;
-      const double vx = xs > 0 ? vprev : 0.0;
-      const double v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
+      const T vy = hy ? (tym > 0 ? from_y : Word<T>::value(cy[u])) : T(0);
+      const T vz = hz ? (tzm > 0 ? from_z : Word<T>::value(cz[u])) : T(0);
+      const T vx = xs > 0 ? vprev : T(0);
+      const T v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
       // rows y-1 / z-1 of my tile computed my next neighbours just now
       from_y = __shfl_up_sync(kAll, v, 1);
       from_z = __shfl_up_sync(kAll, v, kTY);
@@ -464,16 +548,18 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
 }
 
 // ctrl: [0] ticket, [1] abort flag.  `out` is the vector the operator
-// publishes into (pre-filled with kNotReady on every cell).  Shared memory:
-// per warp, the operand ring [kG][kU][Op::kN][32].  Each warp claims tiles
-// on its own; cross-tile values travel through L2.
+// publishes into (pre-filled with the sentinel on every cell).  Shared
+// memory: per warp, the operand ring [kG][kU][Op::kN][32].  Each warp
+// claims tiles on its own.
 template <class Op, bool kBackward>
 __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, Op op,
-                                                                const double* out, int* ctrl,
-                                                                int* status) {
-  extern __shared__ double smem[];
+                                                                const typename Op::Scalar* out,
+                                                                int* ctrl, int* status) {
+  using T = typename Op::Scalar;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
+  T* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
   const int ntiles = sk.nty * sk.ntz;
   for (;;) {
     int t = 0;
@@ -484,13 +570,6 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
     tile_of_ticket(t, sk.nty, sk.ntz, Ym, Zm);
     if (!sweep_tile<Op, kBackward>(g, sk, op, out, ctrl + 1, status, ring, lane, Ym, Zm)) return;
   }
-}
-
-__global__ void k_fill_not_ready(long long n, double* a, double* b) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  a[i] = __longlong_as_double((long long)kNotReady);
-  if (b) b[i] = __longlong_as_double((long long)kNotReady);
 }
 
 // Bounded wait used by the self-test: polls a counter that nothing sets.
@@ -513,16 +592,96 @@ inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 template <class Op>
 constexpr int warp_smem() {
-  return (int)sizeof(double) * kWarps * kG * kU * Op::kN * kR;
+  return (int)sizeof(typename Op::Scalar) * kWarps * kG * kU * Op::kN * kR;
 }
 
 template <class Op, bool kBackward>
-cudaError_t launch_sweep(const Geo& g, const Skew& sk, int grid, const Op& op, const double* out,
-                         Buffers& b, cudaStream_t s) {
+cudaError_t launch_sweep(const Geo& g, const Skew& sk, int grid, const Op& op,
+                         const typename Op::Scalar* out, Buffers& b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
   if (e != cudaSuccess) return e;
   k_sweep_warp<Op, kBackward><<<grid, 32 * kWarps, warp_smem<Op>(), s>>>(g, sk, op, out, b.ctrl,
                                                                          b.status);
+  return cudaGetLastError();
+}
+
+template <class Op, bool kBackward>
+void set_sweep_smem() {
+  cudaFuncSetAttribute(k_sweep_warp<Op, kBackward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       warp_smem<Op>());
+}
+
+// The vectors of one precision's smoother.
+template <class T>
+struct IluSet {
+  const T *Ad, *Ax, *Ay, *Az;
+  T* dinv;
+  T *Lx, *Ly, *Lz, *Ux, *Uy, *Uz;
+  T *rds, *w, *z;
+};
+
+IluSet<double> set_of(Buffers& b, double*) {
+  return IluSet<double>{b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly, b.Lz, b.Ux, b.Uy, b.Uz,
+                        b.rds, b.w, b.z};
+}
+IluSet<float> set_of(Buffers& b, float*) {
+  const SingleBuffers& f = b.f32;
+  return IluSet<float>{f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
+                       f.rds, f.w, f.z};
+}
+
+template <class T>
+cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s) {
+  const Skew sk = make_skew(g);
+  const IluSet<T> v = set_of(b, (T*)nullptr);
+  Factor<T> fa{v.Ad, v.Ax, v.Ay, v.Az, v.dinv, b.status};
+  int n = 1;
+  if (!pipelined) {
+    const int blocks = blocks_for((long long)g.ny * g.nz, 256);
+    const int levels = g.nx + g.ny + g.nz - 2;
+    for (int L = 0; L < levels; ++L)
+      k_sweep_level<Factor<T>, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, v.dinv);
+    n += levels;
+  } else {
+    k_fill_not_ready<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, v.dinv, nullptr);
+    cudaError_t e = launch_sweep<Factor<T>, false>(g, sk, grid, fa, v.dinv, b, s);
+    if (e != cudaSuccess) return e;
+    // sweep outputs start "not computed"; the sweeps keep it so from here on
+    const long long S = ilu_skew_len(g);
+    k_fill_not_ready<T><<<blocks_for(S, 256), 256, 0, s>>>(S, v.w, v.z);
+    n += 3;
+  }
+  k_ilu_scale<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, v.Ax, v.Ay, v.Az, v.dinv, v.Lx, v.Ly,
+                                                      v.Lz, v.Ux, v.Uy, v.Uz);
+  count_launches(n);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
+                       T* xv, cudaStream_t s) {
+  const Skew sk = make_skew(g);
+  const IluSet<T> v = set_of(b, (T*)nullptr);
+  FwdSolve<T> fw{v.rds, v.Lx, v.Ly, v.Lz, v.w, v.z};
+  BwdSolve<T> bw{v.Ux, v.Uy, v.Uz, v.w, v.z};
+  if (!pipelined) {
+    const int blocks = blocks_for((long long)g.ny * g.nz, 256);
+    const int levels = g.nx + g.ny + g.nz - 2;
+    for (int L = 0; L < levels; ++L) {
+      if (!backward) k_sweep_level<FwdSolve<T>, false><<<blocks, 256, 0, s>>>(g, sk, L, fw, v.w);
+      else k_sweep_level<BwdSolve<T>, true><<<blocks, 256, 0, s>>>(g, sk, L, bw, v.z);
+    }
+    count_launches(levels);
+  } else {
+    cudaError_t e = !backward ? launch_sweep<FwdSolve<T>, false>(g, sk, grid, fw, v.w, b, s)
+                              : launch_sweep<BwdSolve<T>, true>(g, sk, grid, bw, v.z, b, s);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  if (backward) {
+    k_apply_z<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, v.z, xv);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -541,71 +700,50 @@ int ilu_ctrl_ints(const Geo& g) {
 int ilu_pipe_grid(const Geo& g, int num_sms) {
   const Skew k = make_skew(g);
   const int ctas = (k.nty * k.ntz + kWarps - 1) / kWarps;
-  cudaFuncSetAttribute(k_sweep_warp<FwdSolve, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       warp_smem<FwdSolve>());
-  cudaFuncSetAttribute(k_sweep_warp<BwdSolve, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       warp_smem<BwdSolve>());
-  cudaFuncSetAttribute(k_sweep_warp<Factor, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       warp_smem<Factor>());
+  set_sweep_smem<FwdSolve<double>, false>();
+  set_sweep_smem<BwdSolve<double>, true>();
+  set_sweep_smem<Factor<double>, false>();
+  set_sweep_smem<FwdSolve<float>, false>();
+  set_sweep_smem<BwdSolve<float>, true>();
+  set_sweep_smem<Factor<float>, false>();
   // one CTA per SM: more sweeping warps per SM would share the FP64 pipes
   return ctas < num_sms ? ctas : num_sms;
 }
 
-cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s) {
-  const Skew sk = make_skew(g);
-  Factor fa{b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.status};
-  int n = 1;
-  if (!pipelined) {
-    const int blocks = blocks_for((long long)g.ny * g.nz, 256);
-    const int levels = g.nx + g.ny + g.nz - 2;
-    for (int L = 0; L < levels; ++L)
-      k_sweep_level<Factor, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, b.dinv);
-    n += levels;
-  } else {
-    k_fill_not_ready<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.dinv, nullptr);
-    cudaError_t e = launch_sweep<Factor, false>(g, sk, grid, fa, b.dinv, b, s);
-    if (e != cudaSuccess) return e;
-    // sweep outputs start "not computed"; the sweeps keep it so from here on
-    const long long S = ilu_skew_len(g);
-    k_fill_not_ready<<<blocks_for(S, 256), 256, 0, s>>>(S, b.w, b.z);
-    n += 3;
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, bool single,
+                              cudaStream_t s) {
+  if (single) {
+    k_matrix_to_single<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.Ad, b.Ax, b.Ay, b.Az, b.f32.Ad,
+                                                            b.f32.Ax, b.f32.Ay, b.f32.Az);
+    count_launches(1);
+    return factor_impl<float>(g, b, pipelined, grid, s);
   }
-  k_ilu_scale<<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly,
-                                                   b.Lz, b.Ux, b.Uy, b.Uz);
-  count_launches(n);
-  return cudaGetLastError();
+  return factor_impl<double>(g, b, pipelined, grid, s);
 }
 
-cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, cudaStream_t s) {
-  k_resid_scaled<<<blocks_for(g.N, 256), 256, 0, s>>>(g, make_skew(g), b.Ad, b.Ax, b.Ay, b.Az,
-                                                      b.f, b.p, b.dinv, b.rds);
+cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s) {
+  const Skew sk = make_skew(g);
+  if (single) {
+    const SingleBuffers& f = b.f32;
+    k_resid_scaled<double, float><<<blocks_for(g.N, 256), 256, 0, s>>>(
+        g, sk, f.Ad, f.Ax, f.Ay, f.Az, b.r, f.d, f.dinv, f.rds);
+  } else {
+    k_resid_scaled<double, double><<<blocks_for(g.N, 256), 256, 0, s>>>(
+        g, sk, b.Ad, b.Ax, b.Ay, b.Az, b.f, b.p, b.dinv, b.rds);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
-                             cudaStream_t s) {
-  const Skew sk = make_skew(g);
-  FwdSolve fw{b.rds, b.Lx, b.Ly, b.Lz, b.w, b.z};
-  BwdSolve bw{b.Ux, b.Uy, b.Uz, b.w, b.z};
-  if (!pipelined) {
-    const int blocks = blocks_for((long long)g.ny * g.nz, 256);
-    const int levels = g.nx + g.ny + g.nz - 2;
-    for (int L = 0; L < levels; ++L) {
-      if (!backward) k_sweep_level<FwdSolve, false><<<blocks, 256, 0, s>>>(g, sk, L, fw, b.w);
-      else k_sweep_level<BwdSolve, true><<<blocks, 256, 0, s>>>(g, sk, L, bw, b.z);
-    }
-    count_launches(levels);
-  } else {
-    cudaError_t e = !backward ? launch_sweep<FwdSolve, false>(g, sk, grid, fw, b.w, b, s)
-                              : launch_sweep<BwdSolve, true>(g, sk, grid, bw, b.z, b, s);
-    count_launches(1);
-    if (e != cudaSuccess) return e;
-  }
-  if (backward) {
-    k_apply_z<<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, b.z, b.p);
-    count_launches(1);
-  }
+                             bool single, cudaStream_t s) {
+  return single ? sweep_impl<float>(g, b, backward, pipelined, grid, b.f32.d, s)
+                : sweep_impl<double>(g, b, backward, pipelined, grid, b.p, s);
+}
+
+cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s) {
+  k_add_correction<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.f32.d, b.p);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,7 @@ def gpu_handle(case: Case, memspace=0):
     opt = cams.make_options(w.coarse, basis=w.basis, restriction=w.restriction, n_pre=w.n_pre,
                             n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
                             adapt_theta=w.adapt_theta, max_newton=w.max_newton,
-                            max_cams=w.max_cams, memspace=memspace)
+                            max_cams=w.max_cams, memspace=memspace, precision=w.precision)
     h = cams.cams_setup(grid, fluid, opt, inp["kx"], inp["ky"], inp["kz"])
     bc, keep = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
                             inp["src_cell"] if len(inp["src_cell"]) else None,

@@ -49,6 +49,7 @@ class Workload:
     adapt_theta: float = 0.1
     max_newton: int = 50
     max_cams: int = 200
+    precision: int = 0        # engine option: 0 = FP64, 1 = FP32 preconditioner in FP64 refinement
     seeds: tuple = (0,)
 
     @property
@@ -79,6 +80,13 @@ WORKLOADS = {
         name="3d-200x200x100", nx=200, ny=200, nz=100, coarse=(10, 10, 10),
         sigma=3.0, corr=(0.1, 0.1, 0.1), c_or_eta=0.1, steps=1, basis=4,
         restriction=0, n_post=5, nl_tol=1e-8, seeds=(0,)),
+    # The same problem with the multiscale preconditioner in FP32 (basis
+    # solves, P, ILU(0) smoother) inside FP64 iterative refinement; FP64
+    # residual, update and coarse factorisation.
+    "3d-200x200x100-mixed": Workload(
+        name="3d-200x200x100-mixed", nx=200, ny=200, nz=100, coarse=(10, 10, 10),
+        sigma=3.0, corr=(0.1, 0.1, 0.1), c_or_eta=0.1, steps=1, basis=4,
+        restriction=0, n_post=5, nl_tol=1e-8, seeds=(0,), precision=1),
 }
 
 
