@@ -49,6 +49,7 @@ struct cams_handle {
   long long launch_base = 0;
   bool single = false;          // mixed precision: FP32 preconditioner (b.f32)
   bool ilu_pipelined = true;    // false: level-scheduled sweeps (CAMS_ILU_LEVEL=1)
+  bool ilu_cta = false;         // 2 x 2 tile blocks per CTA, else one tile per warp
   bool coarse_cluster = false;  // MSFE coarse solve across a cluster (CAMS_COARSE_CLUSTER=0: one CTA)
   int ilu_grid = 1;
   // per-kernel-class profiling (cams_profile)
@@ -453,7 +454,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
     CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
     CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
   }
-  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->single, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, h->single, h->stream));
   return check_status(h);
 }
 
@@ -473,8 +474,8 @@ int residual_norm(cams_handle* h, double* out) {
 int ilu_smooth(cams_handle* h) {
   const bool s = h->single;
   LAUNCH(CAMS_PROF_ILU_RESID, launch_ilu_resid(h->g, h->b, s, h->stream));
-  LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, s, h->stream));
-  LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, s, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, s, h->stream));
+  LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, s, h->stream));
   return CAMS_OK;
 }
 
@@ -626,6 +627,12 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     const char* lv = std::getenv("CAMS_ILU_LEVEL");
     h->ilu_pipelined = !(lv && lv[0] == '1');
     h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
+    // 2 x 2 tile blocks per CTA pay off for the FP32 smoother (measured ~5%
+    // faster sweeps); the FP64 one is faster with one tile per warp.
+    // CAMS_ILU_CTA=1 / 0 forces either.
+    const char* ct = std::getenv("CAMS_ILU_CTA");
+    const bool want = ct ? ct[0] == '1' : h->single;
+    h->ilu_cta = want && ilu_cta_ok(h->g, (int)prop.sharedMemPerBlockOptin);
     const char* cc = std::getenv("CAMS_COARSE_CLUSTER");
     h->coarse_cluster = !(cc && cc[0] == '0') &&
                         coarse_cluster_ok(h->c.Nc, (int)prop.sharedMemPerBlockOptin);

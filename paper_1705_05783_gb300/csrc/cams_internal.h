@@ -167,11 +167,14 @@ cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers
                                cudaStream_t s);
 // single: the FP32 smoother of the mixed-precision preconditioner (on
 // A delta = r, vectors in b.f32); otherwise the FP64 smoother on A p = f.
-cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, bool single,
-                              cudaStream_t s);
+// sms: the SM count (from ilu_pipe_grid); cta: tiles in 2 x 2 blocks per CTA
+// with shared-memory edges (ilu_cta_ok), else one tile per warp.
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
+                              bool single, cudaStream_t s);
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s);
-cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
-                             bool single, cudaStream_t s);
+cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int sms,
+                             bool cta, bool single, cudaStream_t s);
+bool ilu_cta_ok(const Geo& g, int max_smem);
 cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s);   // p += delta
 int ilu_ctrl_ints(const Geo& g);
 // Rows per wavefront tile (y, z) and the length of a skewed sweep vector.

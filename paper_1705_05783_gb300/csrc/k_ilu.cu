@@ -374,11 +374,41 @@ __device__ __forceinline__ void tile_of_ticket(int t, int nty, int ntz, int& Y, 
 // the tile's first steps and every tile downstream of it.
 template <class T>
 __device__ __forceinline__ typename Word<T>::U wait_bits(const T* p, int* abort_flag, int* status) {
+  unsigned nap = 32;
   for (long long it = 0; it < kSpinLimit; ++it) {
     const typename Word<T>::U b = ld_relaxed(p);
     if (b != Word<T>::kNotReady) return b;
     if ((it & 63) == 63 && ld_relaxed_int(abort_flag)) return Word<T>::kNotReady;
-    __nanosleep(32);
+    __nanosleep(nap);
+    nap = nap < 256 ? 2 * nap : 256;      // back off while the upstream tile is far away
+  }
+  atomicOr(status, kStatTimeout);
+  atomicExch(abort_flag, 1);
+  return Word<T>::kNotReady;
+}
+
+// Shared-memory edge values between the warps of one CTA (volatile: every
+// access is performed; aligned 4- and 8-byte accesses are single-copy atomic).
+template <class T>
+__device__ __forceinline__ typename Word<T>::U ld_shared_bits(const T* p) {
+  return *reinterpret_cast<const volatile typename Word<T>::U*>(p);
+}
+template <class T>
+__device__ __forceinline__ void st_shared(T* p, T v) {
+  *reinterpret_cast<volatile T*>(p) = v;
+}
+
+// wait_bits for a value another warp of this CTA writes into shared memory
+template <class T>
+__device__ __forceinline__ typename Word<T>::U wait_shared(const T* p, int* abort_flag,
+                                                          int* status) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    const typename Word<T>::U b = ld_shared_bits(p);
+    if (b != Word<T>::kNotReady) return b;
+    if ((it & 63) == 63) {
+      if (ld_relaxed_int(abort_flag)) return Word<T>::kNotReady;
+      __nanosleep(20);
+    }
   }
   atomicOr(status, kStatTimeout);
   atomicExch(abort_flag, 1);
@@ -394,11 +424,19 @@ __device__ __forceinline__ typename Word<T>::U wait_bits(const T* p, int* abort_
 // values; values still unset are re-polled together; the kU steps
 // themselves are straight-line code.  Returns false after an abort or a
 // timeout (the warp's copies drained).
-template <class Op, bool kBackward>
+//
+// With kCta, the upstream tile in y (z) may be run by another warp of the
+// same CTA: then ey (ez) is this lane's shared-memory edge buffer, indexed
+// by x in the sweep frame, which that warp fills; py / pz are the edge
+// buffers this lane fills for the downstream warps of the CTA (null: none).
+template <class Op, bool kBackward, bool kCta = false>
 __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const Op& op,
                                            const typename Op::Scalar* out, int* abort_flag,
                                            int* status, typename Op::Scalar* ring, int lane, int Ym,
-                                           int Zm) {
+                                           int Zm, const typename Op::Scalar* ey = nullptr,
+                                           const typename Op::Scalar* ez = nullptr,
+                                           typename Op::Scalar* py = nullptr,
+                                           typename Op::Scalar* pz = nullptr) {
   using T = typename Op::Scalar;
   using U = typename Word<T>::U;
   constexpr U kNR = Word<T>::kNotReady;
@@ -422,6 +460,9 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
   const bool hz = valid && (kBackward ? z < g.nz - 1 : z > 0);
   const bool ext_y = hy && tym == 0;                              // ... in another tile
   const bool ext_z = hz && tzm == 0;
+  const bool sy = kCta && ext_y && ey != nullptr;                 // ... another warp of my CTA
+  const bool sz = kCta && ext_z && ez != nullptr;
+  const bool gy = ext_y && !sy, gz = ext_z && !sz;                // ... another CTA (via L2)
   // indices at sweep step 0.  x in the sweep frame is step - xoff; the
   // backward sweep walks the tile's records from the last one down, and its
   // first ns - (nx + kTY + kTZ - 2) steps are padding.
@@ -458,20 +499,38 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
     for (int u = 0; u < kU; ++u) {
       const int xq = gs + u - xoff;
       const bool in_row = xq >= 0 && xq < g.nx;
-      cy[u] = ld_relaxed_if(ext_y && in_row, out + oy0 + (gs + u) * od);
-      cz[u] = ld_relaxed_if(ext_z && in_row, out + oz0 + (gs + u) * od);
+      cy[u] = ld_relaxed_if(gy && in_row, out + oy0 + (gs + u) * od);
+      cz[u] = ld_relaxed_if(gz && in_row, out + oz0 + (gs + u) * od);
     }
   };
-  {
-    // the first group's last upstream values (the first wait is the long one)
-    const int xq = kU - 1 - xoff;
-    bool ok = true;
-    if (ext_y && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oy0 + (kU - 1) * od, abort_flag, status) != kNR;
-    if (ext_z && xq >= 0 && xq < g.nx) ok &= wait_bits(out + oz0 + (kU - 1) * od, abort_flag, status) != kNR;
-    if (__any_sync(kAll, !ok)) return false;
-  }
+  // the operands of the first two groups do not depend on other tiles:
+  // their copies overlap the first wait
   stage(0, 0);
   stage(kU, 1);
+  {
+    // The first group's upstream values (the first wait is the long one).
+    // A tile publishes in step order, and among my edge lanes the one with
+    // the largest skew needs the latest value, so that lane alone polls for
+    // each direction (tz = 3 in y, ty = 7 in z): few pollers keep L2 quiet
+    // for the tiles that are running.
+    // (Every lane takes part in both shuffles.)
+    const int xq = kU - 1 - xoff;
+    bool ok = true;
+    const bool in_row = xq >= 0 && xq < g.nx;
+    const bool need_y = ext_y && in_row, need_z = ext_z && in_row;
+    const bool des_y = __shfl_sync(kAll, need_y, tym + (kTZ - 1) * kTY);   // tz = 3 of my column
+    const bool des_z = __shfl_sync(kAll, need_z, (kTY - 1) + tzm * kTY);   // ty = 7 of my row
+    const bool last_y = tzm == kTZ - 1 || !des_y;
+    const bool last_z = tym == kTY - 1 || !des_z;
+    if (gy && in_row && last_y) ok &= wait_bits(out + oy0 + (kU - 1) * od, abort_flag, status) != kNR;
+    if (gz && in_row && last_z) ok &= wait_bits(out + oz0 + (kU - 1) * od, abort_flag, status) != kNR;
+    if (kCta && sy && in_row && last_y) ok &= wait_shared(ey + xq, abort_flag, status) != kNR;
+    if (kCta && sz && in_row && last_z) ok &= wait_shared(ez + xq, abort_flag, status) != kNR;
+    if (__any_sync(kAll, !ok)) {
+      cp_async_wait<0>();
+      return false;
+    }
+  }
   U cy[kU], cz[kU];
   fetch(0, cy, cz);
   T vprev = T(0), from_y = T(0), from_z = T(0);
@@ -480,6 +539,15 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
     stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
     U ny_[kU], nz_[kU];
     fetch(s0 + kU, ny_, nz_);
+    if (kCta && (sy || sz)) {   // edge values of this group from my CTA's shared memory
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int xq = s0 + u - xoff;
+        const bool in_row = xq >= 0 && xq < g.nx;
+        if (sy) cy[u] = in_row ? ld_shared_bits(ey + xq) : U(0);
+        if (sz) cz[u] = in_row ? ld_shared_bits(ez + xq) : U(0);
+      }
+    }
     // values still unset: re-poll them together (one round trip per poll)
     bool pending = false;
 #pragma unroll
@@ -491,11 +559,11 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
           if (cy[u] == kNR) {
-            cy[u] = ld_relaxed(out + oy0 + (s0 + u) * od);
+            cy[u] = sy ? ld_shared_bits(ey + (s0 + u - xoff)) : ld_relaxed(out + oy0 + (s0 + u) * od);
             pending |= cy[u] == kNR;
           }
           if (cz[u] == kNR) {
-            cz[u] = ld_relaxed(out + oz0 + (s0 + u) * od);
+            cz[u] = sz ? ld_shared_bits(ez + (s0 + u - xoff)) : ld_relaxed(out + oz0 + (s0 + u) * od);
             pending |= cz[u] == kNR;
           }
         }
@@ -531,6 +599,10 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
       const T vz = hz ? (tzm > 0 ? from_z : Word<T>::value(cz[u])) : T(0);
       const T vx = xs > 0 ? vprev : T(0);
       const T v = op.apply(in[u], i0 + s * di, j0 + s * dj, cell, vx, vy, vz);
+      if (kCta) {   // feed the downstream warps of my CTA
+        if (py != nullptr && cell) st_shared(py + xs, v);
+        if (pz != nullptr && cell) st_shared(pz + xs, v);
+      }
       // rows y-1 / z-1 of my tile computed my next neighbours just now
       from_y = __shfl_up_sync(kAll, v, 1);
       from_z = __shfl_up_sync(kAll, v, kTY);
@@ -572,6 +644,60 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
   }
 }
 
+// The 4 warps of a CTA take a 2 x 2 block of tiles (16 x 8 x-rows) together:
+// warp w runs tile (2 CY + (w & 1), 2 CZ + (w >> 1)) of CTA block (CY, CZ)
+// in the sweep frame.  Edges between the block's tiles pass through shared
+// memory (12 buffers of nx values per warp pair, kNotReady until written);
+// edges between blocks pass through L2 as in k_sweep_warp.  Blocks are
+// claimed by ticket in anti-diagonal order; a CTA resets its edge buffers
+// between blocks.  Shared memory: the operand rings, then the edges:
+// [2 (block column wz)][4 (tz)][nx] in y, then [2 (wy)][8 (ty)][nx] in z.
+template <class Op, bool kBackward>
+__global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_cta(Geo g, Skew sk, Op op,
+                                                               const typename Op::Scalar* out,
+                                                               int* ctrl, int* status) {
+  static_assert(kWarps == 4, "a CTA block is 2 x 2 tiles");
+  using T = typename Op::Scalar;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  __shared__ int s_ticket;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tym = lane % kTY, tzm = lane / kTY;
+  const int wy = warp & 1, wz = warp >> 1;
+  T* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
+  T* edges = smem + kWarps * (kG * kU * Op::kN * kR);
+  const long long nx = g.nx;
+  T* ey_row = edges + (wz * kTZ + tzm) * nx;                  // y-edge of block column wz, row tz
+  T* ez_row = edges + 2 * kTZ * nx + (wy * kTY + tym) * nx;    // z-edge of block row wy, row ty
+  const T* ey = wy == 1 ? ey_row : nullptr;                     // I read what warp (0, wz) writes
+  const T* ez = wz == 1 ? ez_row : nullptr;                     // ... what warp (wy, 0) writes
+  T* py = (wy == 0 && tym == kTY - 1) ? ey_row : nullptr;
+  T* pz = (wz == 0 && tzm == kTZ - 1) ? ez_row : nullptr;
+  const int ncy = (sk.nty + 1) / 2, ncz = (sk.ntz + 1) / 2, nblocks = ncy * ncz;
+  const int nedge = 2 * (kTZ + kTY) * g.nx;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = atomicAdd(&ctrl[0], 1);
+      if (ld_relaxed_int(ctrl + 1)) t = nblocks;   // after an abort: stop
+      s_ticket = t;
+    }
+    __syncthreads();
+    const int t = s_ticket;
+    if (t >= nblocks) return;
+    for (int e = threadIdx.x; e < nedge; e += blockDim.x) edges[e] = not_ready<T>();
+    __syncthreads();
+    int CY, CZ;
+    tile_of_ticket(t, ncy, ncz, CY, CZ);
+    const int Ym = 2 * CY + wy, Zm = 2 * CZ + wz;
+    if (Ym < sk.nty && Zm < sk.ntz)
+      sweep_tile<Op, kBackward, true>(g, sk, op, out, ctrl + 1, status, ring, lane, Ym, Zm, ey,
+                                      ez, py, pz);
+    // a warp that failed falls through: the others see the abort flag in
+    // their waits, and the next claim ends the CTA
+    __syncthreads();
+  }
+}
+
 // Bounded wait used by the self-test: polls a counter that nothing sets.
 __device__ __forceinline__ bool wait_at_least(int* ctr, int need, int* abort_flag, int* status) {
   for (long long it = 0; it < kSpinLimit; ++it) {
@@ -595,13 +721,27 @@ constexpr int warp_smem() {
   return (int)sizeof(typename Op::Scalar) * kWarps * kG * kU * Op::kN * kR;
 }
 
+template <class Op>
+int cta_smem(const Geo& g) {
+  return warp_smem<Op>() + (int)sizeof(typename Op::Scalar) * 2 * (kTZ + kTY) * g.nx;
+}
+
+// sms: the device's SM count; cta: run k_sweep_cta (else k_sweep_warp).
+// One CTA per SM: more sweeping warps per SM would share the FP64 pipes.
 template <class Op, bool kBackward>
-cudaError_t launch_sweep(const Geo& g, const Skew& sk, int grid, const Op& op,
+cudaError_t launch_sweep(const Geo& g, const Skew& sk, int sms, bool cta, const Op& op,
                          const typename Op::Scalar* out, Buffers& b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.ctrl, 0, sizeof(int) * (size_t)ilu_ctrl_ints(g), s);
   if (e != cudaSuccess) return e;
-  k_sweep_warp<Op, kBackward><<<grid, 32 * kWarps, warp_smem<Op>(), s>>>(g, sk, op, out, b.ctrl,
-                                                                         b.status);
+  if (cta) {
+    const int blocks = ((sk.nty + 1) / 2) * ((sk.ntz + 1) / 2);
+    k_sweep_cta<Op, kBackward><<<blocks < sms ? blocks : sms, 32 * kWarps, cta_smem<Op>(g), s>>>(
+        g, sk, op, out, b.ctrl, b.status);
+  } else {
+    const int ctas = (sk.nty * sk.ntz + kWarps - 1) / kWarps;
+    k_sweep_warp<Op, kBackward><<<ctas < sms ? ctas : sms, 32 * kWarps, warp_smem<Op>(), s>>>(
+        g, sk, op, out, b.ctrl, b.status);
+  }
   return cudaGetLastError();
 }
 
@@ -609,6 +749,13 @@ template <class Op, bool kBackward>
 void set_sweep_smem() {
   cudaFuncSetAttribute(k_sweep_warp<Op, kBackward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        warp_smem<Op>());
+}
+
+template <class Op, bool kBackward>
+bool set_cta_smem(const Geo& g) {
+  return cudaFuncSetAttribute(k_sweep_cta<Op, kBackward>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              cta_smem<Op>(g)) == cudaSuccess;
 }
 
 // The vectors of one precision's smoother.
@@ -631,7 +778,8 @@ IluSet<float> set_of(Buffers& b, float*) {
 }
 
 template <class T>
-cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int grid, cudaStream_t s) {
+cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
+                        cudaStream_t s) {
   const Skew sk = make_skew(g);
   const IluSet<T> v = set_of(b, (T*)nullptr);
   Factor<T> fa{v.Ad, v.Ax, v.Ay, v.Az, v.dinv, b.status};
@@ -644,7 +792,7 @@ cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int grid, cuda
     n += levels;
   } else {
     k_fill_not_ready<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, v.dinv, nullptr);
-    cudaError_t e = launch_sweep<Factor<T>, false>(g, sk, grid, fa, v.dinv, b, s);
+    cudaError_t e = launch_sweep<Factor<T>, false>(g, sk, sms, cta, fa, v.dinv, b, s);
     if (e != cudaSuccess) return e;
     // sweep outputs start "not computed"; the sweeps keep it so from here on
     const long long S = ilu_skew_len(g);
@@ -658,7 +806,7 @@ cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int grid, cuda
 }
 
 template <class T>
-cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
+cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, int sms, bool cta,
                        T* xv, cudaStream_t s) {
   const Skew sk = make_skew(g);
   const IluSet<T> v = set_of(b, (T*)nullptr);
@@ -673,8 +821,8 @@ cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, 
     }
     count_launches(levels);
   } else {
-    cudaError_t e = !backward ? launch_sweep<FwdSolve<T>, false>(g, sk, grid, fw, v.w, b, s)
-                              : launch_sweep<BwdSolve<T>, true>(g, sk, grid, bw, v.z, b, s);
+    cudaError_t e = !backward ? launch_sweep<FwdSolve<T>, false>(g, sk, sms, cta, fw, v.w, b, s)
+                              : launch_sweep<BwdSolve<T>, true>(g, sk, sms, cta, bw, v.z, b, s);
     count_launches(1);
     if (e != cudaSuccess) return e;
   }
@@ -698,27 +846,34 @@ int ilu_ctrl_ints(const Geo& g) {
 }
 
 int ilu_pipe_grid(const Geo& g, int num_sms) {
-  const Skew k = make_skew(g);
-  const int ctas = (k.nty * k.ntz + kWarps - 1) / kWarps;
+  (void)g;
   set_sweep_smem<FwdSolve<double>, false>();
   set_sweep_smem<BwdSolve<double>, true>();
   set_sweep_smem<Factor<double>, false>();
   set_sweep_smem<FwdSolve<float>, false>();
   set_sweep_smem<BwdSolve<float>, true>();
   set_sweep_smem<Factor<float>, false>();
-  // one CTA per SM: more sweeping warps per SM would share the FP64 pipes
-  return ctas < num_sms ? ctas : num_sms;
+  return num_sms;
 }
 
-cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int grid, bool single,
-                              cudaStream_t s) {
+bool ilu_cta_ok(const Geo& g, int max_smem) {
+  if (cta_smem<FwdSolve<double>>(g) > max_smem) return false;   // FP64 needs the most
+  bool ok = set_cta_smem<FwdSolve<double>, false>(g) && set_cta_smem<BwdSolve<double>, true>(g) &&
+            set_cta_smem<Factor<double>, false>(g) && set_cta_smem<FwdSolve<float>, false>(g) &&
+            set_cta_smem<BwdSolve<float>, true>(g) && set_cta_smem<Factor<float>, false>(g);
+  cudaGetLastError();
+  return ok;
+}
+
+cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
+                              bool single, cudaStream_t s) {
   if (single) {
     k_matrix_to_single<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.Ad, b.Ax, b.Ay, b.Az, b.f32.Ad,
                                                             b.f32.Ax, b.f32.Ay, b.f32.Az);
     count_launches(1);
-    return factor_impl<float>(g, b, pipelined, grid, s);
+    return factor_impl<float>(g, b, pipelined, sms, cta, s);
   }
-  return factor_impl<double>(g, b, pipelined, grid, s);
+  return factor_impl<double>(g, b, pipelined, sms, cta, s);
 }
 
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s) {
@@ -735,10 +890,10 @@ cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int grid,
-                             bool single, cudaStream_t s) {
-  return single ? sweep_impl<float>(g, b, backward, pipelined, grid, b.f32.d, s)
-                : sweep_impl<double>(g, b, backward, pipelined, grid, b.p, s);
+cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int sms,
+                             bool cta, bool single, cudaStream_t s) {
+  return single ? sweep_impl<float>(g, b, backward, pipelined, sms, cta, b.f32.d, s)
+                : sweep_impl<double>(g, b, backward, pipelined, sms, cta, b.p, s);
 }
 
 cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s) {

@@ -1,6 +1,6 @@
 """Engine-level GPU checks that need no oracle arithmetic: the pipelined
-ILU(0) wavefronts (factorisation and both sweeps) equal the level-scheduled
-ones bit for bit, the
+ILU(0) wavefronts (factorisation and both sweeps; one tile per warp or 2 x 2
+tile blocks per CTA) equal the level-scheduled ones bit for bit, the
 bounded device-side wait times out cleanly, a handle can be reused for a
 new permeability field, and the host and device memory spaces agree."""
 import os
@@ -19,16 +19,22 @@ def cams():
     return cams
 
 
-def _iterate(cams, case, n, level):
-    old = os.environ.get("CAMS_ILU_LEVEL")
-    os.environ["CAMS_ILU_LEVEL"] = "1" if level else "0"
+def _iterate(cams, case, n, mode):
+    """mode: 'level' (one launch per hyperplane), 'warp' (one tile per warp,
+    tile edges through L2) or 'cta' (2 x 2 tile blocks per CTA, edges inside
+    a block through shared memory)."""
+    env = {"CAMS_ILU_LEVEL": "1" if mode == "level" else "0",
+           "CAMS_ILU_CTA": "1" if mode == "cta" else "0"}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         h, bc, keep = gpu_handle(case)
     finally:
-        if old is None:
-            del os.environ["CAMS_ILU_LEVEL"]
-        else:
-            os.environ["CAMS_ILU_LEVEL"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
     try:
         rng = np.random.default_rng(3)
         p_nu = rng.uniform(0, 1, case.N)
@@ -51,11 +57,12 @@ def test_pipelined_sweeps_equal_level_schedule(cams, shape, coarse):
     arithmetic, same bits."""
     case = make_case("3d-200x200x100", nx=shape[0], ny=shape[1], nz=shape[2], coarse=coarse,
                      n_post=3, n_pre=1)
-    r1, p1, d1 = _iterate(cams, case, 3, level=False)
-    r2, p2, d2 = _iterate(cams, case, 3, level=True)
-    assert np.array_equal(d1, d2)          # ILU(0) factorisation wavefront
-    assert np.array_equal(p1, p2)          # forward/backward sweeps
-    assert np.array_equal(r1, r2)
+    r0, p0, d0 = _iterate(cams, case, 3, "level")
+    for mode in ("warp", "cta"):
+        r1, p1, d1 = _iterate(cams, case, 3, mode)
+        assert np.array_equal(d1, d0), mode    # ILU(0) factorisation wavefront
+        assert np.array_equal(p1, p0), mode    # forward/backward sweeps
+        assert np.array_equal(r1, r0), mode
 
 
 def test_bounded_wait_times_out_and_context_survives(cams):

@@ -98,21 +98,24 @@ def test_mixed_basis_close_to_oracle(cams, cname, kw):
 
 
 def test_mixed_pipelined_sweeps_equal_level_schedule(cams):
-    """The FP32 wavefronts: pipelined and level-scheduled give the same bits."""
+    """The FP32 wavefronts: pipelined (CTA blocks or warp tiles) and
+    level-scheduled give the same bits."""
     import os
     case = make_case("3d-200x200x100", nx=20, ny=72, nz=40, coarse=(10, 8, 8), n_post=3,
                      precision=1)
     out = []
-    for level in (False, True):
-        old = os.environ.get("CAMS_ILU_LEVEL")
-        os.environ["CAMS_ILU_LEVEL"] = "1" if level else "0"
+    for level, cta in ((False, "1"), (False, "0"), (True, "0")):
+        env = {"CAMS_ILU_LEVEL": "1" if level else "0", "CAMS_ILU_CTA": cta}
+        old = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
         try:
             h, bc, keep = gpu_handle(case)
         finally:
-            if old is None:
-                del os.environ["CAMS_ILU_LEVEL"]
-            else:
-                os.environ["CAMS_ILU_LEVEL"] = old
+            for k, v in old.items():
+                if v is None:
+                    del os.environ[k]
+                else:
+                    os.environ[k] = v
         try:
             rng = np.random.default_rng(3)
             p_nu = rng.uniform(0, 1, case.N)
@@ -125,10 +128,11 @@ def test_mixed_pipelined_sweeps_equal_level_schedule(cams):
             out.append((d, p, res))
         finally:
             cams.cams_destroy(h)
-    (d1, p1, r1), (d2, p2, r2) = out
-    assert np.array_equal(d1, d2)
-    assert np.array_equal(p1, p2)
-    assert np.array_equal(r1, r2)
+    d0, p0, r0 = out[-1]
+    for d1, p1, r1 in out[:-1]:
+        assert np.array_equal(d1, d0)
+        assert np.array_equal(p1, p0)
+        assert np.array_equal(r1, r0)
 
 
 def test_mixed_full_size_matches_fp64_engine(cams):
