@@ -46,7 +46,7 @@ from .ilu import ilu0, ilu_apply
 class Options:
     coarse: tuple = (5, 5, 1)
     basis: int = 4
-    restriction: int = 0
+    restriction: int = 0   # 0 MSFE, 1 MSFV, 2 MSFE then one closing MSFV correction (Sec. 4.3)
     n_pre: int = 0
     n_post: int = 1
     lin_rtol: float = 0.1
@@ -143,6 +143,7 @@ class StepStats:
     eps_hist: list = field(default_factory=list)
     cams_per_newton: list = field(default_factory=list)
     res_final: float = 0.0
+    msfv_final: bool = False     # the closing MSFV correction was applied (restriction 2)
 
 
 def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
@@ -167,7 +168,7 @@ def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
         Ab = basis_operator(pb, opt.basis, lin.rho, lin.c, p_n, dt)
         st.basis_rebuilt += state.update(Ab, opt.adapt_theta)
         P = state.matrix()
-        R = restriction(opt.restriction, P, wb)
+        R = restriction(0 if opt.restriction == 2 else opt.restriction, P, wb)
         lu = coarse_factor(coarse_operator(R, lin.A, P))
         r0 = float(np.linalg.norm(lin.f - lin.A @ p))
         its = 0
@@ -181,6 +182,16 @@ def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
         st.cams_its += its
         st.cams_per_newton.append(its)
         st.newton_its += 1
+    if opt.restriction == 2 and st.converged and st.newton_its > 0:
+        # Sec. 4.3: converge with MSFE, then one MSFV coarse correction of the
+        # last linearisation (A, f at the converged p) with the current basis:
+        # p <- p + P (R_FV A P)^{-1} R_FV (f - A p).  Afterwards R_FV (f - A p)
+        # vanishes: the linearised fluxes balance on every primal block.
+        P = state.matrix()
+        Rfv = restriction(1, P, wb)
+        lu_fv = coarse_factor(coarse_operator(Rfv, lin.A, P))
+        p = p + P @ coarse_solve(lu_fv, Rfv @ (lin.f - lin.A @ p))
+        st.msfv_final = True
     return p, st
 
 

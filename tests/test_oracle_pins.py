@@ -444,3 +444,36 @@ def test_newton_control_counts(rng):
         assert s.converged and s.newton_its == len(s.cams_per_newton)
         assert all(c >= 1 for c in s.cams_per_newton)
         assert s.eps_hist[-1] < 1e-8 * s.eps_hist[0] <= s.eps_hist[-2]
+
+
+def test_msfe_then_msfv_closing_correction(rng):
+    """Restriction 2 (Sec. 4.3): the step converges with MSFE exactly as with
+    restriction 0, then one MSFV coarse correction of the last linearisation
+    makes the restricted residual vanish block by block, without undoing the
+    nonlinear convergence."""
+    g = _grid(12, 10, 6)
+    pb = _problem(g, _lognormal(g.N, rng, 2.0), c=0.2)
+    wb0 = build_wirebasket(g, (4, 5, 3))
+    p_n = np.zeros(g.N)
+    dt = 0.01
+    out = {}
+    for R in (0, 2):
+        opt = Options(coarse=(4, 5, 3), basis=4, restriction=R, n_post=2, nl_tol=1e-9)
+        p, st = solve_step(pb, wb0, BasisState(wb0), opt, p_n, dt)
+        out[R] = (p, st)
+    (p0, s0), (p2, s2) = out[0], out[2]
+    assert s0.converged and s2.converged and s2.msfv_final and not s0.msfv_final
+    assert s2.newton_its == s0.newton_its and s2.cams_per_newton == s0.cams_per_newton
+    # the correction is the MSFV coarse step on the linearisation at p0
+    lin = assemble(pb, p0, p_n, dt)
+    st = BasisState(wb0)
+    st.update(basis_operator(pb, 4, lin.rho, lin.c, p_n, dt), 0.1)
+    Rv = restriction(1, st.matrix(), wb0)
+    blk = Rv @ (lin.f - lin.A @ p2)
+    scale = np.abs(Rv @ np.abs(lin.A @ p0)).max()
+    assert np.abs(blk).max() <= 1e-12 * scale
+    # whereas the MSFE solution itself is not conservative on the blocks
+    assert np.abs(Rv @ (lin.f - lin.A @ p0)).max() > 1e3 * np.abs(blk).max()
+    e0 = np.linalg.norm(epsilon(pb, p0, p_n, dt))
+    e2 = np.linalg.norm(epsilon(pb, p2, p_n, dt))
+    assert e2 < 10 * e0 + 1e-12
