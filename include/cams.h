@@ -88,7 +88,10 @@ typedef struct {
   int coarse[3];       /* primal-coarse block size per direction; must divide
                           the grid; >= 2 on active directions, 1 on inactive */
   int basis;           /* 1..4: basis equation (B1)..(B4) (Eqs. 8-11) */
-  int restriction;     /* 0 = MSFE (R = P^T), 1 = MSFV (Eq. 7) */
+  int restriction;     /* 0 = MSFE (R = P^T), 1 = MSFV (Eq. 7), 2 = MSFE iterations, then,
+                          once the step's Newton loop has converged, one MSFV coarse
+                          correction of the last linearisation for mass conservation
+                          (Sec. 4.3) */
   int n_pre, n_post;   /* ILU(0) pre- / post-smoothing steps per iteration */
   double lin_rtol;     /* inner stop: ||r^i|| / ||r^0|| < lin_rtol (0.1 in Sec. 4.1.1) */
   double nl_tol;       /* outer stop: ||eps|| < nl_tol * ||eps at p^n|| (or absolute) */

@@ -330,7 +330,7 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
     }
   }
   if (o->basis < 1 || o->basis > 4) return fail(nullptr, CAMS_EINVAL, "basis must be 1..4");
-  if (o->restriction != 0 && o->restriction != 1) return fail(nullptr, CAMS_EINVAL, "restriction must be 0 or 1");
+  if (o->restriction < 0 || o->restriction > 2) return fail(nullptr, CAMS_EINVAL, "restriction must be 0, 1 or 2");
   if (o->n_pre < 0 || o->n_post < 0) return fail(nullptr, CAMS_EINVAL, "smoothing counts must be >= 0");
   if (o->max_newton < 1 || o->max_newton > kMaxNewton) return fail(nullptr, CAMS_EINVAL, "max_newton must be 1..64");
   if (o->max_cams < 1) return fail(nullptr, CAMS_EINVAL, "max_cams must be >= 1");
@@ -444,13 +444,14 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   h->last_rebuilt = rebuilt;
   if (n_rebuilt) *n_rebuilt = rebuilt;
   // Galerkin coarse operator and its factorisation
-  if (o.restriction == 0)
+  // restriction 2 iterates with MSFE (its MSFV correction closes the step)
+  if (o.restriction != 1)
     LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
   else
     LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
-    const int sym = o.restriction == 0;   // MSFE: R A P = P^T A P is symmetric
+    const int sym = o.restriction != 1;   // MSFE: R A P = P^T A P is symmetric
     CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
     CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
   }
@@ -499,8 +500,9 @@ int cams_step(cams_handle* h) {
     if (s) LAUNCH(CAMS_PROF_ILU_BWD, launch_add_correction(h->g, b, h->stream));
     LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
   }
-  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, h->opt.restriction, b.r, s, b, h->stream));
-  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, h->opt.restriction == 0,
+  const int fv = h->opt.restriction == 1;
+  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, fv, b.r, s, b, h->stream));
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv,
                                                    h->coarse_cluster, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, s, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
@@ -749,6 +751,26 @@ int cams_update_basis(cams_handle* h, int force, int* n_rebuilt_out) {
   return update_operators(h, force, n_rebuilt_out);
 }
 
+// Restriction 2 (Sec. 4.3): after the step's Newton loop has converged with
+// MSFE, one MSFV coarse correction of the last linearisation (A, f at the
+// converged p) with the current basis: p += P (R_FV A P)^{-1} R_FV (f - A p).
+// The restricted residual then vanishes on every primal block.  FP64 in
+// either precision (the mixed preconditioner's FP32 P is read and widened).
+int closing_msfv(cams_handle* h) {
+  Buffers& b = h->b;
+  LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
+  {
+    ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
+    CK(launch_band_fill(h->c, h->mc, 0, b, h->stream));
+    CK(launch_band_factor(h->c.Nc, h->mc, 0, b, h->stream));
+  }
+  LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
+  LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, 1, b.r, h->single, b, h->stream));
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, 0, false, b, h->stream));
+  LAUNCH(CAMS_PROF_PROLONG, launch_prolong_to_p(h->g, h->c, h->single, b, h->stream));
+  return check_status(h);
+}
+
 int cams_iterate(cams_handle* h, int n, double* res_norms) {
   if (!h) return CAMS_EINVAL;
   if (!h->built) return fail(h, CAMS_EINVAL, "cams_update_basis must come first");
@@ -829,6 +851,10 @@ int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc, 
     st.cams_its += its;
     if (st.newton_its < 64) st.cams_per_newton[st.newton_its] = its;
     st.newton_its += 1;
+  }
+  if (result == CAMS_OK && o.restriction == 2 && st.newton_its > 0) {
+    rc = closing_msfv(h);
+    if (rc) return rc;
   }
   rc = check_status(h);
   if (rc) return rc;

@@ -165,6 +165,9 @@ bool coarse_cluster_ok(int Nc, int max_smem);
 // FP64: p += P p_c; single: delta = P p_c (FP32 P and delta)
 cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                cudaStream_t s);
+// p += P p_c in FP64 whatever the precision of P
+cudaError_t launch_prolong_to_p(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                                cudaStream_t s);
 // single: the FP32 smoother of the mixed-precision preconditioner (on
 // A delta = r, vectors in b.f32); otherwise the FP64 smoother on A p = f.
 // sms: the SM count (from ilu_pipe_grid); cta: tiles in 2 x 2 blocks per CTA

@@ -812,9 +812,9 @@ __global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double
 }
 
 // p += P p_c (FP64), or delta = P p_c (the mixed-precision preconditioner:
-// P, p_c and delta in FP32)
-template <class TP, class TO, bool kSet>
-__global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TP* __restrict__ pc,
+// P, p_c and delta in FP32); the sum is formed in p_c's precision
+template <class TP, class TC, class TO, bool kSet>
+__global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TC* __restrict__ pc,
                           const int* __restrict__ perm, TO* p) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
@@ -824,12 +824,12 @@ __global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TP* __r
     Jl[d][0] = corner_d(c, d, xc[d], 0);
     Jl[d][1] = corner_d(c, d, xc[d], 1);
   }
-  TP s = TP(0);
+  TC s = TC(0);
 #pragma unroll
   for (int sl = 0; sl < 8; ++sl) {
     const int jx = Jl[0][sl & 1], jy = Jl[1][(sl >> 1) & 1], jz = Jl[2][(sl >> 2) & 1];
     if (jx < 0 || jy < 0 || jz < 0) continue;
-    s += P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
+    s += (TC)P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
   }
   if (kSet) p[i] = (TO)s;
   else p[i] += (TO)s;
@@ -984,10 +984,23 @@ cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers
   const int blocks = (int)((g.N + 255) / 256);
   if (single) {
     k_to_single<<<(c.Nc + 255) / 256, 256, 0, s>>>(c.Nc, b.pc, b.f32.pc);
-    k_prolong<float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm, b.f32.d);
+    k_prolong<float, float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm,
+                                                              b.f32.d);
     count_launches(1);
-  } else
-    k_prolong<double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+  } else {
+    k_prolong<double, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_to_p(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                                cudaStream_t s) {
+  const int blocks = (int)((g.N + 255) / 256);
+  if (single)
+    k_prolong<float, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.pc, b.perm, b.p);
+  else
+    k_prolong<double, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
   count_launches(1);
   return cudaGetLastError();
 }

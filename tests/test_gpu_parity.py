@@ -229,3 +229,17 @@ def test_solve_3d_wells_adaptive(cams, R):
     for (p, n, c, r, per), so in zip(out, sto):
         assert abs(n - so.newton_its) <= 1
         assert r == so.basis_rebuilt
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
+def test_msfe_then_msfv_step(cams, precision, tol):
+    """Restriction 2: MSFE iterations, then one closing MSFV correction of the
+    last linearisation (Sec. 4.3), FP64 and mixed precision, against the
+    oracle (whose correction zeroes the MSFV-restricted residual)."""
+    case = make_case("3d-200x200x100", nx=24, ny=20, nz=12, coarse=(4, 5, 4), restriction=2,
+                     steps=1, nl_tol=1e-9, precision=precision)
+    out, q, sto = _run_both(cams, case, 1)
+    pg, nwt, cit, rb, per = out[-1]
+    assert sto[0].msfv_final
+    assert _rel(pg, q) < tol
+    assert abs(nwt - sto[0].newton_its) <= 1
