@@ -15,6 +15,10 @@ for the rho-weighted ones, which does not change the local solutions):
 Reading R10: A_b holds internal faces only; the global Dirichlet faces and
 the sources do not enter the local problems, whose boundary conditions are
 the reduced-problem (localisation) conditions.
+Reading R19: prescribed-pressure cells are eliminated from A_b as from A
+(unit rows, no couplings; free rows keep their diagonal), so the local
+problems see a homogeneous Dirichlet condition there and the basis values
+of a fixed cell are zero.
 
 Reading R9 (the paper cites the algebraic multiscale solver for the
 reduced-problem conditions without restating them): wirebasket construction.
@@ -35,7 +39,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
-from .problem import Problem, accumulation_coefficient
+from .problem import Problem, accumulation_coefficient, eliminate_fixed
 from .wirebasket import Wirebasket
 
 
@@ -61,6 +65,8 @@ def basis_operator(pb: Problem, kind: int, rho_nu, c_nu, p_n, dt) -> sp.csr_matr
     Ab = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
     Ab.sum_duplicates()
     Ab.sort_indices()
+    if pb.has_fixed:
+        Ab = eliminate_fixed(Ab, pb.fixed)
     return Ab
 
 

@@ -21,6 +21,14 @@ on a Dirichlet face it is rho(p_boundary).
 Reading R6: the saturation S^n of Eq. 19 is 1 (single phase).
 Reading R7: every row of Eq. 3 is multiplied by V_i rho_i^nu, which makes the
 matrix A = C + A~ of Eq. 6 symmetric and leaves its solution unchanged.
+Reading R19 (Test Case 2 of Sec. 4.2.2 prescribes p at the centres of two
+vertical columns of cells without saying how): the prescribed ("fixed") cells
+are taken out of the unknowns by symmetric elimination.  Their entries of
+the iterate hold the prescribed values, each fixed row of A reads
+p_i = p_D (unit diagonal, no couplings), the couplings of free cells to
+fixed cells move to the right-hand side, and Eq. 19 is not imposed at fixed
+cells (eps = 0 there).  A fixed cell may not be a coarse node: eliminating
+it would remove a coarse unknown.
 """
 from __future__ import annotations
 
@@ -76,17 +84,31 @@ class Fluid:
 class BC:
     """Dirichlet pressure on the west (x = 0) and east (x = nx-1) faces, or
     none (no-flow everywhere); plus point sources with volumetric rates
-    Q_i = q_i dV_i (the integrated source of Eq. 6), positive = injection."""
+    Q_i = q_i dV_i (the integrated source of Eq. 6), positive = injection;
+    plus cells whose centre pressure is prescribed (Reading R19)."""
     dirichlet: bool = True
     p_west: float = 1.0
     p_east: float = 0.0
     src_cell: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     src_rate: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    fix_cell: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    fix_value: np.ndarray = field(default_factory=lambda: np.zeros(0))
 
     def source_vector(self, N):
         Q = np.zeros(N)
         np.add.at(Q, np.asarray(self.src_cell, dtype=np.int64), np.asarray(self.src_rate, dtype=np.float64))
         return Q
+
+    def fixed_cells(self, N):
+        """(mask, values): the prescribed cells and their pressures; a cell
+        listed more than once takes the last value listed."""
+        mask = np.zeros(N, bool)
+        val = np.zeros(N)
+        for c, v in zip(np.asarray(self.fix_cell, np.int64).tolist(),
+                        np.asarray(self.fix_value, np.float64).tolist()):
+            mask[c] = True
+            val[c] = v
+        return mask, val
 
 
 @dataclass(frozen=True)
@@ -140,11 +162,41 @@ class Problem:
     bc: BC
     faces: Faces
     Q: np.ndarray     # integrated volumetric source per cell
+    fixed: np.ndarray = None   # bool mask of the prescribed cells (Reading R19)
+    p_fix: np.ndarray = None   # their pressures (0 elsewhere)
 
     @staticmethod
     def build(grid: Grid, fluid: Fluid, bc: BC, kx, ky, kz) -> "Problem":
+        mask, val = bc.fixed_cells(grid.N)
         return Problem(grid, fluid, bc, transmissibilities(grid, kx, ky, kz, fluid.mu, bc),
-                       bc.source_vector(grid.N))
+                       bc.source_vector(grid.N), mask, val)
+
+    @property
+    def has_fixed(self) -> bool:
+        return self.fixed is not None and bool(self.fixed.any())
+
+    def with_fixed(self, p):
+        """A copy of p carrying the prescribed values at the fixed cells."""
+        p = np.array(p, dtype=np.float64, copy=True)
+        if self.has_fixed:
+            p[self.fixed] = self.p_fix[self.fixed]
+        return p
+
+
+def eliminate_fixed(M: sp.csr_matrix, fixed: np.ndarray) -> sp.csr_matrix:
+    """Symmetric elimination of the fixed unknowns (Reading R19): every entry
+    in a row or a column of a fixed cell is dropped, then each fixed row gets
+    a unit diagonal."""
+    coo = M.tocoo()
+    keep = ~(fixed[coo.row] | fixed[coo.col])
+    F = np.flatnonzero(fixed)
+    rows = np.concatenate([coo.row[keep], F])
+    cols = np.concatenate([coo.col[keep], F])
+    vals = np.concatenate([coo.data[keep], np.ones(F.size)])
+    out = sp.coo_matrix((vals, (rows, cols)), shape=M.shape).tocsr()
+    out.sum_duplicates()
+    out.sort_indices()
+    return out
 
 
 def _flux_sum(pb: Problem, rho, p):
@@ -183,7 +235,10 @@ def epsilon(pb: Problem, p, p_n, dt):
     rho_n = fl.rho(p_n)
     q = pb.Q / g.V
     div = -_flux_sum(pb, rho, p) / g.V
-    return q - fl.phi / dt + (fl.phi / dt) * rho_n / rho + div / rho
+    e = q - fl.phi / dt + (fl.phi / dt) * rho_n / rho + div / rho
+    if pb.has_fixed:
+        e[pb.fixed] = 0.0       # Reading R19: no equation at a fixed cell
+    return e
 
 
 @dataclass
@@ -215,6 +270,7 @@ def assemble(pb: Problem, p, p_n, dt) -> Linearised:
     """
     g, fl, fc = pb.grid, pb.fluid, pb.faces
     N, V = g.N, g.V
+    p = pb.with_fixed(p)
     rho = fl.rho(p)
     rho_n = fl.rho(p_n)
     c = accumulation_coefficient(fl, p, p_n, dt)
@@ -237,4 +293,11 @@ def assemble(pb: Problem, p, p_n, dt) -> Linearised:
     A.sum_duplicates()
     A.sort_indices()
     f = V * rho * b + rhs_b + Cdiag * p
+    if pb.has_fixed:
+        # Reading R19: with p_F known, row j of A p = f reads
+        # sum_{k free} a_jk p_k = f_j - sum_{k fixed} a_jk p_k
+        Fm = pb.fixed
+        f = f - A[:, Fm] @ p[Fm]
+        f[Fm] = p[Fm]
+        A = eliminate_fixed(A, Fm)
     return Linearised(A, f, epsilon(pb, p, p_n, dt), rho, c, Cdiag)

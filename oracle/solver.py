@@ -149,7 +149,8 @@ class StepStats:
 def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
                p_n: np.ndarray, dt: float, p_init=None):
     """One implicit time step from p^n: returns (p^{n+1}, StepStats)."""
-    p = (p_n if p_init is None else p_init).copy()
+    check_fixed(pb, wb)
+    p = pb.with_fixed(p_n if p_init is None else p_init)
     st = StepStats()
     eps0 = None
     for nu in range(opt.max_newton + 1):
@@ -193,6 +194,12 @@ def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
         p = p + P @ coarse_solve(lu_fv, Rfv @ (lin.f - lin.A @ p))
         st.msfv_final = True
     return p, st
+
+
+def check_fixed(pb: Problem, wb: Wirebasket):
+    """Reading R19: a prescribed-pressure cell may not be a coarse node."""
+    if pb.has_fixed and np.any(wb.level[pb.fixed] == 0):
+        raise ValueError("a fixed cell is a coarse node")
 
 
 def run(pb: Problem, opt: Options, p0: np.ndarray, dt: float, steps: int):

@@ -477,3 +477,135 @@ def test_msfe_then_msfv_closing_correction(rng):
     e0 = np.linalg.norm(epsilon(pb, p0, p_n, dt))
     e2 = np.linalg.norm(epsilon(pb, p2, p_n, dt))
     assert e2 < 10 * e0 + 1e-12
+
+
+# ------------------------------------ Test Case 2: prescribed cells, alpha --
+
+def _tc2_problem(g, k, cells, vals, law=1, c=1.0, dirichlet=False):
+    fl = Fluid(law, c, 1.0, 1.0, 0.1)
+    bc = BC(dirichlet, 1.0, 0.0, fix_cell=np.asarray(cells), fix_value=np.asarray(vals))
+    return Problem.build(g, fl, bc, *k)
+
+
+def _columns(g, a, b):
+    z = np.arange(g.nz)
+    ca = a[0] + g.nx * (a[1] + g.ny * z)
+    cb = b[0] + g.nx * (b[1] + g.ny * z)
+    return np.concatenate([ca, cb]), np.concatenate([np.ones(g.nz), np.zeros(g.nz)])
+
+
+@pytest.mark.parametrize("alpha", [1.0, 5.0])
+def test_prescribed_columns_solve_the_mass_balance(rng, alpha):
+    """Sec. 4.2.2 (Reading R19): with p prescribed on two vertical columns of
+    cells, the converged step holds exactly those values there and is a root
+    of the discrete mass balance (Eq. 2, evaluated by the flux-sum residual,
+    not by the linear system) on every other cell."""
+    nx, ny, nz = 12, 10, 8
+    h = 1.0 / nx
+    g = Grid(nx, ny, nz, alpha * h, h, h)
+    cells, vals = _columns(g, (0, 0), (nx - 1, ny - 1))
+    pb = _tc2_problem(g, _lognormal(g.N, rng, 2.0), cells, vals)
+    p_n = np.zeros(g.N)
+    dt = 0.4 * 0.1 * alpha ** 2
+    opt = Options(coarse=(4, 5, 4), basis=4, n_post=5, nl_tol=1e-12, max_newton=30)
+    p, st = run(pb, opt, p_n, dt, 1)
+    assert st[0].converged
+    assert np.array_equal(p[cells], vals)
+    free = np.ones(g.N, bool)
+    free[cells] = False
+    F0 = residual(pb, pb.with_fixed(p_n), p_n, dt)
+    F = residual(pb, p, p_n, dt)
+    assert np.abs(F[free]).max() < 1e-9 * np.abs(F0[free]).max()
+    # the columns drive flow from the p = 1 column to the p = 0 column
+    assert 0.0 < p[free].min() and p[free].max() < 1.0
+    assert p[0 + nx * 1] > p[(nx - 1) + nx * (ny - 2)]
+
+
+def test_prescribing_the_solution_changes_nothing(rng):
+    """Fixing interior cells at the values the unconstrained problem takes
+    there leaves the solution unchanged: the elimination adds nothing but
+    the known values (a wrong sign or a lost coupling would move it)."""
+    g = _grid(12, 10, 6)
+    k = _lognormal(g.N, rng, 1.5)
+    p_n = np.zeros(g.N)
+    dt = 0.01
+    opt = Options(coarse=(4, 5, 3), basis=4, n_post=3, nl_tol=1e-12, max_newton=30)
+    pb0 = _problem(g, k, law=0, c=0.3)
+    p_ref, st = run(pb0, opt, p_n, dt, 1)
+    assert st[0].converged
+    z = np.arange(g.nz)
+    cells = np.concatenate([3 + g.nx * (4 + g.ny * z), 9 + g.nx * (8 + g.ny * z)])
+    fl = Fluid(0, 0.3, 1.0, 1.0, 0.1)
+    bc = BC(True, 1.0, 0.0, fix_cell=cells, fix_value=p_ref[cells])
+    pb1 = Problem.build(g, fl, bc, *k)
+    p_fix, st1 = run(pb1, opt, p_n, dt, 1)
+    assert st1[0].converged
+    np.testing.assert_allclose(p_fix, p_ref, rtol=0, atol=1e-9)
+    # whereas fixing them elsewhere does move it
+    bc2 = BC(True, 1.0, 0.0, fix_cell=cells, fix_value=p_ref[cells] + 0.1)
+    p_off, _ = run(Problem.build(g, fl, bc2, *k), opt, p_n, dt, 1)
+    assert np.abs(p_off - p_ref).max() > 1e-3
+
+
+def test_prescribed_cells_leave_a_symmetric_system_and_zero_basis_rows(rng):
+    """Reading R19: the eliminated A and A_b stay symmetric, fixed rows are
+    unit rows, and the basis functions vanish on fixed cells; the coarse
+    operator P^T A P stays symmetric positive definite."""
+    g = _grid(12, 10, 8)
+    cells, vals = _columns(g, (0, 0), (11, 9))
+    pb = _tc2_problem(g, _lognormal(g.N, rng, 2.0), cells, vals)
+    p_n = np.zeros(g.N)
+    lin = assemble(pb, p_n, p_n, 0.04)
+    A = lin.A.toarray()
+    np.testing.assert_array_equal(A, A.T)
+    np.testing.assert_array_equal(A[cells], np.eye(g.N)[cells])
+    np.testing.assert_array_equal(lin.f[cells], vals)
+    assert np.all(lin.eps[cells] == 0.0)
+    wb = build_wirebasket(g, (4, 5, 4))
+    Ab = basis_operator(pb, 4, lin.rho, lin.c, p_n, 0.04)
+    Abd = Ab.toarray()
+    np.testing.assert_array_equal(Abd, Abd.T)
+    P = prolongation(Ab, wb).to_csr(wb.Nc).toarray()
+    assert np.all(P[cells] == 0.0)
+    Ac = P.T @ A @ P
+    np.testing.assert_allclose(Ac, Ac.T, rtol=1e-12, atol=1e-14 * np.abs(Ac).max())
+    assert np.linalg.eigvalsh(0.5 * (Ac + Ac.T)).min() > 0
+    # the basis still sums to one away from the columns' dual blocks
+    far = (np.abs(g.coords()[0] - 6) <= 1) & (np.abs(g.coords()[1] - 5) <= 1)
+    np.testing.assert_allclose(P.sum(axis=1)[far], 1.0, rtol=1e-12)
+
+
+def test_prescribed_coarse_node_is_rejected():
+    """A fixed cell may not be a coarse node (Reading R19)."""
+    g = _grid(8, 8, 1)
+    wb = build_wirebasket(g, (4, 4, 1))
+    node = int(np.flatnonzero(wb.level == 0)[0])
+    one = np.ones(g.N)
+    pb = _tc2_problem(g, (one, one, one), [node], [0.5])
+    with pytest.raises(ValueError):
+        run(pb, Options(coarse=(4, 4, 1)), np.zeros(g.N), 0.01, 1)
+
+
+@pytest.mark.parametrize("alpha", [5.0, 10.0])
+def test_stretched_grid_closed_forms(alpha):
+    """Delta x / alpha = Delta y = Delta z: for homogeneous k the face
+    transmissibilities are k dy dz / dx and k dx dz / dy, so T_x / T_y =
+    1 / alpha^2; and the incompressible west-east solution is still
+    p_i = 1 - (x_i + 1/2)/nx, which C-AMS reaches."""
+    nx, ny, nz = 12, 8, 6
+    h = 1.0 / nx
+    g = Grid(nx, ny, nz, alpha * h, h, h)
+    one = np.ones(g.N)
+    pb = _problem(g, (one, one, one), law=1, c=0.0)
+    fc = pb.faces
+    d = fc.hi - fc.lo
+    tx, ty, tz = fc.T[d == 1], fc.T[d == nx], fc.T[d == nx * ny]
+    np.testing.assert_allclose(tx, h * h / (alpha * h), rtol=1e-14)
+    np.testing.assert_allclose(ty, alpha * h * h / h, rtol=1e-14)
+    np.testing.assert_allclose(tx[0] / ty[0], 1.0 / alpha ** 2, rtol=1e-14)
+    np.testing.assert_allclose(tz, ty[0], rtol=1e-14)
+    opt = Options(coarse=(2, 4, 3), basis=4, n_post=3, nl_tol=1e-13, max_newton=20)
+    p, st = run(pb, opt, np.zeros(g.N), 1e-3, 1)
+    x, _, _ = g.coords()
+    np.testing.assert_allclose(p, 1.0 - (x + 0.5) / g.nx, atol=1e-12)
+    assert st[0].converged

@@ -2,10 +2,12 @@
 step and solver options of the synthetic cases, and the recipe that turns
 one into concrete input arrays.
 
-Non-dimensionalisation follows Sec. 4 of the paper: the domain has unit
-length in x (cells are cubes of side h = 1/nx), Delta p = p_west - p_east = 1,
+Non-dimensionalisation follows Sec. 4 of the paper: h = 1/nx, cells of
+h x h x h (stretched to alpha h x h x h when the aspect ratio alpha != 1, so
+the domain is alpha L long in x with L = 1), Delta p = p_west - p_east = 1,
 mu = 1, phi = 0.1, and the time step is Delta t = Delta t* . tau with
-tau = mu phi L^2 / (K_bar Delta p), K_bar the geometric mean of k (Eq. 18).
+tau = mu phi (alpha L)^2 / (K_bar Delta p), K_bar the geometric mean of k
+(Sec. 4; Test Case 2 of Sec. 4.2.2 takes alpha L as the length scale).
 """
 from __future__ import annotations
 
@@ -34,7 +36,7 @@ class Workload:
     rho0: float = 1.0
     mu: float = 1.0
     phi: float = 0.1
-    bc: str = "dirichlet_we"  # or "wells"
+    bc: str = "dirichlet_we"  # or "wells", or "lines" (two prescribed vertical columns)
     p_west: float = 1.0
     p_east: float = 0.0
     well_rate: float = 0.02   # drawdown scale of the well rates (wells only)
@@ -50,6 +52,7 @@ class Workload:
     max_newton: int = 50
     max_cams: int = 200
     precision: int = 0        # engine option: 0 = FP64, 1 = FP32 preconditioner in FP64 refinement
+    alpha: float = 1.0        # grid aspect ratio: dx / alpha = dy = dz
     seeds: tuple = (0,)
 
     @property
@@ -89,6 +92,30 @@ WORKLOADS = {
         restriction=0, n_post=5, nl_tol=1e-8, seeds=(0,), precision=1),
 }
 
+# Test Case 2 of Sec. 4.2.2: the 64^3 patchy set (spherical variogram, ln k
+# variance 4, correlation length 0.125 L in every direction), rho* = 1 + p*
+# (eta = 1), pressure prescribed at the centres of the vertical columns
+# (0, 0, z) = 1 and (63, 63, z) = 0 with no-flow faces, grid aspect ratio
+# alpha in {1, 5, 10}, the first time step t* = 0 -> 0.4, (B4), MSFE,
+# 5 ILU(0) post steps, coarsening 8x8x8 (alpha 1) and 2x8x8 (alpha 5, 10).
+for _a, _cb in ((1, (8, 8, 8)), (5, (2, 8, 8)), (10, (2, 8, 8))):
+    _n = f"3d-64x64x64-lines-a{_a}"
+    WORKLOADS[_n] = Workload(
+        name=_n, nx=64, ny=64, nz=64, coarse=_cb, sigma=2.0, corr=(0.125, 0.125, 0.125),
+        cov="spherical", law=1, c_or_eta=1.0, bc="lines", steps=1, dt_star=0.4, basis=4,
+        restriction=0, n_post=5, nl_tol=1e-6, alpha=float(_a), seeds=tuple(range(20)))
+
+
+def line_columns(w: Workload):
+    """Cells and values of the two prescribed columns of Test Case 2: the
+    column (0, 0, z) at p_west and the column (nx-1, ny-1, z) at p_east."""
+    z = np.arange(w.nz, dtype=np.int64)
+    a = 0 + w.nx * (0 + w.ny * z)
+    b = (w.nx - 1) + w.nx * ((w.ny - 1) + w.ny * z)
+    cells = np.concatenate([a, b]).astype(np.int32)
+    vals = np.concatenate([np.full(w.nz, w.p_west), np.full(w.nz, w.p_east)])
+    return cells, vals
+
 
 def _cell_transmissibility_sum(w: Workload, kx, ky, kz, h):
     """Sum over the internal faces of each cell of A_f / (h/(2k_a) + h/(2k_b))
@@ -114,7 +141,8 @@ def make_inputs(w: Workload, seed: int | None = None):
 
     Returns a dict with grid spacing, kx/ky/kz (float64, length N, index
     x + nx*(y + ny*z)), the time step dt, the initial pressure p0 (zero, as
-    in Sec. 4.1.3) and the source list (cell ids and volumetric rates q_i dV_i).
+    in Sec. 4.1.3), the source list (cell ids and volumetric rates q_i dV_i)
+    and the prescribed cells with their pressures.
     """
     seed = w.seeds[0] if seed is None else seed
     kx, ky, kz = lognormal_permeability(
@@ -123,10 +151,14 @@ def make_inputs(w: Workload, seed: int | None = None):
     h = 1.0 / w.nx
     k_bar = math.exp(float(np.mean(np.log(kx))))
     dp = 1.0
-    tau = w.mu * w.phi * 1.0 ** 2 / (k_bar * dp)
+    tau = w.mu * w.phi * w.alpha ** 2 / (k_bar * dp)
     dt = w.dt_star * tau
     src_cell = np.zeros(0, dtype=np.int32)
     src_rate = np.zeros(0, dtype=np.float64)
+    fix_cell = np.zeros(0, dtype=np.int32)
+    fix_value = np.zeros(0, dtype=np.float64)
+    if w.bc == "lines":
+        fix_cell, fix_value = line_columns(w)
     if w.bc == "wells":
         # Vertical line wells through all layers at columns (0,0) (injector)
         # and (nx-1, ny-1) (producer).  Rates are fixed for the whole run.
@@ -140,8 +172,9 @@ def make_inputs(w: Workload, seed: int | None = None):
         tsum = _cell_transmissibility_sum(w, kx, ky, kz, h)
         src_rate = np.concatenate([w.well_rate * tsum[inj], -w.well_rate * tsum[prod]])
     return dict(
-        nx=w.nx, ny=w.ny, nz=w.nz, dx=h, dy=h, dz=h,
+        nx=w.nx, ny=w.ny, nz=w.nz, dx=w.alpha * h, dy=h, dz=h,
         kx=kx, ky=ky, kz=kz, dt=dt, tau=tau, k_bar=k_bar,
         p0=np.zeros(w.n_cells), src_cell=src_cell, src_rate=src_rate,
+        fix_cell=fix_cell, fix_value=fix_value,
         dirichlet=(w.bc == "dirichlet_we"), p_west=w.p_west, p_east=w.p_east,
     )
