@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import WORKLOADS, make_inputs  # noqa: E402
+from workloads import WORKLOADS, make_inputs, line_columns  # noqa: E402
 
 METRIC = ("Newton-step wall time & fine-cell·iters/s to 1e-8 residual; "
           "learned/FP32 vs FP64 C-AMS")
@@ -188,8 +188,13 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
     if len(inp["src_cell"]):
         src = (torch.from_numpy(inp["src_cell"].astype(np.int32)).to(dev),
                torch.from_numpy(inp["src_rate"]).to(dev))
+    fix = None
+    if len(inp["fix_cell"]):
+        fix = (torch.from_numpy(inp["fix_cell"].astype(np.int32)).to(dev),
+               torch.from_numpy(inp["fix_value"]).to(dev))
     bc, keep = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
-                            src[0] if src else None, src[1] if src else None)
+                            src[0] if src else None, src[1] if src else None,
+                            fix[0] if fix else None, fix[1] if fix else None)
     stream = torch.cuda.current_stream(dev)
     h = _handles(cams, w, inp, cams.CAMS_DEVICE, dk)
     cams.cams_set_stream(h, stream.cuda_stream)
@@ -251,7 +256,9 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
     h_host = _handles(cams, w, inp, cams.CAMS_HOST)
     bch, keeph = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
                               inp["src_cell"] if len(inp["src_cell"]) else None,
-                              inp["src_rate"] if len(inp["src_rate"]) else None)
+                              inp["src_rate"] if len(inp["src_rate"]) else None,
+                              inp["fix_cell"] if len(inp["fix_cell"]) else None,
+                              inp["fix_value"] if len(inp["fix_value"]) else None)
     ph = np.empty(N)
     for _ in range(1):
         cams.cams_set_permeability(h_host, inp["kx"], inp["ky"], inp["kz"])
@@ -309,13 +316,21 @@ def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
     import oracle
     if inp is None:
         inp = make_inputs(w, seed)
-    nx, ny, nz = sub
+    # each side a whole number of coarse blocks, within the grid
+    nx, ny, nz = (min(n, max(2 * b, (s // b) * b))
+                  for n, b, s in zip((w.nx, w.ny, w.nz), w.coarse, sub))
     kx = inp["kx"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
     ky = inp["ky"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
     kz = inp["kz"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
     g = oracle.Grid(nx, ny, nz, inp["dx"], inp["dy"], inp["dz"])
+    if w.bc == "lines":
+        # the two prescribed columns at the sample box's own corners
+        fc, fv = line_columns(w.with_(nx=nx, ny=ny, nz=nz))
+        bc = oracle.BC(False, w.p_west, w.p_east, fix_cell=fc, fix_value=fv)
+    else:
+        bc = oracle.BC(True, w.p_west, w.p_east)
     pb = oracle.Problem.build(g, oracle.Fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi),
-                              oracle.BC(True, w.p_west, w.p_east), kx, ky, kz)
+                              bc, kx, ky, kz)
     opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
                          n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
                          adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams)

@@ -74,13 +74,29 @@ typedef struct {
  * other face is no-flow.  n_src point sources: src_cell[k] is a cell index,
  * src_rate[k] the integrated volumetric rate q_i dV_i of Eq. 6 (positive =
  * injection).  src_cell/src_rate follow cams_options.memspace and may be
- * NULL when n_src == 0.  Repeated cells add up. */
+ * NULL when n_src == 0.  Repeated cells add up.
+ *
+ * n_fix prescribed cell-centre pressures (Test Case 2 of Sec. 4.2.2 fixes
+ * two vertical columns of cells): cell fix_cell[k] holds p = fix_value[k];
+ * a cell listed more than once takes its last value.  The fixed cells are
+ * eliminated symmetrically: their entries of the iterate are set to the
+ * prescribed values on entry (and returned so in p_inout), each fixed row
+ * of A reads p_i = fix_value (unit diagonal, no couplings), the couplings of
+ * the free neighbours move to their right-hand side, Eq. 19 is not imposed
+ * there (eps = 0), and the basis operators are eliminated the same way, so
+ * the basis values of a fixed cell are 0.  A fixed cell may not be a
+ * coarse node (CAMS_EINVAL), since that would remove a coarse unknown.
+ * fix_cell/fix_value follow cams_options.memspace and may be NULL when
+ * n_fix == 0; they are read during the call only. */
 typedef struct {
   int dirichlet;
   double p_west, p_east;
   int n_src;
   const int* src_cell;
   const double* src_rate;
+  int n_fix;
+  const int* fix_cell;
+  const double* fix_value;
 } cams_bc;
 
 /* Solver options (Table 1 and Sec. 4.1). */

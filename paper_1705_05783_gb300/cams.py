@@ -51,7 +51,8 @@ class cams_fluid(C.Structure):
 
 class cams_bc(C.Structure):
     _fields_ = [("dirichlet", C.c_int), ("p_west", C.c_double), ("p_east", C.c_double),
-                ("n_src", C.c_int), ("src_cell", C.c_void_p), ("src_rate", C.c_void_p)]
+                ("n_src", C.c_int), ("src_cell", C.c_void_p), ("src_rate", C.c_void_p),
+                ("n_fix", C.c_int), ("fix_cell", C.c_void_p), ("fix_value", C.c_void_p)]
 
 
 class cams_options(C.Structure):
@@ -121,11 +122,13 @@ def _check(code, h=None):
         raise CamsError(code, _lib.cams_last_error(h).decode())
 
 
-def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None):
+def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None,
+            fix_cell=None, fix_value=None):
     """cams_bc plus the arrays it points to (kept alive by the returned tuple)."""
     keep = []
     n = 0 if src_cell is None else len(src_cell)
-    bc = cams_bc(int(bool(dirichlet)), float(p_west), float(p_east), n, None, None)
+    nf = 0 if fix_cell is None else len(fix_cell)
+    bc = cams_bc(int(bool(dirichlet)), float(p_west), float(p_east), n, None, None, nf, None, None)
     if n:
         if isinstance(src_cell, np.ndarray):
             src_cell = np.ascontiguousarray(src_cell, dtype=np.int32)
@@ -133,6 +136,13 @@ def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None
         keep += [src_cell, src_rate]
         bc.src_cell = _ptr(src_cell)
         bc.src_rate = _ptr(src_rate)
+    if nf:
+        if isinstance(fix_cell, np.ndarray):
+            fix_cell = np.ascontiguousarray(fix_cell, dtype=np.int32)
+            fix_value = np.ascontiguousarray(fix_value, dtype=np.float64)
+        keep += [fix_cell, fix_value]
+        bc.fix_cell = _ptr(fix_cell)
+        bc.fix_value = _ptr(fix_value)
     return bc, keep
 
 

@@ -42,6 +42,8 @@ struct cams_handle {
   bool built = false;
   bool assembled = false;
   bool have_src = false;
+  bool have_fix = false;        // prescribed cells in the current boundary conditions
+  int fix_cap = 0;              // capacity of b.fixc / b.fixv
   double dt = 0.0;
   int dirichlet = 0;
   double pw = 0.0, pe = 0.0, rhow = 1.0, rhoe = 1.0;
@@ -303,7 +305,8 @@ void free_all(cams_handle* h) {
                   b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
-                  b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort};
+                  b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
+                  b.fixc, b.fixv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   const SingleBuffers& f = b.f32;
@@ -343,7 +346,65 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
 
 // ----------------------------------------------------------- operations --
 
+// True when fine cell i is a coarse node (a vertex of the wirebasket).
+bool is_coarse_node(const cams_handle* h, long long i) {
+  const int n[3] = {h->g.nx, h->g.ny, h->g.nz};
+  const int xc[3] = {(int)(i % n[0]), (int)((i / n[0]) % n[1]), (int)(i / ((long long)n[0] * n[1]))};
+  for (int d = 0; d < 3; ++d) {
+    const int sft = xc[d] - h->c.o[d];
+    if (sft < 0 || sft % h->c.b[d] != 0) return false;
+  }
+  return true;
+}
+
+// Prescribed cell-centre pressures: validated on the host, copied into the
+// handle's list, then marked in b.fixm and written into the iterate b.p
+// (which must already hold this call's pressure).
+int set_fixed(cams_handle* h, const cams_bc* bc) {
+  const int n = bc ? bc->n_fix : 0;
+  if (n < 0) return fail(h, CAMS_EINVAL, "n_fix < 0");
+  h->have_fix = false;
+  if (n == 0) return CAMS_OK;
+  if (!bc->fix_cell || !bc->fix_value) return fail(h, CAMS_EINVAL, "null fixed-cell arrays");
+  std::vector<int> cells(n);
+  CK(cudaMemcpyAsync(cells.data(), bc->fix_cell, sizeof(int) * n,
+                     h->opt.memspace == CAMS_DEVICE ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < n; ++k) {
+    if (cells[k] < 0 || cells[k] >= h->g.N) return fail(h, CAMS_EINVAL, "fixed cell out of range");
+    if (is_coarse_node(h, cells[k])) return fail(h, CAMS_EINVAL, "a fixed cell is a coarse node");
+  }
+  Buffers& b = h->b;
+  if (!b.fixm) {
+    int rc = dalloc(h, &b.fixm, (size_t)h->g.N);
+    if (rc) return rc;
+  }
+  if (n > h->fix_cap) {
+    if (b.fixc) cudaFree(b.fixc);
+    if (b.fixv) cudaFree(b.fixv);
+    b.fixc = nullptr;
+    b.fixv = nullptr;
+    h->fix_cap = 0;
+    int rc = dalloc(h, &b.fixc, n);
+    if (rc) return rc;
+    rc = dalloc(h, &b.fixv, n);
+    if (rc) return rc;
+    h->fix_cap = n;
+  }
+  CK(cudaMemcpyAsync(b.fixc, cells.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(b.fixv, bc->fix_value, sizeof(double) * n, kind_in(h), h->stream));
+  CK(cudaMemsetAsync(b.fixm, 0, (size_t)h->g.N, h->stream));
+  CK(launch_fix_cells(n, b.fixc, b.fixv, b.fixm, b.p, h->g.N, h->stream));
+  // the host copy of the cell list must outlive the copy above
+  CK(cudaStreamSynchronize(h->stream));
+  h->have_fix = true;
+  return CAMS_OK;
+}
+
 int set_sources(cams_handle* h, const cams_bc* bc) {
+  int rcf = set_fixed(h, bc);
+  if (rcf) return rcf;
   h->dirichlet = bc ? bc->dirichlet : 0;
   h->pw = bc ? bc->p_west : 0.0;
   h->pe = bc ? bc->p_east : 0.0;
@@ -389,7 +450,8 @@ int assemble(cams_handle* h, double* eps_norm) {
   {
     ProfScope ps_(h, CAMS_PROF_ASSEMBLE);
     cudaError_t e = launch_density(h->g, h->fl, b.p, b.rho, h->stream);
-    if (e == cudaSuccess) e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe, b, h->stream);
+    if (e == cudaSuccess) e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe,
+                                                   h->have_fix ? b.fixm : nullptr, b, h->stream);
     b.src = src_saved;
     CK(e);
   }
@@ -407,7 +469,8 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   Buffers& b = h->b;
   const cams_options& o = h->opt;
   const int ne = (int)h->ents.size();
-  LAUNCH(CAMS_PROF_BASIS_OP, launch_basis_operator(h->g, h->fl, o.basis, h->dt, b, h->stream));
+  LAUNCH(CAMS_PROF_BASIS_OP, launch_basis_operator(h->g, h->fl, o.basis, h->dt,
+                                                     h->have_fix ? b.fixm : nullptr, b, h->stream));
   const bool adaptive = o.basis != 4;
   int rebuilt = 0;
   if (!h->built || force || o.adapt_theta < 0) {
@@ -446,9 +509,9 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   // Galerkin coarse operator and its factorisation
   // restriction 2 iterates with MSFE (its MSFV correction closes the step)
   if (o.restriction != 1)
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->single, b, h->stream));
   else
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, b, h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     const int sym = o.restriction != 1;   // MSFE: R A P = P^T A P is symmetric
@@ -758,7 +821,7 @@ int cams_update_basis(cams_handle* h, int force, int* n_rebuilt_out) {
 // either precision (the mixed preconditioner's FP32 P is read and widened).
 int closing_msfv(cams_handle* h) {
   Buffers& b = h->b;
-  LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->dirichlet, h->rhow, h->rhoe, h->single, b, h->stream));
+  LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, b, h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     CK(launch_band_fill(h->c, h->mc, 0, b, h->stream));

@@ -83,6 +83,9 @@ struct Buffers {
   double *Cacc = nullptr;                                 // V rho c (diagonal of C)
   double *f = nullptr, *eps = nullptr;
   double *src = nullptr;                                  // dense Q_i (N) or null
+  unsigned char* fixm = nullptr;                          // prescribed-cell mask (N) or null
+  int* fixc = nullptr;                                    // prescribed cells (list)
+  double* fixv = nullptr;                                 // their pressures
   double *Abd = nullptr, *Abx = nullptr, *Aby = nullptr, *Abz = nullptr;  // basis operator
   double *snap = nullptr;                                 // 7N snapshot (adaptive)
   double *P = nullptr;                                    // 8N, slot-major
@@ -131,15 +134,18 @@ cudaError_t launch_transmissibility(const Geo& g, double mu, const double* kx, c
                                     const double* kz, int dirichlet, Buffers& b, cudaStream_t s);
 cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, double* rho,
                            cudaStream_t s);
+// fixm: prescribed-cell mask (N bytes) or null
 cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int dirichlet, double pw,
-                            double pe, Buffers& b, cudaStream_t s);
+                            double pe, const unsigned char* fixm, Buffers& b, cudaStream_t s);
 cudaError_t launch_add_sources(int n, const int* cell, const double* rate, double* src,
                                long long N, cudaStream_t s);
+cudaError_t launch_fix_cells(int n, const int* cell, const double* val, unsigned char* fixm,
+                             double* p, long long N, cudaStream_t s);
 cudaError_t launch_sumsq(const double* x, long long N, double* red, double* out, cudaStream_t s);
 cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, double* r,
                             double* red, double* out, cudaStream_t s);
 cudaError_t launch_basis_operator(const Geo& g, const FluidK& fl, int kind, double dt,
-                                  Buffers& b, cudaStream_t s);
+                                  const unsigned char* fixm, Buffers& b, cudaStream_t s);
 cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,
                                Buffers& b, unsigned char* flag, cudaStream_t s);
 cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& b,
@@ -151,10 +157,10 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
                                 int count, int smem, int grid, long long lstride, int adaptive,
                                 bool single, Buffers& b, cudaStream_t s);
 cudaError_t set_entity_smem(int smem);
-cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, bool single, Buffers& b, cudaStream_t s);
-cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, bool single, Buffers& b, cudaStream_t s);
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s);
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s);
 cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, bool single,

@@ -65,14 +65,27 @@ __device__ __forceinline__ int sym_idx(int s, int t) {   // upper triangle of 8x
   return s * 8 - (s * (s - 1)) / 2 + (t - s);
 }
 
+// A = sum over the coupled faces of w_f (e_i - e_j)(e_i - e_j)^T + diag(D):
+// D_i is the row sum of A (the accumulation term, the Dirichlet faces and,
+// for a free cell, the faces to prescribed cells; 1 on a prescribed row).
+__device__ __forceinline__ double row_sum(const Geo& g, const double* __restrict__ Ad,
+                                          const double* __restrict__ Ax,
+                                          const double* __restrict__ Ay,
+                                          const double* __restrict__ Az, long long i, int x, int y,
+                                          int z) {
+  double s = Ad[i] + Ax[i] + Ay[i] + Az[i];
+  if (x < g.nx - 1) s += Ax[i + 1];
+  if (y < g.ny - 1) s += Ay[i + g.sy];
+  if (z < g.nz - 1) s += Az[i + g.sz];
+  return s;
+}
+
 // MSFE: per dual block, the 8x8 block sum over its cells and its low-side
-// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T  (A = sum of face
-// terms + diagonal D = C + Dirichlet terms).
+// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T.
 template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fe_local(
-    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const TP* __restrict__ P,
+    Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
     const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
-    const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
     double* loc) {
   __shared__ double sh[36 * 32];
   const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
@@ -91,11 +104,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     double pi[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) pi[s] = (double)P[(long long)s * g.N + i];
-    double Dd = Cacc[i];
-    if (dirichlet) {
-      if (x == 0) Dd += Tbw[y + (long long)g.ny * z] * rhow;
-      if (x == g.nx - 1) Dd += Tbe[y + (long long)g.ny * z] * rhoe;
-    }
+    const double Dd = row_sum(g, Ad, Ax, Ay, Az, i, x, y, z);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const double a = Dd * pi[s];
@@ -169,9 +178,8 @@ __global__ void k_galerkin_fe_gather(CGeo c, const double* __restrict__ loc, dou
 // i.e. D_i P_i plus the fluxes w (P_i - P_j) through the block's faces.
 template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fv(
-    Geo g, CGeo c, int dirichlet, double rhow, double rhoe, const TP* __restrict__ P,
+    Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
     const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
-    const double* __restrict__ Cacc, const double* __restrict__ Tbw, const double* __restrict__ Tbe,
     double* Acs) {
   extern __shared__ double acc[];   // 27 * blockDim
   const int I = blockIdx.x;
@@ -199,12 +207,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fv(
     const int x = Ic[0] * bx + l % bx, y = Ic[1] * by + (l / bx) % by, z = Ic[2] * bz + l / (bx * by);
     const long long i = x + g.sy * y + g.sz * z;
     const int xc[3] = {x, y, z};
-    double Dd = Cacc[i];
-    if (dirichlet) {
-      if (x == 0) Dd += Tbw[y + (long long)g.ny * z] * rhow;
-      if (x == g.nx - 1) Dd += Tbe[y + (long long)g.ny * z] * rhoe;
-    }
-    add_cell(i, xc, Dd);
+    add_cell(i, xc, row_sum(g, Ad, Ax, Ay, Az, i, x, y, z));
     for (int d = 0; d < 3; ++d) {
       const int bd = c.b[d];
       for (int side = 0; side < 2; ++side) {
@@ -264,7 +267,15 @@ __global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ A
 // factor Lc (column-major: Lc[q*(m+1) + (r-q)], Lc[q*(m+1)] = d_q).  The
 // working band W is only read in the block columns and only written right of
 // them, so CTAs of one launch never race.
+//
+// FP64 instructions occupy a sub-partition's FP64 pipe for many cycles, so
+// the kernel keeps their count and their dependent chains short: one thread
+// per element of the diagonal block's lower triangle, the reciprocal of the
+// next pivot formed by its owner as soon as that pivot is final, the panel
+// rows solved by four threads per row (one warp per sub-partition), and the
+// products d_q l_cq kept from the elimination instead of recomputed.
 constexpr int kTB = 16;
+constexpr int kTri = kTB * (kTB + 1) / 2;   // lower-triangle elements of a diagonal block
 
 __device__ __forceinline__ double band_at(const double* W, int m, int r, int c) {
   // lower band, column-major; 0 outside the band
@@ -273,105 +284,120 @@ __device__ __forceinline__ double band_at(const double* W, int m, int r, int c) 
 
 __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const double* __restrict__ Wr,
                                                     double* W, double* Lc, int* status) {
-  __shared__ double Ld[kTB][kTB];     // diagonal block: unit L below, d on the diagonal
-  __shared__ double PR[kTB][kTB + 1]; // panel rows of my row tile:  l_rq
-  __shared__ double PC[kTB][kTB + 1]; // panel rows of my column tile
+  __shared__ double A[kTB][kTB + 1];        // diagonal block; column q keeps d_q l_rq
+  __shared__ double L[kTB][kTB + 1];        // l_rq below the diagonal
+  __shared__ double rinv[kTB];              // 1 / d_q
+  __shared__ double V[2 * kTB][kTB + 1];    // panel rows: a_rq in, l_rq out
+  __shared__ double VD[2 * kTB][kTB + 1];   // d_q l_rq of the panel rows
   const int c1 = min(c0 + kTB, N) - 1;
   const int tb = c1 - c0 + 1;
   const int tid = threadIdx.x;
-  // --- factor the diagonal block (every CTA) ---
-  for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-    const int r = e / kTB, q = e % kTB;
-    Ld[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : 0.0;
-  }
-  __syncthreads();
-  for (int q = 0; q < tb; ++q) {
-    double dq = Ld[q][q];
-    if (!(dq > 0.0) || !isfinite(dq)) {
-      if (tid == 0 && blockIdx.x == 0) atomicOr(status, kStatSingular);
-      dq = 1.0;
-    }
-    // column q below the diagonal: l_rq = a_rq / d_q ; then rank-1 update
-    __syncthreads();
-    if (tid > q && tid < tb) Ld[tid][q] = Ld[tid][q] / dq;
-    __syncthreads();
-    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-      const int r = e / kTB, cc = e % kTB;
-      if (r < tb && cc > q && cc <= r) Ld[r][cc] -= Ld[r][q] * dq * Ld[cc][q];
-    }
-    __syncthreads();
-  }
-  // reciprocal pivots and d-scaled columns of the diagonal block
-  __shared__ double rinv[kTB];
-  __shared__ double LdD[kTB][kTB];    // LdD[r][q] = l_rq d_q
-  if (tid < kTB) rinv[tid] = tid < tb ? 1.0 / Ld[tid][tid] : 0.0;
-  for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-    const int r = e / kTB, q = e % kTB;
-    LdD[r][q] = (r < tb && q < r) ? Ld[r][q] * Ld[q][q] : 0.0;
-  }
-  __syncthreads();
-  // --- my tile of the trailing triangle ---
+  // my tile of the trailing triangle, enumerated row by row (bj <= bi)
   const int rlo = c1 + 1;
   const int rhi = min(c1 + m, N - 1);
   const int nb = rhi >= rlo ? (rhi - rlo + kTB) / kTB : 0;
   int bi = 0, bj = 0;
   {
-    int t = blockIdx.x;          // tiles enumerated row by row, bj <= bi
+    int t = blockIdx.x;
     while (t > bi) { t -= bi + 1; ++bi; }
     bj = t;
   }
   const bool have_tile = nb > 0 && bi < nb;
   const int r0 = rlo + bi * kTB, cc0 = rlo + bj * kTB;
-  // panel rows: thread k < kTB handles row r0+k, thread kTB + k row cc0+k
-  if (have_tile && tid < 2 * kTB) {
-    const int k = tid % kTB;
-    const int r = (tid < kTB ? r0 : cc0) + k;
-    double v[kTB];
+  // Programmatic dependent launch: the next block's launch may begin now;
+  // its CTAs wait below until this grid has completed and its writes are
+  // visible (a no-op when launched without the attribute).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // --- stage the diagonal block and the 2 kTB panel rows ---
+  {
+    const int r = tid / kTB, q = tid % kTB;
+    A[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : 0.0;
+  }
+  for (int e = tid; e < 2 * kTB * kTB; e += blockDim.x) {
+    const int k = e / kTB, q = e % kTB;
+    const int r = (k < kTB ? r0 + k : cc0 + k - kTB);
+    V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : 0.0;
+  }
+  // element of the lower triangle owned by this thread (row-major order)
+  int er = 0, ec = -1;
+  if (tid < kTri) {
+    int t = tid;
+    while (t > er) { t -= er + 1; ++er; }
+    ec = t;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double d = A[0][0];
+    if (!(d > 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
+    rinv[0] = 1.0 / d;
+  }
+  __syncthreads();
+  // --- factor the diagonal block ---
+  for (int q = 0; q < tb; ++q) {
+    if (ec >= 0 && er < tb) {
+      const double rq = rinv[q];
+      if (ec == q && er > q) {
+        L[er][q] = A[er][q] * rq;
+      } else if (ec > q) {
+        const double t = A[er][q] * rq;
+        const double v = fma(-t, A[ec][q], A[er][ec]);
+        A[er][ec] = v;
+        if (er == q + 1 && ec == q + 1) {     // the next pivot is final
+          double d = v;
+          if (!(d > 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
+          rinv[q + 1] = 1.0 / d;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // --- panel rows: l_rq = (a_rq - sum_{k<q} l_rk d_k l_qk) / d_q, four threads a row ---
+  if (tid < 4 * 2 * kTB) {
+    const int k = tid >> 2, t = tid & 3;
+    double v[kTB / 4];
 #pragma unroll
-    for (int q = 0; q < kTB; ++q) v[q] = (r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : 0.0;
+    for (int j = 0; j < kTB / 4; ++j) v[j] = V[k][4 * j + t];
+    const unsigned mask = 0xffffffffu;
+    const int src0 = (threadIdx.x & 31) & ~3;
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
-      if (q < tb) {
-        const double l = v[q] * rinv[q];
-        v[q] = l;
+      if (q < tb) {                              // uniform across the CTA
+        double l = 0.0;
+        if (t == (q & 3)) {
+          VD[k][q] = v[q >> 2];
+          l = v[q >> 2] * rinv[q];
+          v[q >> 2] = l;
+        }
+        l = __shfl_sync(mask, l, src0 | (q & 3));
 #pragma unroll
-        for (int q2 = q + 1; q2 < kTB; ++q2)
-          if (q2 < tb) v[q2] -= l * LdD[q2][q];
+        for (int j = 0; j < kTB / 4; ++j)
+          if (4 * j + 3 > q && 4 * j + t > q) v[j] = fma(-l, A[4 * j + t][q], v[j]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kTB; ++q) {
-      if (tid < kTB) PR[k][q] = v[q];
-      else PC[k][q] = v[q];
-    }
+    for (int j = 0; j < kTB / 4; ++j) V[k][4 * j + t] = v[j];
   }
   __syncthreads();
   if (have_tile) {
-    // W[r][c] -= sum_q l_rq d_q l_cq
-    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-      const int a = e / kTB, b = e % kTB;
-      const int r = r0 + a, cc = cc0 + b;
-      if (r > rhi || cc > rhi || cc > r || r - cc > m) continue;
+    // W[r][c] -= sum_q l_rq d_q l_cq, one element a thread
+    const int a = tid / kTB, b = tid % kTB;
+    const int r = r0 + a, cc = cc0 + b;
+    if (r <= rhi && cc <= rhi && cc <= r && r - cc <= m) {
       double s = 0.0;
-      for (int q = 0; q < tb; ++q) s += PR[a][q] * Ld[q][q] * PC[b][q];
+      for (int q = 0; q < tb; ++q) s = fma(V[a][q], VD[kTB + b][q], s);
       W[(long long)cc * (m + 1) + (r - cc)] -= s;
     }
     // diagonal tiles publish their panel rows
     if (bi == bj) {
-      for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-        const int a = e / kTB, q = e % kTB;
-        const int r = r0 + a, col = c0 + q;
-        if (r <= rhi && q < tb && r - col <= m) Lc[(long long)col * (m + 1) + (r - col)] = PR[a][q];
-      }
+      const int a2 = tid / kTB, q = tid % kTB;
+      const int r2 = r0 + a2, col = c0 + q;
+      if (r2 <= rhi && q < tb && r2 - col <= m) Lc[(long long)col * (m + 1) + (r2 - col)] = V[a2][q];
     }
   }
-  // the first CTA publishes the diagonal block
-  if (blockIdx.x == 0) {
-    for (int e = tid; e < kTB * kTB; e += blockDim.x) {
-      const int r = e / kTB, q = e % kTB;
-      if (r < tb && q <= r && r - q <= m) Lc[(long long)(c0 + q) * (m + 1) + (r - q)] = Ld[r][q];
-    }
-  }
+  // the first CTA publishes the diagonal block: l below, d_q on the diagonal
+  if (blockIdx.x == 0 && ec >= 0 && er < tb && er - ec <= m)
+    Lc[(long long)(c0 + ec) * (m + 1) + (er - ec)] = er == ec ? A[er][er] : L[er][ec];
 }
 
 // Row-major copy of L for the backward substitution: Lr[k*(m+1) + a] = l_{k,k-a}.
@@ -842,29 +868,27 @@ __global__ void k_to_single(int n, const double* __restrict__ a, float* b) {
 
 }  // namespace
 
-cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, bool single, Buffers& b, cudaStream_t s) {
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s) {
   const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
   if (single)
-    k_galerkin_fe_local<float><<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.f32.P, b.Ax, b.Ay,
-                                                  b.Az, b.Cacc, b.Tbw, b.Tbe, b.loc);
+    k_galerkin_fe_local<float><<<nd, 256, 0, s>>>(g, c, b.f32.P, b.Ad, b.Ax, b.Ay, b.Az, b.loc);
   else
-    k_galerkin_fe_local<double><<<nd, 256, 0, s>>>(g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay,
-                                                   b.Az, b.Cacc, b.Tbw, b.Tbe, b.loc);
+    k_galerkin_fe_local<double><<<nd, 256, 0, s>>>(g, c, b.P, b.Ad, b.Ax, b.Ay, b.Az, b.loc);
   count_launches(1);
   k_galerkin_fe_gather<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, b.loc, b.Acs); count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, int dirichlet, double rhow,
-                               double rhoe, bool single, Buffers& b, cudaStream_t s) {
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s) {
   const int T = 128;
   if (single)
-    k_galerkin_fv<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
-        g, c, dirichlet, rhow, rhoe, b.f32.P, b.Ax, b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+    k_galerkin_fv<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, b.f32.P, b.Ad, b.Ax,
+                                                                  b.Ay, b.Az, b.Acs);
   else
-    k_galerkin_fv<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
-        g, c, dirichlet, rhow, rhoe, b.P, b.Ax, b.Ay, b.Az, b.Cacc, b.Tbw, b.Tbe, b.Acs);
+    k_galerkin_fv<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, b.P, b.Ad, b.Ax, b.Ay,
+                                                                   b.Az, b.Acs);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -882,13 +906,27 @@ cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t 
     k_band_lu<<<1, 1024, 0, s>>>(Nc, m, b.band, b.status); count_launches(1);
     return cudaGetLastError();
   }
+  // one launch per column block, each allowed to start while the previous
+  // one drains (programmatic dependent launch; the kernel waits for it)
   int launches = 0;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   for (int c0 = 0; c0 < Nc; c0 += kTB) {
     const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
     const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
     const int nb = rhi > c1 ? (rhi - c1 - 1 + kTB) / kTB : 0;
     const int grid = nb > 0 ? nb * (nb + 1) / 2 : 1;
-    k_ldlt_block<<<grid, 256, 0, s>>>(Nc, m, c0, b.band, b.band, b.Lc, b.status);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = c0 == 0 ? 0 : 1;      // the first block follows the band fill normally
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_ldlt_block, Nc, m, c0, (const double*)b.band,
+                                       b.band, b.Lc, b.status);
+    if (e != cudaSuccess) return e;
     ++launches;
   }
   const long long n = (long long)Nc * (m + 1);

@@ -62,20 +62,27 @@ __global__ void k_density(long long N, FluidK fl, const double* __restrict__ p, 
 }
 
 // Table 1 step 1: A = C + A~, f, eps (Eq. 19) and per-block sums of eps^2.
+// fixm (null when no cell is fixed) marks the prescribed-pressure cells of
+// Test Case 2 (Sec. 4.2.2), which are eliminated symmetrically: a face with a
+// fixed end stores no coupling, a free cell moves w p_j of a fixed
+// neighbour j to its right-hand side (p_j holds the prescribed value), and a
+// fixed row reads p_i = p_i with a unit diagonal and eps_i = 0.
 __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw, double pe,
                            double rhow, double rhoe, const double* __restrict__ p,
                            const double* __restrict__ rho, const double* __restrict__ rhon,
                            const double* __restrict__ Tx, const double* __restrict__ Ty,
                            const double* __restrict__ Tz, const double* __restrict__ Tbw,
                            const double* __restrict__ Tbe, const double* __restrict__ src,
-                           double* Ad, double* Ax, double* Ay, double* Az, double* Cacc,
-                           double* f, double* eps, double* red) {
+                           const unsigned char* __restrict__ fixm, double* Ad, double* Ax,
+                           double* Ay, double* Az, double* Cacc, double* f, double* eps,
+                           double* red) {
   double e2 = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
        i += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(g, i, x, y, z);
     const double pi = p[i], ri = rho[i];
+    const bool fi = fixm && fixm[i];
     double flux = 0.0, dsum = 0.0, rhsb = 0.0;
     // Reading R4: face density = arithmetic mean of the two cell densities
 #define CAMS_FACE(cond, T, j, lowslot)                              \
@@ -83,7 +90,11 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
       const double w = (T) * (0.5 * (ri + rho[j]));                 \
       dsum += w;                                                    \
       flux += w * (pi - p[j]);                                      \
-      lowslot;                                                      \
+      if (fixm && (fi || fixm[j])) {                                \
+        if (!fi) rhsb += w * p[j];                                  \
+      } else {                                                      \
+        lowslot;                                                    \
+      }                                                             \
     }
     double ax = 0.0, ay = 0.0, az = 0.0;
     CAMS_FACE(x > 0, Tx[i], i - 1, ax = -w)
@@ -94,13 +105,13 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
     CAMS_FACE(z < g.nz - 1, Tz[i + g.sz], i + g.sz, (void)0)
 #undef CAMS_FACE
     if (dirichlet) {
-      const long long fi = y + (long long)g.ny * z;
+      const long long fi2 = y + (long long)g.ny * z;
       if (x == 0) {
-        const double wb = Tbw[fi] * rhow;
+        const double wb = Tbw[fi2] * rhow;
         dsum += wb; flux += wb * (pi - pw); rhsb += wb * pw;
       }
       if (x == g.nx - 1) {
-        const double wb = Tbe[fi] * rhoe;
+        const double wb = Tbe[fi2] * rhoe;
         dsum += wb; flux += wb * (pi - pe); rhsb += wb * pe;
       }
     }
@@ -111,16 +122,36 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
     const double C = g.V * ri * cc;
     const double q = src ? src[i] / g.V : 0.0;
     const double b = -fl.phi / dt + fl.phi * rn / (dt * ri) + q;   // Eq. 5
-    Ad[i] = C + dsum;
     Ax[i] = ax; Ay[i] = ay; Az[i] = az;
     Cacc[i] = C;
-    f[i] = g.V * ri * b + rhsb + C * pi;
-    const double e = q - fl.phi / dt + (fl.phi / dt) * rn / ri + (-flux / g.V) / ri;  // Eq. 19
+    double e = 0.0;
+    if (fi) {
+      Ad[i] = 1.0;
+      f[i] = pi;
+    } else {
+      Ad[i] = C + dsum;
+      f[i] = g.V * ri * b + rhsb + C * pi;
+      e = q - fl.phi / dt + (fl.phi / dt) * rn / ri + (-flux / g.V) / ri;  // Eq. 19
+    }
     eps[i] = e;
     e2 += e * e;
   }
   const double s = block_sum(e2);
   if (threadIdx.x == 0) red[blockIdx.x] = s;
+}
+
+// Prescribed cells in list order (a repeated cell keeps its last value):
+// mark the cell and put its value into the iterate.
+__global__ void k_fix_cells(int n, const int* __restrict__ cell, const double* __restrict__ val,
+                            unsigned char* fixm, double* p, long long N) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int k = 0; k < n; ++k) {
+    const int c = cell[k];
+    if (c >= 0 && c < N) {
+      fixm[c] = 1;
+      p[c] = val[k];
+    }
+  }
 }
 
 __global__ void k_add_sources(int n, const int* __restrict__ cell, const double* __restrict__ rate,
@@ -174,29 +205,40 @@ __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* _
 }
 
 // Basis operators A_b (Eqs. 8-11, Reading R10: internal faces only).
+// Prescribed cells (fixm, null when none) are eliminated as in A: no
+// coupling across a face with a fixed end, the free row keeps the face on
+// its diagonal, a fixed row is a unit row.
 __global__ void k_basis_operator(Geo g, FluidK fl, int kind, double dt,
                                  const double* __restrict__ Tx, const double* __restrict__ Ty,
-                                 const double* __restrict__ Tz, const double* __restrict__ Ax,
-                                 const double* __restrict__ Ay, const double* __restrict__ Az,
+                                 const double* __restrict__ Tz, const double* __restrict__ rho,
                                  const double* __restrict__ Cacc, const double* __restrict__ pn,
-                                 double* Abd, double* Abx, double* Aby, double* Abz) {
+                                 const unsigned char* __restrict__ fixm, double* Abd, double* Abx,
+                                 double* Aby, double* Abz) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   int x, y, z;
   cell_xyz(g, i, x, y, z);
-  double bx, by, bz, d = 0.0;
-  if (kind <= 2) {  // rho_f-weighted: the couplings of A
-    bx = Ax[i]; by = Ay[i]; bz = Az[i];
-    if (x < g.nx - 1) d -= Ax[i + 1];
-    if (y < g.ny - 1) d -= Ay[i + g.sy];
-    if (z < g.nz - 1) d -= Az[i + g.sz];
-  } else {
-    bx = -Tx[i]; by = -Ty[i]; bz = -Tz[i];
-    if (x < g.nx - 1) d += Tx[i + 1];
-    if (y < g.ny - 1) d += Ty[i + g.sy];
-    if (z < g.nz - 1) d += Tz[i + g.sz];
+  const bool fi = fixm && fixm[i];
+  if (fi) {
+    Abd[i] = 1.0; Abx[i] = 0.0; Aby[i] = 0.0; Abz[i] = 0.0;
+    return;
   }
-  d -= bx + by + bz;
+  // (B1), (B2): rho_f-weighted faces, the couplings of A; (B3), (B4): T
+  const double ri = kind <= 2 ? rho[i] : 0.0;
+  double bx = 0.0, by = 0.0, bz = 0.0, d = 0.0;
+#define CAMS_BFACE(cond, T, j, lowslot)                                 \
+  if (cond) {                                                           \
+    const double w = kind <= 2 ? (T) * (0.5 * (ri + rho[j])) : (T);     \
+    d += w;                                                             \
+    if (!(fixm && fixm[j])) { lowslot; }                                \
+  }
+  CAMS_BFACE(x > 0, Tx[i], i - 1, bx = -w)
+  CAMS_BFACE(x < g.nx - 1, Tx[i + 1], i + 1, (void)0)
+  CAMS_BFACE(y > 0, Ty[i], i - g.sy, by = -w)
+  CAMS_BFACE(y < g.ny - 1, Ty[i + g.sy], i + g.sy, (void)0)
+  CAMS_BFACE(z > 0, Tz[i], i - g.sz, bz = -w)
+  CAMS_BFACE(z < g.nz - 1, Tz[i + g.sz], i + g.sz, (void)0)
+#undef CAMS_BFACE
   if (kind == 1) d += Cacc[i];
   if (kind == 3) {
     const double pp = pn[i];
@@ -225,14 +267,14 @@ cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, doub
 }
 
 cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int dirichlet, double pw,
-                            double pe, Buffers& b, cudaStream_t s) {
+                            double pe, const unsigned char* fixm, Buffers& b, cudaStream_t s) {
   FluidK f2 = fl;
   const double rhow = fl.law == 0 ? fl.rho0 * std::exp(fl.c * pw) : fl.rho0 * (1.0 + fl.c * pw);
   const double rhoe = fl.law == 0 ? fl.rho0 * std::exp(fl.c * pe) : fl.rho0 * (1.0 + fl.c * pe);
   k_assemble<<<kRedBlocks, kRedThreads, 0, s>>>(g, f2, dt, dirichlet, pw, pe, rhow, rhoe, b.p,
                                                 b.rho, b.rhon, b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe,
-                                                b.src, b.Ad, b.Ax, b.Ay, b.Az, b.Cacc, b.f, b.eps,
-                                                b.red); count_launches(1);
+                                                b.src, fixm, b.Ad, b.Ax, b.Ay, b.Az, b.Cacc, b.f,
+                                                b.eps, b.red); count_launches(1);
   k_finish_sum<<<1, 1024, 0, s>>>(b.red, kRedBlocks, b.scal); count_launches(1);
   return cudaGetLastError();
 }
@@ -240,6 +282,12 @@ cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int diric
 cudaError_t launch_add_sources(int n, const int* cell, const double* rate, double* src,
                                long long N, cudaStream_t s) {
   k_add_sources<<<1, 32, 0, s>>>(n, cell, rate, src, N); count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fix_cells(int n, const int* cell, const double* val, unsigned char* fixm,
+                             double* p, long long N, cudaStream_t s) {
+  k_fix_cells<<<1, 32, 0, s>>>(n, cell, val, fixm, p, N); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -257,10 +305,10 @@ cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, dou
 }
 
 cudaError_t launch_basis_operator(const Geo& g, const FluidK& fl, int kind, double dt,
-                                  Buffers& b, cudaStream_t s) {
-  k_basis_operator<<<blocks_for(g.N, 256), 256, 0, s>>>(g, fl, kind, dt, b.Tx, b.Ty, b.Tz, b.Ax,
-                                                        b.Ay, b.Az, b.Cacc, b.pn, b.Abd, b.Abx,
-                                                        b.Aby, b.Abz); count_launches(1);
+                                  const unsigned char* fixm, Buffers& b, cudaStream_t s) {
+  k_basis_operator<<<blocks_for(g.N, 256), 256, 0, s>>>(g, fl, kind, dt, b.Tx, b.Ty, b.Tz, b.rho,
+                                                        b.Cacc, b.pn, fixm, b.Abd, b.Abx, b.Aby,
+                                                        b.Abz); count_launches(1);
   return cudaGetLastError();
 }
 

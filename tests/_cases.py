@@ -30,7 +30,8 @@ def make_case(name=None, w=None, seed=0, **overrides):
     inp = make_inputs(w, seed)
     g = oracle.Grid(w.nx, w.ny, w.nz, inp["dx"], inp["dy"], inp["dz"])
     fl = oracle.Fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi)
-    bc = oracle.BC(inp["dirichlet"], w.p_west, w.p_east, inp["src_cell"], inp["src_rate"])
+    bc = oracle.BC(inp["dirichlet"], w.p_west, w.p_east, inp["src_cell"], inp["src_rate"],
+                   inp["fix_cell"], inp["fix_value"])
     pb = oracle.Problem.build(g, fl, bc, inp["kx"], inp["ky"], inp["kz"])
     opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
                          n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
@@ -51,7 +52,9 @@ def gpu_handle(case: Case, memspace=0):
     h = cams.cams_setup(grid, fluid, opt, inp["kx"], inp["ky"], inp["kz"])
     bc, keep = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
                             inp["src_cell"] if len(inp["src_cell"]) else None,
-                            inp["src_rate"] if len(inp["src_rate"]) else None)
+                            inp["src_rate"] if len(inp["src_rate"]) else None,
+                            inp["fix_cell"] if len(inp["fix_cell"]) else None,
+                            inp["fix_value"] if len(inp["fix_value"]) else None)
     return h, bc, keep
 
 
