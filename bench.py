@@ -31,12 +31,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import WORKLOADS, make_inputs, line_columns  # noqa: E402
+from workloads import WORKLOADS, ensemble_members, make_inputs, line_columns  # noqa: E402
 
 METRIC = ("Newton-step wall time & fine-cell·iters/s to 1e-8 residual; "
           "learned/FP32 vs FP64 C-AMS")
 UNIT = "fine-cell·iters/s"
 DEFAULT_WORKLOAD = "3d-200x200x100-mixed"
+ENSEMBLE = "ensemble-64"
 
 # Algorithmic bytes per fine cell of each kernel class (FP64; every array
 # touched once, neighbour re-reads served on chip).
@@ -70,7 +71,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cams", choices=["cams", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + [ENSEMBLE])
+    ap.add_argument("--workers", type=int, default=0,
+                    help="host threads of the ensemble (0: min(16, CPU count))")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true",
@@ -307,6 +311,89 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
     return out
 
 
+# ------------------------------------------------------------ ensemble --
+
+def run_ensemble(args, rank, world, local_rank):
+    """64 independent realisations (sigma in [1, 4], 32^3 .. 128x128x64,
+    mixed precision), one implicit step each: all members concurrently
+    through cams_ensemble_solve, against the same members one at a time."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1705_05783_gb300 import cams
+
+    members = ensemble_members(64, seed=args.seed)
+    workers = args.workers or min(16, os.cpu_count() or 1)
+    hs, bcs, keep, dks, p0s, ps, dts, cells = [], [], [], [], [], [], [], []
+    for w in members:
+        inp = make_inputs(w)
+        dk = [torch.from_numpy(inp[k]).to(dev) for k in ("kx", "ky", "kz")]
+        hs.append(_handles(cams, w, inp, cams.CAMS_DEVICE, dk))
+        bc, kp = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east)
+        bcs.append(bc); keep.append(kp); dks.append(dk)
+        p0 = torch.from_numpy(inp["p0"]).to(dev)
+        p0s.append(p0); ps.append(torch.empty_like(p0)); dts.append(inp["dt"])
+        cells.append(w.n_cells)
+
+    def reset():
+        for h, dk, p, p0 in zip(hs, dks, ps, p0s):
+            cams.cams_set_permeability(h, *dk)
+            p.copy_(p0)
+        torch.cuda.synchronize()
+
+    def ensemble():
+        reset()
+        status, st = cams.cams_ensemble_solve(hs, p0s, dts, bcs, ps, workers)
+        if any(s != cams.CAMS_OK for s in status):
+            raise RuntimeError(f"ensemble member failed: {status}")
+        return st
+
+    def sequential():
+        reset()
+        return [cams.cams_solve(h, p0, dt, bc, p) for h, p0, dt, bc, p in zip(hs, p0s, dts, bcs, ps)]
+
+    out = {}
+    results = {}
+    for name, fn in (("sequential", sequential), ("ensemble", ensemble)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        l0 = cams.launches(hs[0])
+        per, units = [], 0.0
+        with ClockSampler(local_rank) as clk:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                st = fn()
+                per += [s.t_total for s in st]
+                units += sum(n * s.cams_its for n, s in zip(cells, st))
+            torch.cuda.synchronize()
+            t_ms = (time.perf_counter() - t0) * 1e3
+        t_ms, units = aggregate_replicas(t_ms, units, world, dev)
+        out[name] = {"value": units / (t_ms / 1e3), "ms_per_step": t_ms / args.steps,
+                     "per_solve_ms": {"p50": float(np.percentile(per, 50)),
+                                      "p99": float(np.percentile(per, 99))},
+                     "gpu_launches": int(cams.launches(hs[0]) - l0), "clocks": clk.summary(),
+                     "cams_its_per_step": sum(s.cams_its for s in st)}
+        results[name] = [p.cpu().numpy() for p in ps]
+    same = all(np.array_equal(a, b) for a, b in zip(results["sequential"], results["ensemble"]))
+    for h in hs:
+        cams.cams_destroy(h)
+    ens, seq = out["ensemble"], out["sequential"]
+    return {"metric": "ensemble fine-cell·iters/s, one implicit step of 64 realisations",
+            "value": ens["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ens["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{ENSEMBLE}: 64 seeded realisations, sigma U(1,4), grids "
+                       "32^3 .. 128x128x64, coarse 8^3, (B4) MSFE, 5 ILU post, tol 1e-8, mixed "
+                       "precision", "members": len(hs), "cells": int(sum(cells)),
+                       "workers": workers,
+                       "l2": "members' fields total > 10 GB; every step streams from HBM"},
+            "per_solve_ms": ens["per_solve_ms"], "gpu_launches": ens["gpu_launches"],
+            "clocks": ens["clocks"], "cams_its_per_step": ens["cams_its_per_step"],
+            "sequential": seq, "speedup_vs_sequential": seq["ms_per_step"] / ens["ms_per_step"],
+            "bitwise_equal_to_sequential": bool(same)}
+
+
 # ---------------------------------------------------- oracle (CPU) legs --
 
 def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
@@ -370,6 +457,23 @@ def run_reference(args, w, rank, world):
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
+    if args.workload == ENSEMBLE:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the ensemble leg has no "
+                              "oracle arm; run the oracle on single workloads"}), flush=True)
+            return
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        out = run_ensemble(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     w = WORKLOADS[args.workload]
     if world > 1:
         import torch

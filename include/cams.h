@@ -239,6 +239,28 @@ int cams_iterate(cams_handle* h, int n, double* res_norms);
 int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc,
                double* p_inout, cams_stats* stats);
 
+/* Ensemble of independent time steps (batches of realisations, such as the
+ * statistically equivalent permeability fields the paper averages over,
+ * Sec. 4): for k < n the same as
+ *   status[k] = cams_solve(h[k], p_n[k], dt[k], bc[k], p_inout[k], &stats[k]),
+ * with the members run concurrently on the GPU.  n_workers host threads
+ * (0: one per hardware thread; never more than n) each take the next member
+ * in index order and run it on a stream of their own, so the kernels of
+ * different members overlap.  A member's result is bit-for-bit the one
+ * cams_solve gives: no kernel depends on the stream or on what else runs.
+ * The handles must be distinct and each follows its own memspace rule for
+ * its pointers; work already queued on a handle's stream is completed
+ * before its member starts and the handle's stream is restored afterwards.
+ * dt, bc, status (n entries) and stats (n entries, may be NULL) are host
+ * arrays.  Returns CAMS_OK when every member returned CAMS_OK, else the
+ * status of the lowest-index member that did not; bad arguments give
+ * CAMS_EINVAL before any member runs (message in cams_last_error(NULL)).
+ * cams_get(CAMS_Q_LAUNCHES) counts the launches of all handles that ran
+ * meanwhile. */
+int cams_ensemble_solve(int n, cams_handle* const* h, const double* const* p_n, const double* dt,
+                        const cams_bc* const* bc, double* const* p_inout, cams_stats* stats,
+                        int* status, int n_workers);
+
 /* Copy an internal quantity (CAMS_Q_*) to dst (memspace of the handle, except
  * CAMS_Q_SIZES which is always host).  dst must hold the documented size. */
 int cams_get(cams_handle* h, int what, double* dst);

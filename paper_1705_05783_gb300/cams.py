@@ -29,7 +29,8 @@ PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_fa
 
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
            "cams_set_stream",
-           "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve", "cams_get",
+           "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve",
+           "cams_ensemble_solve", "cams_get",
            "cams_get_int", "cams_last_error", "cams_destroy", "cams_residual_norm_noalloc")
 
 
@@ -89,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "cams_iterate": (C.c_int, [P, C.c_int, P]),
         "cams_solve": (C.c_int, [P, P, C.c_double, C.POINTER(cams_bc), P,
                                  C.POINTER(cams_stats)]),
+        "cams_ensemble_solve": (C.c_int, [C.c_int, P, P, P, P, P, P, P, C.c_int]),
         "cams_get": (C.c_int, [P, C.c_int, P]),
         "cams_get_int": (C.c_int, [P, C.c_int, P]),
         "cams_last_error": (C.c_char_p, [P]),
@@ -222,6 +224,23 @@ def cams_solve(h, p_n, dt, bc, p_inout, allow_noconv=False):
     if not (allow_noconv and code == CAMS_ENOCONV):
         _check(code, h)
     return st
+
+
+def cams_ensemble_solve(hs, p_ns, dts, bcs, p_inouts, n_workers=0):
+    """cams_ensemble_solve over lists of equal length.  Returns
+    (status list, cams_stats list); raises on a bad-argument error."""
+    n = len(hs)
+    H = (C.c_void_p * n)(*[h.value for h in hs])
+    PN = (C.c_void_p * n)(*[_ptr(a) for a in p_ns])
+    PI = (C.c_void_p * n)(*[_ptr(a) for a in p_inouts])
+    DT = (C.c_double * n)(*[float(d) for d in dts])
+    BC = (C.c_void_p * n)(*[C.addressof(b) for b in bcs])
+    ST = (cams_stats * n)()
+    SS = (C.c_int * n)()
+    code = _lib.cams_ensemble_solve(n, H, PN, DT, BC, PI, ST, SS, int(n_workers))
+    if code == CAMS_EINVAL and all(s == CAMS_OK for s in SS):
+        raise CamsError(code, _lib.cams_last_error(None).decode())
+    return list(SS), list(ST)
 
 
 def cams_get(h, what, dst):

@@ -10,7 +10,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cams_internal.h"
@@ -587,6 +590,20 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 namespace cams {
 void set_global_error(const std::string& msg) { g_setup_error = msg; }
 void count_launches(long long n) { lc::total += n; }
+
+cudaError_t raise_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limit[{dev, func}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 long long launches_total() { return lc::total.load(); }
 }  // namespace cams
 
@@ -931,6 +948,73 @@ int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc, 
   if (stats) *stats = st;
   if (result == CAMS_ENOCONV) fail(h, CAMS_ENOCONV, "max_newton reached without convergence");
   return result;
+}
+
+int cams_ensemble_solve(int n, cams_handle* const* h, const double* const* p_n, const double* dt,
+                        const cams_bc* const* bc, double* const* p_inout, cams_stats* stats,
+                        int* status, int n_workers) {
+  if (n < 0) return fail(nullptr, CAMS_EINVAL, "n < 0");
+  if (n == 0) return CAMS_OK;
+  if (!h || !p_n || !dt || !bc || !p_inout || !status)
+    return fail(nullptr, CAMS_EINVAL, "null ensemble array");
+  {
+    std::vector<cams_handle*> v(h, h + n);
+    for (cams_handle* x : v)
+      if (!x) return fail(nullptr, CAMS_EINVAL, "null handle in the ensemble");
+    std::sort(v.begin(), v.end());
+    if (std::adjacent_find(v.begin(), v.end()) != v.end())
+      return fail(nullptr, CAMS_EINVAL, "a handle appears twice in the ensemble");
+  }
+  int nw = n_workers > 0 ? n_workers : (int)std::thread::hardware_concurrency();
+  nw = std::max(1, std::min(nw, n));
+  for (int k = 0; k < n; ++k) status[k] = CAMS_OK;
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaStream_t s = nullptr;
+    int sdev = -1;
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      cams_handle* hk = h[k];
+      if (cudaSetDevice(hk->dev) != cudaSuccess || cudaStreamSynchronize(hk->stream) != cudaSuccess) {
+        status[k] = fail(hk, CAMS_ECUDA, "cannot reach the handle's device or stream");
+        continue;
+      }
+      if (sdev != hk->dev) {
+        if (s) cudaStreamDestroy(s);
+        s = nullptr;
+        sdev = -1;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+          s = nullptr;
+          status[k] = fail(hk, CAMS_ECUDA, "cudaStreamCreate failed");
+          continue;
+        }
+        sdev = hk->dev;
+      }
+      cudaStream_t own = hk->stream;
+      hk->stream = s;
+      status[k] = cams_solve(hk, p_n[k], dt[k], bc[k], p_inout[k], stats ? &stats[k] : nullptr);
+      hk->stream = own;
+    }
+    if (s) {
+      cudaSetDevice(sdev);
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nw; ++w) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {
+      break;   // fewer workers: the remaining ones take the members
+    }
+  }
+  worker();
+  for (std::thread& t : pool) t.join();
+  for (int k = 0; k < n; ++k)
+    if (status[k] != CAMS_OK) return status[k];
+  return CAMS_OK;
 }
 
 int cams_get(cams_handle* h, int what, double* dst) {

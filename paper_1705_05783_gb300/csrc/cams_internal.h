@@ -120,6 +120,15 @@ enum : int { kStatSingular = 1, kStatNan = 2, kStatTimeout = 4, kStatBounds = 8 
 // Message returned by cams_last_error(NULL).
 void set_global_error(const std::string& msg);
 
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current
+// device to at least `bytes`.  Handles of different sizes share the kernels,
+// so the limit is the largest any of them asked for; thread-safe.
+cudaError_t raise_smem_limit(const void* func, int bytes);
+template <class F>
+cudaError_t raise_smem_limit(F* func, int bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(func), bytes);
+}
+
 // Kernels launched by this library in this process (read per handle as a
 // difference around its calls).
 void count_launches(long long n);

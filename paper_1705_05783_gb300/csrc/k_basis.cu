@@ -348,11 +348,9 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
 }
 
 cudaError_t set_entity_smem(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_entity_solve<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_limit(k_entity_solve<double>, smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_entity_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem);
+  return raise_smem_limit(k_entity_solve<float>, smem);
 }
 
 cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,

@@ -43,14 +43,15 @@ __device__ __forceinline__ void dual_range(const CGeo& c, const Geo& g, int d, i
   hi = j == c.nc[d] ? n - 1 : j * c.b[d] + c.o[d] - 1;
 }
 
-template <int K>
-__device__ void block_sum_k(double (&v)[K], double* sh /* K*32 */, double* out) {
+// Warp sums in the accumulation type TA, the sum over warps in FP64.
+template <int K, class TA>
+__device__ void block_sum_k(TA (&v)[K], double* sh /* K*32 */, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double t = v[k];
+    TA t = v[k];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) sh[k * 32 + wid] = t;
+    if (lane == 0) sh[k * 32 + wid] = (double)t;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -81,7 +82,7 @@ __device__ __forceinline__ double row_sum(const Geo& g, const double* __restrict
 }
 
 // MSFE: per dual block, the 8x8 block sum over its cells and its low-side
-// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T.
+// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T, in FP64.
 template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
@@ -95,19 +96,20 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
   for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
   const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
   const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-  double acc[36];
+  using TA = double;
+  TA acc[36];
 #pragma unroll
-  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 36; ++k) acc[k] = TA(0);
   for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
     const int x = lo[0] + l % ex, y = lo[1] + (l / ex) % ey, z = lo[2] + l / (ex * ey);
     const long long i = x + g.sy * y + g.sz * z;
-    double pi[8];
+    TA pi[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) pi[s] = (double)P[(long long)s * g.N + i];
-    const double Dd = row_sum(g, Ad, Ax, Ay, Az, i, x, y, z);
+    for (int s = 0; s < 8; ++s) pi[s] = P[(long long)s * g.N + i];
+    const TA Dd = (TA)row_sum(g, Ad, Ax, Ay, Az, i, x, y, z);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const double a = Dd * pi[s];
+      const TA a = Dd * pi[s];
 #pragma unroll
       for (int t = s; t < 8; ++t) acc[sym_idx(s, t)] += a * pi[t];
     }
@@ -116,19 +118,19 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     for (int d = 0; d < 3; ++d) {
       if (xc[d] >= nd_of(g, d) - 1) continue;
       const long long jn = i + sd_of(g, d);
-      const double w = -(d == 0 ? Ax[jn] : (d == 1 ? Ay[jn] : Az[jn]));
+      const TA w = (TA)(-(d == 0 ? Ax[jn] : (d == 1 ? Ay[jn] : Az[jn])));
       const bool inside = xc[d] + 1 <= hi[d];
-      double dv[8];
+      TA dv[8];
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
-        double pj;
-        if (inside) pj = (double)P[(long long)s * g.N + jn];
-        else pj = (s & (1 << d)) ? (double)P[(long long)(s & ~(1 << d)) * g.N + jn] : 0.0;
+        TA pj;
+        if (inside) pj = P[(long long)s * g.N + jn];
+        else pj = (s & (1 << d)) ? P[(long long)(s & ~(1 << d)) * g.N + jn] : TA(0);
         dv[s] = pi[s] - pj;
       }
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
-        const double a = w * dv[s];
+        const TA a = w * dv[s];
 #pragma unroll
         for (int t = s; t < 8; ++t) acc[sym_idx(s, t)] += a * dv[t];
       }
@@ -786,8 +788,8 @@ __global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const 
   for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
   const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
   const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-  // products and each thread's partial sums in P's precision, the block
-  // tree in FP64 (with FP32 P this widens 8 values per thread, not per cell)
+  // products, each thread's and each warp's sums in P's precision, the sum
+  // over the block's warps in FP64
   TP tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
     const long long i = (lo[0] + l % ex) + g.sy * (lo[1] + (l / ex) % ey) + g.sz * (lo[2] + l / (ex * ey));
@@ -961,8 +963,7 @@ static int coarse_cluster_smem(int Nc) {
 bool coarse_cluster_ok(int Nc, int max_smem) {
   const int smem = coarse_cluster_smem(Nc);
   if (smem > max_smem) return false;
-  if (cudaFuncSetAttribute(k_coarse_solve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           smem) != cudaSuccess) {
+  if (raise_smem_limit(k_coarse_solve_cluster, smem) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -1007,7 +1008,7 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
   }
   if (sym) {
     const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
-    cudaError_t e = cudaFuncSetAttribute(k_ldlt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_smem_limit(k_ldlt_solve, smem);
     if (e != cudaSuccess) return e;
     k_ldlt_solve<<<1, 256, smem, s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
   } else {

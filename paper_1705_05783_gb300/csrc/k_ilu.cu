@@ -747,15 +747,12 @@ cudaError_t launch_sweep(const Geo& g, const Skew& sk, int sms, bool cta, const 
 
 template <class Op, bool kBackward>
 void set_sweep_smem() {
-  cudaFuncSetAttribute(k_sweep_warp<Op, kBackward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       warp_smem<Op>());
+  raise_smem_limit(k_sweep_warp<Op, kBackward>, warp_smem<Op>());
 }
 
 template <class Op, bool kBackward>
 bool set_cta_smem(const Geo& g) {
-  return cudaFuncSetAttribute(k_sweep_cta<Op, kBackward>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              cta_smem<Op>(g)) == cudaSuccess;
+  return raise_smem_limit(k_sweep_cta<Op, kBackward>, cta_smem<Op>(g)) == cudaSuccess;
 }
 
 // The vectors of one precision's smoother.

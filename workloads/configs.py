@@ -106,6 +106,30 @@ for _a, _cb in ((1, (8, 8, 8)), (5, (2, 8, 8)), (10, (2, 8, 8))):
         restriction=0, n_post=5, nl_tol=1e-6, alpha=float(_a), seeds=tuple(range(20)))
 
 
+# The batched ensemble: independent realisations with sigma drawn uniformly
+# in [1, 4] and grid sizes drawn from a ladder between 32^3 and 128x128x64,
+# each solved for one implicit step with the 4M-cell workload's options
+# (Dirichlet W/E, (B4), MSFE, 5 ILU(0) post steps, tolerance 1e-8, the
+# FP32 preconditioner in FP64 refinement), coarse blocks of 8^3.
+ENSEMBLE_SHAPES = ((32, 32, 32), (48, 48, 32), (64, 48, 32), (64, 64, 32), (64, 64, 64),
+                   (96, 64, 48), (96, 96, 48), (128, 96, 64), (128, 128, 64))
+
+
+def ensemble_members(n=64, seed=0, precision=1):
+    """The n member workloads of the ensemble (seeded draw of shapes and
+    sigmas; member k uses field seed 1000 + k)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nx, ny, nz = ENSEMBLE_SHAPES[int(rng.integers(len(ENSEMBLE_SHAPES)))]
+        sigma = float(rng.uniform(1.0, 4.0))
+        out.append(Workload(
+            name=f"ensemble-{k}-{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, coarse=(8, 8, 8),
+            sigma=sigma, corr=(0.1, 0.1, 0.1), c_or_eta=0.1, steps=1, basis=4, restriction=0,
+            n_post=5, nl_tol=1e-8, precision=precision, seeds=(1000 + k,)))
+    return out
+
+
 def line_columns(w: Workload):
     """Cells and values of the two prescribed columns of Test Case 2: the
     column (0, 0, z) at p_west and the column (nx-1, ny-1, z) at p_east."""
