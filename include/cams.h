@@ -118,13 +118,13 @@ typedef struct {
   int max_cams;        /* C-AMS iterations per linearisation */
   int memspace;        /* CAMS_HOST or CAMS_DEVICE for every pointer argument */
   int precision;       /* CAMS_PREC_FP64: every stage in FP64.  CAMS_PREC_MIXED: the
-                          multiscale preconditioner (basis solves and P, restriction and
-                          prolongation, ILU(0) factor and sweeps) runs in FP32 on the
-                          correction equation A delta = r inside FP64 iterative refinement;
-                          assembly, the residual r = f - A p, the update p += delta, the
-                          Galerkin product R A P and the coarse factorisation and solve stay
-                          FP64.  Converges to the same fixed point (the FP64 residual decides
-                          the stopping tests). */
+                          multiscale preconditioner (basis solves and P, the products of
+                          R A P, restriction and prolongation, ILU(0) factor and sweeps) runs
+                          in FP32 on the correction equation A delta = r inside FP64 iterative
+                          refinement (block sums of R A P and of R r in FP64); assembly, the
+                          residual r = f - A p, the update p += delta and the coarse
+                          factorisation and solve stay FP64.  Converges to the same fixed
+                          point (the FP64 residual decides the stopping tests). */
 } cams_options;
 
 #define CAMS_PREC_FP64  0

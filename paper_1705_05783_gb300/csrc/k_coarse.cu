@@ -82,7 +82,10 @@ __device__ __forceinline__ double row_sum(const Geo& g, const double* __restrict
 }
 
 // MSFE: per dual block, the 8x8 block sum over its cells and its low-side
-// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T, in FP64.
+// faces of  D_i P_i P_i^T + w_f (P_i - P_j)(P_i - P_j)^T.  The products and
+// each thread's and warp's sums are in P's precision (FP32 for the mixed
+// preconditioner, whose FP64 instruction count would otherwise bind the
+// kernel), the sum over the block's warps in FP64.
 template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
   for (int d = 0; d < 3; ++d) dual_range(c, g, d, j[d], lo[d], hi[d]);
   const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
   const int ncell = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-  using TA = double;
+  using TA = TP;
   TA acc[36];
 #pragma unroll
   for (int k = 0; k < 36; ++k) acc[k] = TA(0);
@@ -797,10 +800,7 @@ __global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const 
 #pragma unroll
     for (int s = 0; s < 8; ++s) tacc[s] += P[(long long)s * g.N + i] * ri;
   }
-  double acc[8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) acc[s] = (double)tacc[s];
-  block_sum_k<8>(acc, sh, part + (long long)D * 8);
+  block_sum_k<8>(tacc, sh, part + (long long)D * 8);
 }
 
 // MSFE restriction, part 2: coarse node J sums its (up to 8) dual blocks.
