@@ -34,6 +34,7 @@ struct cams_handle {
   std::vector<Entity> ents;
   int lev_first[4] = {0, 0, 0, 0}, lev_count[4] = {0, 0, 0, 0}, lev_smem[4] = {0, 0, 0, 0};
   int lev_grid[4] = {0, 0, 0, 0};
+  bool lev_blocked[4] = {false, false, false, false};
   long long lev_lstride[4] = {0, 0, 0, 0};
   long long lscratch_len = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -503,7 +504,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
       const int f = h->lev_first[lev];
       CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
                              h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, h->single,
-                             b, h->stream));
+                             h->lev_blocked[lev], b, h->stream));
     }
   }
   h->built = true;
@@ -657,13 +658,16 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   }
   int smem_max = 0;
   for (int lev = 1; lev <= 3; ++lev) {
-    int sm = 0;
+    int sm = 0, mmax = 0;
     long long ls = 0;
+    for (int e = h->lev_first[lev]; e < h->lev_first[lev] + h->lev_count[lev]; ++e)
+      mmax = std::max(mmax, h->ents[e].m);
+    // wide bands (the 3D dual-block interiors) take the blocked local solver
+    h->lev_blocked[lev] = mmax >= 16;
     for (int e = h->lev_first[lev]; e < h->lev_first[lev] + h->lev_count[lev]; ++e) {
       const Entity& E = h->ents[e];
-      const int mp = E.m + 1;
-      sm = std::max(sm, (int)(h->single ? sizeof(float) : sizeof(double)) * (mp * mp + E.n * E.nrhs + 2 * mp));
-      ls = std::max(ls, (long long)E.n * mp);
+      sm = std::max(sm, entity_smem_bytes(E, h->single, h->lev_blocked[lev]));
+      ls = std::max(ls, (long long)E.n * (E.m + 1));
     }
     h->lev_smem[lev] = sm;
     h->lev_lstride[lev] = ls;

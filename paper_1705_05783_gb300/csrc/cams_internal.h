@@ -22,6 +22,19 @@ struct Geo {
   double dx, dy, dz, V;
 };
 
+#ifdef __CUDACC__
+// (x, y, z) of cell i.  Grids are below 2^31 cells (checked at setup), so
+// 32-bit division will do (64-bit division is a long instruction sequence).
+__device__ __forceinline__ void xyz_of(const Geo& g, long long i, int& x, int& y, int& z) {
+  const unsigned u = (unsigned)i, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned t = u / nx;
+  x = (int)(u - t * nx);
+  const unsigned s = t / ny;
+  y = (int)(t - s * ny);
+  z = (int)s;
+}
+#endif
+
 // Coarse-grid geometry: primal block size b, coarse-node offset o = b/2,
 // number of coarse cells nc per direction (inactive directions: b = 1,
 // o = 0, nc = 1).
@@ -162,9 +175,12 @@ cudaError_t launch_adapt_propagate(const Geo& g, int first, int count, Buffers& 
 cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out, cudaStream_t s);
 // single: P and the local solves in FP32 (mixed precision), else FP64.
 cudaError_t launch_vertices(const Geo& g, const CGeo& c, Buffers& b, bool single, cudaStream_t s);
+// blocked: panels of pivots with a register-tiled trailing update (large
+// local problems); otherwise one pivot at a time.
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                bool single, Buffers& b, cudaStream_t s);
+                                bool single, bool blocked, Buffers& b, cudaStream_t s);
+int entity_smem_bytes(const Entity& E, bool single, bool blocked);
 cudaError_t set_entity_smem(int smem);
 cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                cudaStream_t s);

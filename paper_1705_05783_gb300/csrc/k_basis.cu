@@ -237,6 +237,239 @@ __global__ void __launch_bounds__(256) k_entity_solve(
   }
 }
 
+// ---- blocked variant for the large local problems (dual-block interiors) ----
+// The per-pivot rank-1 update above issues several instructions per FMA
+// (ring addressing, partial warps), which bounds it.  Here pivots go in
+// panels of kKB: the panel's columns are eliminated pivot by pivot (only
+// within the panel), then the trailing window takes one rank-kKB update in
+// 4x4 register tiles, and the right-hand sides one kKB-term update.  The
+// ring holds m + kKB rows; the backward substitution also goes kKB rows at a
+// time, with those rows of L staged in shared memory.  Same arithmetic as the
+// per-pivot kernel up to the order of the additions.
+constexpr int kKB = 8;
+constexpr int kLPS = kKB + 1;   // panel row stride (odd: no shared-memory bank conflicts)
+
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
+template <class T>
+__global__ void __launch_bounds__(256) k_entity_solve_blk(
+    Geo g, const Entity* __restrict__ ents, int count, const unsigned char* __restrict__ flag,
+    int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
+    const double* __restrict__ Aby, const double* __restrict__ Abz, T* P, double* snap,
+    T* lscratch, long long lstride, int* status) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T* Lg = lscratch + (long long)blockIdx.x * lstride;
+  __shared__ T s_d[kKB], s_dinv[kKB];
+  for (int e = blockIdx.x; e < count; e += gridDim.x) {
+    if (flag && !flag[e]) continue;
+    const Entity E = ents[e];
+    const int n = E.n, m = E.m, nr = E.nrhs, mp = m + 1, R = m + kKB;
+    const int lnr = __ffs(nr) - 1;                 // nr is a power of two
+    T* W = sm;                                     // ring: row i in slot i % R, entry (i, i-dd) at dd
+    T* Y = W + round4(R * mp);                     // n x nr right-hand sides
+    T* Lp = Y + round4(n * nr);                    // panel: Lp[(i-k)*kLPS + q] = l_{i,k+q}
+    T* Ls = W;                                     // backward sweep: kKB staged rows of L
+    for (int l = tid; l < n; l += nt) {
+      T* row = (l < R) ? W + l * mp : Lg + (long long)l * mp;
+      build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
+    }
+    __syncthreads();
+    for (int k = 0; k < n; k += kKB) {
+      const int kb = min(kKB, n - k);
+      const int k_slot = k % R;                    // ring slot of row k
+      const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+      for (int t = tid; t < (m + kKB) * kLPS; t += nt) Lp[t] = T(0);
+      if (tid == 0) {
+        T d = W[k_slot * mp];
+        if (!(d > T(0)) || !isfinite(d)) { atomicOr(status, kStatSingular); d = T(1); }
+        s_d[0] = d;
+        s_dinv[0] = T(1) / d;
+        for (int q = kb; q < kKB; ++q) { s_d[q] = T(0); s_dinv[q] = T(0); }
+      }
+      __syncthreads();
+      {  // scale column k: l_{i,k} = a_{i,k} / d_k
+        const int rmax = min(m, n - 1 - k);
+        const T dinv = s_dinv[0];
+        for (int a = 1 + tid; a <= rmax; a += nt) {
+          int sl = k_slot + a;
+          if (sl >= R) sl -= R;
+          T* w = W + sl * mp + a;
+          const T l = *w * dinv;
+          *w = l;
+          Lp[a * kLPS] = l;
+        }
+      }
+      __syncthreads();
+      // --- the panel's pivots, eliminating within the panel only.  Warp c
+      // updates column k+q+1+c; warp 0 then also forms pivot q+1 and scales
+      // its column, so one barrier per pivot suffices. ---
+      for (int q = 0; q < kb; ++q) {
+        const int kq = k + q;
+        const int rmax = min(m, n - 1 - kq);       // rows kq+1 .. kq+rmax hold column kq
+        const T dq = s_d[q];
+        const int ncol = kb - 1 - q;
+        for (int c = warp; c < ncol; c += nwarp) {
+          //   a_{i,k+q'} -= l_{i,kq} d_q l_{k+q',kq},  rows k+q' .. kq+rmax
+          const int qp = q + 1 + c;
+          const T u = Lp[qp * kLPS + q] * dq;
+          int base = k_slot + qp;                  // slot of row k+q'
+          if (base >= R) base -= R;
+          for (int a = lane; a < rmax - c; a += 32) {
+            int sl = base + a;
+            if (sl >= R) sl -= R;
+            T* w = W + sl * mp + a;
+            *w -= Lp[(qp + a) * kLPS + q] * u;
+          }
+          if (c == 0) {
+            // column k+q+1 is final: its pivot, then l_{i,k+q+1} for rows
+            // k+q+2 .. k+q+1+rmax1
+            __syncwarp();
+            T d = W[base * mp];
+            if (!(d > T(0)) || !isfinite(d)) {
+              if (lane == 0) atomicOr(status, kStatSingular);
+              d = T(1);
+            }
+            const T dinv = T(1) / d;
+            if (lane == 0) { s_d[q + 1] = d; s_dinv[q + 1] = dinv; }
+            const int rmax1 = min(m, n - 1 - (kq + 1));
+            for (int a = 1 + lane; a <= rmax1; a += 32) {
+              int sl = base + a;
+              if (sl >= R) sl -= R;
+              T* w = W + sl * mp + a;
+              const T l = *w * dinv;
+              *w = l;
+              Lp[(qp + a) * kLPS + qp] = l;
+            }
+          }
+        }
+        // right-hand sides of the panel's later rows
+        for (int t = tid; t < (ncol << lnr); t += nt) {
+          const int i = kq + 1 + (t >> lnr), r = t & (nr - 1);
+          Y[i * nr + r] -= Lp[(i - k) * kLPS + q] * Y[kq * nr + r];
+        }
+        __syncthreads();
+      }
+      // --- rank-kb update of the trailing window and of the right-hand sides ---
+      const int me = min(m, n - (k + kb));        // trailing rows k+kb .. k+kb+me-1
+      if (me > 0) {
+        const int nT = (me + 3) >> 2;
+        const int ntile = nT * (nT + 1) / 2;
+        for (int t = tid; t < ntile; t += nt) {
+          int tu = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          while (tu * (tu + 1) / 2 > t) --tu;
+          while ((tu + 1) * (tu + 2) / 2 <= t) ++tu;
+          const int tv = t - tu * (tu + 1) / 2;
+          T acc[4][4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+          const int u0 = 4 * tu, v0 = 4 * tv;
+#pragma unroll
+          for (int q = 0; q < kKB; ++q) {
+            const T dq = s_d[q];
+            T av[4], bv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              av[r] = (u0 + r < me) ? Lp[(kb + u0 + r) * kLPS + q] : T(0);
+              bv[r] = (v0 + r < me) ? Lp[(kb + v0 + r) * kLPS + q] * dq : T(0);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] += av[r] * bv[c];
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int u = u0 + r;
+            if (u >= me) continue;
+            int sl = k_slot + kb + u;              // row k+kb+u, < 2R
+            if (sl >= R) sl -= R;
+            T* wrow = W + sl * mp;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int v = v0 + c;
+              if (v < me && v <= u) wrow[u - v] -= acc[r][c];
+            }
+          }
+        }
+        for (int t = tid; t < (me << lnr); t += nt) {
+          const int u = t >> lnr, r = t & (nr - 1);
+          const int i = k + kb + u;
+          T s = T(0);
+#pragma unroll
+          for (int q = 0; q < kKB; ++q)
+            if (q < kb) s += Lp[(kb + u) * kLPS + q] * Y[(k + q) * nr + r];
+          Y[i * nr + r] -= s;
+        }
+      }
+      __syncthreads();
+      // --- rows k .. k+kb-1 are final: to the scratch (1/d_i, l_{i,i-1..i-m});
+      //     their slots take rows k+R .. k+R+kb-1 ---
+      for (int qq = 0; qq < kb; ++qq) {
+        const int i = k + qq;
+        int sl = k_slot + qq;
+        if (sl >= R) sl -= R;
+        for (int dd = tid; dd < mp; dd += nt) {
+          T* w = W + sl * mp + dd;
+          Lg[(long long)i * mp + dd] = (dd == 0) ? s_dinv[qq] : *w;
+          const int inew = i + R;
+          if (inew < n) *w = Lg[(long long)inew * mp + dd];
+        }
+      }
+      __syncthreads();
+    }
+    // D^{-1}
+    for (int t = tid; t < (n << lnr); t += nt) Y[t] *= Lg[(long long)(t >> lnr) * mp];
+    __syncthreads();
+    // backward substitution with L^T, kKB rows at a time from the end
+    for (int b1 = n - 1; b1 > 0; b1 -= kKB) {
+      const int b0 = max(0, b1 - kKB + 1);
+      const int nb = b1 - b0 + 1;
+      for (int t = tid; t < nb * mp; t += nt) Ls[t] = Lg[(long long)b0 * mp + t];
+      __syncthreads();
+      if (tid < 32) {                              // inside the block, row by row
+        for (int kk = b1; kk > b0; --kk) {
+          for (int t = tid; t < ((kk - b0) << lnr); t += 32) {
+            const int j = b0 + (t >> lnr), r = t & (nr - 1);
+            if (kk - j <= m) Y[j * nr + r] -= Ls[(kk - b0) * mp + (kk - j)] * Y[kk * nr + r];
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      const int jlo = max(0, b0 - m);
+      for (int t = tid; t < ((b0 - jlo) << lnr); t += nt) {
+        const int j = jlo + (t >> lnr), r = t & (nr - 1);
+        T s = T(0);
+        for (int kk = b0; kk <= b1; ++kk)
+          if (kk - j <= m) s += Ls[(kk - b0) * mp + (kk - j)] * Y[kk * nr + r];
+        Y[j * nr + r] -= s;
+      }
+      __syncthreads();
+    }
+    // write the basis values (slots on lattice bits stay zero)
+    for (int l = tid; l < n; l += nt) {
+      Local c = local_cell(E, l);
+      const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = T(0);
+      for (int r = 0; r < nr; ++r) P[(long long)slot_of(r, E.free_mask) * g.N + i] = Y[l * nr + r];
+      if (adaptive) {
+        snap[0 * g.N + i] = Abd[i];
+        snap[1 * g.N + i] = c.c[0] > 0 ? Abx[i] : 0.0;
+        snap[2 * g.N + i] = c.c[0] < g.nx - 1 ? Abx[i + 1] : 0.0;
+        snap[3 * g.N + i] = c.c[1] > 0 ? Aby[i] : 0.0;
+        snap[4 * g.N + i] = c.c[1] < g.ny - 1 ? Aby[i + g.sy] : 0.0;
+        snap[5 * g.N + i] = c.c[2] > 0 ? Abz[i] : 0.0;
+        snap[6 * g.N + i] = c.c[2] < g.nz - 1 ? Abz[i + g.sz] : 0.0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __device__ double block_max(double v) {
   __shared__ double sh[32];
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -329,28 +562,49 @@ cudaError_t launch_vertices(const Geo& g, const CGeo& c, Buffers& b, bool single
   return cudaGetLastError();
 }
 
+// Shared memory of one entity's local solve (bytes).
+int entity_smem_bytes(const Entity& E, bool single, bool blocked) {
+  const int mp = E.m + 1;
+  const int elems = blocked ? round4((E.m + kKB) * mp) + round4(E.n * E.nrhs) + (E.m + kKB) * kLPS
+                            : mp * mp + E.n * E.nrhs + 2 * mp;
+  return elems * (int)(single ? sizeof(float) : sizeof(double));
+}
+
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                bool single, Buffers& b, cudaStream_t s) {
+                                bool single, bool blocked, Buffers& b, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (grid > count) grid = count;
-  if (single)
-    k_entity_solve<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
-                                                  b.Aby, b.Abz, b.f32.P, b.snap,
-                                                  reinterpret_cast<float*>(b.lscratch), lstride,
-                                                  b.status);
-  else
-    k_entity_solve<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
-                                                   b.Aby, b.Abz, b.P, b.snap, b.lscratch, lstride,
-                                                   b.status);
+  if (single) {
+    float* ls = reinterpret_cast<float*>(b.lscratch);
+    if (blocked)
+      k_entity_solve_blk<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd,
+                                                        b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls,
+                                                        lstride, b.status);
+    else
+      k_entity_solve<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
+                                                    b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
+                                                    b.status);
+  } else {
+    if (blocked)
+      k_entity_solve_blk<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd,
+                                                         b.Abx, b.Aby, b.Abz, b.P, b.snap,
+                                                         b.lscratch, lstride, b.status);
+    else
+      k_entity_solve<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
+                                                     b.Aby, b.Abz, b.P, b.snap, b.lscratch, lstride,
+                                                     b.status);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t set_entity_smem(int smem) {
   cudaError_t e = raise_smem_limit(k_entity_solve<double>, smem);
-  if (e != cudaSuccess) return e;
-  return raise_smem_limit(k_entity_solve<float>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve<float>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<double>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<float>, smem);
+  return e;
 }
 
 cudaError_t launch_adapt_flags(const Geo& g, const Entity* ents, int count, double theta,

@@ -846,7 +846,8 @@ __global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TC* __r
                           const int* __restrict__ perm, TO* p) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  const int xc[3] = {(int)(i % g.nx), (int)((i / g.nx) % g.ny), (int)(i / ((long long)g.nx * g.ny))};
+  int xc[3];
+  xyz_of(g, i, xc[0], xc[1], xc[2]);
   int Jl[3][2];
   for (int d = 0; d < 3; ++d) {
     Jl[d][0] = corner_d(c, d, xc[d], 0);

@@ -13,10 +13,7 @@ namespace cams {
 namespace {
 
 __device__ __forceinline__ void cell_xyz(const Geo& g, long long i, int& x, int& y, int& z) {
-  x = (int)(i % g.nx);
-  long long t = i / g.nx;
-  y = (int)(t % g.ny);
-  z = (int)(t / g.ny);
+  xyz_of(g, i, x, y, z);
 }
 
 // Block-wide sum; every thread passes its value, thread 0 gets the total.
@@ -77,6 +74,7 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
                            double* Ay, double* Az, double* Cacc, double* f, double* eps,
                            double* red) {
   double e2 = 0.0;
+  const double inv_dt = 1.0 / dt, inv_V = 1.0 / g.V;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
        i += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
@@ -116,12 +114,17 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
       }
     }
     const double rn = rhon[i];
-    const double drho = fl.law == 0 ? fl.c * fl.rho0 * exp(fl.c * pi) : fl.rho0 * fl.c;
+    // d rho / dp: c rho for the exponential law (rho_i already holds
+    // rho0 exp(c p_i)), rho0 eta for the linear one
+    const double drho = fl.law == 0 ? fl.c * ri : fl.rho0 * fl.c;
+    // FP64 divisions are long dependent sequences on this GPU: one per cell
+    const double rinv = 1.0 / ri;
+    const double phidt = fl.phi * inv_dt;
     // Eq. 4 with d phi/dp = 0, then the row scaling V rho (Reading R7)
-    const double cc = fl.phi * rn * drho / (dt * ri * ri);
+    const double cc = phidt * rn * drho * rinv * rinv;
     const double C = g.V * ri * cc;
-    const double q = src ? src[i] / g.V : 0.0;
-    const double b = -fl.phi / dt + fl.phi * rn / (dt * ri) + q;   // Eq. 5
+    const double q = src ? src[i] * inv_V : 0.0;
+    const double b = -phidt + phidt * rn * rinv + q;   // Eq. 5
     Ax[i] = ax; Ay[i] = ay; Az[i] = az;
     Cacc[i] = C;
     double e = 0.0;
@@ -131,7 +134,7 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
     } else {
       Ad[i] = C + dsum;
       f[i] = g.V * ri * b + rhsb + C * pi;
-      e = q - fl.phi / dt + (fl.phi / dt) * rn / ri + (-flux / g.V) / ri;  // Eq. 19
+      e = q - phidt + phidt * rn * rinv - flux * inv_V * rinv;  // Eq. 19
     }
     eps[i] = e;
     e2 += e * e;

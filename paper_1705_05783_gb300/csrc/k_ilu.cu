@@ -166,9 +166,8 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* _
                             T* Lz, T* Ux, T* Uy, T* Uz) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  const int x = (int)(i % g.nx);
-  const int y = (int)((i / g.nx) % g.ny);
-  const int z = (int)(i / g.sz);
+  int x, y, z;
+  xyz_of(g, i, x, y, z);
   const long long j = skew_index(sk, x, y, z);
   const T di = dinv[i];
   Lx[j] = Ax[i] * di;
@@ -188,9 +187,8 @@ __global__ void k_resid_scaled(Geo g, Skew sk, const T* __restrict__ Ad, const T
                                const T* __restrict__ dinv, T* rd) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  const int x = (int)(i % g.nx);
-  const int y = (int)((i / g.nx) % g.ny);
-  const int z = (int)(i / g.sz);
+  int x, y, z;
+  xyz_of(g, i, x, y, z);
   const long long j = skew_index(sk, x, y, z);
   T a = T(bv[i]) - Ad[i] * xv[i];
   if (x > 0) a -= Ax[i] * xv[i - 1];
@@ -207,9 +205,8 @@ template <class T>
 __global__ void k_apply_z(Geo g, Skew sk, const T* __restrict__ zs, T* xv) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
-  const int x = (int)(i % g.nx);
-  const int y = (int)((i / g.nx) % g.ny);
-  const int z = (int)(i / g.sz);
+  int x, y, z;
+  xyz_of(g, i, x, y, z);
   xv[i] += zs[skew_index(sk, x, y, z)];
 }
 
