@@ -53,6 +53,13 @@ BYTES_PER_CELL = {
     "ilu_factor": 88,          # A x4 -> 1/d, scaled couplings x6
     "basis_op": 64,
 }
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum + write.sum) for
+# a kernel class on a workload, for the kernels as they stand: the ilu_bwd
+# class (backward sweep + p += z) of the 4M-cell mixed step, summed over its
+# two kernels (profiles/dram_ilu_bwd_3d-200x200x100-mixed.md).  Cleared when
+# those kernels change.
+MEASURED_TRAFFIC = {("3d-200x200x100-mixed", "ilu_bwd"): 103.6e6}
+
 # the same classes with the FP32 preconditioner (4-byte operands; r stays FP64)
 BYTES_PER_CELL_MIXED = dict(BYTES_PER_CELL, **{
     "restrict": 40,            # P x8 (FP32), r
@@ -301,7 +308,8 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
         "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": None, "bytes_per_launch": bytes_per_launch,
+                     "traffic": MEASURED_TRAFFIC.get((w.name, dom)),
+                     "bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": avg_ms},
         "e2e": e2e,
         "gpu_launches": int(launches),
