@@ -19,6 +19,8 @@ Layout (one module per part of the method):
   ilu         the ILU(0) second-stage smoother of Sec. 3 / Table 1
   solver      Table 1 iteration inside the Newton loop of Sec. 4.1.1 with
               the adaptive operator updates of Sec. 4.1.2
+  net         the learned basis surrogate's network (convolutions, ReLU,
+              masked MSE, Adam) for checking the GPU layer kernels
 
 Every floating-point quantity is float64.  Readings of points the paper
 leaves open are marked "Reading R<n>" at the place they are used.

@@ -609,3 +609,82 @@ def test_stretched_grid_closed_forms(alpha):
     x, _, _ = g.coords()
     np.testing.assert_allclose(p, 1.0 - (x + 0.5) / g.nx, atol=1e-12)
     assert st[0].converged
+
+
+# ------------------------------------------- the learned surrogate's network --
+
+def test_net_conv_matches_brute_force(rng):
+    """The oracle's convolution against the defining sum written as loops,
+    with zero padding; a single centre tap of weight 1 is the identity and an
+    off-centre tap a shift."""
+    from oracle.net import conv_forward
+    B, ci, co, S = 2, 3, 2, 4
+    x = rng.standard_normal((B, ci, S, S, S))
+    w = rng.standard_normal((co, ci, 27))
+    b = rng.standard_normal(co)
+    y = conv_forward(x, w, b, relu=False)
+    ref = np.zeros_like(y)
+    for bb in range(B):
+        for o in range(co):
+            for z in range(S):
+                for yy in range(S):
+                    for xx in range(S):
+                        s = b[o]
+                        for i in range(ci):
+                            for t in range(27):
+                                dx, dy, dz = t % 3 - 1, (t // 3) % 3 - 1, t // 9 - 1
+                                u, v, q = xx + dx, yy + dy, z + dz
+                                if 0 <= u < S and 0 <= v < S and 0 <= q < S:
+                                    s += w[o, i, t] * x[bb, i, q, v, u]
+                        ref[bb, o, z, yy, xx] = s
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+    wi = np.zeros((1, 1, 27)); wi[0, 0, 13] = 1.0
+    np.testing.assert_array_equal(conv_forward(x[:, :1], wi, np.zeros(1), False), x[:, :1])
+    ws = np.zeros((1, 1, 27)); ws[0, 0, 14] = 1.0                    # dx = +1
+    sh = conv_forward(x[:, :1], ws, np.zeros(1), False)
+    np.testing.assert_array_equal(sh[..., :-1], x[:, :1, :, :, 1:])
+    assert np.all(sh[..., -1] == 0.0)
+
+
+def test_net_gradients_match_finite_differences(rng):
+    """Backward pass of a 3-layer network (ReLU between layers) against
+    central finite differences of the masked MSE loss."""
+    from oracle.net import mse, network_backward, network_forward
+    S, B = 4, 2
+    chans = [2, 3, 3, 2]
+    layers = [(0.4 * rng.standard_normal((chans[k + 1], chans[k], 27)),
+               0.1 * rng.standard_normal(chans[k + 1])) for k in range(3)]
+    x = rng.standard_normal((B, chans[0], S, S, S))
+    target = rng.standard_normal((B, chans[-1], S, S, S))
+    mask = (rng.random((B, chans[-1], S, S, S)) < 0.6).astype(float)
+    count = mask.sum()
+
+    def loss(ls):
+        y, _ = network_forward(x, ls)
+        return mse(y, target, mask, count)[0]
+
+    y, acts = network_forward(x, layers)
+    _, gy = mse(y, target, mask, count)
+    grads = network_backward(acts, layers, gy)
+    h = 1e-6
+    for k in range(3):
+        for which in (0, 1):
+            arr = layers[k][which]
+            flat = arr.reshape(-1)
+            for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+                old = flat[idx]
+                flat[idx] = old + h; lp = loss(layers)
+                flat[idx] = old - h; lm = loss(layers)
+                flat[idx] = old
+                fd = (lp - lm) / (2 * h)
+                an = grads[k][which].reshape(-1)[idx]
+                assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (k, which, idx, fd, an)
+
+
+def test_net_adam_first_step_is_signed_lr():
+    """With zero moments the first Adam step moves each parameter by
+    -lr * g / (|g| + eps): the sign step of size lr (bias correction)."""
+    from oracle.net import adam_step
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p, m, v = adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 0.01, 0.9, 0.999, 1e-12, 1)
+    np.testing.assert_allclose(p, -0.01 * np.sign(g), rtol=1e-9, atol=1e-12)
