@@ -38,6 +38,7 @@ METRIC = ("Newton-step wall time & fine-cell·iters/s to 1e-8 residual; "
 UNIT = "fine-cell·iters/s"
 DEFAULT_WORKLOAD = "3d-200x200x100-mixed"
 ENSEMBLE = "ensemble-64"
+LEARNED_GATE = 0.5      # gate of the learned-surrogate leg: strict enough to keep the C-AMS count
 
 # Algorithmic bytes per fine cell of each kernel class (FP64; every array
 # touched once, neighbour re-reads served on chip).
@@ -84,6 +85,8 @@ def parse():
                     help="host threads of the ensemble (0: min(16, CPU count))")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the leg with the learned basis surrogate")
     ap.add_argument("--no-fp64", action="store_true",
                     help="mixed-precision workloads: skip the FP64 comparison run")
     return ap.parse_args()
@@ -183,7 +186,9 @@ def _handles(cams, w, inp, memspace, dev_arrays=None):
     return cams.cams_setup(grid, fluid, opt, *k)
 
 
-def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
+def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
+    """surrogate: (parameters, gate tolerance) to build the interiors with the
+    learned surrogate, or None for the exact local solves."""
     import torch
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -208,6 +213,8 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
                             fix[0] if fix else None, fix[1] if fix else None)
     stream = torch.cuda.current_stream(dev)
     h = _handles(cams, w, inp, cams.CAMS_DEVICE, dk)
+    if surrogate is not None:
+        cams.cams_set_surrogate(h, surrogate[0], surrogate[1])
     cams.cams_set_stream(h, stream.cuda_stream)
 
     def step():
@@ -252,9 +259,13 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
 
     p_final = p.cpu().numpy()
+    surr = None
+    if surrogate is not None:
+        sizes = cams.cams_get_int(h, cams.CAMS_Q_SIZES, np.zeros(8, np.int32))
+        surr = {"interiors_supplied": int(sizes[7]), "gate_tol": float(surrogate[1])}
     if not e2e_leg:
         cams.cams_destroy(h)
-        return {"value": value, "unit": UNIT, "ms_per_step": t_ms / args.steps,
+        return {"value": value, "unit": UNIT, "ms_per_step": t_ms / args.steps, "surrogate": surr,
                 "dtype": "f32+f64" if w.precision else "f64",
                 "newton_its_per_step": newton / args.steps, "cams_its_per_step": its / args.steps,
                 "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items() if v[0]},
@@ -265,6 +276,8 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True):
 
     # end to end through the C-ABI with HOST buffers (copies inside the timed region)
     h_host = _handles(cams, w, inp, cams.CAMS_HOST)
+    if surrogate is not None:
+        cams.cams_set_surrogate(h_host, surrogate[0], surrogate[1])
     bch, keeph = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
                               inp["src_cell"] if len(inp["src_cell"]) else None,
                               inp["src_rate"] if len(inp["src_rate"]) else None,
@@ -500,6 +513,17 @@ def main():
             out["error_vs_fp64"] = {"rel_linf": err, "note": "final pressure of the mixed step "
                                     "against the FP64 step (the FP64 engine is held to the "
                                     "FP64 oracle by the parity tests)"}
+        if w.precision and not args.no_learned:
+            # the same step with the learned surrogate supplying the interiors it passes
+            from paper_1705_05783_gb300 import surrogate as sg
+            if os.path.exists(sg.PARAMS_FILE):
+                lrn = run_cams(args, w, rank, world, local_rank, e2e_leg=False,
+                               surrogate=(sg.load_params(), LEARNED_GATE))
+                pl = lrn.pop("_p")
+                ref_p = p64 if "fp64" in out else out["_p"]
+                lrn["error_vs_fp64" if "fp64" in out else "difference_vs_exact_basis"] = float(
+                    np.abs(pl - ref_p).max() / max(np.abs(ref_p).max(), 1e-300))
+                out["learned"] = lrn
         out.pop("_p", None)
         if rank == 0 and world == 1 and not args.no_baseline:
             v, dt, st, sample = oracle_sample(w, args.seed)

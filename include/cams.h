@@ -156,10 +156,14 @@ typedef struct {
 #define CAMS_Q_ILU_DIAG   9  /* double N: ILU(0) pivots d~_i (the only entries ILU(0) changes);
                                 of the FP32 copy of A in mixed precision */
 #define CAMS_Q_RESIDUAL  10  /* double N: f - A p for the current p */
-#define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, entities rebuilt by the last update, 0 */
+#define CAMS_Q_SIZES     11  /* int 8: N, Nc, ncx, ncy, ncz, entities, entities rebuilt by the last update,
+                                interiors supplied by the surrogate in the last update */
 #define CAMS_Q_PROFILE   12  /* double 3*CAMS_PROF_CLASSES: per kernel class {launches, total ms,
                                 kernels}; accumulated while profiling is on (cams_profile) */
 #define CAMS_Q_LAUNCHES  13  /* double 1: kernels launched by this handle since cams_setup */
+#define CAMS_Q_SURR_RATIO 14  /* double n (n = full interiors, cams_surrogate_data with 0): the
+                                surrogate's gate ratio of each full interior in the last build that
+                                used it (CAMS_EINVAL without a surrogate) */
 
 /* kernel classes of CAMS_Q_PROFILE */
 #define CAMS_PROF_ASSEMBLE      0   /* density + linear-system population (a2) */
@@ -260,6 +264,74 @@ int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc,
 int cams_ensemble_solve(int n, cams_handle* const* h, const double* const* p_n, const double* dt,
                         const cams_bc* const* bc, double* const* p_inout, cams_stats* stats,
                         int* status, int n_workers);
+
+/* ---- Learned basis surrogate (interior stage of the basis construction) ----
+ *
+ * A small 3D convolutional network predicts the basis functions of each full
+ * dual-block interior (the (b-1)^3 cells between the vertex planes of a
+ * dual block of (b+1)^3 cells, cubic coarse blocks of size b) from the
+ * block's basis-operator coefficients and the exact edge and face values of
+ * its 8 corner functions.  Input channels (CAMS_NET_IN, on the (b+1)^3
+ * patch): the logs of the three lower-face couplings of A_b minus their patch
+ * mean, the relative accumulation term (A_b diagonal minus the coupling sum,
+ * over the coupling sum), and for each corner function its deviation from
+ * the multilinear interpolant of the corner values on the patch boundary (0
+ * inside).  Output (CAMS_NET_OUT channels): the deviation from that
+ * interpolant, used on the interior cells.  Layers: 3x3x3 convolutions with
+ * zero padding, CAMS_NET_IN -> CAMS_NET_HID -> CAMS_NET_HID -> CAMS_NET_HID
+ * -> CAMS_NET_OUT, ReLU between them.  Parameters (CAMS_NET_PARAMS floats):
+ * w1, b1, w2, b2, w3, b3, w4, b4 in that order; w_l is [co][ci][27] with
+ * tap t = (dx+1) + 3(dy+1) + 9(dz+1).  A prediction is kept only when the
+ * residual of the interior equations it leaves, scaled by the diagonal
+ * (D^{-1} A_b P on the interior cells, 2-norm, worst of the 8 corner
+ * functions), is at most gate_tol times the norm of the boundary data's
+ * scaled contribution; otherwise the exact local solve runs. */
+#define CAMS_NET_IN      12
+#define CAMS_NET_HID     32
+#define CAMS_NET_OUT      8
+#define CAMS_NET_PARAMS  72680
+
+/* Enable the surrogate on a 3D handle with cubic coarse blocks: params
+ * (host, CAMS_NET_PARAMS floats) are copied; gate_tol > 0 is the residual
+ * threshold.  gate_tol <= 0 (params may be NULL) disables it.  The surrogate
+ * is used whenever every local entity is rebuilt (first build, forced or
+ * theta < 0); adaptive partial rebuilds use the exact solves.  CAMS_Q_SIZES[7]
+ * reports the interiors it supplied in the last build. */
+int cams_set_surrogate(cams_handle* h, const float* params, double gate_tol);
+
+/* Training data from the handle's current basis (after cams_update_basis
+ * with exact solves): for the first n = min(max_patches, number of full
+ * interiors) patches, x (n x CAMS_NET_IN x (b+1)^3), target (n x
+ * CAMS_NET_OUT x (b+1)^3: the deviation from the multilinear interpolant)
+ * and mask (same shape: 1 on interior cells, 0 elsewhere).  Device pointers,
+ * FP32.  *n_out receives n; with max_patches <= 0 nothing is written and
+ * *n_out receives the number of full interiors. */
+int cams_surrogate_data(cams_handle* h, int max_patches, float* x, float* target, float* mask,
+                        int* n_out);
+
+/* Layer kernels of the network, used for training and by the engine
+ * (device pointers, FP32; work is queued on `stream`, a cudaStream_t or
+ * NULL, and the call returns after queueing; CAMS_ECUDA on a launch error).
+ * Activations are [B][C][S][S][S], x fastest.
+ *   forward:  y = conv(x; w, bias), then ReLU when relu != 0.
+ *   backward: with gy = dL/dy (of the pre-ReLU output), gw = dL/dw,
+ *             gbias = dL/dbias and, when gx != NULL, gx = dL/dx multiplied
+ *             by the ReLU mask xact > 0 of the layer's input when xact !=
+ *             NULL (the gradient with respect to the previous layer's
+ *             pre-activation).  gw and gbias are overwritten.
+ *   mse:      loss = sum(mask (pred - target)^2) / count into *loss (device
+ *             double), grad = 2 mask (pred - target) / count; scratch holds
+ *             512 doubles.
+ *   adam:     one Adam step (Kingma and Ba) at step number step >= 1. */
+int cams_net_conv_forward(int B, int S, int ci, int co, const float* x, const float* w,
+                          const float* bias, int relu, float* y, void* stream);
+int cams_net_conv_backward(int B, int S, int ci, int co, const float* x, const float* w,
+                           const float* gy, const float* xact, float* gx, float* gw,
+                           float* gbias, void* stream);
+int cams_net_mse(long long n, const float* pred, const float* target, const float* mask,
+                 double count, float* grad, double* loss, double* scratch, void* stream);
+int cams_net_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int step, void* stream);
 
 /* Copy an internal quantity (CAMS_Q_*) to dst (memspace of the handle, except
  * CAMS_Q_SIZES which is always host).  dst must hold the documented size. */

@@ -22,7 +22,7 @@ CAMS_HOST, CAMS_DEVICE = 0, 1
 CAMS_PREC_FP64, CAMS_PREC_MIXED = 0, 1
 CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 4, 5
 CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
-CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES = 11, 12, 13
+CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES, CAMS_Q_SURR_RATIO = 11, 12, 13, 14
 PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
                 "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
                 "ilu_bwd", "ilu_resid")
@@ -30,7 +30,9 @@ PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_fa
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
            "cams_set_stream",
            "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve",
-           "cams_ensemble_solve", "cams_get",
+           "cams_ensemble_solve", "cams_set_surrogate", "cams_surrogate_data",
+           "cams_net_conv_forward", "cams_net_conv_backward", "cams_net_mse", "cams_net_adam",
+           "cams_get",
            "cams_get_int", "cams_last_error", "cams_destroy", "cams_residual_norm_noalloc")
 
 
@@ -91,6 +93,13 @@ def load_library(path: str = LIB_PATH):
         "cams_solve": (C.c_int, [P, P, C.c_double, C.POINTER(cams_bc), P,
                                  C.POINTER(cams_stats)]),
         "cams_ensemble_solve": (C.c_int, [C.c_int, P, P, P, P, P, P, P, C.c_int]),
+        "cams_set_surrogate": (C.c_int, [P, P, C.c_double]),
+        "cams_surrogate_data": (C.c_int, [P, C.c_int, P, P, P, C.POINTER(C.c_int)]),
+        "cams_net_conv_forward": (C.c_int, [C.c_int] * 4 + [P, P, P, C.c_int, P, P]),
+        "cams_net_conv_backward": (C.c_int, [C.c_int] * 4 + [P] * 7 + [P]),
+        "cams_net_mse": (C.c_int, [C.c_longlong, P, P, P, C.c_double, P, P, P, P]),
+        "cams_net_adam": (C.c_int, [C.c_longlong, P, P, P, P, C.c_float, C.c_float, C.c_float,
+                                    C.c_float, C.c_int, P]),
         "cams_get": (C.c_int, [P, C.c_int, P]),
         "cams_get_int": (C.c_int, [P, C.c_int, P]),
         "cams_last_error": (C.c_char_p, [P]),
@@ -241,6 +250,52 @@ def cams_ensemble_solve(hs, p_ns, dts, bcs, p_inouts, n_workers=0):
     if code == CAMS_EINVAL and all(s == CAMS_OK for s in SS):
         raise CamsError(code, _lib.cams_last_error(None).decode())
     return list(SS), list(ST)
+
+
+CAMS_NET_IN, CAMS_NET_HID, CAMS_NET_OUT, CAMS_NET_PARAMS = 12, 32, 8, 72680
+
+
+def cams_set_surrogate(h, params, gate_tol):
+    """params: float32 host array of CAMS_NET_PARAMS values (None with
+    gate_tol <= 0 disables the surrogate)."""
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.size != CAMS_NET_PARAMS:
+            raise ValueError("wrong number of surrogate parameters")
+    _check(_lib.cams_set_surrogate(h, _ptr(params), float(gate_tol)), h)
+
+
+def cams_surrogate_data(h, max_patches, x=None, target=None, mask=None):
+    """Writes up to max_patches training patches into the device tensors;
+    returns the number written."""
+    n = C.c_int(0)
+    _check(_lib.cams_surrogate_data(h, int(max_patches), _ptr(x), _ptr(target), _ptr(mask),
+                                    C.byref(n)), h)
+    return n.value
+
+
+def _stream(stream):
+    return None if stream is None else int(stream)
+
+
+def cams_net_conv_forward(B, S, ci, co, x, w, b, relu, y, stream=None):
+    _check(_lib.cams_net_conv_forward(B, S, ci, co, _ptr(x), _ptr(w), _ptr(b), int(relu),
+                                      _ptr(y), _stream(stream)))
+
+
+def cams_net_conv_backward(B, S, ci, co, x, w, gy, xact, gx, gw, gb, stream=None):
+    _check(_lib.cams_net_conv_backward(B, S, ci, co, _ptr(x), _ptr(w), _ptr(gy), _ptr(xact),
+                                       _ptr(gx), _ptr(gw), _ptr(gb), _stream(stream)))
+
+
+def cams_net_mse(n, pred, target, mask, count, grad, loss, scratch, stream=None):
+    _check(_lib.cams_net_mse(int(n), _ptr(pred), _ptr(target), _ptr(mask), float(count),
+                             _ptr(grad), _ptr(loss), _ptr(scratch), _stream(stream)))
+
+
+def cams_net_adam(n, p, g, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _check(_lib.cams_net_adam(int(n), _ptr(p), _ptr(g), _ptr(m), _ptr(v), float(lr),
+                              float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
 
 
 def cams_get(h, what, dst):

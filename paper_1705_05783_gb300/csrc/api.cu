@@ -58,6 +58,14 @@ struct cams_handle {
   bool ilu_cta = false;         // 2 x 2 tile blocks per CTA, else one tile per warp
   bool coarse_cluster = false;  // MSFE coarse solve across a cluster (CAMS_COARSE_CLUSTER=0: one CTA)
   int ilu_grid = 1;
+  // learned surrogate of the interior basis stage (cams_set_surrogate)
+  double surr_tol = 0.0;           // > 0: enabled
+  int surr_b = 0, surr_n = 0, surr_chunk = 0, surr_accepted = 0;
+  float* net = nullptr;            // device parameters (kNetParams)
+  int* surr_org = nullptr;         // device: lower corner of each full interior's patch
+  int* surr_ent = nullptr;         // device: its entity index
+  float *surr_x = nullptr, *surr_h1 = nullptr, *surr_h2 = nullptr, *surr_y = nullptr;
+  float* surr_ratio = nullptr;     // device: gate ratio of each full interior (last build)
   // per-kernel-class profiling (cams_profile)
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; long long k0, k1; };
@@ -348,6 +356,79 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
   return CAMS_OK;
 }
 
+// ------------------------------------------------------------ surrogate --
+
+void free_surrogate(cams_handle* h) {
+  void* ptrs[] = {h->net, h->surr_org, h->surr_ent, h->surr_x, h->surr_h1, h->surr_h2, h->surr_y,
+                  h->surr_ratio};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->net = nullptr; h->surr_org = h->surr_ent = nullptr;
+  h->surr_x = h->surr_h1 = h->surr_h2 = h->surr_y = h->surr_ratio = nullptr;
+  h->surr_tol = 0.0; h->surr_n = 0; h->surr_chunk = 0;
+}
+
+// The full dual-block interiors ((b-1)^3 cells) with their patch corners.
+int surrogate_tables(cams_handle* h) {
+  const int b = h->c.b[0];
+  std::vector<int> org, ent;
+  for (int e = h->lev_first[3]; e < h->lev_first[3] + h->lev_count[3]; ++e) {
+    const Entity& E = h->ents[e];
+    if (E.L[0] != b - 1 || E.L[1] != b - 1 || E.L[2] != b - 1) continue;
+    for (int d = 0; d < 3; ++d) org.push_back(E.org[d] - 1);
+    ent.push_back(e);
+  }
+  h->surr_b = b;
+  h->surr_n = (int)ent.size();
+  if (h->surr_n == 0) return CAMS_OK;
+  int rc = dalloc(h, &h->surr_org, org.size());
+  if (!rc) rc = dalloc(h, &h->surr_ent, ent.size());
+  if (rc) return rc;
+  CK(cudaMemcpy(h->surr_org, org.data(), sizeof(int) * org.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->surr_ent, ent.data(), sizeof(int) * ent.size(), cudaMemcpyHostToDevice));
+  return CAMS_OK;
+}
+
+// y = network(x) for n patches (x: n x kNetIn x S^3, y: n x kNetOut x S^3).
+cudaError_t net_forward(cams_handle* h, int n, const float* x, float* y) {
+  const int S = h->surr_b + 1;
+  const float* p = h->net;
+  const float *w1 = p, *b1 = w1 + kNetHid * kNetIn * 27;
+  const float *w2 = b1 + kNetHid, *b2 = w2 + kNetHid * kNetHid * 27;
+  const float *w3 = b2 + kNetHid, *b3 = w3 + kNetHid * kNetHid * 27;
+  const float *w4 = b3 + kNetHid, *b4 = w4 + kNetOut * kNetHid * 27;
+  cudaError_t e = launch_conv_fwd(n, S, kNetIn, kNetHid, x, w1, b1, 1, h->surr_h1, h->stream);
+  if (e == cudaSuccess) e = launch_conv_fwd(n, S, kNetHid, kNetHid, h->surr_h1, w2, b2, 1, h->surr_h2, h->stream);
+  if (e == cudaSuccess) e = launch_conv_fwd(n, S, kNetHid, kNetHid, h->surr_h2, w3, b3, 1, h->surr_h1, h->stream);
+  if (e == cudaSuccess) e = launch_conv_fwd(n, S, kNetHid, kNetOut, h->surr_h1, w4, b4, 0, y, h->stream);
+  return e;
+}
+
+// Interior stage by the surrogate: predict every full interior, keep the
+// predictions that pass the residual gate (flag 0), leave flag 1 for the
+// exact solve.  Called with every level-3 flag set to 1.
+int surrogate_interiors(cams_handle* h) {
+  Buffers& b = h->b;
+  const int S = h->surr_b + 1;
+  for (int p0 = 0; p0 < h->surr_n; p0 += h->surr_chunk) {
+    const int n = std::min(h->surr_chunk, h->surr_n - p0);
+    CK(launch_patch_inputs(h->g, h->surr_b, n, h->surr_org + 3 * p0, h->single, b, h->surr_x,
+                           nullptr, nullptr, h->stream));
+    CK(net_forward(h, n, h->surr_x, h->surr_y));
+    CK(launch_patch_apply(h->g, h->surr_b, n, h->surr_org + 3 * p0, h->surr_y, h->single, b,
+                          h->stream));
+  }
+  (void)S;
+  CK(launch_patch_gate(h->g, h->surr_b, h->surr_n, h->surr_org, h->surr_ent, h->surr_tol,
+                       h->single, b, b.flag, h->surr_ratio, h->stream));
+  CK(launch_count_flags(h->lev_count[3], b.flag + h->lev_first[3], b.scal, h->stream));
+  double cnt = 0.0;
+  int rc = read_scalar(h, &cnt);
+  if (rc) return rc;
+  h->surr_accepted = h->lev_count[3] - (int)cnt;
+  return CAMS_OK;
+}
+
 // ----------------------------------------------------------- operations --
 
 // True when fine cell i is a coarse node (a vertex of the wirebasket).
@@ -500,8 +581,13 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   if (rebuilt > 0) {
     ProfScope ps_(h, CAMS_PROF_BASIS);
     if (!h->built) CK(launch_vertices(h->g, h->c, b, h->single, h->stream));
+    h->surr_accepted = 0;
     for (int lev = 1; lev <= 3; ++lev) {
       const int f = h->lev_first[lev];
+      if (lev == 3 && h->surr_tol > 0.0 && h->surr_n > 0 && rebuilt == ne) {
+        const int rc = surrogate_interiors(h);
+        if (rc) return rc;
+      }
       CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
                              h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, h->single,
                              h->lev_blocked[lev], b, h->stream));
@@ -1021,6 +1107,96 @@ int cams_ensemble_solve(int n, cams_handle* const* h, const double* const* p_n, 
   return CAMS_OK;
 }
 
+int cams_set_surrogate(cams_handle* h, const float* params, double gate_tol) {
+  if (!h) return CAMS_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  free_surrogate(h);
+  if (!(gate_tol > 0.0)) return CAMS_OK;
+  if (!params) return fail(h, CAMS_EINVAL, "null surrogate parameters");
+  const CGeo& c = h->c;
+  if (h->g.nx < 2 || h->g.ny < 2 || h->g.nz < 2 || c.b[0] != c.b[1] || c.b[0] != c.b[2] || c.b[0] < 3)
+    return fail(h, CAMS_EINVAL, "the surrogate needs a 3D grid with cubic coarse blocks (b >= 3)");
+  int rc = surrogate_tables(h);
+  if (rc) { free_surrogate(h); return rc; }
+  const long long S3 = (long long)(h->surr_b + 1) * (h->surr_b + 1) * (h->surr_b + 1);
+  h->surr_chunk = std::max(1, std::min(h->surr_n, 1024));
+  rc = dalloc(h, &h->net, (size_t)kNetParams);
+  if (!rc) rc = dalloc(h, &h->surr_x, (size_t)(h->surr_chunk * kNetIn * S3));
+  if (!rc) rc = dalloc(h, &h->surr_h1, (size_t)(h->surr_chunk * kNetHid * S3));
+  if (!rc) rc = dalloc(h, &h->surr_h2, (size_t)(h->surr_chunk * kNetHid * S3));
+  if (!rc) rc = dalloc(h, &h->surr_y, (size_t)(h->surr_chunk * kNetOut * S3));
+  if (!rc) rc = dalloc(h, &h->surr_ratio, (size_t)h->surr_n);
+  if (rc) { free_surrogate(h); return rc; }
+  CK(cudaMemcpy(h->net, params, sizeof(float) * kNetParams, cudaMemcpyHostToDevice));
+  h->surr_tol = gate_tol;
+  return CAMS_OK;
+}
+
+int cams_surrogate_data(cams_handle* h, int max_patches, float* x, float* target, float* mask,
+                        int* n_out) {
+  if (!h || !n_out) return CAMS_EINVAL;
+  if (!h->built) return fail(h, CAMS_EINVAL, "cams_update_basis must come first");
+  if (h->surr_n == 0 && !h->surr_org) {
+    const CGeo& c = h->c;
+    if (h->g.nx < 2 || h->g.ny < 2 || h->g.nz < 2 || c.b[0] != c.b[1] || c.b[0] != c.b[2] || c.b[0] < 3)
+      return fail(h, CAMS_EINVAL, "the surrogate needs a 3D grid with cubic coarse blocks (b >= 3)");
+    int rc = surrogate_tables(h);
+    if (rc) return rc;
+  }
+  if (max_patches <= 0) {           // how many there are
+    *n_out = h->surr_n;
+    return CAMS_OK;
+  }
+  const int n = std::min(max_patches, h->surr_n);
+  *n_out = n;
+  if (n == 0) return CAMS_OK;
+  if (!x || !target || !mask) return fail(h, CAMS_EINVAL, "null patch arrays");
+  CK(launch_patch_inputs(h->g, h->surr_b, n, h->surr_org, h->single, h->b, x, target, mask,
+                         h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CAMS_OK;
+}
+
+int cams_net_conv_forward(int B, int S, int ci, int co, const float* x, const float* w,
+                          const float* bias, int relu, float* y, void* stream) {
+  if (B < 0 || S < 1 || ci < 1 || co < 1 || !x || !w || !bias || !y)
+    return fail(nullptr, CAMS_EINVAL, "bad convolution arguments");
+  if (B == 0) return CAMS_OK;
+  cudaError_t e = launch_conv_fwd(B, S, ci, co, x, w, bias, relu, y, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  return CAMS_OK;
+}
+
+int cams_net_conv_backward(int B, int S, int ci, int co, const float* x, const float* w,
+                           const float* gy, const float* xact, float* gx, float* gw,
+                           float* gbias, void* stream) {
+  if (B < 1 || S < 1 || ci < 1 || co < 1 || !x || !w || !gy || !gw || !gbias)
+    return fail(nullptr, CAMS_EINVAL, "bad convolution arguments");
+  cudaError_t e = launch_conv_bwd(B, S, ci, co, x, w, gy, xact, gx, gw, gbias,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  return CAMS_OK;
+}
+
+int cams_net_mse(long long n, const float* pred, const float* target, const float* mask,
+                 double count, float* grad, double* loss, double* scratch, void* stream) {
+  if (n < 1 || !(count > 0.0) || !pred || !target || !mask || !grad || !loss || !scratch)
+    return fail(nullptr, CAMS_EINVAL, "bad loss arguments");
+  cudaError_t e = launch_mse(n, pred, target, mask, count, grad, scratch, loss,
+                             static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  return CAMS_OK;
+}
+
+int cams_net_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int step, void* stream) {
+  if (n < 1 || step < 1 || !p || !g || !m || !v) return fail(nullptr, CAMS_EINVAL, "bad Adam arguments");
+  cudaError_t e = launch_adam(n, p, g, m, v, lr, beta1, beta2, eps, step,
+                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  return CAMS_OK;
+}
+
 int cams_get(cams_handle* h, int what, double* dst) {
   if (!h || !dst) return CAMS_EINVAL;
   const long long N = h->g.N;
@@ -1089,6 +1265,17 @@ int cams_get(cams_handle* h, int what, double* dst) {
       CK(cudaStreamSynchronize(s));
       break;
     }
+    case CAMS_Q_SURR_RATIO: {
+      if (!h->surr_ratio) return fail(h, CAMS_EINVAL, "no surrogate on this handle");
+      std::vector<float> tf(h->surr_n);
+      std::vector<double> td(h->surr_n);
+      CK(cudaMemcpyAsync(tf.data(), h->surr_ratio, sizeof(float) * h->surr_n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int k = 0; k < h->surr_n; ++k) td[k] = tf[k];
+      CK(cudaMemcpyAsync(dst, td.data(), sizeof(double) * h->surr_n,
+                         h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+      break;
+    }
     case CAMS_Q_RESIDUAL: {
       CK(launch_residual(h->g, b, b.p, b.r, b.red, b.scal, s));
       CK(cudaMemcpyAsync(dst, b.r, sizeof(double) * N, k, s));
@@ -1105,7 +1292,7 @@ int cams_get_int(cams_handle* h, int what, int* dst) {
   const long long N = h->g.N;
   if (what == CAMS_Q_SIZES) {
     dst[0] = (int)N; dst[1] = h->c.Nc; dst[2] = h->c.nc[0]; dst[3] = h->c.nc[1]; dst[4] = h->c.nc[2];
-    dst[5] = (int)h->ents.size(); dst[6] = h->last_rebuilt; dst[7] = 0;
+    dst[5] = (int)h->ents.size(); dst[6] = h->last_rebuilt; dst[7] = h->surr_accepted;
     return CAMS_OK;
   }
   if (what != CAMS_Q_PROLONG_J) return fail(h, CAMS_EINVAL, "unknown integer quantity");
@@ -1145,6 +1332,7 @@ const char* cams_last_error(cams_handle* h) {
 void cams_destroy(cams_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  free_surrogate(h);
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   prof_flush(h);

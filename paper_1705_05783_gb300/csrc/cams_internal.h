@@ -217,4 +217,29 @@ long long ilu_skew_len(const Geo& g);
 int ilu_pipe_grid(const Geo& g, int num_sms);
 cudaError_t launch_wait_selftest(const Geo& g, Buffers& b, cudaStream_t s);
 
+// ---- learned basis surrogate (k_net.cu) ----
+constexpr int kNetIn = 12, kNetHid = 32, kNetOut = 8;
+constexpr long long kNetParams = (long long)kNetHid * kNetIn * 27 + kNetHid +
+                                 2 * ((long long)kNetHid * kNetHid * 27 + kNetHid) +
+                                 (long long)kNetOut * kNetHid * 27 + kNetOut;
+cudaError_t launch_conv_fwd(int B, int S, int ci, int co, const float* x, const float* w,
+                            const float* bias, int relu, float* y, cudaStream_t s);
+cudaError_t launch_conv_bwd(int B, int S, int ci, int co, const float* x, const float* w,
+                            const float* gy, const float* xact, float* gx, float* gw,
+                            float* gbias, cudaStream_t s);
+cudaError_t launch_mse(long long n, const float* p, const float* t, const float* mask,
+                       double count, float* grad, double* part, double* loss, cudaStream_t s);
+cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
+                        float b1, float b2, float eps, int step, cudaStream_t s);
+int mse_partial_blocks();
+// patches of the full interior dual blocks: org = lower corner (x, y, z) per patch
+cudaError_t launch_patch_inputs(const Geo& g, int b, int n, const int* org, bool single,
+                                const Buffers& bf, float* x, float* target, float* mask,
+                                cudaStream_t s);
+cudaError_t launch_patch_apply(const Geo& g, int b, int n, const int* org, const float* y,
+                               bool single, Buffers& bf, cudaStream_t s);
+cudaError_t launch_patch_gate(const Geo& g, int b, int n, const int* org, const int* ent,
+                              double tol, bool single, Buffers& bf, unsigned char* flag,
+                              float* ratio, cudaStream_t s);
+
 }  // namespace cams
