@@ -505,6 +505,7 @@ __global__ void __launch_bounds__(256) k_ldlt_solve(int N, int m, const double* 
 // (kNotReady until written) and the owner of a block stores its values into
 // every CTA's copy through distributed shared memory.
 constexpr int kCB = 32;                      // rows per block
+constexpr int kCBlocks = 3;                  // per block: L_JJ^{-1}, M_J, M'_J
 constexpr int kCC = 8;                       // CTAs per cluster
 constexpr unsigned long long kCNotReady = 0x7FF4DEADBEEF0002ull;   // signalling NaN
 constexpr long long kCSpinLimit = 1LL << 22;
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(256) k_coarse_prep(int N, int m, const double*
   __shared__ double Li[kCB][kCB + 1];
   __shared__ double Lo[kCB][kCB + 1];
   const int J = blockIdx.x, NB = gridDim.x, base = J * kCB, tid = threadIdx.x;
-  double* out = blk + (long long)J * 3 * kCB * kCB;
+  double* out = blk + (long long)J * kCBlocks * kCB * kCB;
   for (int e = tid; e < kCB * kCB; e += blockDim.x) {
     const int r = e / kCB, q = e % kCB;
     Lj[r][q] = q == r ? 1.0 : lower_at(Lc, N, m, base + r, base + q);
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
     acc = sum8(acc);
     if (h == 0) uv[r] = acc;
     __syncthreads();
-    const double* Li = blk + (long long)J * 3 * kCB * kCB;
+    const double* Li = blk + (long long)J * kCBlocks * kCB * kCB;
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += Li[r * kCB + 4 * h + k] * uv[4 * h + k];
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
     acc = sum8(acc);
     if (h == 0) uv[r] = acc;
     __syncthreads();
-    const double* Li = blk + (long long)I * 3 * kCB * kCB;
+    const double* Li = blk + (long long)I * kCBlocks * kCB * kCB;
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += Li[(4 * h + k) * kCB + r] * uv[4 * h + k];
@@ -844,24 +845,28 @@ __global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double
 template <class TP, class TC, class TO, bool kSet>
 __global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TC* __restrict__ pc,
                           const int* __restrict__ perm, TO* p) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
-  int xc[3];
-  xyz_of(g, i, xc[0], xc[1], xc[2]);
-  int Jl[3][2];
-  for (int d = 0; d < 3; ++d) {
-    Jl[d][0] = corner_d(c, d, xc[d], 0);
-    Jl[d][1] = corner_d(c, d, xc[d], 1);
-  }
-  TC s = TC(0);
+  // warps take whole x-rows: the y and z corners are per row, only x's per cell
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
+  for (unsigned row = blockIdx.x * nw + warp; row < rows; row += gridDim.x * nw) {
+    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    const int Jy[2] = {corner_d(c, 1, y, 0), corner_d(c, 1, y, 1)};
+    const int Jz[2] = {corner_d(c, 2, z, 0), corner_d(c, 2, z, 1)};
+    const long long base = g.sy * y + g.sz * z;
+    for (int x = lane; x < g.nx; x += 32) {
+      const long long i = base + x;
+      const int Jx[2] = {corner_d(c, 0, x, 0), corner_d(c, 0, x, 1)};
+      TC s = TC(0);
 #pragma unroll
-  for (int sl = 0; sl < 8; ++sl) {
-    const int jx = Jl[0][sl & 1], jy = Jl[1][(sl >> 1) & 1], jz = Jl[2][(sl >> 2) & 1];
-    if (jx < 0 || jy < 0 || jz < 0) continue;
-    s += (TC)P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
+      for (int sl = 0; sl < 8; ++sl) {
+        const int jx = Jx[sl & 1], jy = Jy[(sl >> 1) & 1], jz = Jz[(sl >> 2) & 1];
+        if (jx < 0 || jy < 0 || jz < 0) continue;
+        s += (TC)P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
+      }
+      if (kSet) p[i] = (TO)s;
+      else p[i] += (TO)s;
+    }
   }
-  if (kSet) p[i] = (TO)s;
-  else p[i] += (TO)s;
 }
 
 __global__ void k_to_single(int n, const double* __restrict__ a, float* b) {
@@ -954,7 +959,7 @@ cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double*
 }
 
 long long coarse_blocks_len(int Nc) {
-  return (long long)((Nc + kCB - 1) / kCB) * 3 * kCB * kCB;
+  return (long long)((Nc + kCB - 1) / kCB) * kCBlocks * kCB * kCB;
 }
 
 static int coarse_cluster_smem(int Nc) {
@@ -1021,7 +1026,7 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
 
 cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                cudaStream_t s) {
-  const int blocks = (int)((g.N + 255) / 256);
+  const int blocks = (int)(((long long)g.ny * g.nz + 7) / 8);   // one warp per x-row
   if (single) {
     k_to_single<<<(c.Nc + 255) / 256, 256, 0, s>>>(c.Nc, b.pc, b.f32.pc);
     k_prolong<float, float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm,
@@ -1036,7 +1041,7 @@ cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers
 
 cudaError_t launch_prolong_to_p(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                 cudaStream_t s) {
-  const int blocks = (int)((g.N + 255) / 256);
+  const int blocks = (int)(((long long)g.ny * g.nz + 7) / 8);   // one warp per x-row
   if (single)
     k_prolong<float, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.pc, b.perm, b.p);
   else

@@ -183,25 +183,30 @@ __global__ void k_finish_sum(const double* __restrict__ red, int n, double* out)
   if (threadIdx.x == 0) out[0] = s;
 }
 
-// r = f - A p and per-block sums of r^2.
+// r = f - A p and per-block sums of r^2.  Warps take whole x-rows (lanes
+// along x, coalesced), so the cell coordinates cost one division per row.
 __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* __restrict__ Ax,
                            const double* __restrict__ Ay, const double* __restrict__ Az,
                            const double* __restrict__ f, const double* __restrict__ p, double* r,
                            double* red) {
   double s2 = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-       i += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(g, i, x, y, z);
-    double a = f[i] - Ad[i] * p[i];
-    if (x > 0) a -= Ax[i] * p[i - 1];
-    if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
-    if (y > 0) a -= Ay[i] * p[i - g.sy];
-    if (y < g.ny - 1) a -= Ay[i + g.sy] * p[i + g.sy];
-    if (z > 0) a -= Az[i] * p[i - g.sz];
-    if (z < g.nz - 1) a -= Az[i + g.sz] * p[i + g.sz];
-    if (r) r[i] = a;
-    s2 += a * a;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
+  for (unsigned row = blockIdx.x * nw + warp; row < rows; row += gridDim.x * nw) {
+    const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
+    const long long base = g.sy * y + g.sz * z;
+    for (int x = lane; x < g.nx; x += 32) {
+      const long long i = base + x;
+      double a = f[i] - Ad[i] * p[i];
+      if (x > 0) a -= Ax[i] * p[i - 1];
+      if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
+      if (y > 0) a -= Ay[i] * p[i - g.sy];
+      if (y < g.ny - 1) a -= Ay[i + g.sy] * p[i + g.sy];
+      if (z > 0) a -= Az[i] * p[i - g.sz];
+      if (z < g.nz - 1) a -= Az[i + g.sz] * p[i + g.sz];
+      if (r) r[i] = a;
+      s2 += a * a;
+    }
   }
   s2 = block_sum(s2);
   if (threadIdx.x == 0) red[blockIdx.x] = s2;

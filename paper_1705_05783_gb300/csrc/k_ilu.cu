@@ -178,36 +178,84 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* _
   Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : T(0);
 }
 
+// The two conversions between the natural layout and the skewed sweep
+// layout run as tile transposes: one CTA per (tile, kXC positions along x).
+// Rows are read or written in the natural layout by warps along x
+// (coalesced); records are written or read in the skewed layout by warps
+// whose lanes are the tile's 32 rows (one 128- or 256-byte record each);
+// shared memory holds the kR x kXC block in between.
+constexpr int kXC = 64;
+
 // rd = D^{-1} (b - A x), stored skewed; b is read in its own precision and
 // rounded to T.
 template <class B, class T>
-__global__ void k_resid_scaled(Geo g, Skew sk, const T* __restrict__ Ad, const T* __restrict__ Ax,
-                               const T* __restrict__ Ay, const T* __restrict__ Az,
-                               const B* __restrict__ bv, const T* __restrict__ xv,
-                               const T* __restrict__ dinv, T* rd) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
-  int x, y, z;
-  xyz_of(g, i, x, y, z);
-  const long long j = skew_index(sk, x, y, z);
-  T a = T(bv[i]) - Ad[i] * xv[i];
-  if (x > 0) a -= Ax[i] * xv[i - 1];
-  if (x < g.nx - 1) a -= Ax[i + 1] * xv[i + 1];
-  if (y > 0) a -= Ay[i] * xv[i - g.sy];
-  if (y < g.ny - 1) a -= Ay[i + g.sy] * xv[i + g.sy];
-  if (z > 0) a -= Az[i] * xv[i - g.sz];
-  if (z < g.nz - 1) a -= Az[i + g.sz] * xv[i + g.sz];
-  rd[j] = a * dinv[i];
+__global__ void __launch_bounds__(256) k_resid_scaled(Geo g, Skew sk, const T* __restrict__ Ad,
+                                                      const T* __restrict__ Ax,
+                                                      const T* __restrict__ Ay,
+                                                      const T* __restrict__ Az,
+                                                      const B* __restrict__ bv,
+                                                      const T* __restrict__ xv,
+                                                      const T* __restrict__ dinv, T* rd) {
+  __shared__ T blk[kR][kXC + 1];
+  const int tile = blockIdx.x, x0 = blockIdx.y * kXC;
+  const int Y = tile % sk.nty, Z = tile / sk.nty;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int r = warp; r < kR; r += nwarp) {
+    const int y = Y * kTY + r % kTY, z = Z * kTZ + r / kTY;
+    if (y >= g.ny || z >= g.nz) continue;
+    for (int h = lane; h < kXC; h += 32) {
+      const int x = x0 + h;
+      if (x >= g.nx) break;
+      const long long i = x + g.sy * y + g.sz * z;
+      T a = T(bv[i]) - Ad[i] * xv[i];
+      if (x > 0) a -= Ax[i] * xv[i - 1];
+      if (x < g.nx - 1) a -= Ax[i + 1] * xv[i + 1];
+      if (y > 0) a -= Ay[i] * xv[i - g.sy];
+      if (y < g.ny - 1) a -= Ay[i + g.sy] * xv[i + g.sy];
+      if (z > 0) a -= Az[i] * xv[i - g.sz];
+      if (z < g.nz - 1) a -= Az[i + g.sz] * xv[i + g.sz];
+      blk[r][h] = a * dinv[i];
+    }
+  }
+  __syncthreads();
+  // record q holds row (ty, tz) = (lane % kTY, lane / kTY) at x = q - ty - tz
+  const int ty = lane % kTY, tz = lane / kTY;
+  const bool row_ok = Y * kTY + ty < g.ny && Z * kTZ + tz < g.nz;
+  for (int q = x0 + warp; q < x0 + kXC + kTY + kTZ - 2; q += nwarp) {
+    const int x = q - ty - tz;
+    if (row_ok && x >= x0 && x < x0 + kXC && x < g.nx)
+      rd[((long long)tile * sk.ns + q + kPad) * kR + lane] = blk[lane][x - x0];
+  }
 }
 
 // x += z (the correction of one smoothing step), z stored skewed.
 template <class T>
-__global__ void k_apply_z(Geo g, Skew sk, const T* __restrict__ zs, T* xv) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= g.N) return;
-  int x, y, z;
-  xyz_of(g, i, x, y, z);
-  xv[i] += zs[skew_index(sk, x, y, z)];
+__global__ void __launch_bounds__(256) k_apply_z(Geo g, Skew sk, const T* __restrict__ zs, T* xv) {
+  __shared__ T blk[kR][kXC + 1];
+  const int tile = blockIdx.x, x0 = blockIdx.y * kXC;
+  const int Y = tile % sk.nty, Z = tile / sk.nty;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int ty = lane % kTY, tz = lane / kTY;
+  const bool row_ok = Y * kTY + ty < g.ny && Z * kTZ + tz < g.nz;
+  for (int q = x0 + warp; q < x0 + kXC + kTY + kTZ - 2; q += nwarp) {
+    const int x = q - ty - tz;
+    if (row_ok && x >= x0 && x < x0 + kXC && x < g.nx)
+      blk[lane][x - x0] = zs[((long long)tile * sk.ns + q + kPad) * kR + lane];
+  }
+  __syncthreads();
+  for (int r = warp; r < kR; r += nwarp) {
+    const int y = Y * kTY + r % kTY, z = Z * kTZ + r / kTY;
+    if (y >= g.ny || z >= g.nz) continue;
+    for (int h = lane; h < kXC; h += 32) {
+      const int x = x0 + h;
+      if (x >= g.nx) break;
+      xv[x + g.sy * y + g.sz * z] += blk[r][h];
+    }
+  }
+}
+
+inline dim3 transpose_grid(const Geo& g, const Skew& sk) {
+  return dim3(sk.nty * sk.ntz, (g.nx + kXC - 1) / kXC);
 }
 
 template <class T>
@@ -821,7 +869,7 @@ cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, 
     if (e != cudaSuccess) return e;
   }
   if (backward) {
-    k_apply_z<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, v.z, xv);
+    k_apply_z<T><<<transpose_grid(g, sk), 256, 0, s>>>(g, sk, v.z, xv);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -874,10 +922,10 @@ cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t
   const Skew sk = make_skew(g);
   if (single) {
     const SingleBuffers& f = b.f32;
-    k_resid_scaled<double, float><<<blocks_for(g.N, 256), 256, 0, s>>>(
+    k_resid_scaled<double, float><<<transpose_grid(g, sk), 256, 0, s>>>(
         g, sk, f.Ad, f.Ax, f.Ay, f.Az, b.r, f.d, f.dinv, f.rds);
   } else {
-    k_resid_scaled<double, double><<<blocks_for(g.N, 256), 256, 0, s>>>(
+    k_resid_scaled<double, double><<<transpose_grid(g, sk), 256, 0, s>>>(
         g, sk, b.Ad, b.Ax, b.Ay, b.Az, b.f, b.p, b.dinv, b.rds);
   }
   count_launches(1);
