@@ -91,3 +91,28 @@ def network_backward(acts, layers, gy):
         if k > 0:
             g = gx * (acts[k] > 0.0)                      # ReLU of the previous layer
     return grads
+
+
+def energy_loss(pred, target, mask, x):
+    """Energy norm of the interior error, the norm in which the basis
+    functions' error costs the coarse space: with e = mask (pred - target)
+    (zero on the patch boundary, whose values are exact) and relative face
+    couplings w = exp(x[:, d]) read from the log-coupling input channels
+    (channel d at a cell holds the coupling to its lower neighbour along d),
+        E = sum_faces w (e_u - e_v)^2 / count,
+    count = the number of interior entries.  Returns (E, dE/dpred)."""
+    e = (pred - target) * mask
+    count = mask.sum()
+    g = np.zeros_like(e)
+    E = 0.0
+    for d, axis in ((0, 4), (1, 3), (2, 2)):            # x, y, z axes of (B, C, z, y, x)
+        w = np.exp(x[:, d:d + 1])                         # (B, 1, S, S, S): coupling to the lower cell
+        lo = [slice(None)] * 5; hi = [slice(None)] * 5
+        lo[axis] = slice(0, -1); hi[axis] = slice(1, None)
+        diff = e[tuple(hi)] - e[tuple(lo)]                # e_u - e_{u - 1} at the upper cell u
+        wf = w[tuple(hi)]
+        E += float((wf * diff * diff).sum())
+        gu = 2.0 * wf * diff
+        g[tuple(hi)] += gu
+        g[tuple(lo)] -= gu
+    return E / count, g * mask / count

@@ -688,3 +688,30 @@ def test_net_adam_first_step_is_signed_lr():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     p, m, v = adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 0.01, 0.9, 0.999, 1e-12, 1)
     np.testing.assert_allclose(p, -0.01 * np.sign(g), rtol=1e-9, atol=1e-12)
+
+
+def test_net_energy_loss_gradient_and_null_space(rng):
+    """The energy loss's gradient against finite differences, and two facts
+    of the norm: a constant error on a patch whose boundary error is zero is
+    not free (the boundary pins it), and with unit couplings the energy of a
+    single unit error is the number of its interior-facing plus boundary
+    faces (six for an inner cell)."""
+    from oracle.net import energy_loss
+    B, C, S = 2, 3, 5
+    x = rng.standard_normal((B, 3, S, S, S))
+    t = rng.standard_normal((B, C, S, S, S))
+    mask = np.zeros((B, C, S, S, S)); mask[:, :, 1:-1, 1:-1, 1:-1] = 1.0
+    p = t + 0.1 * rng.standard_normal(t.shape)
+    E, g = energy_loss(p, t, mask, x)
+    h = 1e-6
+    for idx in [(0, 1, 2, 2, 2), (1, 0, 1, 3, 2), (0, 2, 3, 1, 1), (1, 1, 0, 2, 2)]:
+        pp = p.copy(); pp[idx] += h
+        pm = p.copy(); pm[idx] -= h
+        fd = (energy_loss(pp, t, mask, x)[0] - energy_loss(pm, t, mask, x)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd))
+    assert g[1, 1, 0, 2, 2] == 0.0                       # boundary entries carry no gradient
+    e1 = np.zeros_like(t); e1[0, 0, 2, 2, 2] = 1.0
+    E1, _ = energy_loss(t + e1, t, mask, np.zeros_like(x))
+    np.testing.assert_allclose(E1 * mask.sum(), 6.0)
+    const = np.where(mask > 0, 1.0, 0.0)
+    assert energy_loss(t + const, t, mask, np.zeros_like(x))[0] > 0.0
