@@ -322,6 +322,14 @@ int cams_surrogate_data(cams_handle* h, int max_patches, float* x, float* target
  *   mse:      loss = sum(mask (pred - target)^2) / count into *loss (device
  *             double), grad = 2 mask (pred - target) / count; scratch holds
  *             512 doubles.
+ *   energy:   the energy norm of the interior error, the norm in which a
+ *             basis function's error costs the coarse space: e = mask
+ *             (pred - target) on B patches of C channels, relative face
+ *             couplings w = exp(x[b][d]) from channels d = 0, 1, 2 of the
+ *             network input x (cx channels; channel d at a cell is the log
+ *             coupling to its lower neighbour along d), loss = sum over the
+ *             patch's faces of w (e_u - e_v)^2 / count into *loss, grad = mask
+ *             d loss / d pred; scratch holds 512 doubles.
  *   adam:     one Adam step (Kingma and Ba) at step number step >= 1. */
 int cams_net_conv_forward(int B, int S, int ci, int co, const float* x, const float* w,
                           const float* bias, int relu, float* y, void* stream);
@@ -330,6 +338,9 @@ int cams_net_conv_backward(int B, int S, int ci, int co, const float* x, const f
                            float* gbias, void* stream);
 int cams_net_mse(long long n, const float* pred, const float* target, const float* mask,
                  double count, float* grad, double* loss, double* scratch, void* stream);
+int cams_net_energy(int B, int S, int C, int cx, const float* pred, const float* target,
+                    const float* mask, const float* x, double count, float* grad, double* loss,
+                    double* scratch, void* stream);
 int cams_net_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                   float beta1, float beta2, float eps, int step, void* stream);
 

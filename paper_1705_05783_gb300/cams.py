@@ -31,7 +31,8 @@ EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest
            "cams_set_stream",
            "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve",
            "cams_ensemble_solve", "cams_set_surrogate", "cams_surrogate_data",
-           "cams_net_conv_forward", "cams_net_conv_backward", "cams_net_mse", "cams_net_adam",
+           "cams_net_conv_forward", "cams_net_conv_backward", "cams_net_mse", "cams_net_energy",
+           "cams_net_adam",
            "cams_get",
            "cams_get_int", "cams_last_error", "cams_destroy", "cams_residual_norm_noalloc")
 
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "cams_net_conv_forward": (C.c_int, [C.c_int] * 4 + [P, P, P, C.c_int, P, P]),
         "cams_net_conv_backward": (C.c_int, [C.c_int] * 4 + [P] * 7 + [P]),
         "cams_net_mse": (C.c_int, [C.c_longlong, P, P, P, C.c_double, P, P, P, P]),
+        "cams_net_energy": (C.c_int, [C.c_int] * 4 + [P] * 4 + [C.c_double, P, P, P, P]),
         "cams_net_adam": (C.c_int, [C.c_longlong, P, P, P, P, C.c_float, C.c_float, C.c_float,
                                     C.c_float, C.c_int, P]),
         "cams_get": (C.c_int, [P, C.c_int, P]),
@@ -291,6 +293,12 @@ def cams_net_conv_backward(B, S, ci, co, x, w, gy, xact, gx, gw, gb, stream=None
 def cams_net_mse(n, pred, target, mask, count, grad, loss, scratch, stream=None):
     _check(_lib.cams_net_mse(int(n), _ptr(pred), _ptr(target), _ptr(mask), float(count),
                              _ptr(grad), _ptr(loss), _ptr(scratch), _stream(stream)))
+
+
+def cams_net_energy(B, S, C_, cx, pred, target, mask, x, count, grad, loss, scratch, stream=None):
+    _check(_lib.cams_net_energy(int(B), int(S), int(C_), int(cx), _ptr(pred), _ptr(target),
+                                _ptr(mask), _ptr(x), float(count), _ptr(grad), _ptr(loss),
+                                _ptr(scratch), _stream(stream)))
 
 
 def cams_net_adam(n, p, g, m, v, lr, beta1, beta2, eps, step, stream=None):

@@ -1188,6 +1188,18 @@ int cams_net_mse(long long n, const float* pred, const float* target, const floa
   return CAMS_OK;
 }
 
+int cams_net_energy(int B, int S, int C, int cx, const float* pred, const float* target,
+                    const float* mask, const float* x, double count, float* grad, double* loss,
+                    double* scratch, void* stream) {
+  if (B < 1 || S < 2 || C < 1 || cx < 3 || !(count > 0.0) || !pred || !target || !mask || !x ||
+      !grad || !loss || !scratch)
+    return fail(nullptr, CAMS_EINVAL, "bad energy-loss arguments");
+  cudaError_t e = launch_energy(B, S, C, cx, pred, target, mask, x, count, grad, scratch, loss,
+                                static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  return CAMS_OK;
+}
+
 int cams_net_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                   float beta1, float beta2, float eps, int step, void* stream) {
   if (n < 1 || step < 1 || !p || !g || !m || !v) return fail(nullptr, CAMS_EINVAL, "bad Adam arguments");

@@ -231,6 +231,9 @@ cudaError_t launch_mse(long long n, const float* p, const float* t, const float*
                        double count, float* grad, double* part, double* loss, cudaStream_t s);
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, int step, cudaStream_t s);
+cudaError_t launch_energy(int B, int S, int C, int cx, const float* p, const float* t,
+                          const float* mask, const float* x, double count, float* grad, double* part,
+                          double* loss, cudaStream_t s);
 int mse_partial_blocks();
 // patches of the full interior dual blocks: org = lower corner (x, y, z) per patch
 cudaError_t launch_patch_inputs(const Geo& g, int b, int n, const int* org, bool single,

@@ -210,6 +210,58 @@ __global__ void k_mse_final(int nb, const double* __restrict__ part, double inv_
   out[0] = s * inv_count;
 }
 
+// Energy norm of the interior error (the norm the coarse space pays in):
+// e = mask (p - t), relative face couplings w = exp(x[b][d][u]) for the face
+// between u and its lower neighbour along d (x: the network input, whose
+// channels 0-2 are the log couplings), E = sum_faces w (e_u - e_v)^2 / count,
+// grad = mask dE/dp.  One thread per (patch, channel, cell), grid-stride.
+__device__ __forceinline__ float e_at(const float* p, const float* t, const float* mk, long long o) {
+  return (p[o] - t[o]) * mk[o];
+}
+
+__global__ void k_energy_partial(int B, int S, int C, int cx, const float* __restrict__ p,
+                                 const float* __restrict__ t, const float* __restrict__ mk,
+                                 const float* __restrict__ x, float inv_count, float* grad,
+                                 double* part) {
+  __shared__ double red[32];
+  const int S3 = S * S * S;
+  const long long n = (long long)B * C * S3;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(e % S3);
+    const long long bc = e / S3;
+    const int b = (int)(bc / C);
+    const int l[3] = {v % S, (v / S) % S, v / (S * S)};
+    const int st[3] = {1, S, S * S};
+    const float ev = e_at(p, t, mk, e);
+    float gsum = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float* xd = x + ((long long)b * cx + d) * S3;
+      if (l[d] > 0) {                          // face to the lower neighbour
+        const float w = expf(xd[v]);
+        const float diff = ev - e_at(p, t, mk, e - st[d]);
+        acc += (double)(w * diff * diff);
+        gsum += w * diff;
+      }
+      if (l[d] < S - 1) {                      // face to the upper neighbour
+        const float w = expf(xd[v + st[d]]);
+        gsum += w * (ev - e_at(p, t, mk, e + st[d]));
+      }
+    }
+    grad[e] = 2.0f * gsum * mk[e] * inv_count;
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tsum = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tsum += red[k];
+    part[blockIdx.x] = tsum;
+  }
+}
+
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
 // p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 __global__ void k_adam(long long n, float* p, const float* __restrict__ g, float* m, float* v,
@@ -260,6 +312,16 @@ cudaError_t launch_conv_bwd(int B, int S, int ci, int co, const float* x, const 
 cudaError_t launch_mse(long long n, const float* p, const float* t, const float* mask,
                        double count, float* grad, double* part, double* loss, cudaStream_t s) {
   k_mse_partial<<<kMseBlocks, 256, 0, s>>>(n, p, t, mask, (float)(1.0 / count), grad, part);
+  k_mse_final<<<1, 32, 0, s>>>(kMseBlocks, part, 1.0 / count, loss);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(int B, int S, int C, int cx, const float* p, const float* t,
+                          const float* mask, const float* x, double count, float* grad, double* part,
+                          double* loss, cudaStream_t s) {
+  k_energy_partial<<<kMseBlocks, 256, 0, s>>>(B, S, C, cx, p, t, mask, x, (float)(1.0 / count), grad,
+                                              part);
   k_mse_final<<<1, 32, 0, s>>>(kMseBlocks, part, 1.0 / count, loss);
   count_launches(2);
   return cudaGetLastError();

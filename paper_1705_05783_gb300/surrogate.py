@@ -1,7 +1,9 @@
 """Training of the learned basis surrogate on the GPU.
 
 The network (4 layers of 3x3x3 convolutions, see cams.h) is trained on basis
-functions that the method itself computes: for seeded permeability fields the
+functions that the method itself computes, by default in the energy norm of
+the interior error (the norm a basis function's error costs the coarse space;
+a masked MSE is the alternative): for seeded permeability fields the
 engine builds the basis with its exact local solves, cams_surrogate_data cuts
 every full dual-block interior's patch into network inputs and targets, and
 the library's own layer kernels (cams_net_conv_forward/backward, cams_net_mse,
@@ -54,10 +56,10 @@ class Trainer:
     """Parameters, gradients, Adam moments and activation buffers for
     batches of B patches of edge S, all on the GPU."""
 
-    def __init__(self, params, B, S, device, lr=1e-3):
+    def __init__(self, params, B, S, device, lr=1e-3, loss="energy"):
         import torch
         self.torch = torch
-        self.B, self.S, self.lr = B, S, lr
+        self.B, self.S, self.lr, self.kind = B, S, lr, loss
         f32 = dict(dtype=torch.float32, device=device)
         self.p = torch.from_numpy(np.asarray(params, np.float32)).to(device)
         self.g = torch.zeros_like(self.p)
@@ -101,9 +103,7 @@ class Trainer:
         """Loss (device) and its gradient with respect to every parameter
         (self.g, in the parameter layout) for one batch."""
         y = self.forward(x)
-        count = float(mask.sum().item())
-        cams.cams_net_mse(y.numel(), y, target, mask, max(count, 1.0), self.gy, self.loss,
-                          self.scratch)
+        self.loss_of(y, x, target, mask)
         g = self.gy
         for k in range(len(LAYERS) - 1, -1, -1):
             ci, co = LAYERS[k]
@@ -114,6 +114,17 @@ class Trainer:
             cams.cams_net_conv_backward(self.B, self.S, ci, co, self.acts[k], w, g, xact,
                                         None if gx is None else gx[:, :ci], gw, gb)
             g = gx[:, :ci] if gx is not None else None
+        return self.loss
+
+    def loss_of(self, y, x, target, mask, kind=None):
+        """The batch loss into self.loss and its gradient into self.gy:
+        the energy norm of the interior error (default) or the masked MSE."""
+        count = max(float(mask.sum().item()), 1.0)
+        if (kind or self.kind) == "energy":
+            cams.cams_net_energy(y.shape[0], self.S, cams.CAMS_NET_OUT, cams.CAMS_NET_IN, y, target,
+                                 mask, x, count, self.gy, self.loss, self.scratch)
+        else:
+            cams.cams_net_mse(y.numel(), y, target, mask, count, self.gy, self.loss, self.scratch)
         return self.loss
 
     def params(self):
@@ -159,12 +170,12 @@ def generate(fields, device, max_per_field=100000):
     return torch.cat(xs), torch.cat(ts), torch.cat(ms)
 
 
-def train(x, t, m, S, steps=3000, batch=64, lr=1e-3, seed=0, log=None, val=None):
+def train(x, t, m, S, steps=3000, batch=64, lr=1e-3, seed=0, log=None, val=None, loss="energy"):
     """Adam on shuffled batches; the learning rate halves at 50% and 75% of
     the steps.  Returns (params, [(step, train loss, val loss)])."""
     import torch
     device = x.device
-    tr = Trainer(init_params(seed), batch, S, device, lr)
+    tr = Trainer(init_params(seed), batch, S, device, lr, loss)
     gen = torch.Generator(device="cpu").manual_seed(seed)
     n = x.shape[0]
     hist = []
@@ -180,22 +191,23 @@ def train(x, t, m, S, steps=3000, batch=64, lr=1e-3, seed=0, log=None, val=None)
         pos += batch
         loss = tr.step(x[idx].contiguous(), t[idx].contiguous(), m[idx].contiguous())
         if s == 1 or s % 250 == 0 or s == steps:
-            vl = evaluate(tr, *val) if val is not None else None
+            vl = evaluate(tr, *val, kind=tr.kind) if val is not None else None
             hist.append((s, float(loss.item()), vl))
             if log:
                 log(f"step {s} loss {hist[-1][1]:.4e} val {vl}")
     return tr.params(), hist
 
 
-def evaluate(tr, x, t, m):
-    """Masked MSE of the current parameters over a data set (whole batches)."""
+def evaluate(tr, x, t, m, kind="mse"):
+    """Masked MSE (or the energy loss) of the current parameters over a data
+    set (whole batches)."""
     tot, cnt = 0.0, 0.0
     for p0 in range(0, x.shape[0] - tr.B + 1, tr.B):
-        y = tr.forward(x[p0:p0 + tr.B].contiguous())
+        xb = x[p0:p0 + tr.B].contiguous()
+        y = tr.forward(xb)
         mb = m[p0:p0 + tr.B].contiguous()
         c = float(mb.sum().item())
-        cams.cams_net_mse(y.numel(), y, t[p0:p0 + tr.B].contiguous(), mb, max(c, 1.0), tr.gy,
-                          tr.loss, tr.scratch)
+        tr.loss_of(y, xb, t[p0:p0 + tr.B].contiguous(), mb, kind)
         tot += float(tr.loss.item()) * c
         cnt += c
     return tot / max(cnt, 1.0)
@@ -208,6 +220,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--loss", default="energy", choices=["energy", "mse"])
     a = ap.parse_args(argv)
     import torch
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -223,7 +236,7 @@ def main(argv=None):
     S = round(x.shape[2] ** (1.0 / 3.0))
     t1 = time.time()
     params, hist = train(x, t, m, S, a.steps, a.batch, a.lr, val=(xv, tv, mv),
-                         log=lambda s: print(s, flush=True))
+                         log=lambda s: print(s, flush=True), loss=a.loss)
     print(f"training: {time.time() - t1:.1f} s", flush=True)
     np.save(a.out, params)
     print(f"saved {a.out}", flush=True)

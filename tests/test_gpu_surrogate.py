@@ -8,7 +8,7 @@ generates lowers the loss.  In the engine: with the trained parameters a
 solve still reaches the oracle's pressure (the surrogate only changes the
 preconditioner), the residual gate hands the rejected interiors to the exact
 solve, and on an unseen field the trained network predicts the interior
-basis values with less than half the squared error of the multilinear
+basis values with less than half the energy-norm error of the multilinear
 baseline alone (the network with all-zero parameters) and lower gate ratios."""
 import os
 
@@ -93,6 +93,27 @@ def test_mse_and_adam_match_oracle(env):
     assert np.abs(par.cpu().numpy() - P).max() < 1e-5
 
 
+def test_energy_loss_matches_oracle(env):
+    torch, cams, _ = env
+    from oracle.net import energy_loss
+    rng = np.random.default_rng(8)
+    B, C, S, cx = 3, 8, 6, 12
+    x = rng.standard_normal((B, cx, S, S, S))
+    t = rng.standard_normal((B, C, S, S, S))
+    p = t + 0.2 * rng.standard_normal(t.shape)
+    m = np.zeros_like(t); m[:, :, 1:-1, 1:-1, 1:-1] = 1.0
+    grad = torch.zeros((B, C, S, S, S), device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    scratch = torch.zeros(512, dtype=torch.float64, device="cuda")
+    cams.cams_net_energy(B, S, C, cx, _dev(torch, p), _dev(torch, t), _dev(torch, m), _dev(torch, x),
+                         m.sum(), grad, loss, scratch)
+    torch.cuda.synchronize()
+    f = lambda a: a.astype(np.float32).astype(np.float64)
+    E, G = energy_loss(f(p), f(t), m, f(x)[:, :3])
+    assert abs(loss.item() - E) < 1e-5 * E
+    assert _rel(grad.cpu().numpy(), G) < 1e-5
+
+
 def test_network_gradient_matches_oracle(env):
     """Whole 4-layer network: the library's forward and backward kernels
     against the oracle's, same parameters and data."""
@@ -100,7 +121,7 @@ def test_network_gradient_matches_oracle(env):
     rng = np.random.default_rng(7)
     B, S = 2, 7
     params = surrogate.init_params(3)
-    tr = surrogate.Trainer(params, B, S, torch.device("cuda"))
+    tr = surrogate.Trainer(params, B, S, torch.device("cuda"), loss="mse")
     x = rng.standard_normal((B, cams.CAMS_NET_IN, S ** 3))
     t = 0.1 * rng.standard_normal((B, cams.CAMS_NET_OUT, S ** 3))
     m = (rng.random((B, cams.CAMS_NET_OUT, S ** 3)) < 0.7).astype(np.float64)
@@ -129,7 +150,7 @@ def test_training_on_engine_patches_lowers_the_loss(env):
     assert x.shape[0] == 3 * 5 * 5 * 3                      # full interiors of 6x6x4 coarse cells
     # targets: exact basis values minus the multilinear baseline, mask = interior
     assert float(m.sum().item()) == x.shape[0] * 8 * 9 ** 3
-    params, hist = surrogate.train(x, t, m, 11, steps=300, batch=16, lr=2e-3)
+    params, hist = surrogate.train(x, t, m, 11, steps=300, batch=16, lr=2e-3, loss="energy")
     first, last = hist[0][1], hist[-1][1]
     assert np.isfinite(last) and last < 0.5 * first
 
@@ -165,8 +186,8 @@ def test_surrogate_solve_matches_oracle(env, precision, tol):
 
 def test_trained_network_gains_over_the_baseline(env):
     """On a field it was not trained on: the trained network's error in the
-    interior basis values is well below the multilinear baseline's (the
-    all-zero network), its gate ratios are lower, and with it the step
+    interior basis values (energy norm) is well below the multilinear
+    baseline's (the all-zero network), its gate ratios are lower, and with it the step
     still converges to the exact-basis pressure (at a 1e-10 nonlinear
     tolerance: a different P takes a different path to the tolerance)."""
     torch, cams, surrogate = env
@@ -189,7 +210,7 @@ def test_trained_network_gains_over_the_baseline(env):
     err = {}
     for name, pr in (("trained", params), ("baseline", zero)):
         tr = surrogate.Trainer(pr, 5, 11, torch.device("cuda"))
-        err[name] = surrogate.evaluate(tr, x, t, m)
+        err[name] = surrogate.evaluate(tr, x, t, m, kind="energy")
     # gate ratios and the solve
     out = {}
     for name, pr in (("trained", params), ("baseline", zero), ("exact", None)):
@@ -208,7 +229,7 @@ def test_trained_network_gains_over_the_baseline(env):
     print("\ninterior MSE", err, "median gate ratio",
           {k: float(np.median(v[3])) for k, v in out.items() if v[3] is not None},
           "C-AMS its", {k: v[0] for k, v in out.items()})
-    assert err["trained"] < 0.5 * err["baseline"]
+    assert err["trained"] < 0.5 * err["baseline"]          # energy norm of the interior error
     assert np.median(out["trained"][3]) < np.median(out["baseline"][3])
     assert out["trained"][1] and out["baseline"][1]
     assert _rel(out["trained"][2], out["exact"][2]) < 1e-6
