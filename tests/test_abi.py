@@ -78,3 +78,26 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
         cams.cams_setup(g, f, o, k)
     assert e.value.code == cams.CAMS_EINVAL
     assert "basis" in cams.cams_last_error()
+
+
+def test_ensemble_and_network_entry_points_reject_bad_arguments_without_a_gpu():
+    """Argument checks of the ensemble, surrogate and network entry points
+    come before any CUDA call."""
+    import ctypes as C
+    from paper_1705_05783_gb300 import cams
+    lib = cams._lib
+    assert lib.cams_ensemble_solve(-1, None, None, None, None, None, None, None, 0) == cams.CAMS_EINVAL
+    assert lib.cams_ensemble_solve(0, None, None, None, None, None, None, None, 0) == cams.CAMS_OK
+    assert lib.cams_ensemble_solve(2, None, None, None, None, None, None, None, 0) == cams.CAMS_EINVAL
+    assert lib.cams_set_surrogate(None, None, 0.5) == cams.CAMS_EINVAL
+    n = C.c_int(7)
+    assert lib.cams_surrogate_data(None, 0, None, None, None, C.byref(n)) == cams.CAMS_EINVAL
+    assert lib.cams_net_conv_forward(1, 0, 1, 1, None, None, None, 0, None, None) == cams.CAMS_EINVAL
+    assert lib.cams_net_conv_backward(0, 4, 1, 1, None, None, None, None, None, None, None,
+                                      None) == cams.CAMS_EINVAL
+    assert lib.cams_net_mse(0, None, None, None, 1.0, None, None, None, None) == cams.CAMS_EINVAL
+    assert lib.cams_net_energy(1, 1, 8, 12, None, None, None, None, 1.0, None, None, None,
+                               None) == cams.CAMS_EINVAL
+    assert lib.cams_net_adam(10, None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 0,
+                             None) == cams.CAMS_EINVAL
+    assert "Adam" in cams.cams_last_error()
