@@ -66,6 +66,11 @@ struct cams_handle {
   int* surr_ent = nullptr;         // device: its entity index
   float *surr_x = nullptr, *surr_h1 = nullptr, *surr_h2 = nullptr, *surr_y = nullptr;
   float* surr_ratio = nullptr;     // device: gate ratio of each full interior (last build)
+  // the C-AMS iteration as a CUDA graph (captured once, replayed per iteration)
+  bool graphs = true;               // CAMS_GRAPHS=0 launches every kernel directly
+  cudaGraphExec_t step_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  long long step_launches = 0;
   // per-kernel-class profiling (cams_profile)
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; long long k0, k1; };
@@ -140,6 +145,7 @@ int read_scalar(cams_handle* h, double* out) {
 
 namespace lc {
 std::atomic<long long> total{0};
+thread_local long long mine = 0;     // launches issued by this thread
 }
 
 cudaEvent_t pool_get(cams_handle* h) {
@@ -641,7 +647,7 @@ int ilu_smooth(cams_handle* h) {
 // p += delta; f - A(p + delta) = r - A delta, so this is the FP64
 // iteration with the preconditioner rounded to FP32.  Pre-smoothing steps
 // are applied the same way and added to p before the coarse correction.
-int cams_step(cams_handle* h) {
+int cams_step_direct(cams_handle* h) {
   Buffers& b = h->b;
   const bool s = h->single;
   if (h->opt.n_pre > 0) {
@@ -666,6 +672,56 @@ int cams_step(cams_handle* h) {
   return CAMS_OK;
 }
 
+// Capture one iteration's launches (no host reads happen inside it) on a
+// private stream into a graph.  Every pointer and size it uses is fixed for
+// the handle's lifetime, so the graph is captured once and replayed on the
+// handle's current stream.
+int capture_step(cams_handle* h) {
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t own = h->stream;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(h, CAMS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  h->stream = h->cap_stream;
+  const long long l0 = lc::mine;
+  const int rc = cams_step_direct(h);
+  const long long l1 = lc::mine;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->cap_stream, &graph);
+  h->stream = own;
+  lc::total -= l1 - l0;                        // captured, not launched
+  lc::mine -= l1 - l0;
+  if (rc || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc ? rc : fail(h, CAMS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&h->step_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->step_exec = nullptr;
+    cudaGetLastError();
+    return fail(h, CAMS_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+  }
+  h->step_launches = l1 - l0;
+  return CAMS_OK;
+}
+
+// One C-AMS iteration: the captured graph, or direct launches while
+// per-kernel-class profiling is on (its events bracket every class).
+int cams_step(cams_handle* h) {
+  if (h->prof || !h->graphs) return cams_step_direct(h);
+  if (!h->step_exec) {
+    const int rc = capture_step(h);
+    if (rc) {
+      h->graphs = false;                       // keep the direct launches for this handle
+      return cams_step_direct(h);
+    }
+  }
+  CK(cudaGraphLaunch(h->step_exec, h->stream));
+  count_launches(h->step_launches);
+  return CAMS_OK;
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -676,7 +732,10 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 namespace cams {
 void set_global_error(const std::string& msg) { g_setup_error = msg; }
-void count_launches(long long n) { lc::total += n; }
+void count_launches(long long n) {
+  lc::total += n;
+  lc::mine += n;
+}
 
 cudaError_t raise_smem_limit(const void* func, int bytes) {
   static std::mutex mu;
@@ -796,6 +855,8 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   for (auto& x : h->ev) cudaEventCreate(&x);
   h->launch_base = launches_total();
   {
+    const char* gr = std::getenv("CAMS_GRAPHS");
+    h->graphs = !(gr && gr[0] == '0');
     const char* lv = std::getenv("CAMS_ILU_LEVEL");
     h->ilu_pipelined = !(lv && lv[0] == '1');
     h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
@@ -1345,6 +1406,8 @@ void cams_destroy(cams_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   free_surrogate(h);
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   prof_flush(h);
