@@ -185,3 +185,35 @@ def prolongation_global(Ab: sp.csr_matrix, wb: Wirebasket) -> sp.csr_matrix:
     red = sp.csc_matrix((vals, (rows, cols)), shape=(N, N))
     E = sp.csc_matrix((np.ones(wb.Nc), (wb.vertex_cell, np.arange(wb.Nc))), shape=(N, wb.Nc))
     return sp.csr_matrix(spl.spsolve(red, E))
+
+
+def correction_function(Ab: sp.csr_matrix, wb: Wirebasket, r: np.ndarray) -> np.ndarray:
+    """Correction function Psi (Sec. 3: the local problems of Eqs. 8-11 with
+    their right-hand side kept; Table 1, step 4, the pre-smoothing stage).
+
+    Reading R21: the same reduced problems as the basis functions, with the
+    fine-scale residual r as the source: Psi = 0 on the vertices, then level
+    by level (edges, faces, interiors) M_e Psi_e = r_e - A_b[e, lower] Psi[lower],
+    M_e = A_b[e, e] with the level-(k+1) neighbours lumped onto the diagonal."""
+    psi = np.zeros(wb.grid.N)
+    for k in range(1, wb.d_active + 1):
+        for e in wb.entities:
+            if e.level != k:
+                continue
+            S = e.cells
+            m = len(S)
+            sub = Ab[S].tocoo()
+            rr, c, v = sub.row, sub.col, sub.data
+            pos = np.full(Ab.shape[0], -1, np.int64)
+            pos[S] = np.arange(m)
+            inS = pos[c] >= 0
+            lev = wb.level[c]
+            M = np.zeros((m, m))
+            np.add.at(M, (rr[inS], pos[c[inS]]), v[inS])
+            up = (~inS) & (lev == k + 1)
+            M[np.arange(m), np.arange(m)] += np.bincount(rr[up], weights=v[up], minlength=m)
+            lo = (~inS) & (lev == k - 1)
+            rhs = np.array(r[S], dtype=np.float64)
+            np.add.at(rhs, rr[lo], -v[lo] * psi[c[lo]])
+            psi[S] = np.linalg.solve(M, rhs)
+    return psi

@@ -37,7 +37,7 @@ import numpy as np
 
 from .problem import Problem, assemble
 from .wirebasket import Wirebasket, build_wirebasket
-from .basis import basis_operator, prolongation, PRows
+from .basis import basis_operator, correction_function, prolongation, PRows
 from .coarse import restriction, coarse_operator, coarse_factor, coarse_solve
 from .ilu import ilu0, ilu_apply
 
@@ -55,6 +55,7 @@ class Options:
     adapt_theta: float = 0.1
     max_newton: int = 50
     max_cams: int = 200
+    cf: bool = False       # correction functions as the pre-smoother (Table 1 step 4, Reading R21)
 
 
 class BasisState:
@@ -123,8 +124,12 @@ class BasisState:
         return self.P.to_csr(self.wb.Nc)
 
 
-def cams_iteration(A, f, p, P, R, lu, LU, n_pre, n_post):
-    """One C-AMS iteration (Table 1, steps 4-7, ILU(0) smoother)."""
+def cams_iteration(A, f, p, P, R, lu, LU, n_pre, n_post, cf=None):
+    """One C-AMS iteration (Table 1, steps 4-7, ILU(0) smoother); cf, when
+    given, maps a residual to its correction function (the pre-smoothing
+    stage of step 4)."""
+    if cf is not None:
+        p = p + cf(f - A @ p)
     for _ in range(n_pre):
         p = p + ilu_apply(LU, f - A @ p)
     r = f - A @ p
@@ -174,7 +179,8 @@ def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
         r0 = float(np.linalg.norm(lin.f - lin.A @ p))
         its = 0
         while its < opt.max_cams:
-            p = cams_iteration(lin.A, lin.f, p, P, R, lu, LU, opt.n_pre, opt.n_post)
+            cf = (lambda r: correction_function(Ab, wb, r)) if opt.cf else None
+            p = cams_iteration(lin.A, lin.f, p, P, R, lu, LU, opt.n_pre, opt.n_post, cf)
             its += 1
             rn = float(np.linalg.norm(lin.f - lin.A @ p))
             if rn < opt.lin_rtol * r0:

@@ -715,3 +715,91 @@ def test_net_energy_loss_gradient_and_null_space(rng):
     np.testing.assert_allclose(E1 * mask.sum(), 6.0)
     const = np.where(mask > 0, 1.0, 0.0)
     assert energy_loss(t + const, t, mask, np.zeros_like(x))[0] > 0.0
+
+
+# -------------------------------------------- correction functions (A14) --
+
+def _reduced_system(Ab, wb):
+    """The whole block-triangular reduced system in the natural order (same
+    construction as the global prolongation): an independent route."""
+    N = wb.grid.N
+    coo = Ab.tocoo()
+    r, c, v = coo.row, coo.col, coo.data
+    lr, lc = wb.level[r], wb.level[c]
+    keep = (r != c) & ((lc == lr) | (lc == lr - 1)) & (lr > 0)
+    lump = (r != c) & (lc == lr + 1) & (lr > 0)
+    diag = np.where(wb.level > 0, Ab.diagonal(), 1.0) + np.bincount(r[lump], weights=v[lump], minlength=N)
+    return sp.csc_matrix((np.concatenate([v[keep], diag]),
+                          (np.concatenate([r[keep], np.arange(N)]), np.concatenate([c[keep], np.arange(N)]))),
+                         shape=(N, N))
+
+
+@pytest.mark.parametrize("shape,coarse", [((12, 10, 1), (4, 5, 1)), ((12, 10, 6), (4, 5, 3))])
+def test_correction_function_equals_the_global_reduced_solve(rng, shape, coarse):
+    """Reading R21: the staged local solves with the residual as source equal
+    one solve of the global reduced system whose vertex rows are zero."""
+    from oracle.basis import correction_function
+    g = _grid(*shape)
+    pb = _problem(g, _lognormal(g.N, rng, 1.5))
+    lin = assemble(pb, np.zeros(g.N), np.zeros(g.N), 0.01)
+    wb = build_wirebasket(g, coarse)
+    Ab = basis_operator(pb, 1, lin.rho, lin.c, np.zeros(g.N), 0.01)
+    r = rng.standard_normal(g.N)
+    psi = correction_function(Ab, wb, r)
+    rhs = r.copy(); rhs[wb.vertex_cell] = 0.0
+    ref = spl.spsolve(_reduced_system(Ab, wb), rhs)
+    np.testing.assert_allclose(psi, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    assert np.all(psi[wb.vertex_cell] == 0.0)
+
+
+def test_correction_function_with_msfe_is_exact_in_1d(rng):
+    """1D, no-flow ends, compressible with the (B1) basis operator, which is
+    then A itself: the local problems between vertices decouple, the basis
+    functions are A-orthogonal to every function that vanishes on the
+    vertices, so one correction-function stage followed by the MSFE stage (no
+    smoothing) returns the exact solution of A p = f from any start."""
+    from oracle.basis import correction_function
+    n = 24
+    g = Grid(n, 1, 1, 1.0 / n, 1.0, 1.0)
+    k = np.exp(1.5 * rng.standard_normal(n))
+    pb = _problem(g, (k, k, k), law=0, c=0.2, dirichlet=False)
+    p_nu = rng.uniform(0, 1, n)
+    lin = assemble(pb, p_nu, np.zeros(n), 0.01)
+    wb = build_wirebasket(g, (6, 1, 1))
+    Ab = basis_operator(pb, 1, lin.rho, lin.c, np.zeros(n), 0.01)
+    np.testing.assert_allclose(Ab.toarray(), lin.A.toarray(), rtol=1e-13, atol=1e-15)
+    P = prolongation(Ab, wb).to_csr(wb.Nc)
+    R = restriction(0, P, wb)
+    lu = coarse_factor(coarse_operator(R, lin.A, P))
+    p0 = rng.standard_normal(n)
+    p1 = cams_iteration(lin.A, lin.f, p0, P, R, lu, ilu0(lin.A), 0, 0,
+                        cf=lambda r: correction_function(Ab, wb, r))
+    exact = spl.spsolve(lin.A.tocsc(), lin.f)
+    np.testing.assert_allclose(p1, exact, rtol=1e-10, atol=1e-12 * np.abs(exact).max())
+    # without the correction function one iteration is not exact
+    p2 = cams_iteration(lin.A, lin.f, p0, P, R, lu, ilu0(lin.A), 0, 0)
+    assert np.abs(p2 - exact).max() > 1e-3 * np.abs(exact).max()
+
+
+def test_correction_function_is_local_and_keeps_the_fixed_point(rng):
+    """A residual inside one dual-block interior gives a correction function
+    supported on that interior only; with correction functions on, the step
+    converges to the same pressure as without."""
+    from oracle.basis import correction_function
+    g = _grid(12, 10, 1)
+    pb = _problem(g, _lognormal(g.N, rng, 1.5), c=0.2)
+    wb = build_wirebasket(g, (4, 5, 1))
+    lin = assemble(pb, np.zeros(g.N), np.zeros(g.N), 0.01)
+    Ab = basis_operator(pb, 4, lin.rho, lin.c, np.zeros(g.N), 0.01)
+    interior = [e for e in wb.entities if e.level == wb.d_active and len(e.cells) > 1][0]
+    r = np.zeros(g.N); r[interior.cells[0]] = 1.0
+    psi = correction_function(Ab, wb, r)
+    assert set(np.flatnonzero(psi)) <= set(interior.cells.tolist())
+    assert psi[interior.cells[0]] != 0.0
+    out = []
+    for cf in (False, True):
+        opt = Options(coarse=(4, 5, 1), basis=4, n_post=1, nl_tol=1e-11, cf=cf, max_newton=30)
+        p, st = run(pb, opt, np.zeros(g.N), 0.01, 1)
+        assert st[0].converged
+        out.append(p)
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-8)
