@@ -21,6 +21,11 @@ on a Dirichlet face it is rho(p_boundary).
 Reading R6: the saturation S^n of Eq. 19 is 1 (single phase).
 Reading R7: every row of Eq. 3 is multiplied by V_i rho_i^nu, which makes the
 matrix A = C + A~ of Eq. 6 symmetric and leaves its solution unchanged.
+Reading R22 (the full-Jacobian variant; the paper's own step is Eq. 3):
+Newton on the paper's equation (Eq. 2 divided by rho, in volume units) with
+every term differentiated, the flux density and the flux term's 1/rho
+included, and rows multiplied by V rho^nu as in R7.  Both steps solve
+A dp = -F(p^nu) for the same residual F, so they share the root.
 Reading R19 (Test Case 2 of Sec. 4.2.2 prescribes p at the centres of two
 vertical columns of cells without saying how): the prescribed ("fixed") cells
 are taken out of the unknowns by symmetric elimination.  Their entries of
@@ -258,7 +263,31 @@ def accumulation_coefficient(fl: Fluid, p, p_n, dt):
     return fl.phi * fl.rho(p_n) * fl.drho(p) / (dt * rho * rho)
 
 
-def assemble(pb: Problem, p, p_n, dt) -> Linearised:
+def flux_density_terms(pb: Problem, p, rho):
+    """What the lagged step of Eq. 3 leaves out of the derivative of the
+    paper's equation (Eq. 2 over rho, rows times V rho^nu; Reading R22):
+    with Phi_i the mass flux leaving cell i and G_i = ... + Phi_i / (V rho_i),
+      V rho_i dG_i/dp_j - (lagged row) = dPhi_i/dp_j|_(through rho_f)
+                                         - delta_ij Phi_i rho'_i / rho_i.
+    On a face (a, b) with q = T rho_f (p_a - p_b) and rho_f = (rho_a + rho_b)/2,
+    q changes with p_a through rho_f by T rho'_a (p_a - p_b) / 2 (and alike
+    for p_b); row a carries +q and row b carries -q.  The Dirichlet faces'
+    density is fixed by the boundary value, so they add nothing there."""
+    fl, fc = pb.fluid, pb.faces
+    N = pb.grid.N
+    dr = fl.drho(p)
+    s = 0.5 * fc.T * (p[fc.lo] - p[fc.hi])
+    phi_rho = _flux_sum(pb, rho, p) * dr / rho
+    rows = np.concatenate([fc.lo, fc.lo, fc.hi, fc.hi, np.arange(N)])
+    cols = np.concatenate([fc.lo, fc.hi, fc.lo, fc.hi, np.arange(N)])
+    vals = np.concatenate([s * dr[fc.lo], s * dr[fc.hi], -s * dr[fc.lo], -s * dr[fc.hi], -phi_rho])
+    X = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    X.sum_duplicates()
+    X.sort_indices()
+    return X
+
+
+def assemble(pb: Problem, p, p_n, dt, full_jacobian=False) -> Linearised:
     """Linear-system population (Table 1, step 1).
 
     Eq. 3 multiplied by V rho^nu gives, for the unknown p^{nu+1},
@@ -267,6 +296,8 @@ def assemble(pb: Problem, p, p_n, dt) -> Linearised:
     with b from Eq. 5.  Hence A = C + A~ with C = diag(V rho c) and
     A~ the rho_f-weighted TPFA matrix including the Dirichlet faces, and
     f = V rho b + sum_b T_b rho_b p_b + C p^nu.
+    full_jacobian adds the flux-density derivative terms of Reading R22
+    (A is then not symmetric).
     """
     g, fl, fc = pb.grid, pb.fluid, pb.faces
     N, V = g.N, g.V
@@ -293,6 +324,14 @@ def assemble(pb: Problem, p, p_n, dt) -> Linearised:
     A.sum_duplicates()
     A.sort_indices()
     f = V * rho * b + rhs_b + Cdiag * p
+    if full_jacobian:
+        # Reading R22: A p^{nu+1} = f still means A dp = -F(p^nu), so the
+        # added derivative terms X enter f as X p^nu.
+        X = flux_density_terms(pb, p, rho)
+        A = (A + X).tocsr()
+        A.sum_duplicates()
+        A.sort_indices()
+        f = f + X @ p
     if pb.has_fixed:
         # Reading R19: with p_F known, row j of A p = f reads
         # sum_{k free} a_jk p_k = f_j - sum_{k fixed} a_jk p_k

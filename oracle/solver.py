@@ -56,6 +56,7 @@ class Options:
     max_newton: int = 50
     max_cams: int = 200
     cf: bool = False       # correction functions as the pre-smoother (Table 1 step 4, Reading R21)
+    full_jacobian: bool = False   # Newton with the flux density differentiated (Reading R22)
 
 
 class BasisState:
@@ -159,7 +160,7 @@ def solve_step(pb: Problem, wb: Wirebasket, state: BasisState, opt: Options,
     st = StepStats()
     eps0 = None
     for nu in range(opt.max_newton + 1):
-        lin = assemble(pb, p, p_n, dt)
+        lin = assemble(pb, p, p_n, dt, opt.full_jacobian)
         en = float(np.linalg.norm(lin.eps))
         st.eps_hist.append(en)
         if eps0 is None:

@@ -803,3 +803,96 @@ def test_correction_function_is_local_and_keeps_the_fixed_point(rng):
         assert st[0].converged
         out.append(p)
     np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-8)
+
+
+# ---------------------------------------------- full-Jacobian Newton (R22) --
+
+@pytest.mark.parametrize("law,c", [(0, 0.8), (1, 0.5)])
+def test_full_jacobian_matches_finite_differences(rng, law, c):
+    """Reading R22: the full-Jacobian matrix is V rho_i^nu times the
+    derivative of the paper's equation in volume units (the mass residual
+    over V rho), here taken by central differences of the residual function
+    (heterogeneous, Dirichlet faces, wells, uneven pressure).  The lagged
+    matrix of Eq. 3 misses it by far more than the difference error.  At rest
+    (no-flow, uniform pressure) and for an incompressible fluid both agree."""
+    g = _grid(5, 4, 3)
+    k = _lognormal(g.N, rng, 1.0)
+    src = (np.array([3, g.N - 2]), np.array([0.3, -0.2]))
+    pb = _problem(g, k, law=law, c=c, src=src)
+    p = rng.uniform(0.0, 1.0, g.N)
+    pn = rng.uniform(0.0, 1.0, g.N)
+    dt = 0.05
+    G = lambda q: residual(pb, q, pn, dt) / (g.V * pb.fluid.rho(q))
+    h = 1e-6
+    J = np.zeros((g.N, g.N))
+    for j in range(g.N):
+        e = np.zeros(g.N); e[j] = h
+        J[:, j] = (G(p + e) - G(p - e)) / (2 * h)
+    J *= (g.V * pb.fluid.rho(p))[:, None]
+    full = assemble(pb, p, pn, dt, full_jacobian=True).A.toarray()
+    lag = assemble(pb, p, pn, dt).A.toarray()
+    scale = np.abs(J).max()
+    np.testing.assert_allclose(full, J, rtol=0, atol=1e-7 * scale)
+    assert np.abs(lag - J).max() > 1e-3 * scale
+    # at rest the flux and its density derivative vanish
+    pbr = _problem(g, k, law=law, c=c, dirichlet=False)
+    u = np.full(g.N, 0.7)
+    np.testing.assert_array_equal(assemble(pbr, u, pn, dt, True).A.toarray(),
+                                  assemble(pbr, u, pn, dt).A.toarray())
+    pbi = _problem(g, k, law=1, c=0.0, src=src)
+    np.testing.assert_array_equal(assemble(pbi, p, pn, dt, True).A.toarray(),
+                                  assemble(pbi, p, pn, dt).A.toarray())
+
+
+def _newton_norms(pb, pn, dt, full):
+    """||F|| / ||F_0|| along Newton steps with exact linear solves."""
+    p = pn.copy()
+    hist = []
+    for _ in range(40):
+        hist.append(float(np.linalg.norm(residual(pb, p, pn, dt))))
+        if hist[-1] < 1e-13 * hist[0]:
+            break
+        lin = assemble(pb, p, pn, dt, full)
+        p = spl.spsolve(lin.A.tocsc(), lin.f)
+    return np.array(hist) / hist[0], p
+
+
+@pytest.mark.parametrize("law,c", [(0, 2.0), (1, 0.8)])
+def test_full_jacobian_newton_is_quadratic(rng, law, c):
+    """Reading R22: with exact linear solves the full-Jacobian step converges
+    at order 2 (the last error-reduction exponents log(e_{k+1}/e_k) /
+    log(e_k/e_{k-1}) near 2), while the lagged step of Eq. 3 converges at
+    order 1; both reach the same root."""
+    g = _grid(8, 6, 1)
+    k = _lognormal(g.N, rng, 1.0)
+    pb = _problem(g, k, law=law, c=c)
+    pn = np.zeros(g.N)
+    order = lambda e: np.log(e[2:] / e[1:-1]) / np.log(e[1:-1] / e[:-2])
+    ef, pf = _newton_norms(pb, pn, 1.0, True)
+    el, pl = _newton_norms(pb, pn, 1.0, False)
+    tail = ef[ef > 1e-12]
+    assert 1.8 < order(tail)[-1] < 2.3
+    assert np.median(order(el[el > 1e-12])[-4:]) < 1.2
+    assert ef.size < el.size
+    np.testing.assert_allclose(pf, pl, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("restriction", [0, 1])
+def test_full_jacobian_cams_step_reaches_the_same_root(rng, restriction):
+    """The C-AMS solve of a full-Jacobian (nonsymmetric) linearisation, with
+    a fixed cell and a well, converges to the pressure the lagged step finds,
+    in no more Newton steps."""
+    g = _grid(12, 10, 1)
+    k = _lognormal(g.N, rng, 1.5)
+    bc = BC(True, 1.0, 0.0, np.array([25]), np.array([0.05]), np.array([62]), np.array([0.4]))
+    pb = Problem.build(g, Fluid(0, 1.5, 1.0, 1.0, 0.1), bc, *k)
+    out = []
+    for full in (False, True):
+        opt = Options(coarse=(4, 5, 1), basis=1, restriction=restriction, n_post=2,
+                      nl_tol=1e-11, full_jacobian=full, max_newton=60)
+        p, st = run(pb, opt, np.zeros(g.N), 0.2, 1)
+        assert st[0].converged
+        out.append((p, st[0].newton_its))
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=0, atol=1e-9)
+    assert out[1][1] <= out[0][1]
+    assert out[1][0][62] == 0.4
