@@ -125,6 +125,11 @@ typedef struct {
                           residual r = f - A p, the update p += delta and the coarse
                           factorisation and solve stay FP64.  Converges to the same fixed
                           point (the FP64 residual decides the stopping tests). */
+  int cf;              /* 1: correction functions (Sec. 3; Table 1 step 4) open every C-AMS
+                          iteration: p += Psi, Psi solving the basis stages' local problems
+                          with the residual f - A p as the source (zero on the vertices),
+                          before any ILU(0) pre-smoothing.  Costs one set of local solves per
+                          iteration (the paper leaves them out, Sec. 4.1.4).  0: off. */
 } cams_options;
 
 #define CAMS_PREC_FP64  0

@@ -64,7 +64,7 @@ class cams_options(C.Structure):
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("lin_rtol", C.c_double),
                 ("nl_tol", C.c_double), ("tol_abs", C.c_int), ("adapt_theta", C.c_double),
                 ("max_newton", C.c_int), ("max_cams", C.c_int), ("memspace", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("cf", C.c_int)]
 
 
 class cams_stats(C.Structure):
@@ -161,7 +161,7 @@ def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None
 
 def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1,
                  nl_tol=1e-6, tol_abs=False, adapt_theta=0.1, max_newton=50, max_cams=200,
-                 memspace=CAMS_HOST, precision=CAMS_PREC_FP64):
+                 memspace=CAMS_HOST, precision=CAMS_PREC_FP64, cf=False):
     o = cams_options()
     o.coarse[:] = [int(v) for v in coarse]
     o.basis, o.restriction, o.n_pre, o.n_post = int(basis), int(restriction), int(n_pre), int(n_post)
@@ -169,6 +169,7 @@ def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1
     o.adapt_theta, o.max_newton, o.max_cams = float(adapt_theta), int(max_newton), int(max_cams)
     o.memspace = int(memspace)
     o.precision = int(precision)
+    o.cf = int(bool(cf))
     return o
 
 

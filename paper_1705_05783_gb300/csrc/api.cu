@@ -310,6 +310,12 @@ int alloc_all(cams_handle* h) {
   }
   AL(b.ctrl, ilu_ctrl_ints(h->g));
   AL(b.r, N);
+  if (h->opt.cf && !h->single) {
+    AL(b.cf, N);
+    // vertex cells are in no entity: their correction value stays zero
+    if (cudaMemset(b.cf, 0, sizeof(double) * (size_t)N) != cudaSuccess)
+      return fail(h, CAMS_ECUDA, "cudaMemset failed");
+  }
   AL(b.red, kRedBlocks);
   AL(b.scal, 8);
   AL(b.status, 1);
@@ -324,7 +330,7 @@ void free_all(cams_handle* h) {
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
-                  b.fixc, b.fixv};
+                  b.fixc, b.fixv, b.cf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   const SingleBuffers& f = b.f32;
@@ -358,6 +364,7 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
   if (o->memspace != CAMS_HOST && o->memspace != CAMS_DEVICE) return fail(nullptr, CAMS_EINVAL, "bad memspace");
   if (o->precision != CAMS_PREC_FP64 && o->precision != CAMS_PREC_MIXED)
     return fail(nullptr, CAMS_EINVAL, "precision must be CAMS_PREC_FP64 or CAMS_PREC_MIXED");
+  if (o->cf != 0 && o->cf != 1) return fail(nullptr, CAMS_EINVAL, "cf must be 0 or 1");
   if ((long long)gr->nx * gr->ny * gr->nz > (1LL << 31) - 1) return fail(nullptr, CAMS_EINVAL, "grid too large");
   return CAMS_OK;
 }
@@ -647,11 +654,22 @@ int ilu_smooth(cams_handle* h) {
 // p += delta; f - A(p + delta) = r - A delta, so this is the FP64
 // iteration with the preconditioner rounded to FP32.  Pre-smoothing steps
 // are applied the same way and added to p before the coarse correction.
+// With options.cf the pre-smoothing stage starts with the correction
+// functions of r (Table 1 step 4): p += Psi, level by level.
 int cams_step_direct(cams_handle* h) {
   Buffers& b = h->b;
   const bool s = h->single;
-  if (h->opt.n_pre > 0) {
+  if (h->opt.n_pre > 0 || h->opt.cf) {
     if (s) CK(cudaMemsetAsync(b.f32.d, 0, sizeof(float) * h->g.N, h->stream));
+    if (h->opt.cf) {
+      ProfScope ps_(h, CAMS_PROF_BASIS);         // the same local solves as the basis stages
+      for (int lev = 1; lev <= 3; ++lev) {
+        const int f = h->lev_first[lev];
+        CK(launch_entity_cf(h->g, b.ents + f, h->lev_count[lev], h->lev_smem[lev],
+                            h->lev_grid[lev], h->lev_lstride[lev], s, h->lev_blocked[lev], b,
+                            h->stream));
+      }
+    }
     for (int k = 0; k < h->opt.n_pre; ++k) {
       int rc = ilu_smooth(h);
       if (rc) return rc;

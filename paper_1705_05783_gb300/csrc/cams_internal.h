@@ -121,6 +121,7 @@ struct Buffers {
   double *rds = nullptr, *w = nullptr, *z = nullptr;      // D^{-1} r, forward / backward sweeps
   int* ctrl = nullptr;                                    // wavefront tickets, abort flag
   double* r = nullptr;                                    // residual (natural order)
+  double* cf = nullptr;                                   // correction function Psi (N; FP64 with options.cf)
   double* red = nullptr;                                  // reduction partials
   double* scal = nullptr;                                 // reduced scalars (device)
   int* status = nullptr;                                  // device status word
@@ -181,6 +182,9 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
                                 int count, int smem, int grid, long long lstride, int adaptive,
                                 bool single, bool blocked, Buffers& b, cudaStream_t s);
 int entity_smem_bytes(const Entity& E, bool single, bool blocked);
+cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int smem, int grid,
+                             long long lstride, bool single, bool blocked, Buffers& b,
+                             cudaStream_t s);
 cudaError_t set_entity_smem(int smem);
 cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                cudaStream_t s);

@@ -13,6 +13,12 @@
 // backward substitution.  No atomics, so the result is deterministic.  The
 // local solve and P are FP64, or FP32 for the mixed-precision preconditioner
 // (the basis operator is read in FP64 and rounded).
+//
+// The same kernels in their kCF form apply the correction functions of
+// Table 1 step 4 (Sec. 3): the same local systems with one right-hand side,
+// the fine residual r minus the couplings to the correction values Psi
+// already found on the lower levels (zero on the vertices), launched level
+// by level like the basis stages.
 #include "cams_internal.h"
 
 namespace cams {
@@ -65,15 +71,22 @@ __device__ __forceinline__ int local_stride(const Entity& E, int d) {
   return d == E.ord[0] ? 1 : (d == E.ord[1] ? L0 : L0 * L1);
 }
 
-// Build row l of M (lower band, ring slot) and the right-hand sides of row l.
-template <class T>
+// Build row l of M (lower band, ring slot) and the right-hand sides of row l:
+// one per corner vertex for the basis functions, or (kCF) the single
+// correction-function right-hand side r_i - sum over lower neighbours j of
+// a_ij Psi_j.
+template <class T, bool kCF>
 __device__ void build_row(const Geo& g, const Entity& E, int l, T* Wrow, T* Yrow,
                           const double* Abd, const double* Abx, const double* Aby,
-                          const double* Abz, const T* P) {
+                          const double* Abz, const T* P, const double* rin, const T* psi) {
   Local c = local_cell(E, l);
   const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
   for (int dd = 0; dd <= E.m; ++dd) Wrow[dd] = T(0);
-  for (int r = 0; r < E.nrhs; ++r) Yrow[r] = T(0);
+  if constexpr (kCF) {
+    Yrow[0] = T(rin[i]);
+  } else {
+    for (int r = 0; r < E.nrhs; ++r) Yrow[r] = T(0);
+  }
   double diag = Abd[i];
   for (int d = 0; d < 3; ++d) {
     const int n_d = gextent(g, d);
@@ -92,18 +105,26 @@ __device__ void build_row(const Geo& g, const Entity& E, int l, T* Wrow, T* Yrow
       Wrow[local_stride(E, d)] = T(lo);
     } else if (c.c[d] > 0) {
       const long long j = i - sd;
-      for (int r = 0; r < E.nrhs; ++r) {
-        const int s = slot_of(r, E.free_mask);
-        if (!(s & (1 << d))) Yrow[r] -= T(lo) * P[(long long)s * g.N + j];
+      if constexpr (kCF) {
+        Yrow[0] -= T(lo) * psi[j];
+      } else {
+        for (int r = 0; r < E.nrhs; ++r) {
+          const int s = slot_of(r, E.free_mask);
+          if (!(s & (1 << d))) Yrow[r] -= T(lo) * P[(long long)s * g.N + j];
+        }
       }
     }
     if (c.c[d] < E.org[d] + E.L[d] - 1) {
       // upper in-box neighbour: its entry is stored in the neighbour's row
     } else if (c.c[d] < n_d - 1) {
       const long long j = i + sd;
-      for (int r = 0; r < E.nrhs; ++r) {
-        const int s = slot_of(r, E.free_mask);
-        if (s & (1 << d)) Yrow[r] -= T(up) * P[(long long)(s & ~(1 << d)) * g.N + j];
+      if constexpr (kCF) {
+        Yrow[0] -= T(up) * psi[j];
+      } else {
+        for (int r = 0; r < E.nrhs; ++r) {
+          const int s = slot_of(r, E.free_mask);
+          if (s & (1 << d)) Yrow[r] -= T(up) * P[(long long)(s & ~(1 << d)) * g.N + j];
+        }
       }
     }
   }
@@ -120,12 +141,13 @@ __global__ void k_vertices(Geo g, CGeo c, T* P) {
   for (int s = 0; s < 8; ++s) P[(long long)s * g.N + v] = (s == 0) ? T(1) : T(0);
 }
 
-template <class T>
+template <class T, bool kCF>
 __global__ void __launch_bounds__(256) k_entity_solve(
     Geo g, const Entity* __restrict__ ents, int count, const unsigned char* __restrict__ flag,
     int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
     const double* __restrict__ Aby, const double* __restrict__ Abz, T* P, double* snap,
-    T* lscratch, long long lstride, int* status) {
+    T* lscratch, long long lstride, int* status, const double* __restrict__ rin, T* psi,
+    double* padd) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -133,7 +155,7 @@ __global__ void __launch_bounds__(256) k_entity_solve(
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     if (flag && !flag[e]) continue;
     const Entity E = ents[e];
-    const int n = E.n, m = E.m, nr = E.nrhs, mp = m + 1;
+    const int n = E.n, m = E.m, nr = kCF ? 1 : E.nrhs, mp = m + 1;
     T* W = sm;                      // mp * mp ring
     T* Y = W + mp * mp;             // n * nr
     T* lcol = Y + n * nr;           // mp
@@ -142,7 +164,7 @@ __global__ void __launch_bounds__(256) k_entity_solve(
     // the scratch slice (row l at l*mp) until they enter the ring
     for (int l = tid; l < n; l += nt) {
       T* row = (l <= m) ? W + l * mp : Lg + (long long)l * mp;
-      build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
+      build_row<T, kCF>(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P, rin, psi);
     }
     __syncthreads();
     // banded LDL^T with forward elimination of the right-hand sides.  The
@@ -217,10 +239,16 @@ __global__ void __launch_bounds__(256) k_entity_solve(
       }
       __syncthreads();
     }
-    // write the basis values (slots on lattice bits stay zero)
+    // write the basis values (slots on lattice bits stay zero), or the
+    // correction values (and p += Psi when padd is given)
     for (int l = tid; l < n; l += nt) {
       Local c = local_cell(E, l);
       const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      if constexpr (kCF) {
+        psi[i] = Y[l];
+        if (padd) padd[i] += (double)Y[l];
+        continue;
+      }
       for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = T(0);
       for (int r = 0; r < nr; ++r) P[(long long)slot_of(r, E.free_mask) * g.N + i] = Y[l * nr + r];
       if (adaptive) {
@@ -251,12 +279,13 @@ constexpr int kLPS = kKB + 1;   // panel row stride (odd: no shared-memory bank 
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
-template <class T>
+template <class T, bool kCF>
 __global__ void __launch_bounds__(256) k_entity_solve_blk(
     Geo g, const Entity* __restrict__ ents, int count, const unsigned char* __restrict__ flag,
     int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
     const double* __restrict__ Aby, const double* __restrict__ Abz, T* P, double* snap,
-    T* lscratch, long long lstride, int* status) {
+    T* lscratch, long long lstride, int* status, const double* __restrict__ rin, T* psi,
+    double* padd) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sm = reinterpret_cast<T*>(sm_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -265,7 +294,7 @@ __global__ void __launch_bounds__(256) k_entity_solve_blk(
   for (int e = blockIdx.x; e < count; e += gridDim.x) {
     if (flag && !flag[e]) continue;
     const Entity E = ents[e];
-    const int n = E.n, m = E.m, nr = E.nrhs, mp = m + 1, R = m + kKB;
+    const int n = E.n, m = E.m, nr = kCF ? 1 : E.nrhs, mp = m + 1, R = m + kKB;
     const int lnr = __ffs(nr) - 1;                 // nr is a power of two
     T* W = sm;                                     // ring: row i in slot i % R, entry (i, i-dd) at dd
     T* Y = W + round4(R * mp);                     // n x nr right-hand sides
@@ -273,7 +302,7 @@ __global__ void __launch_bounds__(256) k_entity_solve_blk(
     T* Ls = W;                                     // backward sweep: kKB staged rows of L
     for (int l = tid; l < n; l += nt) {
       T* row = (l < R) ? W + l * mp : Lg + (long long)l * mp;
-      build_row(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P);
+      build_row<T, kCF>(g, E, l, row, Y + l * nr, Abd, Abx, Aby, Abz, P, rin, psi);
     }
     __syncthreads();
     for (int k = 0; k < n; k += kKB) {
@@ -450,10 +479,16 @@ __global__ void __launch_bounds__(256) k_entity_solve_blk(
       }
       __syncthreads();
     }
-    // write the basis values (slots on lattice bits stay zero)
+    // write the basis values (slots on lattice bits stay zero), or the
+    // correction values (and p += Psi when padd is given)
     for (int l = tid; l < n; l += nt) {
       Local c = local_cell(E, l);
       const long long i = c.c[0] + g.sy * c.c[1] + g.sz * c.c[2];
+      if constexpr (kCF) {
+        psi[i] = Y[l];
+        if (padd) padd[i] += (double)Y[l];
+        continue;
+      }
       for (int s = 0; s < 8; ++s) P[(long long)s * g.N + i] = T(0);
       for (int r = 0; r < nr; ++r) P[(long long)slot_of(r, E.free_mask) * g.N + i] = Y[l * nr + r];
       if (adaptive) {
@@ -578,32 +613,68 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
   if (single) {
     float* ls = reinterpret_cast<float*>(b.lscratch);
     if (blocked)
-      k_entity_solve_blk<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd,
-                                                        b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls,
-                                                        lstride, b.status);
+      k_entity_solve_blk<float, false><<<grid, 256, smem, s>>>(
+          g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
+          b.status, nullptr, nullptr, nullptr);
     else
-      k_entity_solve<float><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
-                                                    b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
-                                                    b.status);
+      k_entity_solve<float, false><<<grid, 256, smem, s>>>(
+          g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
+          b.status, nullptr, nullptr, nullptr);
   } else {
     if (blocked)
-      k_entity_solve_blk<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd,
-                                                         b.Abx, b.Aby, b.Abz, b.P, b.snap,
-                                                         b.lscratch, lstride, b.status);
+      k_entity_solve_blk<double, false><<<grid, 256, smem, s>>>(
+          g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.P, b.snap, b.lscratch,
+          lstride, b.status, nullptr, nullptr, nullptr);
     else
-      k_entity_solve<double><<<grid, 256, smem, s>>>(g, ents, count, flag, adaptive, b.Abd, b.Abx,
-                                                     b.Aby, b.Abz, b.P, b.snap, b.lscratch, lstride,
-                                                     b.status);
+      k_entity_solve<double, false><<<grid, 256, smem, s>>>(
+          g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.P, b.snap, b.lscratch,
+          lstride, b.status, nullptr, nullptr, nullptr);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Correction functions of one level's entities from the residual b.r: in
+// FP64 into b.cf with p += Psi; in mixed precision into the FP32 correction
+// b.f32.d (which the caller zeroed: its vertex values are Psi's).
+cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int smem, int grid,
+                             long long lstride, bool single, bool blocked, Buffers& b,
+                             cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (grid > count) grid = count;
+  if (single) {
+    float* ls = reinterpret_cast<float*>(b.lscratch);
+    if (blocked)
+      k_entity_solve_blk<float, true><<<grid, 256, smem, s>>>(
+          g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, nullptr, ls, lstride,
+          b.status, b.r, b.f32.d, nullptr);
+    else
+      k_entity_solve<float, true><<<grid, 256, smem, s>>>(
+          g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, nullptr, ls, lstride,
+          b.status, b.r, b.f32.d, nullptr);
+  } else {
+    if (blocked)
+      k_entity_solve_blk<double, true><<<grid, 256, smem, s>>>(
+          g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.P, nullptr, b.lscratch,
+          lstride, b.status, b.r, b.cf, b.p);
+    else
+      k_entity_solve<double, true><<<grid, 256, smem, s>>>(
+          g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.P, nullptr, b.lscratch,
+          lstride, b.status, b.r, b.cf, b.p);
   }
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t set_entity_smem(int smem) {
-  cudaError_t e = raise_smem_limit(k_entity_solve<double>, smem);
-  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve<float>, smem);
-  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<double>, smem);
-  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<float>, smem);
+  cudaError_t e = raise_smem_limit(k_entity_solve<double, false>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve<float, false>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<double, false>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<float, false>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve<double, true>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve<float, true>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<double, true>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(k_entity_solve_blk<float, true>, smem);
   return e;
 }
 

@@ -40,7 +40,9 @@ def make_case(name=None, w=None, seed=0, **overrides):
     return Case(w, inp, pb, opt)
 
 
-def gpu_handle(case: Case, memspace=0):
+def gpu_handle(case: Case, memspace=0, **extra):
+    """A library handle for the case; extra options (e.g. cf=True) go to
+    make_options."""
     from paper_1705_05783_gb300 import cams
     w, inp = case.w, case.inp
     grid = cams.cams_grid(w.nx, w.ny, w.nz, inp["dx"], inp["dy"], inp["dz"])
@@ -48,7 +50,8 @@ def gpu_handle(case: Case, memspace=0):
     opt = cams.make_options(w.coarse, basis=w.basis, restriction=w.restriction, n_pre=w.n_pre,
                             n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
                             adapt_theta=w.adapt_theta, max_newton=w.max_newton,
-                            max_cams=w.max_cams, memspace=memspace, precision=w.precision)
+                            max_cams=w.max_cams, memspace=memspace, precision=w.precision,
+                            **extra)
     h = cams.cams_setup(grid, fluid, opt, inp["kx"], inp["ky"], inp["kz"])
     bc, keep = cams.make_bc(inp["dirichlet"], w.p_west, w.p_east,
                             inp["src_cell"] if len(inp["src_cell"]) else None,

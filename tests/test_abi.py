@@ -78,6 +78,12 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
         cams.cams_setup(g, f, o, k)
     assert e.value.code == cams.CAMS_EINVAL
     assert "basis" in cams.cams_last_error()
+    o = cams.make_options((5, 5, 1))
+    o.cf = 2
+    with pytest.raises(cams.CamsError) as e:
+        cams.cams_setup(g, f, o, k)
+    assert e.value.code == cams.CAMS_EINVAL
+    assert "cf" in cams.cams_last_error()
 
 
 def test_ensemble_and_network_entry_points_reject_bad_arguments_without_a_gpu():

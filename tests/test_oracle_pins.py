@@ -896,3 +896,37 @@ def test_full_jacobian_cams_step_reaches_the_same_root(rng, restriction):
     np.testing.assert_allclose(out[1][0], out[0][0], rtol=0, atol=1e-9)
     assert out[1][1] <= out[0][1]
     assert out[1][0][62] == 0.4
+
+
+def test_correction_functions_destabilise_large_3d_blocks(rng):
+    """Sec. 4.1.4 finds the iteration with correction functions unstable.
+    A mechanism: for an error e that is smooth along a face patch of b x b
+    cells (unit couplings w), A e ~ (2 pi^2 w / b^2 + 2 w) e, the in-face
+    Laplacian plus the two transverse couplings, while the face's lumped
+    operator keeps the in-face part only; Psi then overshoots e by about
+    b^2 / pi^2.  With blocks of 10^3 cells (~10) the iteration with one
+    ILU(0) step diverges even on a homogeneous field and converges without
+    correction functions; with 2^3 blocks both converge."""
+    from oracle.basis import correction_function
+    out = {}
+    for n, b in ((20, 10), (8, 2)):
+        g = _grid(n, n, n)
+        one = np.ones(g.N)
+        pb = _problem(g, (one, one, one), c=0.1)
+        p_nu = rng.uniform(0, 1, g.N)
+        lin = assemble(pb, p_nu, np.zeros(g.N), 0.01)
+        wb = build_wirebasket(g, (b, b, b))
+        Ab = basis_operator(pb, 4, lin.rho, lin.c, np.zeros(g.N), 0.01)
+        P = prolongation(Ab, wb).to_csr(wb.Nc)
+        R = restriction(0, P, wb)
+        lu = coarse_factor(coarse_operator(R, lin.A, P))
+        LU = ilu0(lin.A)
+        for cf in (False, True):
+            p = np.zeros(g.N)
+            r0 = np.linalg.norm(lin.f)
+            for _ in range(6):
+                p = cams_iteration(lin.A, lin.f, p, P, R, lu, LU, 0, 1,
+                                   (lambda r: correction_function(Ab, wb, r)) if cf else None)
+            out[(b, cf)] = np.linalg.norm(lin.f - lin.A @ p) / r0
+    assert out[(10, False)] < 0.1 and out[(10, True)] > 10.0
+    assert out[(2, False)] < 0.1 and out[(2, True)] < 0.1
