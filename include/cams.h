@@ -130,6 +130,11 @@ typedef struct {
                           with the residual f - A p as the source (zero on the vertices),
                           before any ILU(0) pre-smoothing.  Costs one set of local solves per
                           iteration (the paper leaves them out, Sec. 4.1.4).  0: off. */
+  int jacobian;        /* 0: the Newton step of Eq. 3 (flux density lagged).  1: the full
+                          Jacobian of the paper's equation (Eq. 2 over rho), the flux
+                          density and the flux term's 1/rho differentiated too, rows scaled
+                          by V rho as for Eq. 3; A is then not symmetric: the MSFE coarse
+                          matrix is factorised by band LU.  Both steps have the same root. */
 } cams_options;
 
 #define CAMS_PREC_FP64  0
@@ -149,7 +154,8 @@ typedef struct {
 
 /* Quantities readable with cams_get / cams_get_int (debug and tests). */
 #define CAMS_Q_TRANS      1  /* double 3N: Tx, Ty, Tz; T_d[i] couples i and i - stride_d (0 on the low face) */
-#define CAMS_Q_MATRIX     2  /* double 4N: diag, then the couplings a_{i,i-1}, a_{i,i-nx}, a_{i,i-nx*ny} (0 when absent); A is symmetric */
+#define CAMS_Q_MATRIX     2  /* double 4N: diag, then the couplings a_{i,i-1}, a_{i,i-nx}, a_{i,i-nx*ny} (0 when absent);
+                                with jacobian = 0 A is symmetric and these are also a_{i-1,i} ... */
 #define CAMS_Q_RHS        3  /* double N: f of Eq. 6 (rows scaled by V rho) */
 #define CAMS_Q_EPS        4  /* double N: nonlinear error of Eq. 19 at the linearisation point */
 #define CAMS_Q_PRESSURE   5  /* double N: the handle's current iterate p */
@@ -169,6 +175,9 @@ typedef struct {
 #define CAMS_Q_SURR_RATIO 14  /* double n (n = full interiors, cams_surrogate_data with 0): the
                                 surrogate's gate ratio of each full interior in the last build that
                                 used it (CAMS_EINVAL without a surrogate) */
+#define CAMS_Q_MATRIX_UPPER 15  /* double 3N: the transposed couplings a_{i-1,i}, a_{i-nx,i},
+                                a_{i-nx*ny,i} stored at cell i (0 when absent); equal to the
+                                couplings of CAMS_Q_MATRIX when jacobian = 0 */
 
 /* kernel classes of CAMS_Q_PROFILE */
 #define CAMS_PROF_ASSEMBLE      0   /* density + linear-system population (a2) */

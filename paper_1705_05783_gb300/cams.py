@@ -23,6 +23,7 @@ CAMS_PREC_FP64, CAMS_PREC_MIXED = 0, 1
 CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 4, 5
 CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
 CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES, CAMS_Q_SURR_RATIO = 11, 12, 13, 14
+CAMS_Q_MATRIX_UPPER = 15
 PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
                 "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
                 "ilu_bwd", "ilu_resid")
@@ -64,7 +65,7 @@ class cams_options(C.Structure):
                 ("n_pre", C.c_int), ("n_post", C.c_int), ("lin_rtol", C.c_double),
                 ("nl_tol", C.c_double), ("tol_abs", C.c_int), ("adapt_theta", C.c_double),
                 ("max_newton", C.c_int), ("max_cams", C.c_int), ("memspace", C.c_int),
-                ("precision", C.c_int), ("cf", C.c_int)]
+                ("precision", C.c_int), ("cf", C.c_int), ("jacobian", C.c_int)]
 
 
 class cams_stats(C.Structure):
@@ -161,7 +162,7 @@ def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None
 
 def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1,
                  nl_tol=1e-6, tol_abs=False, adapt_theta=0.1, max_newton=50, max_cams=200,
-                 memspace=CAMS_HOST, precision=CAMS_PREC_FP64, cf=False):
+                 memspace=CAMS_HOST, precision=CAMS_PREC_FP64, cf=False, jacobian=0):
     o = cams_options()
     o.coarse[:] = [int(v) for v in coarse]
     o.basis, o.restriction, o.n_pre, o.n_post = int(basis), int(restriction), int(n_pre), int(n_post)
@@ -170,6 +171,7 @@ def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1
     o.memspace = int(memspace)
     o.precision = int(precision)
     o.cf = int(bool(cf))
+    o.jacobian = int(jacobian)
     return o
 
 

@@ -271,6 +271,13 @@ int alloc_all(cams_handle* h) {
   AL(b.Tbw, (long long)h->g.ny * h->g.nz); AL(b.Tbe, (long long)h->g.ny * h->g.nz);
   AL(b.p, N); AL(b.pn, N); AL(b.rho, N); AL(b.rhon, N);
   AL(b.Ad, N); AL(b.Ax, N); AL(b.Ay, N); AL(b.Az, N); AL(b.Cacc, N);
+  if (h->opt.jacobian) {
+    // A is not symmetric: its transposed couplings and the pivot products
+    AL(b.Axu, N); AL(b.Ayu, N); AL(b.Azu, N);
+    if (!h->single) { AL(b.Qx, N); AL(b.Qy, N); AL(b.Qz, N); }
+  } else {
+    b.Axu = b.Ax; b.Ayu = b.Ay; b.Azu = b.Az;
+  }
   AL(b.f, N); AL(b.eps, N);
   AL(b.Abd, N); AL(b.Abx, N); AL(b.Aby, N); AL(b.Abz, N);
   if (h->opt.basis != 4) AL(b.snap, 7 * N);
@@ -279,6 +286,11 @@ int alloc_all(cams_handle* h) {
     SingleBuffers& f = b.f32;
     const long long S = ilu_skew_len(h->g);
     AL(f.Ad, N); AL(f.Ax, N); AL(f.Ay, N); AL(f.Az, N); AL(f.dinv, N); AL(f.d, N);
+    if (h->opt.jacobian) {
+      AL(f.Axu, N); AL(f.Ayu, N); AL(f.Azu, N); AL(f.Qx, N); AL(f.Qy, N); AL(f.Qz, N);
+    } else {
+      f.Axu = f.Ax; f.Ayu = f.Ay; f.Azu = f.Az;
+    }
     AL(f.P, 8 * N); AL(f.pc, h->c.Nc);
     AL(f.Lx, S); AL(f.Ly, S); AL(f.Lz, S); AL(f.Ux, S); AL(f.Uy, S); AL(f.Uz, S);
     AL(f.rds, S); AL(f.w, S); AL(f.z, S);
@@ -330,12 +342,17 @@ void free_all(cams_handle* h) {
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
-                  b.fixc, b.fixv, b.cf};
+                  b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz,
+                  // the transposed couplings are separate arrays only for a nonsymmetric A
+                  b.Axu != b.Ax ? b.Axu : nullptr, b.Ayu != b.Ay ? b.Ayu : nullptr,
+                  b.Azu != b.Az ? b.Azu : nullptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   const SingleBuffers& f = b.f32;
   void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
-                   f.rds, f.w, f.z, f.d, f.P, f.pc};
+                   f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz,
+                   f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
+                   f.Azu != f.Az ? f.Azu : nullptr};
   for (void* p : fptrs)
     if (p) cudaFree(p);
   h->b = Buffers{};
@@ -365,6 +382,7 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
   if (o->precision != CAMS_PREC_FP64 && o->precision != CAMS_PREC_MIXED)
     return fail(nullptr, CAMS_EINVAL, "precision must be CAMS_PREC_FP64 or CAMS_PREC_MIXED");
   if (o->cf != 0 && o->cf != 1) return fail(nullptr, CAMS_EINVAL, "cf must be 0 or 1");
+  if (o->jacobian != 0 && o->jacobian != 1) return fail(nullptr, CAMS_EINVAL, "jacobian must be 0 or 1");
   if ((long long)gr->nx * gr->ny * gr->nz > (1LL << 31) - 1) return fail(nullptr, CAMS_EINVAL, "grid too large");
   return CAMS_OK;
 }
@@ -549,7 +567,8 @@ int assemble(cams_handle* h, double* eps_norm) {
     ProfScope ps_(h, CAMS_PROF_ASSEMBLE);
     cudaError_t e = launch_density(h->g, h->fl, b.p, b.rho, h->stream);
     if (e == cudaSuccess) e = launch_assemble(h->g, h->fl, h->dt, h->dirichlet, h->pw, h->pe,
-                                                   h->have_fix ? b.fixm : nullptr, b, h->stream);
+                                                   h->have_fix ? b.fixm : nullptr,
+                                                   h->opt.jacobian != 0, b, h->stream);
     b.src = src_saved;
     CK(e);
   }
@@ -611,17 +630,20 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   if (n_rebuilt) *n_rebuilt = rebuilt;
   // Galerkin coarse operator and its factorisation
   // restriction 2 iterates with MSFE (its MSFV correction closes the step)
+  const bool nonsym = o.jacobian != 0;
   if (o.restriction != 1)
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->single, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->single, nonsym, b, h->stream));
   else
-    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, b, h->stream));
+    LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, nonsym, b, h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
-    const int sym = o.restriction != 1;   // MSFE: R A P = P^T A P is symmetric
+    // MSFE with a symmetric A: R A P = P^T A P is symmetric (LDL^T), else band LU
+    const int sym = o.restriction != 1 && !nonsym;
     CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
     CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
   }
-  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, h->single, h->stream));
+  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta,
+                                                  h->single, nonsym, h->stream));
   return check_status(h);
 }
 
@@ -679,7 +701,7 @@ int cams_step_direct(cams_handle* h) {
   }
   const int fv = h->opt.restriction == 1;
   LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, fv, b.r, s, b, h->stream));
-  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv,
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv && !h->opt.jacobian,
                                                    h->coarse_cluster, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, s, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
@@ -1007,7 +1029,8 @@ int cams_update_basis(cams_handle* h, int force, int* n_rebuilt_out) {
 // either precision (the mixed preconditioner's FP32 P is read and widened).
 int closing_msfv(cams_handle* h) {
   Buffers& b = h->b;
-  LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, b, h->stream));
+  LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fv(h->g, h->c, h->single, h->opt.jacobian != 0, b,
+                                                h->stream));
   {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     CK(launch_band_fill(h->c, h->mc, 0, b, h->stream));
@@ -1305,6 +1328,11 @@ int cams_get(cams_handle* h, int what, double* dst) {
       CK(cudaMemcpyAsync(dst + N, b.Ax, sizeof(double) * N, k, s));
       CK(cudaMemcpyAsync(dst + 2 * N, b.Ay, sizeof(double) * N, k, s));
       CK(cudaMemcpyAsync(dst + 3 * N, b.Az, sizeof(double) * N, k, s));
+      break;
+    case CAMS_Q_MATRIX_UPPER:
+      CK(cudaMemcpyAsync(dst, b.Axu, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + N, b.Ayu, sizeof(double) * N, k, s));
+      CK(cudaMemcpyAsync(dst + 2 * N, b.Azu, sizeof(double) * N, k, s));
       break;
     case CAMS_Q_RHS: CK(cudaMemcpyAsync(dst, b.f, sizeof(double) * N, k, s)); break;
     case CAMS_Q_EPS: CK(cudaMemcpyAsync(dst, b.eps, sizeof(double) * N, k, s)); break;

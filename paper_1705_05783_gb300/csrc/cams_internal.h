@@ -77,6 +77,8 @@ __host__ __device__ inline double rho_of(const FluidK& f, double p) {
 // when cams_options.precision is CAMS_PREC_MIXED).
 struct SingleBuffers {
   float *Ad = nullptr, *Ax = nullptr, *Ay = nullptr, *Az = nullptr;   // A in FP32
+  float *Axu = nullptr, *Ayu = nullptr, *Azu = nullptr;   // transposed couplings (alias Ax.. if symmetric)
+  float *Qx = nullptr, *Qy = nullptr, *Qz = nullptr;      // ILU(0) pivot products (nonsymmetric A)
   float* dinv = nullptr;                                  // 1 / ILU(0) pivots
   float *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;      // scaled couplings, skewed
   float *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;
@@ -93,6 +95,10 @@ struct Buffers {
   double *p = nullptr, *pn = nullptr;                     // iterate, previous time level
   double *rho = nullptr, *rhon = nullptr;
   double *Ad = nullptr, *Ax = nullptr, *Ay = nullptr, *Az = nullptr;  // A = C + A~
+  // a_{i-e_d, i} stored at the upper cell i (Ax.. hold a_{i, i-e_d}); the same
+  // arrays as Ax, Ay, Az while A is symmetric (the lagged Newton step)
+  double *Axu = nullptr, *Ayu = nullptr, *Azu = nullptr;
+  double *Qx = nullptr, *Qy = nullptr, *Qz = nullptr;     // a_{i,i-e_d} a_{i-e_d,i} (nonsymmetric A)
   double *Cacc = nullptr;                                 // V rho c (diagonal of C)
   double *f = nullptr, *eps = nullptr;
   double *src = nullptr;                                  // dense Q_i (N) or null
@@ -157,9 +163,11 @@ cudaError_t launch_transmissibility(const Geo& g, double mu, const double* kx, c
                                     const double* kz, int dirichlet, Buffers& b, cudaStream_t s);
 cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, double* rho,
                            cudaStream_t s);
-// fixm: prescribed-cell mask (N bytes) or null
+// fixm: prescribed-cell mask (N bytes) or null; full: the full-Jacobian
+// step (writes the transposed couplings b.Axu.., distinct arrays then)
 cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int dirichlet, double pw,
-                            double pe, const unsigned char* fixm, Buffers& b, cudaStream_t s);
+                            double pe, const unsigned char* fixm, bool full, Buffers& b,
+                            cudaStream_t s);
 cudaError_t launch_add_sources(int n, const int* cell, const double* rate, double* src,
                                long long N, cudaStream_t s);
 cudaError_t launch_fix_cells(int n, const int* cell, const double* val, unsigned char* fixm,
@@ -186,9 +194,10 @@ cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int sm
                              long long lstride, bool single, bool blocked, Buffers& b,
                              cudaStream_t s);
 cudaError_t set_entity_smem(int smem);
-cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
+// nonsym: A is not symmetric (the full-Jacobian step)
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, bool nonsym, Buffers& b,
                                cudaStream_t s);
-cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, Buffers& b,
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, bool nonsym, Buffers& b,
                                cudaStream_t s);
 cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
@@ -207,8 +216,9 @@ cudaError_t launch_prolong_to_p(const Geo& g, const CGeo& c, bool single, Buffer
 // A delta = r, vectors in b.f32); otherwise the FP64 smoother on A p = f.
 // sms: the SM count (from ilu_pipe_grid); cta: tiles in 2 x 2 blocks per CTA
 // with shared-memory edges (ilu_cta_ok), else one tile per warp.
+// nonsym: pivots from the products a_{i,i-e} a_{i-e,i} (b.Qx.., formed here)
 cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
-                              bool single, cudaStream_t s);
+                              bool single, bool nonsym, cudaStream_t s);
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s);
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int sms,
                              bool cta, bool single, cudaStream_t s);

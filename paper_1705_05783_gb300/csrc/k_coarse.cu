@@ -69,15 +69,20 @@ __device__ __forceinline__ int sym_idx(int s, int t) {   // upper triangle of 8x
 // A = sum over the coupled faces of w_f (e_i - e_j)(e_i - e_j)^T + diag(D):
 // D_i is the row sum of A (the accumulation term, the Dirichlet faces and,
 // for a free cell, the faces to prescribed cells; 1 on a prescribed row).
+// Axu.. hold the couplings to the upper neighbours (the same arrays as
+// Ax.. for a symmetric A).
 __device__ __forceinline__ double row_sum(const Geo& g, const double* __restrict__ Ad,
                                           const double* __restrict__ Ax,
                                           const double* __restrict__ Ay,
-                                          const double* __restrict__ Az, long long i, int x, int y,
+                                          const double* __restrict__ Az,
+                                          const double* __restrict__ Axu,
+                                          const double* __restrict__ Ayu,
+                                          const double* __restrict__ Azu, long long i, int x, int y,
                                           int z) {
   double s = Ad[i] + Ax[i] + Ay[i] + Az[i];
-  if (x < g.nx - 1) s += Ax[i + 1];
-  if (y < g.ny - 1) s += Ay[i + g.sy];
-  if (z < g.nz - 1) s += Az[i + g.sz];
+  if (x < g.nx - 1) s += Axu[i + 1];
+  if (y < g.ny - 1) s += Ayu[i + g.sy];
+  if (z < g.nz - 1) s += Azu[i + g.sz];
   return s;
 }
 
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(256) k_galerkin_fe_local(
     TA pi[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) pi[s] = P[(long long)s * g.N + i];
-    const TA Dd = (TA)row_sum(g, Ad, Ax, Ay, Az, i, x, y, z);
+    const TA Dd = (TA)row_sum(g, Ad, Ax, Ay, Az, Ax, Ay, Az, i, x, y, z);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       const TA a = Dd * pi[s];
@@ -181,11 +186,14 @@ __global__ void k_galerkin_fe_gather(CGeo c, const double* __restrict__ loc, dou
 
 // MSFV: row I of R A P = sum over the cells of primal block I of (A P)_i,
 // i.e. D_i P_i plus the fluxes w (P_i - P_j) through the block's faces.
+// For a symmetric A the faces inside the block cancel and are skipped; with
+// nonsym every face of every cell is taken, w = -a_{i,j} of the row.
 template <class TP>
 __global__ void __launch_bounds__(256) k_galerkin_fv(
     Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
     const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
-    double* Acs) {
+    const double* __restrict__ Axu, const double* __restrict__ Ayu,
+    const double* __restrict__ Azu, int nonsym, double* Acs) {
   extern __shared__ double acc[];   // 27 * blockDim
   const int I = blockIdx.x;
   const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
@@ -212,21 +220,103 @@ __global__ void __launch_bounds__(256) k_galerkin_fv(
     const int x = Ic[0] * bx + l % bx, y = Ic[1] * by + (l / bx) % by, z = Ic[2] * bz + l / (bx * by);
     const long long i = x + g.sy * y + g.sz * z;
     const int xc[3] = {x, y, z};
-    add_cell(i, xc, row_sum(g, Ad, Ax, Ay, Az, i, x, y, z));
+    add_cell(i, xc, row_sum(g, Ad, Ax, Ay, Az, Axu, Ayu, Azu, i, x, y, z));
     for (int d = 0; d < 3; ++d) {
       const int bd = c.b[d];
       for (int side = 0; side < 2; ++side) {
         const bool onface = side == 0 ? (xc[d] == Ic[d] * bd) : (xc[d] == Ic[d] * bd + bd - 1);
-        if (!onface) continue;
+        if (!onface && !nonsym) continue;
         const int xn = xc[d] + (side == 0 ? -1 : 1);
         if (xn < 0 || xn >= nd_of(g, d)) continue;
         const long long jn = side == 0 ? i - sd_of(g, d) : i + sd_of(g, d);
-        const long long up = side == 0 ? i : jn;      // coupling stored at the upper cell
-        const double w = -(d == 0 ? Ax[up] : (d == 1 ? Ay[up] : Az[up]));
+        // row i's coupling to jn, stored at the upper cell of the face
+        const double w = side == 0 ? -(d == 0 ? Ax[i] : (d == 1 ? Ay[i] : Az[i]))
+                                   : -(d == 0 ? Axu[jn] : (d == 1 ? Ayu[jn] : Azu[jn]));
         add_cell(i, xc, w);
         int xcn[3] = {xc[0], xc[1], xc[2]};
         xcn[d] = xn;
         add_cell(jn, xcn, -w);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < 27; k += T) {
+    double s = 0.0;
+    for (int q = 0; q < T; ++q) s += acc[k * T + q];
+    Acs[(long long)I * 27 + k] = s;
+  }
+}
+
+// MSFE for a nonsymmetric A (the full-Jacobian step): row I of P^T A P =
+// sum over the cells i of basis function I's support of P_iI (A P)_i, with
+// (A P)_i = D_i P_i + sum over the six faces of w (P_i - P_j), w = -a_{i,j}.
+// One CTA per coarse node; sums in FP64.
+template <class TP>
+__global__ void __launch_bounds__(128) k_galerkin_fe_ns(
+    Geo g, CGeo c, const TP* __restrict__ P, const double* __restrict__ Ad,
+    const double* __restrict__ Ax, const double* __restrict__ Ay, const double* __restrict__ Az,
+    const double* __restrict__ Axu, const double* __restrict__ Ayu,
+    const double* __restrict__ Azu, double* Acs) {
+  extern __shared__ double acc[];   // 27 * blockDim
+  const int I = blockIdx.x;
+  const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
+  const int T = blockDim.x, tid = threadIdx.x;
+  for (int k = 0; k < 27; ++k) acc[k * T + tid] = 0.0;
+  // support of basis function I along d: strictly between the neighbouring vertex planes
+  int lo[3], ext[3];
+  for (int d = 0; d < 3; ++d) {
+    const int X = Ic[d] * c.b[d] + c.o[d];
+    lo[d] = max(0, X - c.b[d] + 1);
+    ext[d] = min(nd_of(g, d) - 1, X + c.b[d] - 1) - lo[d] + 1;
+  }
+  // the slot of coarse node I in a cell's P row, -1 if none
+  auto slot_of_I = [&](const int* xc) {
+    int sl = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (corner_d(c, d, xc[d], 0) == Ic[d]) continue;
+      if (corner_d(c, d, xc[d], 1) == Ic[d]) { sl |= 1 << d; continue; }
+      return -1;
+    }
+    return sl;
+  };
+  auto add_cell = [&](long long cell, const int* xc, double scale) {
+    for (int s = 0; s < 8; ++s) {
+      const double v = (double)P[(long long)s * g.N + cell];
+      if (v == 0.0) continue;
+      int t = 0, mul = 1;
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        const int J = corner_d(c, d, xc[d], (s >> d) & 1);
+        const int o = J - Ic[d] + 1;
+        if (J < 0 || o < 0 || o > 2) { ok = false; break; }
+        t += o * mul;
+        mul *= 3;
+      }
+      if (ok) acc[t * T + tid] += scale * v;
+    }
+  };
+  const int ncell = ext[0] * ext[1] * ext[2];
+  for (int l = tid; l < ncell; l += T) {
+    const int xc[3] = {lo[0] + l % ext[0], lo[1] + (l / ext[0]) % ext[1],
+                       lo[2] + l / (ext[0] * ext[1])};
+    const long long i = xc[0] + g.sy * xc[1] + g.sz * xc[2];
+    const int sI = slot_of_I(xc);
+    if (sI < 0) continue;
+    const double wI = (double)P[(long long)sI * g.N + i];
+    if (wI == 0.0) continue;
+    add_cell(i, xc, wI * row_sum(g, Ad, Ax, Ay, Az, Axu, Ayu, Azu, i, xc[0], xc[1], xc[2]));
+    for (int d = 0; d < 3; ++d) {
+      for (int side = 0; side < 2; ++side) {
+        const int xn = xc[d] + (side == 0 ? -1 : 1);
+        if (xn < 0 || xn >= nd_of(g, d)) continue;
+        const long long jn = side == 0 ? i - sd_of(g, d) : i + sd_of(g, d);
+        const double w = side == 0 ? -(d == 0 ? Ax[i] : (d == 1 ? Ay[i] : Az[i]))
+                                   : -(d == 0 ? Axu[jn] : (d == 1 ? Ayu[jn] : Azu[jn]));
+        if (w == 0.0) continue;
+        add_cell(i, xc, wI * w);
+        int xcn[3] = {xc[0], xc[1], xc[2]};
+        xcn[d] = xn;
+        add_cell(jn, xcn, -wI * w);
       }
     }
   }
@@ -876,8 +966,19 @@ __global__ void k_to_single(int n, const double* __restrict__ a, float* b) {
 
 }  // namespace
 
-cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers& b,
+cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, bool nonsym, Buffers& b,
                                cudaStream_t s) {
+  if (nonsym) {
+    const int T = 128;
+    if (single)
+      k_galerkin_fe_ns<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+          g, c, b.f32.P, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, b.Acs);
+    else
+      k_galerkin_fe_ns<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+          g, c, b.P, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, b.Acs);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
   if (single)
     k_galerkin_fe_local<float><<<nd, 256, 0, s>>>(g, c, b.f32.P, b.Ad, b.Ax, b.Ay, b.Az, b.loc);
@@ -888,15 +989,15 @@ cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, Buffers
   return cudaGetLastError();
 }
 
-cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, Buffers& b,
+cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, bool nonsym, Buffers& b,
                                cudaStream_t s) {
   const int T = 128;
   if (single)
-    k_galerkin_fv<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, b.f32.P, b.Ad, b.Ax,
-                                                                  b.Ay, b.Az, b.Acs);
+    k_galerkin_fv<float><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+        g, c, b.f32.P, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, nonsym ? 1 : 0, b.Acs);
   else
-    k_galerkin_fv<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(g, c, b.P, b.Ad, b.Ax, b.Ay,
-                                                                   b.Az, b.Acs);
+    k_galerkin_fv<double><<<c.Nc, T, 27 * T * sizeof(double), s>>>(
+        g, c, b.P, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, nonsym ? 1 : 0, b.Acs);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -64,6 +64,14 @@ __global__ void k_density(long long N, FluidK fl, const double* __restrict__ p, 
 // fixed end stores no coupling, a free cell moves w p_j of a fixed
 // neighbour j to its right-hand side (p_j holds the prescribed value), and a
 // fixed row reads p_i = p_i with a unit diagonal and eps_i = 0.
+//
+// full (Reading R22): the full-Jacobian step adds what Eq. 3 leaves out of
+// the derivative of the equation over rho, rows times V rho: per face (i, j),
+// h = T (p_i - p_j) / 2 gives h rho'_i on the diagonal and h rho'_j at (i, j);
+// the diagonal also takes - Phi_i rho'_i / rho_i (Phi_i the mass flux
+// leaving i).  A p^{nu+1} = f keeps meaning A dp = -F, so f takes X p^nu over
+// the free columns.  A is then not symmetric: Ax.. hold the row's lower
+// couplings a_{i,i-e}, Axu.. the transposed ones a_{i-e,i}, both at cell i.
 __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw, double pe,
                            double rhow, double rhoe, const double* __restrict__ p,
                            const double* __restrict__ rho, const double* __restrict__ rhon,
@@ -72,7 +80,7 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
                            const double* __restrict__ Tbe, const double* __restrict__ src,
                            const unsigned char* __restrict__ fixm, double* Ad, double* Ax,
                            double* Ay, double* Az, double* Cacc, double* f, double* eps,
-                           double* red) {
+                           double* red, int full, double* Axu, double* Ayu, double* Azu) {
   double e2 = 0.0;
   const double inv_dt = 1.0 / dt, inv_V = 1.0 / g.V;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
@@ -125,6 +133,33 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
     const double C = g.V * ri * cc;
     const double q = src ? src[i] * inv_V : 0.0;
     const double b = -phidt + phidt * rn * rinv + q;   // Eq. 5
+    double xdiag = 0.0, xp = 0.0;
+    if (full) {
+      double axu = 0.0, ayu = 0.0, azu = 0.0;
+#define CAMS_JFACE(cond, T, j, lowslot)                                        \
+      if (cond) {                                                              \
+        const double h = 0.5 * (T) * (pi - p[j]);                              \
+        xdiag += h * drho;                                                     \
+        if (!(fixm && (fi || fixm[j]))) {                                      \
+          const double drj = fl.law == 0 ? fl.c * rho[j] : fl.rho0 * fl.c;     \
+          xp += h * drj * p[j];                                                \
+          lowslot;                                                             \
+        }                                                                      \
+      }
+      // a lower face also gives the transposed entry a_{j,i} = -w - h rho'_i
+      CAMS_JFACE(x > 0, Tx[i], i - 1,
+                 (ax += h * drj, axu = -(Tx[i] * (0.5 * (ri + rho[i - 1]))) - h * drho))
+      CAMS_JFACE(x < g.nx - 1, Tx[i + 1], i + 1, (void)0)
+      CAMS_JFACE(y > 0, Ty[i], i - g.sy,
+                 (ay += h * drj, ayu = -(Ty[i] * (0.5 * (ri + rho[i - g.sy]))) - h * drho))
+      CAMS_JFACE(y < g.ny - 1, Ty[i + g.sy], i + g.sy, (void)0)
+      CAMS_JFACE(z > 0, Tz[i], i - g.sz,
+                 (az += h * drj, azu = -(Tz[i] * (0.5 * (ri + rho[i - g.sz]))) - h * drho))
+      CAMS_JFACE(z < g.nz - 1, Tz[i + g.sz], i + g.sz, (void)0)
+#undef CAMS_JFACE
+      xdiag -= flux * drho * rinv;
+      Axu[i] = axu; Ayu[i] = ayu; Azu[i] = azu;
+    }
     Ax[i] = ax; Ay[i] = ay; Az[i] = az;
     Cacc[i] = C;
     double e = 0.0;
@@ -132,8 +167,14 @@ __global__ void k_assemble(Geo g, FluidK fl, double dt, int dirichlet, double pw
       Ad[i] = 1.0;
       f[i] = pi;
     } else {
-      Ad[i] = C + dsum;
-      f[i] = g.V * ri * b + rhsb + C * pi;
+      double fv = g.V * ri * b + rhsb + C * pi;
+      if (full) {
+        Ad[i] = C + dsum + xdiag;
+        fv += xdiag * pi + xp;
+      } else {
+        Ad[i] = C + dsum;
+      }
+      f[i] = fv;
       e = q - phidt + phidt * rn * rinv - flux * inv_V * rinv;  // Eq. 19
     }
     eps[i] = e;
@@ -183,12 +224,16 @@ __global__ void k_finish_sum(const double* __restrict__ red, int n, double* out)
   if (threadIdx.x == 0) out[0] = s;
 }
 
-// r = f - A p and per-block sums of r^2.  Warps take whole x-rows (lanes
-// along x, coalesced), so the cell coordinates cost one division per row.
+// r = f - A p and per-block sums of r^2 (kNS: Axu.. hold the couplings to
+// the upper neighbours; otherwise A is symmetric and Ax.. serve both).  Warps take whole
+// x-rows (lanes along x, coalesced), so the cell coordinates cost one
+// division per row.
+template <bool kNS>
 __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* __restrict__ Ax,
                            const double* __restrict__ Ay, const double* __restrict__ Az,
-                           const double* __restrict__ f, const double* __restrict__ p, double* r,
-                           double* red) {
+                           const double* __restrict__ Axu, const double* __restrict__ Ayu,
+                           const double* __restrict__ Azu, const double* __restrict__ f,
+                           const double* __restrict__ p, double* r, double* red) {
   double s2 = 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
@@ -199,11 +244,11 @@ __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* _
       const long long i = base + x;
       double a = f[i] - Ad[i] * p[i];
       if (x > 0) a -= Ax[i] * p[i - 1];
-      if (x < g.nx - 1) a -= Ax[i + 1] * p[i + 1];
+      if (x < g.nx - 1) a -= (kNS ? Axu : Ax)[i + 1] * p[i + 1];
       if (y > 0) a -= Ay[i] * p[i - g.sy];
-      if (y < g.ny - 1) a -= Ay[i + g.sy] * p[i + g.sy];
+      if (y < g.ny - 1) a -= (kNS ? Ayu : Ay)[i + g.sy] * p[i + g.sy];
       if (z > 0) a -= Az[i] * p[i - g.sz];
-      if (z < g.nz - 1) a -= Az[i + g.sz] * p[i + g.sz];
+      if (z < g.nz - 1) a -= (kNS ? Azu : Az)[i + g.sz] * p[i + g.sz];
       if (r) r[i] = a;
       s2 += a * a;
     }
@@ -275,14 +320,16 @@ cudaError_t launch_density(const Geo& g, const FluidK& fl, const double* p, doub
 }
 
 cudaError_t launch_assemble(const Geo& g, const FluidK& fl, double dt, int dirichlet, double pw,
-                            double pe, const unsigned char* fixm, Buffers& b, cudaStream_t s) {
+                            double pe, const unsigned char* fixm, bool full, Buffers& b,
+                            cudaStream_t s) {
   FluidK f2 = fl;
   const double rhow = fl.law == 0 ? fl.rho0 * std::exp(fl.c * pw) : fl.rho0 * (1.0 + fl.c * pw);
   const double rhoe = fl.law == 0 ? fl.rho0 * std::exp(fl.c * pe) : fl.rho0 * (1.0 + fl.c * pe);
   k_assemble<<<kRedBlocks, kRedThreads, 0, s>>>(g, f2, dt, dirichlet, pw, pe, rhow, rhoe, b.p,
                                                 b.rho, b.rhon, b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe,
                                                 b.src, fixm, b.Ad, b.Ax, b.Ay, b.Az, b.Cacc, b.f,
-                                                b.eps, b.red); count_launches(1);
+                                                b.eps, b.red, full ? 1 : 0, b.Axu, b.Ayu,
+                                                b.Azu); count_launches(1);
   k_finish_sum<<<1, 1024, 0, s>>>(b.red, kRedBlocks, b.scal); count_launches(1);
   return cudaGetLastError();
 }
@@ -307,7 +354,13 @@ cudaError_t launch_sumsq(const double* x, long long N, double* red, double* out,
 
 cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, double* r,
                             double* red, double* out, cudaStream_t s) {
-  k_residual<<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.f, p, r, red); count_launches(1);
+  if (b.Axu != b.Ax)
+    k_residual<true><<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu,
+                                                        b.Azu, b.f, p, r, red);
+  else
+    k_residual<false><<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu,
+                                                         b.Azu, b.f, p, r, red);
+  count_launches(1);
   k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out); count_launches(1);
   return cudaGetLastError();
 }

@@ -8,7 +8,9 @@
 //   z_i = w_i  - sum_{j>i} (a_ij / d_i) z_j       (backward wavefront)
 //   x += z
 // with the couplings pre-scaled by the row pivot once per factorisation, so
-// every cell of a sweep is a chain of at most three FMAs.  In FP64 (b, x) =
+// every cell of a sweep is a chain of at most three FMAs.  For a
+// nonsymmetric A (the full-Jacobian step) the pivot recurrence takes the
+// products a_{i,j} a_{j,i}, formed once per factorisation.  In FP64 (b, x) =
 // (f, p).  In the mixed-precision preconditioner the smoother runs in FP32
 // on the correction equation A delta = r, (b, x) = (r, delta), with an FP32
 // copy of A; r is the FP64 residual and p += delta is taken in FP64.
@@ -162,8 +164,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // L_d = a_{i,i-e_d} / d_i, U_d = a_{i,i+e_d} / d_i.
 template <class T>
 __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* __restrict__ Ay,
-                            const T* __restrict__ Az, const T* __restrict__ dinv, T* Lx, T* Ly,
-                            T* Lz, T* Ux, T* Uy, T* Uz) {
+                            const T* __restrict__ Az, const T* __restrict__ Axu,
+                            const T* __restrict__ Ayu, const T* __restrict__ Azu,
+                            const T* __restrict__ dinv, T* Lx, T* Ly, T* Lz, T* Ux, T* Uy,
+                            T* Uz) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= g.N) return;
   int x, y, z;
@@ -173,9 +177,9 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* _
   Lx[j] = Ax[i] * di;
   Ly[j] = Ay[i] * di;
   Lz[j] = Az[i] * di;
-  Ux[j] = x < g.nx - 1 ? Ax[i + 1] * di : T(0);
-  Uy[j] = y < g.ny - 1 ? Ay[i + g.sy] * di : T(0);
-  Uz[j] = z < g.nz - 1 ? Az[i + g.sz] * di : T(0);
+  Ux[j] = x < g.nx - 1 ? Axu[i + 1] * di : T(0);
+  Uy[j] = y < g.ny - 1 ? Ayu[i + g.sy] * di : T(0);
+  Uz[j] = z < g.nz - 1 ? Azu[i + g.sz] * di : T(0);
 }
 
 // The two conversions between the natural layout and the skewed sweep
@@ -187,12 +191,16 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* _
 constexpr int kXC = 64;
 
 // rd = D^{-1} (b - A x), stored skewed; b is read in its own precision and
-// rounded to T.
-template <class B, class T>
+// rounded to T.  kNS: Axu.. hold the couplings to the upper neighbours (A
+// not symmetric); otherwise Ax.. serve both.
+template <class B, class T, bool kNS>
 __global__ void __launch_bounds__(256) k_resid_scaled(Geo g, Skew sk, const T* __restrict__ Ad,
                                                       const T* __restrict__ Ax,
                                                       const T* __restrict__ Ay,
                                                       const T* __restrict__ Az,
+                                                      const T* __restrict__ Axu,
+                                                      const T* __restrict__ Ayu,
+                                                      const T* __restrict__ Azu,
                                                       const B* __restrict__ bv,
                                                       const T* __restrict__ xv,
                                                       const T* __restrict__ dinv, T* rd) {
@@ -209,11 +217,11 @@ __global__ void __launch_bounds__(256) k_resid_scaled(Geo g, Skew sk, const T* _
       const long long i = x + g.sy * y + g.sz * z;
       T a = T(bv[i]) - Ad[i] * xv[i];
       if (x > 0) a -= Ax[i] * xv[i - 1];
-      if (x < g.nx - 1) a -= Ax[i + 1] * xv[i + 1];
+      if (x < g.nx - 1) a -= (kNS ? Axu : Ax)[i + 1] * xv[i + 1];
       if (y > 0) a -= Ay[i] * xv[i - g.sy];
-      if (y < g.ny - 1) a -= Ay[i + g.sy] * xv[i + g.sy];
+      if (y < g.ny - 1) a -= (kNS ? Ayu : Ay)[i + g.sy] * xv[i + g.sy];
       if (z > 0) a -= Az[i] * xv[i - g.sz];
-      if (z < g.nz - 1) a -= Az[i + g.sz] * xv[i + g.sz];
+      if (z < g.nz - 1) a -= (kNS ? Azu : Az)[i + g.sz] * xv[i + g.sz];
       blk[r][h] = a * dinv[i];
     }
   }
@@ -279,6 +287,30 @@ __global__ void k_matrix_to_single(long long n, const double* __restrict__ Ad,
   sz[i] = (float)Az[i];
 }
 
+// FP32 copies of three arrays (the transposed couplings of a nonsymmetric A)
+__global__ void k_three_to_single(long long n, const double* __restrict__ a,
+                                  const double* __restrict__ b, const double* __restrict__ c,
+                                  float* sa, float* sb, float* sc) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  sa[i] = (float)a[i];
+  sb[i] = (float)b[i];
+  sc[i] = (float)c[i];
+}
+
+// Q_d[i] = a_{i,i-e_d} a_{i-e_d,i}: the pivot recurrence's products
+template <class T>
+__global__ void k_pivot_products(long long n, const T* __restrict__ Ax, const T* __restrict__ Ay,
+                                 const T* __restrict__ Az, const T* __restrict__ Axu,
+                                 const T* __restrict__ Ayu, const T* __restrict__ Azu, T* Qx,
+                                 T* Qy, T* Qz) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Qx[i] = Ax[i] * Axu[i];
+  Qy[i] = Ay[i] * Ayu[i];
+  Qz[i] = Az[i] * Azu[i];
+}
+
 // p += delta (mixed precision: the FP32 correction enters the FP64 iterate)
 __global__ void k_add_correction(long long n, const float* __restrict__ d, double* p) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -337,8 +369,10 @@ struct BwdSolve {   // z = w - Ux z_{x+1} - Uy z_{y+1} - Uz z_{z+1}  (x += z fol
   }
 };
 
-template <class T>
-struct Factor {     // d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} - a_{i,z-1}^2 / d_{z-1}
+// d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} - a_{i,z-1}^2 / d_{z-1};
+// kProd: the operands are the products a_{i,i-e} a_{i-e,i} (nonsymmetric A)
+template <class T, bool kProd = false>
+struct Factor {
   using Scalar = T;
   static constexpr int kN = 4;
   static constexpr bool kSkewIn = false, kSkewOut = false;
@@ -351,9 +385,15 @@ struct Factor {     // d = a_ii - a_{i,x-1}^2 / d_{x-1} - a_{i,y-1}^2 / d_{y-1} 
   __device__ __forceinline__ T apply(const T* in, long long i, long long, bool cell, T vx, T vy,
                                      T vz) const {
     T d = in[0];
-    d -= in[1] * in[1] * vx;
-    d -= in[2] * in[2] * vy;
-    d -= in[3] * in[3] * vz;
+    if constexpr (kProd) {
+      d -= in[1] * vx;
+      d -= in[2] * vy;
+      d -= in[3] * vz;
+    } else {
+      d -= in[1] * in[1] * vx;
+      d -= in[2] * in[2] * vy;
+      d -= in[3] * in[3] * vz;
+    }
     if (cell && (!(d != T(0)) || !isfinite(d))) {
       atomicOr(status, kStatSingular);
       d = T(1);
@@ -804,45 +844,68 @@ bool set_cta_smem(const Geo& g) {
 template <class T>
 struct IluSet {
   const T *Ad, *Ax, *Ay, *Az;
+  const T *Axu, *Ayu, *Azu;
+  T *Qx, *Qy, *Qz;
   T* dinv;
   T *Lx, *Ly, *Lz, *Ux, *Uy, *Uz;
   T *rds, *w, *z;
 };
 
 IluSet<double> set_of(Buffers& b, double*) {
-  return IluSet<double>{b.Ad, b.Ax, b.Ay, b.Az, b.dinv, b.Lx, b.Ly, b.Lz, b.Ux, b.Uy, b.Uz,
-                        b.rds, b.w, b.z};
+  return IluSet<double>{b.Ad,   b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, b.Qx, b.Qy, b.Qz,
+                        b.dinv, b.Lx, b.Ly, b.Lz, b.Ux,  b.Uy,  b.Uz,  b.rds, b.w, b.z};
 }
 IluSet<float> set_of(Buffers& b, float*) {
   const SingleBuffers& f = b.f32;
-  return IluSet<float>{f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
-                       f.rds, f.w, f.z};
+  return IluSet<float>{f.Ad,   f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, f.Qx, f.Qy, f.Qz,
+                       f.dinv, f.Lx, f.Ly, f.Lz, f.Ux,  f.Uy,  f.Uz,  f.rds, f.w, f.z};
 }
 
-template <class T>
-cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
-                        cudaStream_t s) {
-  const Skew sk = make_skew(g);
-  const IluSet<T> v = set_of(b, (T*)nullptr);
-  Factor<T> fa{v.Ad, v.Ax, v.Ay, v.Az, v.dinv, b.status};
-  int n = 1;
+// The pivot sweep (level-scheduled or pipelined); returns the launch count.
+template <class Op>
+int factor_sweep(const Geo& g, const Skew& sk, Buffers& b, bool pipelined, int sms, bool cta,
+                 const Op& fa, typename Op::Scalar* dinv, cudaStream_t s, cudaError_t& e) {
+  using T = typename Op::Scalar;
+  e = cudaSuccess;
   if (!pipelined) {
     const int blocks = blocks_for((long long)g.ny * g.nz, 256);
     const int levels = g.nx + g.ny + g.nz - 2;
     for (int L = 0; L < levels; ++L)
-      k_sweep_level<Factor<T>, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, v.dinv);
-    n += levels;
+      k_sweep_level<Op, false><<<blocks, 256, 0, s>>>(g, sk, L, fa, dinv);
+    return levels;
+  }
+  k_fill_not_ready<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, dinv, nullptr);
+  e = launch_sweep<Op, false>(g, sk, sms, cta, fa, dinv, b, s);
+  return 2;
+}
+
+template <class T>
+cudaError_t factor_impl(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta, bool nonsym,
+                        cudaStream_t s) {
+  const Skew sk = make_skew(g);
+  const IluSet<T> v = set_of(b, (T*)nullptr);
+  int n = 1;
+  cudaError_t e;
+  if (nonsym) {
+    k_pivot_products<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, v.Ax, v.Ay, v.Az, v.Axu, v.Ayu,
+                                                             v.Azu, v.Qx, v.Qy, v.Qz);
+    ++n;
+    Factor<T, true> fa{v.Ad, v.Qx, v.Qy, v.Qz, v.dinv, b.status};
+    n += factor_sweep(g, sk, b, pipelined, sms, cta, fa, v.dinv, s, e);
   } else {
-    k_fill_not_ready<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, v.dinv, nullptr);
-    cudaError_t e = launch_sweep<Factor<T>, false>(g, sk, sms, cta, fa, v.dinv, b, s);
-    if (e != cudaSuccess) return e;
+    Factor<T> fa{v.Ad, v.Ax, v.Ay, v.Az, v.dinv, b.status};
+    n += factor_sweep(g, sk, b, pipelined, sms, cta, fa, v.dinv, s, e);
+  }
+  if (e != cudaSuccess) return e;
+  if (pipelined) {
     // sweep outputs start "not computed"; the sweeps keep it so from here on
     const long long S = ilu_skew_len(g);
     k_fill_not_ready<T><<<blocks_for(S, 256), 256, 0, s>>>(S, v.w, v.z);
-    n += 3;
+    ++n;
   }
-  k_ilu_scale<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, v.Ax, v.Ay, v.Az, v.dinv, v.Lx, v.Ly,
-                                                      v.Lz, v.Ux, v.Uy, v.Uz);
+  k_ilu_scale<T><<<blocks_for(g.N, 256), 256, 0, s>>>(g, sk, v.Ax, v.Ay, v.Az, v.Axu, v.Ayu,
+                                                      v.Azu, v.dinv, v.Lx, v.Ly, v.Lz, v.Ux,
+                                                      v.Uy, v.Uz);
   count_launches(n);
   return cudaGetLastError();
 }
@@ -895,6 +958,8 @@ int ilu_pipe_grid(const Geo& g, int num_sms) {
   set_sweep_smem<FwdSolve<float>, false>();
   set_sweep_smem<BwdSolve<float>, true>();
   set_sweep_smem<Factor<float>, false>();
+  set_sweep_smem<Factor<double, true>, false>();
+  set_sweep_smem<Factor<float, true>, false>();
   return num_sms;
 }
 
@@ -902,31 +967,46 @@ bool ilu_cta_ok(const Geo& g, int max_smem) {
   if (cta_smem<FwdSolve<double>>(g) > max_smem) return false;   // FP64 needs the most
   bool ok = set_cta_smem<FwdSolve<double>, false>(g) && set_cta_smem<BwdSolve<double>, true>(g) &&
             set_cta_smem<Factor<double>, false>(g) && set_cta_smem<FwdSolve<float>, false>(g) &&
-            set_cta_smem<BwdSolve<float>, true>(g) && set_cta_smem<Factor<float>, false>(g);
+            set_cta_smem<BwdSolve<float>, true>(g) && set_cta_smem<Factor<float>, false>(g) &&
+            set_cta_smem<Factor<double, true>, false>(g) &&
+            set_cta_smem<Factor<float, true>, false>(g);
   cudaGetLastError();
   return ok;
 }
 
 cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int sms, bool cta,
-                              bool single, cudaStream_t s) {
+                              bool single, bool nonsym, cudaStream_t s) {
   if (single) {
     k_matrix_to_single<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.Ad, b.Ax, b.Ay, b.Az, b.f32.Ad,
                                                             b.f32.Ax, b.f32.Ay, b.f32.Az);
     count_launches(1);
-    return factor_impl<float>(g, b, pipelined, sms, cta, s);
+    if (nonsym) {
+      k_three_to_single<<<blocks_for(g.N, 256), 256, 0, s>>>(g.N, b.Axu, b.Ayu, b.Azu, b.f32.Axu,
+                                                             b.f32.Ayu, b.f32.Azu);
+      count_launches(1);
+    }
+    return factor_impl<float>(g, b, pipelined, sms, cta, nonsym, s);
   }
-  return factor_impl<double>(g, b, pipelined, sms, cta, s);
+  return factor_impl<double>(g, b, pipelined, sms, cta, nonsym, s);
 }
 
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s) {
   const Skew sk = make_skew(g);
   if (single) {
     const SingleBuffers& f = b.f32;
-    k_resid_scaled<double, float><<<transpose_grid(g, sk), 256, 0, s>>>(
-        g, sk, f.Ad, f.Ax, f.Ay, f.Az, b.r, f.d, f.dinv, f.rds);
+    if (f.Axu != f.Ax)
+      k_resid_scaled<double, float, true><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, b.r, f.d, f.dinv, f.rds);
+    else
+      k_resid_scaled<double, float, false><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, b.r, f.d, f.dinv, f.rds);
   } else {
-    k_resid_scaled<double, double><<<transpose_grid(g, sk), 256, 0, s>>>(
-        g, sk, b.Ad, b.Ax, b.Ay, b.Az, b.f, b.p, b.dinv, b.rds);
+    if (b.Axu != b.Ax)
+      k_resid_scaled<double, double, true><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, b.f, b.p, b.dinv, b.rds);
+    else
+      k_resid_scaled<double, double, false><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu, b.Azu, b.f, b.p, b.dinv, b.rds);
   }
   count_launches(1);
   return cudaGetLastError();
