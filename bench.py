@@ -89,7 +89,14 @@ def parse():
                     help="skip the leg with the learned basis surrogate")
     ap.add_argument("--no-fp64", action="store_true",
                     help="mixed-precision workloads: skip the FP64 comparison run")
+    ap.add_argument("--jacobian", action="store_true",
+                    help="the full-Jacobian Newton step (flux density differentiated)")
+    ap.add_argument("--cf", action="store_true",
+                    help="correction functions before every multiscale stage")
     return ap.parse_args()
+
+
+VARIANT = {}      # solver options beyond the workload's (--jacobian, --cf)
 
 
 def dist_env():
@@ -181,7 +188,8 @@ def _handles(cams, w, inp, memspace, dev_arrays=None):
     opt = cams.make_options(w.coarse, basis=w.basis, restriction=w.restriction, n_pre=w.n_pre,
                             n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
                             adapt_theta=w.adapt_theta, max_newton=w.max_newton,
-                            max_cams=w.max_cams, memspace=memspace, precision=w.precision)
+                            max_cams=w.max_cams, memspace=memspace, precision=w.precision,
+                            **VARIANT)
     k = dev_arrays if dev_arrays is not None else (inp["kx"], inp["ky"], inp["kz"])
     return cams.cams_setup(grid, fluid, opt, *k)
 
@@ -309,7 +317,9 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
         "data": "synthetic",
         "config": {"workload": f"{w.name} {'mixed FP32/FP64' if w.precision else 'FP64'} C-AMS basis B{w.basis} "
                                f"{'MSFE' if w.restriction == 0 else 'MSFV'} n_post={w.n_post} "
-                               f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}",
+                               f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}"
+                               + (" full-Jacobian Newton" if VARIANT.get("jacobian") else "")
+                               + (" correction functions" if VARIANT.get("cf") else ""),
                    "cells": N, "time_step": "first (full basis build) from p=0",
                    "l2": "inputs > L2 (4M-cell fields, >1 GB touched per step)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -441,7 +451,8 @@ def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
                               bc, kx, ky, kz)
     opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
                          n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
-                         adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams)
+                         adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams,
+                         full_jacobian=bool(VARIANT.get("jacobian")), cf=bool(VARIANT.get("cf")))
     t0 = time.perf_counter()
     _, st = oracle.run(pb, opt, np.zeros(g.N), inp["dt"], 1)
     dt = time.perf_counter() - t0
@@ -477,6 +488,10 @@ def run_reference(args, w, rank, world):
 
 def main():
     args = parse()
+    if args.jacobian:
+        VARIANT["jacobian"] = 1
+    if args.cf:
+        VARIANT["cf"] = True
     rank, world, local_rank = dist_env()
     if args.workload == ENSEMBLE:
         if args.impl == "reference":

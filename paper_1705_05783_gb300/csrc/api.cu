@@ -306,6 +306,7 @@ int alloc_all(cams_handle* h) {
   AL(b.loc, (size_t)h->n_dual * 36);
   AL(b.Acs, 27LL * h->c.Nc);
   AL(b.band, (size_t)h->c.Nc * (2 * h->mc + 1));
+  AL(b.Fc, (size_t)h->c.Nc * (2 * h->mc + 1));
   AL(b.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(b.Lr, (size_t)h->c.Nc * (h->mc + 1));
   AL(b.cblk, coarse_blocks_len(h->c.Nc)); AL(b.cdinv, h->c.Nc); AL(b.cabort, 1);
   AL(b.perm, h->c.Nc);
@@ -342,7 +343,7 @@ void free_all(cams_handle* h) {
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
-                  b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz,
+                  b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz, b.Fc,
                   // the transposed couplings are separate arrays only for a nonsymmetric A
                   b.Axu != b.Ax ? b.Axu : nullptr, b.Ayu != b.Ay ? b.Ayu : nullptr,
                   b.Azu != b.Az ? b.Azu : nullptr};

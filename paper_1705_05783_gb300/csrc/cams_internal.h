@@ -115,6 +115,7 @@ struct Buffers {
   double* loc = nullptr;                                  // FE local 8x8 blocks per dual block (64 each)
   double* Acs = nullptr;                                  // 27*Nc coarse stencil
   double* band = nullptr;                                 // coarse band (column-major)
+  double* Fc = nullptr;                                   // its LU factor (general band layout)
   double *Lc = nullptr, *Lr = nullptr;                    // LDL^T factor, column/row-major
   double *cblk = nullptr, *cdinv = nullptr;               // block inverses / products, 1/d
   int* cabort = nullptr;                                  // abort flag of the cluster solve

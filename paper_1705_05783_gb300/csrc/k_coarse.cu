@@ -818,56 +818,191 @@ __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
   cl_sync();   // no CTA leaves while others may still store into its shared memory
 }
 
-// ---- general (MSFV) coarse matrix: band LU without pivoting, one CTA ----
-// Column-major band Bc[col*(2m+1) + (row-col+m)]; after the factorisation
-// column k holds U above/on the diagonal and the multipliers of L below.
-__global__ void __launch_bounds__(1024) k_band_lu(int Nc, int m, double* Bc, int* status) {
-  const int w = 2 * m + 1;
-  for (int k = 0; k < Nc; ++k) {
-    const int amax = min(m, Nc - 1 - k);
-    double piv = Bc[(long long)k * w + m];
-    if (!(piv != 0.0) || !isfinite(piv)) {
-      if (threadIdx.x == 0) atomicOr(status, kStatSingular);
-      piv = 1.0;
-    }
-    const double inv = 1.0 / piv;
-    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      Bc[(long long)k * w + (m + a)] *= inv;              // l_{k+a,k}
-    __syncthreads();
-    const int np = amax * amax;
-    for (int t = threadIdx.x; t < np; t += blockDim.x) {
-      const int bb = t / amax + 1, a = t % amax + 1;      // column k+bb, row k+a
-      Bc[(long long)(k + bb) * w + (a - bb + m)] -=
-          Bc[(long long)k * w + (m + a)] * Bc[(long long)(k + bb) * w + (m - bb)];
-    }
-    __syncthreads();
-  }
+// ---- general coarse matrix (MSFV, or MSFE of a nonsymmetric A): band LU ----
+// without pivoting, in column blocks of kTB like k_ldlt_block.  Column-major
+// band B[col*(2m+1) + (row-col+m)].  One launch per column block c0..c1:
+// every CTA factors the diagonal block D = L_D U_D, forms its kTB rows of
+// the L panel (A U_D^{-1}, rows c1+1..c1+m) and its kTB columns of the U
+// panel (L_D^{-1} A, columns c1+1..c1+m), and updates its tile of the
+// trailing window (rows and columns c1+1..c1+m, all inside the band).  The
+// factor goes to F (same layout: U on and above the diagonal, the
+// multipliers of L below), so no CTA reads a value another one rewrites.
+__device__ __forceinline__ double gband_at(const double* B, int m, int r, int c) {
+  return (r - c <= m && c - r <= m) ? B[(long long)c * (2 * m + 1) + (r - c + m)] : 0.0;
 }
 
-// Forward (unit L) and backward (U) substitution with the column-major LU.
-__global__ void __launch_bounds__(256) k_band_solve(int Nc, int m, const double* __restrict__ Bc,
-                                                    const double* __restrict__ rc, double* pc) {
-  extern __shared__ double y[];
+__global__ void __launch_bounds__(256) k_lu_block(int N, int m, int c0, const double* __restrict__ Br,
+                                                  double* B, double* F, int* status) {
+  __shared__ double D[kTB][kTB + 1];        // diagonal block: U on and above, work below
+  __shared__ double L[kTB][kTB + 1];        // its multipliers l_rq (r > q)
+  __shared__ double dinv[kTB];              // 1 / u_qq
+  __shared__ double V[kTB][kTB + 1];        // my L-panel rows: a_rq in, l_rq out
+  __shared__ double H[kTB][kTB + 1];        // my U-panel columns: H[q][k] = a_{q, cc0+k} in, u out
   const int w = 2 * m + 1;
-  for (int i = threadIdx.x; i < Nc; i += blockDim.x) y[i] = rc[i];
+  const int c1 = min(c0 + kTB, N) - 1;
+  const int tb = c1 - c0 + 1;
+  const int tid = threadIdx.x;
+  const int rlo = c1 + 1;
+  const int rhi = min(c1 + m, N - 1);
+  const int nb = rhi >= rlo ? (rhi - rlo + kTB) / kTB : 0;
+  const int bi = nb > 0 ? (int)blockIdx.x / nb : 0, bj = nb > 0 ? (int)blockIdx.x % nb : 0;
+  const bool have_tile = nb > 0 && bi < nb;
+  const int r0 = rlo + bi * kTB, cc0 = rlo + bj * kTB;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  {
+    const int r = tid / kTB, q = tid % kTB;
+    D[r][q] = (r < tb && q < tb) ? gband_at(Br, m, c0 + r, c0 + q) : 0.0;
+    V[r][q] = (have_tile && r0 + r <= rhi && q < tb) ? gband_at(Br, m, r0 + r, c0 + q) : 0.0;
+    H[q][r] = (have_tile && cc0 + r <= rhi && q < tb) ? gband_at(Br, m, c0 + q, cc0 + r) : 0.0;
+    L[r][q] = 0.0;
+  }
   __syncthreads();
-  for (int k = 0; k < Nc; ++k) {
-    const int amax = min(m, Nc - 1 - k);
-    const double yk = y[k];
-    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      y[k + a] -= Bc[(long long)k * w + (m + a)] * yk;
+  if (tid == 0) {
+    double d = D[0][0];
+    if (!(d != 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
+    dinv[0] = 1.0 / d;
+  }
+  __syncthreads();
+  // --- D = L_D U_D, one element a thread ---
+  const int er = tid / kTB, ec = tid % kTB;
+  for (int q = 0; q < tb; ++q) {
+    if (er > q && er < tb) {
+      const double t = D[er][q] * dinv[q];
+      if (ec == q) {
+        L[er][q] = t;
+      } else if (ec > q && ec < tb) {
+        const double v = fma(-t, D[q][ec], D[er][ec]);
+        D[er][ec] = v;
+        if (er == q + 1 && ec == q + 1) {     // the next pivot is final
+          double d = v;
+          if (!(d != 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
+          dinv[q + 1] = 1.0 / d;
+        }
+      }
+    }
     __syncthreads();
   }
-  for (int k = Nc - 1; k >= 0; --k) {
-    const double xk = y[k] / Bc[(long long)k * w + m];
-    __syncthreads();
-    if (threadIdx.x == 0) y[k] = xk;
-    const int amax = min(m, k);
-    for (int a = 1 + threadIdx.x; a <= amax; a += blockDim.x)
-      y[k - a] -= Bc[(long long)k * w + (m - a)] * xk;
-    __syncthreads();
+  // --- panels: row k of V by thread k, column k of H by thread kTB + k ---
+  if (tid < kTB) {
+    const int k = tid;
+    for (int q = 0; q < tb; ++q) {
+      double s = V[k][q];
+      for (int j = 0; j < q; ++j) s = fma(-V[k][j], D[j][q], s);
+      V[k][q] = s * dinv[q];
+    }
+  } else if (tid < 2 * kTB) {
+    const int k = tid - kTB;
+    for (int q = 0; q < tb; ++q) {
+      double s = H[q][k];
+      for (int j = 0; j < q; ++j) s = fma(-L[q][j], H[j][k], s);
+      H[q][k] = s;
+    }
   }
-  for (int i = threadIdx.x; i < Nc; i += blockDim.x) pc[i] = y[i];
+  __syncthreads();
+  if (have_tile) {
+    // trailing tile: B[r][c] -= sum_q l_rq u_qc (|r - c| < m inside the window)
+    const int a = tid / kTB, bc = tid % kTB;
+    const int r = r0 + a, c = cc0 + bc;
+    if (r <= rhi && c <= rhi) {
+      double s = 0.0;
+      for (int q = 0; q < tb; ++q) s = fma(V[a][q], H[q][bc], s);
+      B[(long long)c * w + (r - c + m)] -= s;
+    }
+    // the first tile column publishes the L rows, the first tile row the U columns
+    const int k = tid / kTB, q = tid % kTB;
+    if (bj == 0 && q < tb) {
+      const int rr = r0 + k, col = c0 + q;
+      if (rr <= rhi && rr - col <= m) F[(long long)col * w + (rr - col + m)] = V[k][q];
+    }
+    if (bi == 0 && q < tb) {
+      const int row = c0 + q, col = cc0 + k;
+      if (col <= rhi && col - row <= m) F[(long long)col * w + (row - col + m)] = H[q][k];
+    }
+  }
+  // the first CTA publishes the diagonal block
+  if (blockIdx.x == 0 && er < tb && ec < tb && er - ec <= m && ec - er <= m)
+    F[(long long)(c0 + ec) * w + (er - ec + m)] = er > ec ? L[er][ec] : D[er][ec];
+}
+
+// L U x = b, one CTA, with the band LU's columns streamed through shared
+// memory in chunks of kSC (as in k_ldlt_solve; 8-byte copies, since a band
+// column of 2m+1 doubles starts on an 8-byte boundary only): forward with the
+// multipliers l_{k+a,k} of column k, backward with u_{k-a,k} and the pivot.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src));
+}
+
+__global__ void __launch_bounds__(256) k_band_lu_solve(int N, int m, const double* __restrict__ Bc,
+                                                       const double* __restrict__ rc, double* pc) {
+  extern __shared__ __align__(16) double sm[];
+  const int w = 2 * m + 1, mp = m + 1;
+  const int chunk = kSC * mp;
+  double* buf0 = sm;
+  double* buf1 = sm + chunk;
+  double* y = sm + 2 * chunk;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N; i += nt) y[i] = rc[i];
+  const int nchunks = (N + kSC - 1) / kSC;
+  // dst[c*mp + a] = l_{k0+c+a, k0+c}, a = 1..m
+  auto stage_l = [&](double* dst, int k0) {
+    const int nc = min(kSC, N - k0);
+    for (int e = tid; e < nc * m; e += nt) {
+      const int c = e / m, a = e - c * m + 1;
+      cp_async8(dst + c * mp + a, Bc + (long long)(k0 + c) * w + m + a);
+    }
+    cp_async_commit();
+  };
+  // dst[c*mp + a] = u_{k0+c-a, k0+c}, a = 0..m (a = 0: the pivot)
+  auto stage_u = [&](double* dst, int k0) {
+    const int nc = min(kSC, N - k0);
+    for (int e = tid; e < nc * mp; e += nt) {
+      const int c = e / mp, a = e - c * mp;
+      cp_async8(dst + c * mp + a, Bc + (long long)(k0 + c) * w + m - a);
+    }
+    cp_async_commit();
+  };
+  stage_l(buf0, 0);
+  for (int ck = 0; ck < nchunks; ++ck) {
+    double* cur = (ck & 1) ? buf1 : buf0;
+    double* nxt = (ck & 1) ? buf0 : buf1;
+    cp_async_wait_all();
+    __syncthreads();
+    if (ck + 1 < nchunks) stage_l(nxt, (ck + 1) * kSC);
+    const int k0 = ck * kSC;
+    for (int c = 0; c < kSC && k0 + c < N; ++c) {
+      const int k = k0 + c;
+      const double yk = y[k];
+      const int amax = min(m, N - 1 - k);
+      for (int a = 1 + tid; a <= amax; a += nt) y[k + a] -= cur[c * mp + a] * yk;
+      __syncthreads();
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int last0 = (nchunks - 1) * kSC;
+  stage_u(buf0, last0);
+  for (int ck = nchunks - 1, it = 0; ck >= 0; --ck, ++it) {
+    double* cur = (it & 1) ? buf1 : buf0;
+    double* nxt = (it & 1) ? buf0 : buf1;
+    cp_async_wait_all();
+    __syncthreads();
+    if (ck > 0) stage_u(nxt, (ck - 1) * kSC);
+    const int k0 = ck * kSC;
+    for (int c = min(kSC, N - k0) - 1; c >= 0; --c) {
+      const int k = k0 + c;
+      const double xk = y[k] / cur[c * mp];
+      __syncthreads();                         // every thread has read y[k]
+      if (tid == 0) y[k] = xk;
+      const int amax = min(m, k);
+      for (int a = 1 + tid; a <= amax; a += nt) y[k - a] -= cur[c * mp + a] * xk;
+      __syncthreads();
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int i = tid; i < N; i += nt) pc[i] = y[i];
 }
 
 // MSFE restriction, part 1: per dual block the 8 sums  sum_i P_i[s] r_i.
@@ -1011,16 +1146,32 @@ cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStre
 }
 
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s) {
-  if (!sym) {
-    k_band_lu<<<1, 1024, 0, s>>>(Nc, m, b.band, b.status); count_launches(1);
-    return cudaGetLastError();
-  }
   // one launch per column block, each allowed to start while the previous
   // one drains (programmatic dependent launch; the kernel waits for it)
   int launches = 0;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  if (!sym) {
+    for (int c0 = 0; c0 < Nc; c0 += kTB) {
+      const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
+      const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
+      const int nb = rhi > c1 ? (rhi - c1 - 1 + kTB) / kTB : 0;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nb > 0 ? nb * nb : 1);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = c0 == 0 ? 0 : 1;    // the first block follows the band fill normally
+      cudaError_t e = cudaLaunchKernelEx(&cfg, k_lu_block, Nc, m, c0, (const double*)b.band,
+                                         b.band, b.Fc, b.status);
+      if (e != cudaSuccess) return e;
+      ++launches;
+    }
+    count_launches(launches);
+    return cudaGetLastError();
+  }
   for (int c0 = 0; c0 < Nc; c0 += kTB) {
     const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
     const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
@@ -1119,7 +1270,10 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
     if (e != cudaSuccess) return e;
     k_ldlt_solve<<<1, 256, smem, s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
   } else {
-    k_band_solve<<<1, 256, Nc * sizeof(double), s>>>(Nc, m, b.band, b.rc, b.pc);
+    const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
+    cudaError_t e = raise_smem_limit(k_band_lu_solve, smem);
+    if (e != cudaSuccess) return e;
+    k_band_lu_solve<<<1, 256, smem, s>>>(Nc, m, b.Fc, b.rc, b.pc);
   }
   count_launches(1);
   return cudaGetLastError();
