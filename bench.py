@@ -99,6 +99,11 @@ def parse():
 VARIANT = {}      # solver options beyond the workload's (--jacobian, --cf)
 
 
+def variant_suffix():
+    return ((" full-Jacobian Newton" if VARIANT.get("jacobian") else "")
+            + (" correction functions" if VARIANT.get("cf") else ""))
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -318,8 +323,7 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
         "config": {"workload": f"{w.name} {'mixed FP32/FP64' if w.precision else 'FP64'} C-AMS basis B{w.basis} "
                                f"{'MSFE' if w.restriction == 0 else 'MSFV'} n_post={w.n_post} "
                                f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}"
-                               + (" full-Jacobian Newton" if VARIANT.get("jacobian") else "")
-                               + (" correction functions" if VARIANT.get("cf") else ""),
+                               + variant_suffix(),
                    "cells": N, "time_step": "first (full basis build) from p=0",
                    "l2": "inputs > L2 (4M-cell fields, >1 GB touched per step)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -480,7 +484,7 @@ def run_reference(args, w, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "sample": sample},
+            "config": {"workload": w.name + variant_suffix(), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

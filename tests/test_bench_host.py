@@ -1,0 +1,42 @@
+"""Host-side parts of bench.py that need no GPU: the oracle leg (the
+reference arm and cpu_baseline) on a small sample, with and without the
+NEXT-4 solver variants, and the JSON line of the reference arm."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.fixture
+def bench():
+    import bench as b
+    saved = dict(b.VARIANT)
+    yield b
+    b.VARIANT.clear()
+    b.VARIANT.update(saved)
+
+
+@pytest.mark.parametrize("variant", [{}, {"jacobian": 1}, {"cf": True}])
+def test_oracle_sample_runs_the_variants(bench, variant):
+    bench.VARIANT.clear()
+    bench.VARIANT.update(variant)
+    w = bench.WORKLOADS["2d-40x40"]
+    v, dt, st, sample = bench.oracle_sample(w, 0, sub=(20, 20, 1))
+    assert st.converged and v > 0 and dt > 0
+    assert sample.startswith("20x20x1 corner box")
+
+
+def test_reference_arm_line(bench):
+    class Args:
+        seed, steps, warmup = 0, 1, 0
+    bench.VARIANT.clear()
+    bench.VARIANT["jacobian"] = 1
+    w = bench.WORKLOADS["2d-40x40"]
+    out = bench.run_reference(Args, w, 0, 1)
+    assert out["impl"] == "reference" and out["unit"] == bench.UNIT
+    assert out["config"]["workload"].endswith("full-Jacobian Newton")
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+    assert bench.run_reference(Args, w, 1, 2) is None          # only rank 0 runs it
