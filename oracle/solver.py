@@ -209,13 +209,15 @@ def check_fixed(pb: Problem, wb: Wirebasket):
         raise ValueError("a fixed cell is a coarse node")
 
 
-def run(pb: Problem, opt: Options, p0: np.ndarray, dt: float, steps: int):
-    """Several implicit steps; returns (p, [StepStats per step])."""
+def run(pb: Problem, opt: Options, p0: np.ndarray, dt, steps: int):
+    """Several implicit steps of size dt (a number, or one per step);
+    returns (p, [StepStats per step])."""
     wb = build_wirebasket(pb.grid, opt.coarse)
     state = BasisState(wb)
+    dts = [float(dt)] * steps if np.ndim(dt) == 0 else [float(v) for v in dt][:steps]
     p = p0.copy()
     stats = []
-    for _ in range(steps):
-        p, st = solve_step(pb, wb, state, opt, p, dt)
+    for d in dts:
+        p, st = solve_step(pb, wb, state, opt, p, d)
         stats.append(st)
     return p, stats

@@ -54,6 +54,8 @@ class Workload:
     precision: int = 0        # engine option: 0 = FP64, 1 = FP32 preconditioner in FP64 refinement
     alpha: float = 1.0        # grid aspect ratio: dx / alpha = dy = dz
     seeds: tuple = (0,)
+    lnk_mean: float = 0.0     # mean of ln k
+    t_stars: tuple = ()       # end times t* of the steps (non-uniform steps); () = steps x dt_star
 
     @property
     def n_cells(self):
@@ -104,6 +106,26 @@ for _a, _cb in ((1, (8, 8, 8)), (5, (2, 8, 8)), (10, (2, 8, 8))):
         name=_n, nx=64, ny=64, nz=64, coarse=_cb, sigma=2.0, corr=(0.125, 0.125, 0.125),
         cov="spherical", law=1, c_or_eta=1.0, bc="lines", steps=1, dt_star=0.4, basis=4,
         restriction=0, n_post=5, nl_tol=1e-6, alpha=float(_a), seeds=tuple(range(20)))
+
+
+# Test Case 1 of Sec. 4.3.1: permeability Sets 1-6 of Table 2 (ln k variance 4,
+# mean -1, spherical variogram; Sets 1-3 patchy with correlation lengths
+# 0.125 L, Sets 4-6 layered with (0.5, 0.03, 0.01 or 0.06) L and the longest
+# axis at 15 degrees from y), rho* = 1 + p* (eta = 1), Dirichlet 1 / 0 on the
+# west / east faces, three consecutive steps to t* = 0.4, 1 and 2, (B4), MSFE,
+# 5 ILU(0) post steps, coarsening 8^3.
+for _k, _n, _corr, _ang in ((1, 64, (0.125, 0.125, 0.125), 0.0),
+                            (2, 128, (0.125, 0.125, 0.125), 0.0),
+                            (3, 256, (0.125, 0.125, 0.125), 0.0),
+                            (4, 64, (0.03, 0.5, 0.01), 15.0),
+                            (5, 128, (0.03, 0.5, 0.06), 15.0),
+                            (6, 256, (0.03, 0.5, 0.01), 15.0)):
+    _name = f"3d-{_n}x{_n}x{_n}-set{_k}"
+    WORKLOADS[_name] = Workload(
+        name=_name, nx=_n, ny=_n, nz=_n, coarse=(8, 8, 8), sigma=2.0, corr=_corr,
+        cov="spherical", angle_deg=_ang, lnk_mean=-1.0, law=1, c_or_eta=1.0,
+        steps=3, t_stars=(0.4, 1.0, 2.0), basis=4, restriction=0, n_post=5, nl_tol=1e-6,
+        seeds=tuple(range(20)))
 
 
 # The batched ensemble: independent realisations with sigma drawn uniformly
@@ -164,19 +186,25 @@ def make_inputs(w: Workload, seed: int | None = None):
     """Concrete arrays and scalars for one realisation of workload w.
 
     Returns a dict with grid spacing, kx/ky/kz (float64, length N, index
-    x + nx*(y + ny*z)), the time step dt, the initial pressure p0 (zero, as
+    x + nx*(y + ny*z)), the first time step dt and every step's (dts), the
+    initial pressure p0 (zero, as
     in Sec. 4.1.3), the source list (cell ids and volumetric rates q_i dV_i)
     and the prescribed cells with their pressures.
     """
     seed = w.seeds[0] if seed is None else seed
     kx, ky, kz = lognormal_permeability(
-        w.nx, w.ny, w.nz, w.sigma, w.corr, seed, kind=w.cov,
+        w.nx, w.ny, w.nz, w.sigma, w.corr, seed, mean=w.lnk_mean, kind=w.cov,
         kz_ratio=w.kz_ratio, angle_deg=w.angle_deg)
     h = 1.0 / w.nx
     k_bar = math.exp(float(np.mean(np.log(kx))))
     dp = 1.0
     tau = w.mu * w.phi * w.alpha ** 2 / (k_bar * dp)
-    dt = w.dt_star * tau
+    if w.t_stars:
+        ends = [0.0] + [float(t) for t in w.t_stars]
+        dts = [(b - a) * tau for a, b in zip(ends[:-1], ends[1:])]
+    else:
+        dts = [w.dt_star * tau] * w.steps
+    dt = dts[0]
     src_cell = np.zeros(0, dtype=np.int32)
     src_rate = np.zeros(0, dtype=np.float64)
     fix_cell = np.zeros(0, dtype=np.int32)
@@ -197,7 +225,7 @@ def make_inputs(w: Workload, seed: int | None = None):
         src_rate = np.concatenate([w.well_rate * tsum[inj], -w.well_rate * tsum[prod]])
     return dict(
         nx=w.nx, ny=w.ny, nz=w.nz, dx=w.alpha * h, dy=h, dz=h,
-        kx=kx, ky=ky, kz=kz, dt=dt, tau=tau, k_bar=k_bar,
+        kx=kx, ky=ky, kz=kz, dt=dt, dts=dts, tau=tau, k_bar=k_bar,
         p0=np.zeros(w.n_cells), src_cell=src_cell, src_rate=src_rate,
         fix_cell=fix_cell, fix_value=fix_value,
         dirichlet=(w.bc == "dirichlet_we"), p_west=w.p_west, p_east=w.p_east,
