@@ -107,3 +107,30 @@ def test_ensemble_and_network_entry_points_reject_bad_arguments_without_a_gpu():
     assert lib.cams_net_adam(10, None, None, None, None, 1e-3, 0.9, 0.999, 1e-8, 0,
                              None) == cams.CAMS_EINVAL
     assert "Adam" in cams.cams_last_error()
+
+
+def test_binding_constants_match_header():
+    """Every #define CAMS_* integer constant of include/cams.h that the
+    binding mirrors has the header's value, and the quantity, status and
+    precision constants are all mirrored."""
+    from paper_1705_05783_gb300 import cams
+    txt = open(HEADER).read()
+    defs = dict(re.findall(r"^#define\s+(CAMS_\w+)\s+(-?\d+)", txt, re.M))
+    assert len(defs) > 20
+    for name, val in defs.items():
+        if hasattr(cams, name):
+            assert getattr(cams, name) == int(val), name
+    for name in defs:
+        if name.startswith(("CAMS_Q_", "CAMS_PREC_", "CAMS_E", "CAMS_OK", "CAMS_HOST", "CAMS_DEVICE")):
+            assert hasattr(cams, name), name
+
+
+def test_variant_options_are_checked_before_the_gpu():
+    from paper_1705_05783_gb300 import cams
+    g = cams.cams_grid(10, 10, 1, 0.1, 0.1, 0.1)
+    f = cams.cams_fluid(0, 0.1, 1.0, 1.0, 0.1)
+    k = np.ones(100)
+    o = cams.make_options((5, 5, 1), jacobian=3)
+    with pytest.raises(cams.CamsError) as e:
+        cams.cams_setup(g, f, o, k)
+    assert e.value.code == cams.CAMS_EINVAL and "jacobian" in cams.cams_last_error()
