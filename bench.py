@@ -160,6 +160,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def class_rooflines(prof, n_cells, precision, peak):
+    """Achieved algorithmic GB/s and the fraction of the HBM peak of every
+    kernel class with a byte count, from the live per-class profile
+    {class: (launch groups, total ms, kernels)}: bytes per cell x cells per
+    launch group / average group time."""
+    table = BYTES_PER_CELL_MIXED if precision else BYTES_PER_CELL
+    out = {}
+    for k, (n_l, ms_tot, _) in prof.items():
+        if k not in table or n_l <= 0 or ms_tot <= 0.0:
+            continue
+        avg_ms = ms_tot / n_l
+        gbs = table[k] * n_cells / (avg_ms / 1e3) / 1e9
+        out[k] = {"launches": int(n_l), "avg_ms": avg_ms, "gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -338,6 +354,7 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
                      "traffic": MEASURED_TRAFFIC.get((w.name, dom)),
                      "bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": avg_ms},
+        "kernel_roofline": class_rooflines(prof, N, w.precision, peak),
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -40,3 +40,18 @@ def test_reference_arm_line(bench):
     assert out["config"]["workload"].endswith("full-Jacobian Newton")
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
     assert bench.run_reference(Args, w, 1, 2) is None          # only rank 0 runs it
+
+
+def test_class_rooflines(bench):
+    """Per-class achieved bandwidth: algorithmic bytes of one launch group
+    over its average time, against the peak; classes without a byte count
+    or without launches are left out."""
+    prof = {"residual": (10, 5.0, 20), "ilu_fwd": (50, 40.0, 50), "coarse_solve": (45, 17.0, 45),
+            "restrict": (0, 0.0, 0)}
+    out = bench.class_rooflines(prof, 4_000_000, 0, 6800.0)
+    assert set(out) == {"residual", "ilu_fwd"}
+    r = out["residual"]
+    assert r["launches"] == 10 and abs(r["avg_ms"] - 0.5) < 1e-12
+    assert abs(r["gbs"] - 56 * 4e6 / 0.5e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["gbs"] / 6800.0) < 1e-12
+    mixed = bench.class_rooflines(prof, 4_000_000, 1, 6800.0)
+    assert mixed["ilu_fwd"]["gbs"] < out["ilu_fwd"]["gbs"]        # 4-byte operands in mixed precision
