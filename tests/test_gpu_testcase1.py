@@ -4,9 +4,10 @@ copies (24^3 cells, coarse 8^3) of permeability Set 1 (patchy) and Set 4
 the paper's three steps to t* = 0.4, 1 and 2 (non-uniform steps), FP64 and
 mixed precision.
 
-Tolerances: converged pressures (relative 1e-8 on ||eps||) within 1e-8
-relative L_inf in FP64 and 1e-6 in mixed precision after the third step,
-Newton counts within one per step."""
+Tolerances: converged pressures (relative 1e-8 on ||eps||) within 1e-7
+relative L_inf in FP64 and 1e-6 in mixed precision after the third step (two
+iterates that both meet the stopping test differ by up to that much once an
+inner count differs by one), Newton counts within one per step."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,7 @@ def _oracle(name):
 
 
 @pytest.mark.parametrize("name", ["3d-64x64x64-set1", "3d-64x64x64-set4"])
-@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-7), (1, 1e-6)])
 def test_three_steps_to_t_star_2(cams, name, precision, tol):
     case = _case(name, precision)
     h, bc, keep = gpu_handle(case)
