@@ -9,11 +9,13 @@ the library itself never does, and it shares no code with the CUDA path.
 
 Layout (one module per part of the method):
   problem     Sec. 2: grid, fluid, TPFA transmissibilities, nonlinear
-              residual, Eq. 19 error, linearised system of Eqs. 3-6
+              residual, Eq. 19 error, linearised system of Eqs. 3-6 (and
+              the full-Jacobian variant of that linearisation)
   wirebasket  Sec. 3: primal/dual-coarse grids, vertex/edge/face/interior
               classification of fine cells and the local entities
-  basis       Sec. 3, Eqs. 8-11: basis operators and the staged
-              reduced-problem construction of the prolongation P
+  basis       Sec. 3, Eqs. 8-11: basis operators, the staged
+              reduced-problem construction of the prolongation P and the
+              correction functions
   coarse      Sec. 3, Eqs. 7, 13-15: MSFE/MSFV restriction, R A P and
               the coarse direct solve
   ilu         the ILU(0) second-stage smoother of Sec. 3 / Table 1
