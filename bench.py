@@ -93,6 +93,9 @@ def parse():
                     help="the full-Jacobian Newton step (flux density differentiated)")
     ap.add_argument("--cf", action="store_true",
                     help="correction functions before every multiscale stage")
+    ap.add_argument("--restriction", type=int, choices=[0, 1, 2], default=None,
+                    help="override the workload's restriction: 0 MSFE, 1 MSFV, "
+                         "2 MSFE then a closing MSFV correction")
     return ap.parse_args()
 
 
@@ -337,7 +340,7 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.precision else "f64",
         "data": "synthetic",
         "config": {"workload": f"{w.name} {'mixed FP32/FP64' if w.precision else 'FP64'} C-AMS basis B{w.basis} "
-                               f"{'MSFE' if w.restriction == 0 else 'MSFV'} n_post={w.n_post} "
+                               f"{('MSFE', 'MSFV', 'MSFE+closing MSFV')[w.restriction]} n_post={w.n_post} "
                                f"coarse {w.coarse[0]}x{w.coarse[1]}x{w.coarse[2]} tol {w.nl_tol:g}"
                                + variant_suffix(),
                    "cells": N, "time_step": "first (full basis build) from p=0",
@@ -501,7 +504,8 @@ def run_reference(args, w, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name + variant_suffix(), "sample": sample},
+            "config": {"workload": w.name + variant_suffix(), "sample": sample,
+                       "restriction": ("MSFE", "MSFV", "MSFE+closing MSFV")[w.restriction]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -532,6 +536,8 @@ def main():
             print(json.dumps(out), flush=True)
         return
     w = WORKLOADS[args.workload]
+    if args.restriction is not None:
+        w = w.with_(restriction=args.restriction)
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

@@ -55,3 +55,12 @@ def test_class_rooflines(bench):
     assert abs(r["gbs"] - 56 * 4e6 / 0.5e-3 / 1e9) < 1e-9 and abs(r["frac"] - r["gbs"] / 6800.0) < 1e-12
     mixed = bench.class_rooflines(prof, 4_000_000, 1, 6800.0)
     assert mixed["ilu_fwd"]["gbs"] < out["ilu_fwd"]["gbs"]        # 4-byte operands in mixed precision
+
+
+def test_restriction_override_reaches_the_oracle_leg(bench):
+    class Args:
+        seed, steps, warmup = 0, 1, 0
+    bench.VARIANT.clear()
+    w = bench.WORKLOADS["2d-40x40"].with_(restriction=2)
+    out = bench.run_reference(Args, w, 0, 1)
+    assert out["config"]["restriction"] == "MSFE+closing MSFV"
