@@ -163,6 +163,9 @@ def make_bc(dirichlet=True, p_west=1.0, p_east=0.0, src_cell=None, src_rate=None
 def make_options(coarse, basis=4, restriction=0, n_pre=0, n_post=1, lin_rtol=0.1,
                  nl_tol=1e-6, tol_abs=False, adapt_theta=0.1, max_newton=50, max_cams=200,
                  memspace=CAMS_HOST, precision=CAMS_PREC_FP64, cf=False, jacobian=0):
+    """A cams_options (fields as documented in cams.h); cf turns the
+    correction functions on, jacobian = 1 selects the full-Jacobian Newton
+    step."""
     o = cams_options()
     o.coarse[:] = [int(v) for v in coarse]
     o.basis, o.restriction, o.n_pre, o.n_post = int(basis), int(restriction), int(n_pre), int(n_post)
