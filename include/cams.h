@@ -231,6 +231,25 @@ int cams_selftest_wait(cams_handle* h);
  * default stream).  The stream must belong to the handle's device. */
 int cams_set_stream(cams_handle* h, void* stream);
 
+/* Choose between the handle's equivalent kernel schedules (for an autotuner;
+ * setup picks defaults):
+ *   ilu_cta         ILU(0) wavefront sweeps: 0 = one 8x4-row tile per warp,
+ *                   1 = 2x2 tiles per CTA with the edges inside a block in
+ *                   shared memory (the same arithmetic; results are bitwise
+ *                   equal); -1 = unchanged
+ *   coarse_cluster  symmetric (MSFE) coarse solve: 0 = one CTA, 1 = across a
+ *                   thread-block cluster (a different summation order); -1 =
+ *                   unchanged.  The general band solve has one schedule.
+ * Waits for the handle's stream and drops its captured iteration graph (it
+ * is captured again at the next iteration).  Errors: CAMS_EINVAL (null
+ * handle, a value outside {-1, 0, 1}, a schedule this GPU or grid cannot run,
+ * the level-scheduled sweeps of CAMS_ILU_LEVEL=1), CAMS_ECUDA. */
+int cams_set_schedule(cams_handle* h, int ilu_cta, int coarse_cluster);
+
+/* The handle's current schedule (the values of cams_set_schedule); either
+ * pointer may be NULL. */
+int cams_get_schedule(cams_handle* h, int* ilu_cta, int* coarse_cluster);
+
 /* (a2) Linear-system population (Table 1, step 1): from p_nu (iterate) and
  * p_n (previous time level) build A = C + A~ and f (Eq. 6, Eqs. 3-5, rows
  * scaled by V rho^nu), the error eps of Eq. 19 and its 2-norm.  The handle's

@@ -29,7 +29,7 @@ PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_fa
                 "ilu_bwd", "ilu_resid")
 
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
-           "cams_set_stream",
+           "cams_set_stream", "cams_set_schedule", "cams_get_schedule",
            "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve",
            "cams_ensemble_solve", "cams_set_surrogate", "cams_surrogate_data",
            "cams_net_conv_forward", "cams_net_conv_backward", "cams_net_mse", "cams_net_energy",
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
         "cams_setup": (C.c_int, [C.POINTER(cams_grid), C.POINTER(cams_fluid),
                                  C.POINTER(cams_options), P, P, P, C.POINTER(P)]),
         "cams_set_stream": (C.c_int, [P, P]),
+        "cams_set_schedule": (C.c_int, [P, C.c_int, C.c_int]),
+        "cams_get_schedule": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "cams_set_permeability": (C.c_int, [P, P, P, P]),
         "cams_profile": (C.c_int, [P, C.c_int]),
         "cams_selftest_wait": (C.c_int, [P]),
@@ -215,6 +217,17 @@ def launches(h):
 
 def cams_set_stream(h, stream_ptr: int):
     _check(_lib.cams_set_stream(h, C.c_void_p(stream_ptr)), h)
+
+
+def cams_set_schedule(h, ilu_cta=-1, coarse_cluster=-1):
+    _check(_lib.cams_set_schedule(h, int(ilu_cta), int(coarse_cluster)), h)
+
+
+def cams_get_schedule(h):
+    """(ilu_cta, coarse_cluster) of the handle."""
+    a, b = C.c_int(0), C.c_int(0)
+    _check(_lib.cams_get_schedule(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
 
 
 def cams_assemble(h, p_nu, p_n, dt, bc):

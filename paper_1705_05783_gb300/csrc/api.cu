@@ -1000,6 +1000,36 @@ int cams_set_stream(cams_handle* h, void* stream) {
   return CAMS_OK;
 }
 
+int cams_set_schedule(cams_handle* h, int ilu_cta, int coarse_cluster) {
+  if (!h) return CAMS_EINVAL;
+  if (ilu_cta < -1 || ilu_cta > 1 || coarse_cluster < -1 || coarse_cluster > 1)
+    return fail(h, CAMS_EINVAL, "schedule values must be -1, 0 or 1");
+  if (ilu_cta >= 0 && !h->ilu_pipelined)
+    return fail(h, CAMS_EINVAL, "the level-scheduled sweeps have no tile schedule");
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, h->dev));
+  if (ilu_cta == 1 && !h->ilu_cta && !ilu_cta_ok(h->g, (int)prop.sharedMemPerBlockOptin))
+    return fail(h, CAMS_EINVAL, "2x2 tile blocks do not fit this grid's shared memory");
+  if (coarse_cluster == 1 && !h->coarse_cluster &&
+      !coarse_cluster_ok(h->c.Nc, (int)prop.sharedMemPerBlockOptin))
+    return fail(h, CAMS_EINVAL, "the cluster coarse solve is not available for this coarse grid");
+  CK(cudaStreamSynchronize(h->stream));
+  if (ilu_cta >= 0) h->ilu_cta = ilu_cta == 1;
+  if (coarse_cluster >= 0) h->coarse_cluster = coarse_cluster == 1;
+  if (h->step_exec) {                          // it holds the previous schedule's kernels
+    CK(cudaGraphExecDestroy(h->step_exec));
+    h->step_exec = nullptr;
+  }
+  return CAMS_OK;
+}
+
+int cams_get_schedule(cams_handle* h, int* ilu_cta, int* coarse_cluster) {
+  if (!h) return CAMS_EINVAL;
+  if (ilu_cta) *ilu_cta = h->ilu_cta ? 1 : 0;
+  if (coarse_cluster) *coarse_cluster = h->coarse_cluster ? 1 : 0;
+  return CAMS_OK;
+}
+
 int cams_assemble(cams_handle* h, const double* p_nu, const double* p_n, double dt,
                   const cams_bc* bc, double* eps_norm_out) {
   if (!h) return CAMS_EINVAL;
