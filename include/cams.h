@@ -384,13 +384,13 @@ int cams_get_int(cams_handle* h, int what, int* dst);
 
 /* Residual r = f - A p and ||r||_2 of a symmetric 7-point system, without
  * allocating any device memory.  The paper has no counterpart: this is a
- * service for callers that cannot call cudaMalloc -- code being captured
- * into a CUDA graph in global capture mode (allocation calls are refused
- * during capture), frameworks that give all device memory to their own pool,
- * and time-critical loops that cannot afford the device-wide synchronisation
- * cudaMalloc/cudaFree imply.  The reduction's scratch is a file-scope static
- * device array of 32769 doubles (256 KiB), present on every GPU that loads
- * the library until the process exits.
+ * service for callers that cannot call cudaMalloc -- frameworks that give
+ * all device memory to their own pool or arena (an allocation behind the
+ * pool's back can fail or fragment it) and time-critical loops that cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree imply.  The
+ * reduction's scratch is a file-scope static device array of 32769 doubles
+ * (256 KiB), present on every GPU that loads the library until the process
+ * exits.
  *   nx, ny, nz       grid (cell i = x + nx*(y + ny*z)); at most 268,435,456
  *                    cells (32768 partial sums of 8192 cells), else
  *                    CAMS_EINVAL with a message naming the limit
@@ -402,11 +402,13 @@ int cams_get_int(cams_handle* h, int what, int* dst);
  *   norm_out         HOST double receiving ||r||_2, or NULL (not both NULL)
  *   stream           cudaStream_t (NULL = default stream) of the current device
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU race and must be serialised by the caller.  The call returns
- * when the result is ready.  Errors: CAMS_EINVAL (sizes, null pointers),
- * CAMS_ECUDA; the message is cams_last_error(NULL). */
+ * (cudaGetSymbolAddress) with that device current, and so does the first
+ * call after the device's current context has changed (cudaDeviceReset
+ * reloads the module); make the first call on a device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.  The call returns when the result
+ * is ready.  Errors: CAMS_EINVAL (sizes, null pointers), CAMS_ECUDA; the
+ * message is cams_last_error(NULL). */
 int cams_residual_norm_noalloc(int nx, int ny, int nz, const double* diag, const double* ax,
                                const double* ay, const double* az, const double* f,
                                const double* p, double* r, double* norm_out, void* stream);

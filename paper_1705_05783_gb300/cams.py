@@ -339,14 +339,17 @@ def cams_last_error(h=None) -> str:
     return _lib.cams_last_error(h).decode()
 
 
-def cams_residual_norm_noalloc(nx, ny, nz, diag, ax, ay, az, f, p, r=None, stream_ptr=0):
+def cams_residual_norm_noalloc(nx, ny, nz, diag, ax, ay, az, f, p, r=None, stream_ptr=0,
+                               want_norm=True):
     """||f - A p||_2 (and r, if given) with no device allocation; device
-    tensors in, Python float out.  Returns (status, norm)."""
+    tensors in, Python float out (None when want_norm is false, which passes
+    a null norm_out).  Returns (status, norm)."""
     out = C.c_double(0.0)
     code = _lib.cams_residual_norm_noalloc(int(nx), int(ny), int(nz), _ptr(diag), _ptr(ax),
                                            _ptr(ay), _ptr(az), _ptr(f), _ptr(p), _ptr(r),
-                                           C.byref(out), C.c_void_p(stream_ptr))
-    return code, out.value
+                                           C.byref(out) if want_norm else None,
+                                           C.c_void_p(stream_ptr))
+    return code, (out.value if want_norm else None)
 
 
 def cams_destroy(h):

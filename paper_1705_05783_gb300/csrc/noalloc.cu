@@ -1,21 +1,23 @@
 // Residual and 2-norm of a 7-point system with no device allocation.
 //
-// Some callers cannot call cudaMalloc: code being captured into a CUDA graph
-// in global capture mode (allocation calls are refused during capture),
-// frameworks that hand all device memory to their own pool or arena, and
-// time-critical loops that must not pay the device-wide synchronisation that
-// cudaMalloc/cudaFree imply.  This entry point serves them: the caller passes
-// the system and the output buffers, and the reduction's scratch (one partial
-// sum per block of cells plus the total) lives in a file-scope static device
-// array instead of a handle allocation.
+// Some callers cannot call cudaMalloc: frameworks that hand all device memory
+// to their own pool or arena (a cudaMalloc behind the pool's back can fail or
+// fragment it), and time-critical loops that must not pay the device-wide
+// synchronisation that cudaMalloc/cudaFree imply.  This entry point serves
+// them: the caller passes the system and the output buffers, and the
+// reduction's scratch (one partial sum per block of cells plus the total)
+// lives in a file-scope static device array instead of a handle allocation.
 //
 // The array exists once per device that loads the library and stays there
-// until the process exits.  Its device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the
-// first call on the device.  Every call shares the array: calls that overlap
-// on the GPU (different streams, or several host threads) race on it and must
-// be serialised by the caller.  Each call overwrites every slot it reads, so
-// nothing left by an earlier call leaks into a result.
+// until the process exits.  In host code its name is only a host-side stand-in,
+// so its device address is looked up with cudaGetSymbolAddress, with the
+// device current: on the first call on a device, and again whenever the
+// device's current context differs from the one the address was taken in (the
+// module is loaded anew after cudaDeviceReset, and the array may move).
+// Every call shares the array: calls that overlap on the GPU (different
+// streams, or several host threads) race on it and must be serialised by the
+// caller.  Each call overwrites every slot it reads, so nothing left by an
+// earlier call leaks into a result.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -29,11 +31,36 @@ constexpr int kMaxBlocks = 32768;       // partial sums the scratch holds (256 K
 constexpr long long kMaxCells = (long long)kCellsPerBlock * kMaxBlocks;   // 268,435,456
 constexpr int kMaxDevices = 64;
 
+// cuCtxGetCurrent of the driver API, reached through the runtime (no link
+// against libcuda); its CUcontext is held as an opaque pointer.
+using CtxGetCurrentFn = int (*)(void**);
+
 // partial sums [0, kMaxBlocks) and the total at [kMaxBlocks]
 static __device__ __align__(256) double g_noalloc_scratch[kMaxBlocks + 1];
 
 std::mutex g_mutex;
 double* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};      // context the address was taken in
+CtxGetCurrentFn g_ctx_get = nullptr;
+bool g_ctx_get_tried = false;
+
+// The calling thread's current context, or null when it cannot be told.
+void* current_context() {
+  if (!g_ctx_get_tried) {
+    g_ctx_get_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get = reinterpret_cast<CtxGetCurrentFn>(fn);
+    else
+      cudaGetLastError();
+  }
+  void* ctx = nullptr;
+  if (!g_ctx_get || g_ctx_get(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 __device__ double block_sum_na(double v) {
   __shared__ double sh[32];
@@ -111,13 +138,15 @@ extern "C" int cams_residual_norm_noalloc(int nx, int ny, int nz, const double* 
   if (dev < 0 || dev >= kMaxDevices) return fail_na(CAMS_EINVAL, "device ordinal out of range");
   double* scratch = nullptr;
   {
-    // set-up, once per device, with that device current
+    // set-up, once per device and context, with that device current
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
       e = cudaGetSymbolAddress(reinterpret_cast<void**>(&scratch), g_noalloc_scratch);
       if (e != cudaSuccess)
         return fail_na(CAMS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_scratch_addr[dev] = scratch;
+      g_scratch_ctx[dev] = current_context();   // the lookup made the primary context current
     }
     scratch = g_scratch_addr[dev];
   }
