@@ -446,6 +446,68 @@ def test_newton_control_counts(rng):
         assert s.eps_hist[-1] < 1e-8 * s.eps_hist[0] <= s.eps_hist[-2]
 
 
+def _iteration_matrix(A, P, R, lu, LU, n_post):
+    """G with e -> G e the error propagation of one C-AMS iteration, built
+    column by column from the oracle's own iteration on f = 0 (exact solution
+    0, so the iterate is the error)."""
+    n = A.shape[0]
+    f0 = np.zeros(n)
+    return np.column_stack([cams_iteration(A, f0, np.eye(n)[:, j], P, R, lu, LU, 0, n_post)
+                            for j in range(n)])
+
+
+@pytest.mark.parametrize("n_post", [1, 2])
+def test_inner_stopping_rule_on_an_eigenvector(rng, n_post):
+    """Sec. 4.1.1: the inner loop runs C-AMS iterations until
+    ||r^i||_2 / ||r^0||_2 < 0.1, r^0 being the residual of the new
+    linearisation before its first iteration.  On a linear problem (rho
+    constant, one linearisation is exact) started at p* + v, v an eigenvector
+    of the iteration matrix G for its largest eigenvalue lam (real, since
+    MSFE and the symmetric ILU(0) factor make G similar to an A-self-adjoint
+    operator), every iteration scales the error and the residual by lam, so
+    the count is the smallest i with lam^i < 0.1.  Taking r^0 after the first
+    iteration would give one more; comparing with the previous iterate, or
+    a missed cap, would never stop before max_cams."""
+    g = _grid(12, 10, 1)
+    pb = _problem(g, _lognormal(g.N, rng), c=0.0)           # rho = 1: linear
+    opt = Options(coarse=(3, 5, 1), basis=4, n_post=n_post, nl_tol=1e-30, max_newton=1,
+                  max_cams=500)
+    lin = assemble(pb, np.zeros(g.N), np.zeros(g.N), 0.01)
+    A = lin.A.tocsr()
+    assert abs(A - A.T).max() == 0.0
+    wb = build_wirebasket(g, opt.coarse)
+    P = prolongation(basis_operator(pb, 4, lin.rho, lin.c, np.zeros(g.N), 0.01), wb).to_csr(wb.Nc)
+    R = restriction(0, P, wb)
+    lu = coarse_factor(coarse_operator(R, A, P))
+    LU = ilu0(A)
+    G = _iteration_matrix(A, P, R, lu, LU, n_post)
+    lam, V = np.linalg.eig(G)
+    k = int(np.argmax(lam.real))
+    lmax = lam[k].real
+    assert abs(lam[k].imag) < 1e-12 and 0.2 < lmax < 0.99
+    v = V[:, k].real
+    v /= np.abs(v).max()
+    count = int(np.ceil(np.log(0.1) / np.log(lmax)))
+    assert lmax ** count < 0.1 * (1 - 1e-6) and lmax ** (count - 1) > 0.1 * (1 + 1e-6)
+    pstar = spl.spsolve(A.tocsc(), lin.f)
+    # the residual history of the oracle's loop follows lam^i
+    p, hist = pstar + 1e-3 * v, []
+    for _ in range(count + 1):
+        hist.append(np.linalg.norm(lin.f - A @ p))
+        p = cams_iteration(A, lin.f, p, P, R, lu, LU, 0, n_post)
+    ratios = np.array(hist[1:]) / np.array(hist[:-1])
+    np.testing.assert_allclose(ratios, lmax, rtol=1e-6)
+    # the solver's inner loop stops at exactly that count
+    state = BasisState(wb)
+    _, st = solve_step(pb, wb, state, opt, np.zeros(g.N), 0.01, p_init=pstar + 1e-3 * v)
+    assert st.cams_per_newton == [count]
+    # and at the cap when the target is out of reach (and still re-linearises, R14)
+    opt2 = Options(coarse=(3, 5, 1), basis=4, n_post=n_post, lin_rtol=1e-30, nl_tol=1e-30,
+                   max_newton=2, max_cams=7)
+    _, st2 = solve_step(pb, wb, BasisState(wb), opt2, np.zeros(g.N), 0.01, p_init=pstar + 1e-3 * v)
+    assert st2.cams_per_newton == [7, 7] and not st2.converged
+
+
 def test_msfe_then_msfv_closing_correction(rng):
     """Restriction 2 (Sec. 4.3): the step converges with MSFE exactly as with
     restriction 0, then one MSFV coarse correction of the last linearisation
