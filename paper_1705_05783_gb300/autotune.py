@@ -38,6 +38,9 @@ def tune(h, p_n, dt, bc, iters=3, repeats=2, candidates=CANDIDATES, clock=time.p
             cams.cams_set_schedule(h, *cand)
         except cams.CamsError:
             continue
+        # one untimed run: it captures the iteration graph of the new schedule
+        cams.cams_assemble(h, p_n, p_n, dt, bc)
+        cams.cams_iterate(h, 1)
         best = float("inf")
         for _ in range(repeats):
             cams.cams_assemble(h, p_n, p_n, dt, bc)

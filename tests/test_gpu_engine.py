@@ -130,3 +130,47 @@ def test_device_memspace_matches_host(cams):
     finally:
         cams.cams_destroy(hd)
     assert np.array_equal(pd.cpu().numpy(), p)
+
+
+def test_schedule_switch_on_a_live_handle(cams):
+    """cams_set_schedule on a handle that has already iterated (and captured
+    its iteration graph): every accepted ILU(0) tile schedule continues from
+    the same state with the same bits, since the schedules share the per-cell
+    arithmetic; the coarse-solve schedules sum in different orders, so their
+    iterates agree to rounding.  A refused schedule leaves the handle's
+    schedule unchanged."""
+    case = make_case("3d-200x200x100", nx=40, ny=40, nz=20, coarse=(10, 10, 10), n_post=3)
+    h, bc, keep = gpu_handle(case)
+    try:
+        rng = np.random.default_rng(5)
+        p_nu = rng.uniform(0, 1, case.N)
+        cams.cams_assemble(h, p_nu, p_nu, case.inp["dt"], bc)
+        cams.cams_update_basis(h, True)
+        runs = {}
+        for ilu in (0, 1):
+            for cl in (0, 1):
+                try:
+                    cams.cams_set_schedule(h, ilu, cl)
+                except cams.CamsError:
+                    assert cams.cams_get_schedule(h) != (ilu, cl)
+                    continue
+                assert cams.cams_get_schedule(h) == (ilu, cl)
+                cams.cams_assemble(h, p_nu, p_nu, case.inp["dt"], bc)
+                res = cams.cams_iterate(h, 3)
+                p = cams.cams_get(h, cams.CAMS_Q_PRESSURE, np.zeros(case.N))
+                runs[(ilu, cl)] = (res, p)
+        assert runs
+        for cl in (0, 1):
+            if (0, cl) in runs and (1, cl) in runs:
+                assert np.array_equal(runs[(0, cl)][0], runs[(1, cl)][0])
+                assert np.array_equal(runs[(0, cl)][1], runs[(1, cl)][1])
+        ps = [p for _, p in runs.values()]
+        for p in ps[1:]:
+            assert np.abs(p - ps[0]).max() <= 1e-12 * np.abs(ps[0]).max()
+        # a refused value leaves the schedule as it was
+        before = cams.cams_get_schedule(h)
+        with pytest.raises(cams.CamsError):
+            cams.cams_set_schedule(h, 2, 0)
+        assert cams.cams_get_schedule(h) == before
+    finally:
+        cams.cams_destroy(h)
