@@ -6,8 +6,8 @@ Tolerances are relative to the largest magnitude of the compared quantity:
 pivots; the looser end for eps, which divides a flux sum by V rho), a bound
 derived from the local condition numbers for the basis values P and for
 R A P (see p_tolerance), 1e-10 for pressures after a few C-AMS iterations,
-and 1e-9 relative L_inf for converged pressures with Newton counts within
-+-1 and C-AMS counts within one per linearisation (the agreement that FP64
+and 1e-9 relative L_inf for converged pressures with the Newton count and
+the step's total C-AMS count each within one (the agreement that FP64
 rounding-order differences allow when both sides follow the same steps).
 """
 import numpy as np
@@ -18,7 +18,7 @@ import oracle
 from oracle.basis import basis_operator, prolongation
 from oracle.coarse import coarse_factor, coarse_operator, restriction
 from oracle.ilu import ilu0
-from oracle.solver import cams_iteration
+from oracle.solver import BasisState, cams_iteration, solve_step
 from oracle.wirebasket import build_wirebasket
 
 from _cases import coarse_from_gpu, gpu_handle, make_case, matrix_from_gpu, p_from_gpu
@@ -44,9 +44,12 @@ def p_tolerance(Ab, wb):
     """Forward-error bound of the basis values.  Both sides solve every local
     SPD system with a backward-stable direct method (dense pivoted LU on the
     CPU, banded LDL^T on the GPU), so their results differ by at most about
-    n * eps * cond(M_e) per entity, and errors pass on through the stages
+    eps * cond(M_e) per entity, and errors pass on through the stages
     (edge -> face -> interior).  The bound below takes the largest local
-    condition number (2-norm) times 64 * eps (float64), floored at 1e-12."""
+    condition number (2-norm) times eps (float64), floored at 1e-13.
+    Measured on the GPU (max |dP| over all slots): 7.5e-15 on the 2D
+    workload, 1.3e-10 on the layered wells field and 1.0e-13 on the 3D
+    12x8x6 case, 15 to 30 times below this bound."""
     from oracle.basis import PRows, entity_system
     P = PRows(wb.grid.N)
     kmax = 1.0
@@ -54,7 +57,7 @@ def p_tolerance(Ab, wb):
         M, _ = entity_system(Ab, wb, P, e)
         if M.shape[0] > 1:
             kmax = max(kmax, np.linalg.cond(M))
-    return max(1e-12, 64 * np.finfo(float).eps * kmax)
+    return max(1e-13, np.finfo(float).eps * kmax)
 
 
 def _pressures(case, seed=7):
@@ -121,7 +124,10 @@ def test_prolongation(cams, cname, basis):
         Ab = basis_operator(case.pb, basis, lin.rho, lin.c, p_n, dt)
         Po = prolongation(Ab, wb).to_csr(wb.Nc)
         Pg, vals, cols = p_from_gpu(h, N, wb.Nc)
-        assert np.abs((Pg - Po).toarray()).max() < p_tolerance(Ab, wb)
+        err = float(np.abs((Pg - Po).toarray()).max())
+        print(f"[prolongation {cname} B{basis}] max |dP| = {err:.3e}, "
+              f"cond bound {p_tolerance(Ab, wb):.3e}")
+        assert err < p_tolerance(Ab, wb)
         # unused slots hold exact zeros
         assert np.all(vals[cols < 0] == 0.0)
     finally:
@@ -146,7 +152,8 @@ def test_coarse_operator_and_ilu(cams, cname, R):
         P = prolongation(Ab, wb).to_csr(wb.Nc)
         Ac = coarse_operator(restriction(R, P, wb), lin.A, P)
         G, st = coarse_from_gpu(h, wb.nc)
-        assert _rel(G, Ac) < 1e-13 + 4 * p_tolerance(Ab, wb)
+        print(f"[coarse {cname} R{R}] rel |dRAP| = {_rel(G, Ac):.3e}")
+        assert _rel(G, Ac) < 1e-13 + p_tolerance(Ab, wb)
         if R == 0:
             assert np.array_equal(G, G.T)          # bitwise symmetric
         L, U = ilu0(lin.A)
@@ -193,42 +200,72 @@ def _run_both(cams, case, steps):
     try:
         p = case.inp["p0"].copy()
         out = []
-        for _ in range(steps):
+        for d in case.inp["dts"][:steps]:
             pn = p.copy()
-            st = cams.cams_solve(h, pn, case.inp["dt"], bc, p)
+            st = cams.cams_solve(h, pn, d, bc, p)
             out.append((p.copy(), st.newton_its, st.cams_its, st.basis_rebuilt,
                         list(st.cams_per_newton[:st.newton_its])))
     finally:
         cams.cams_destroy(h)
-    q, sto = oracle.run(case.pb, case.opt, case.inp["p0"], case.inp["dt"], steps)
-    return out, q, sto
+    wb = build_wirebasket(case.pb.grid, case.opt.coarse)
+    state = BasisState(wb)
+    q = case.inp["p0"].copy()
+    ref = []
+    for d in case.inp["dts"][:steps]:
+        q, so = solve_step(case.pb, wb, state, case.opt, q, d)
+        ref.append((q.copy(), so))
+    return out, ref
 
 
-@pytest.mark.parametrize("nl_tol", [1e-8, 1e-10])
-def test_solve_2d_five_steps(cams, nl_tol):
-    """The 2D 40x40 workload, five implicit steps."""
-    case = make_case("2d-40x40", nl_tol=nl_tol, steps=5)
-    steps = 5 if nl_tol == 1e-8 else 1
-    out, q, sto = _run_both(cams, case, steps)
-    pg, nwt, cit, rb, per = out[-1]
-    assert _rel(pg, q) < 1e-9
-    for (p, n, c, r, per), so in zip(out, sto):
-        assert abs(n - so.newton_its) <= 1
-        assert abs(c - so.cams_its) <= max(1, n)
-        assert r == so.basis_rebuilt
+def _assert_step_parity(out, ref, p_tol=1e-9):
+    """The bar of every FP64 step: both sides converged, the pressure within
+    p_tol relative L_inf, the Newton count and the step's total C-AMS count
+    each within one, and the adaptive rebuild counts equal."""
+    for k, ((p, n, c, r, per), (q, so)) in enumerate(zip(out, ref)):
+        msg = (f"step {k}: engine {n} Newton {c} C-AMS {per} rebuilt {r}; oracle "
+               f"{so.newton_its} Newton {so.cams_its} C-AMS {so.cams_per_newton} rebuilt "
+               f"{so.basis_rebuilt}; rel {_rel(p, q):.2e}")
+        assert so.converged, msg
+        assert _rel(p, q) < p_tol, msg
+        assert abs(n - so.newton_its) <= 1, msg
+        assert abs(c - so.cams_its) <= 1, msg
+        assert r == so.basis_rebuilt, msg
+
+
+@pytest.mark.parametrize("nl_tol,steps", [(1e-8, 5), (1e-10, 3)])
+def test_solve_2d_steps(cams, nl_tol, steps):
+    """The 2D 40x40 workload at 1e-8 over its five steps, and at 1e-10 over
+    the first three.  From the fourth step on, the last linearisation's
+    target (a few 1e-10 absolute) meets the FP64 rounding floor of f - A p on
+    this field: its inner count then depends on rounding noise (the oracle
+    itself needs 10 iterations there on x86 and 7 on Arm, against 7 before)
+    and the fifth step's last inner loop stalls above 0.1 r^0."""
+    case = make_case("2d-40x40", nl_tol=nl_tol, steps=steps)
+    out, ref = _run_both(cams, case, steps)
+    _assert_step_parity(out, ref)
+
+
+def test_solve_3d_statistics_two_steps(cams):
+    """The 4M-cell workload's statistics (sigma 3, correlation 0.1 L, 10^3
+    blocks, (B4) MSFE, 5 ILU(0) post steps) on a 40x40x20 cut, two steps
+    to a 1e-10 relative ||eps||."""
+    case = make_case("3d-200x200x100", nx=40, ny=40, nz=20, nl_tol=1e-10, steps=2)
+    out, ref = _run_both(cams, case, 2)
+    _assert_step_parity(out, ref)
 
 
 @pytest.mark.parametrize("R", [0, 1])
-def test_solve_3d_wells_adaptive(cams, R):
+@pytest.mark.parametrize("nl_tol,steps", [(1e-10, 1), (1e-9, 2)])
+def test_solve_3d_wells_adaptive(cams, R, nl_tol, steps):
     """Scaled-down 3D wells workload: (B1) basis with adaptive updates at
-    theta = 0.1, MSFE and MSFV, 5 ILU(0) post-smoothing steps, two steps."""
-    case = make_case("3d-100x100x50-wells", nx=40, ny=40, nz=20, restriction=R, steps=2,
-                     nl_tol=1e-6, max_cams=40)
-    out, q, sto = _run_both(cams, case, 2)
-    assert _rel(out[-1][0], q) < 1e-8
-    for (p, n, c, r, per), so in zip(out, sto):
-        assert abs(n - so.newton_its) <= 1
-        assert r == so.basis_rebuilt
+    theta = 0.1, MSFE and MSFV, 5 ILU(0) post-smoothing steps; the first
+    step to 1e-10 and two steps to 1e-9 (the second step's 1e-10 lies below
+    the FP64 floor: the oracle itself does not converge there within 50
+    linearisations).  With MSFV every inner loop runs to its cap of 60."""
+    case = make_case("3d-100x100x50-wells", nx=40, ny=40, nz=20, restriction=R, steps=steps,
+                     nl_tol=nl_tol, max_cams=60)
+    out, ref = _run_both(cams, case, steps)
+    _assert_step_parity(out, ref)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
@@ -238,8 +275,11 @@ def test_msfe_then_msfv_step(cams, precision, tol):
     oracle (whose correction zeroes the MSFV-restricted residual)."""
     case = make_case("3d-200x200x100", nx=24, ny=20, nz=12, coarse=(4, 5, 4), restriction=2,
                      steps=1, nl_tol=1e-9, precision=precision)
-    out, q, sto = _run_both(cams, case, 1)
+    out, ref = _run_both(cams, case, 1)
     pg, nwt, cit, rb, per = out[-1]
-    assert sto[0].msfv_final
+    q, so = ref[-1]
+    assert so.msfv_final
     assert _rel(pg, q) < tol
-    assert abs(nwt - sto[0].newton_its) <= 1
+    assert abs(nwt - so.newton_its) <= 1
+    if precision == 0:
+        assert abs(cit - so.cams_its) <= 1
