@@ -190,11 +190,13 @@ typedef struct {
 #define CAMS_PROF_RESIDUAL      7   /* r = f - A p with its norm */
 #define CAMS_PROF_RESTRICT      8   /* R r */
 #define CAMS_PROF_COARSE_SOLVE  9   /* band substitution */
-#define CAMS_PROF_PROLONG      10   /* p += P p_c */
+#define CAMS_PROF_PROLONG      10   /* p += P p_c (FP64), delta = P p_c (mixed precision) */
 #define CAMS_PROF_ILU_FWD      11   /* ILU(0) forward wavefront sweep */
-#define CAMS_PROF_ILU_BWD      12   /* ILU(0) backward wavefront sweep and update of p */
+#define CAMS_PROF_ILU_BWD      12   /* ILU(0) backward wavefront sweep */
 #define CAMS_PROF_ILU_RESID    13   /* D^{-1}(f - A p) feeding the forward sweep */
-#define CAMS_PROF_CLASSES      14
+#define CAMS_PROF_UPDATE       14   /* p += delta (mixed precision) */
+#define CAMS_PROF_ILU_APPLY    15   /* x += z after the backward sweep */
+#define CAMS_PROF_CLASSES      16
 
 /* (a1) Set up a solver for one grid and permeability field.
  * kx, ky, kz: permeability per cell (> 0, finite); ky and kz may alias kx.
@@ -376,6 +378,30 @@ int cams_net_energy(int B, int S, int C, int cx, const float* pred, const float*
                     double* scratch, void* stream);
 int cams_net_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                   float beta1, float beta2, float eps, int step, void* stream);
+
+/* The network on the tensor cores (tcgen05 MMAs: BF16 operands, FP32
+ * accumulation in tensor memory), the form the engine uses for inference
+ * whenever a patch fits (cubic coarse blocks up to b = 10, S = b + 1 <= 11).
+ * Each 3x3x3 layer is an implicit GEMM over the zero-padded patch: the 27
+ * taps are 27 shifted views of the patch's rows in shared memory.  Inputs,
+ * weights and hidden activations are rounded to BF16 (nearest, ties to
+ * even); biases, accumulation and the outputs below are FP32.  Device
+ * pointers; `work` is caller-owned device memory of at least
+ * cams_net_tc_work_bytes(B, S) bytes (cleared and used by the call).  The
+ * calls queue their work on `stream` and return when it is done.
+ *   conv_forward_tc: one layer, x [B][ci][S^3] -> y [B][co][S^3] FP32
+ *                    (ci, co <= CAMS_NET_HID), ReLU when relu != 0.
+ *   forward_tc:      the whole network (parameters as for cams_set_surrogate),
+ *                    x [B][CAMS_NET_IN][S^3] -> y [B][CAMS_NET_OUT][S^3].
+ * Errors: CAMS_EINVAL (sizes, a workspace that is too small, a patch too
+ * large for shared memory), CAMS_ETIMEOUT (an MMA completion wait gave up),
+ * CAMS_ECUDA; the message is cams_last_error(NULL). */
+long long cams_net_tc_work_bytes(int B, int S);
+int cams_net_conv_forward_tc(int B, int S, int ci, int co, const float* x, const float* w,
+                             const float* bias, int relu, float* y, void* work,
+                             long long work_bytes, void* stream);
+int cams_net_forward_tc(int B, int S, const float* x, const float* params, float* y, void* work,
+                        long long work_bytes, void* stream);
 
 /* Copy an internal quantity (CAMS_Q_*) to dst (memspace of the handle, except
  * CAMS_Q_SIZES which is always host).  dst must hold the documented size. */

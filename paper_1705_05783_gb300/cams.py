@@ -26,14 +26,15 @@ CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES, CAMS_Q_SURR_RATIO = 11, 12, 13, 1
 CAMS_Q_MATRIX_UPPER = 15
 PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
                 "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
-                "ilu_bwd", "ilu_resid")
+                "ilu_bwd", "ilu_resid", "update", "ilu_apply")
 
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
            "cams_set_stream", "cams_set_schedule", "cams_get_schedule",
            "cams_assemble", "cams_update_basis", "cams_iterate", "cams_solve",
            "cams_ensemble_solve", "cams_set_surrogate", "cams_surrogate_data",
            "cams_net_conv_forward", "cams_net_conv_backward", "cams_net_mse", "cams_net_energy",
-           "cams_net_adam",
+           "cams_net_adam", "cams_net_tc_work_bytes", "cams_net_conv_forward_tc",
+           "cams_net_forward_tc",
            "cams_get",
            "cams_get_int", "cams_last_error", "cams_destroy", "cams_residual_norm_noalloc")
 
@@ -105,6 +106,9 @@ def load_library(path: str = LIB_PATH):
         "cams_net_energy": (C.c_int, [C.c_int] * 4 + [P] * 4 + [C.c_double, P, P, P, P]),
         "cams_net_adam": (C.c_int, [C.c_longlong, P, P, P, P, C.c_float, C.c_float, C.c_float,
                                     C.c_float, C.c_int, P]),
+        "cams_net_tc_work_bytes": (C.c_longlong, [C.c_int, C.c_int]),
+        "cams_net_conv_forward_tc": (C.c_int, [C.c_int] * 4 + [P, P, P, C.c_int, P, P, C.c_longlong, P]),
+        "cams_net_forward_tc": (C.c_int, [C.c_int, C.c_int, P, P, P, P, C.c_longlong, P]),
         "cams_get": (C.c_int, [P, C.c_int, P]),
         "cams_get_int": (C.c_int, [P, C.c_int, P]),
         "cams_last_error": (C.c_char_p, [P]),
@@ -350,6 +354,25 @@ def cams_residual_norm_noalloc(nx, ny, nz, diag, ax, ay, az, f, p, r=None, strea
                                            C.byref(out) if want_norm else None,
                                            C.c_void_p(stream_ptr))
     return code, (out.value if want_norm else None)
+
+
+def cams_net_tc_work_bytes(B, S):
+    """Bytes of device workspace the tensor-core network calls need."""
+    return int(_lib.cams_net_tc_work_bytes(int(B), int(S)))
+
+
+def cams_net_conv_forward_tc(B, S, ci, co, x, w, bias, relu, y, work, work_bytes, stream_ptr=0):
+    """One layer on the tensor cores (FP32 in and out, BF16 operands);
+    returns the status code."""
+    return _lib.cams_net_conv_forward_tc(int(B), int(S), int(ci), int(co), _ptr(x), _ptr(w),
+                                         _ptr(bias), int(relu), _ptr(y), _ptr(work),
+                                         int(work_bytes), C.c_void_p(stream_ptr))
+
+
+def cams_net_forward_tc(B, S, x, params, y, work, work_bytes, stream_ptr=0):
+    """The whole network on the tensor cores; returns the status code."""
+    return _lib.cams_net_forward_tc(int(B), int(S), _ptr(x), _ptr(params), _ptr(y), _ptr(work),
+                                    int(work_bytes), C.c_void_p(stream_ptr))
 
 
 def cams_destroy(h):

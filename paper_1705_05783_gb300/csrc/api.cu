@@ -36,6 +36,8 @@ struct cams_handle {
   int lev_grid[4] = {0, 0, 0, 0};
   bool lev_blocked[4] = {false, false, false, false};
   long long lev_lstride[4] = {0, 0, 0, 0};
+  long long lev_gbytes[4] = {0, 0, 0, 0};   // > 0: the level's windows in b.lwork, bytes per CTA
+  long long lwork_len = 0;
   long long lscratch_len = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int d_active = 0;
@@ -65,12 +67,20 @@ struct cams_handle {
   int* surr_org = nullptr;         // device: lower corner of each full interior's patch
   int* surr_ent = nullptr;         // device: its entity index
   float *surr_x = nullptr, *surr_h1 = nullptr, *surr_h2 = nullptr, *surr_y = nullptr;
+  void *surr_ta = nullptr, *surr_tb = nullptr;   // BF16 activations of the tensor-core path
+  bool surr_tc = false;                           // the network runs on the tensor cores
+  int sms = 0;                                    // SM count of the handle's device
   float* surr_ratio = nullptr;     // device: gate ratio of each full interior (last build)
   // the C-AMS iteration as a CUDA graph (captured once, replayed per iteration)
   bool graphs = true;               // CAMS_GRAPHS=0 launches every kernel directly
   cudaGraphExec_t step_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
   long long step_launches = 0;
+  // the whole inner loop of a linearisation as one graph: a conditional WHILE
+  // node around one iteration, the residual norm and the stopping test
+  bool loop_graph = true;           // CAMS_LOOP_GRAPH=0 keeps the host-driven loop
+  cudaGraphExec_t loop_exec = nullptr;
+  long long loop_body_launches = 0;
   // per-kernel-class profiling (cams_profile)
   bool prof = false;
   struct Pending { int cls; cudaEvent_t a, b; long long k0, k1; };
@@ -292,6 +302,8 @@ int alloc_all(cams_handle* h) {
       f.Axu = f.Ax; f.Ayu = f.Ay; f.Azu = f.Az;
     }
     AL(f.P, 8 * N); AL(f.pc, h->c.Nc);
+    AL(f.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(f.Lr, (size_t)h->c.Nc * (h->mc + 1));
+    AL(f.cblk, coarse_blocks_len(h->c.Nc)); AL(f.cdinv, h->c.Nc);
     AL(f.Lx, S); AL(f.Ly, S); AL(f.Lz, S); AL(f.Ux, S); AL(f.Uy, S); AL(f.Uz, S);
     AL(f.rds, S); AL(f.w, S); AL(f.z, S);
     // slots that hold no cell must read as zero (the sweeps run branch-free over them)
@@ -303,6 +315,7 @@ int alloc_all(cams_handle* h) {
   AL(b.ents, h->ents.size());
   AL(b.flag, h->ents.size());
   AL(b.lscratch, (size_t)h->lscratch_len);
+  if (h->lwork_len > 0) AL(b.lwork, (size_t)h->lwork_len);
   AL(b.loc, (size_t)h->n_dual * 36);
   AL(b.Acs, 27LL * h->c.Nc);
   AL(b.band, (size_t)h->c.Nc * (2 * h->mc + 1));
@@ -310,7 +323,7 @@ int alloc_all(cams_handle* h) {
   AL(b.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(b.Lr, (size_t)h->c.Nc * (h->mc + 1));
   AL(b.cblk, coarse_blocks_len(h->c.Nc)); AL(b.cdinv, h->c.Nc); AL(b.cabort, 1);
   AL(b.perm, h->c.Nc);
-  AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc);
+  AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc); AL(b.ywork, h->c.Nc);
   AL(b.dinv, N);
   {
     const long long S = ilu_skew_len(h->g);   // >= N
@@ -343,7 +356,7 @@ void free_all(cams_handle* h) {
                   b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
-                  b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz, b.Fc,
+                  b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz, b.Fc, b.ywork, b.lwork,
                   // the transposed couplings are separate arrays only for a nonsymmetric A
                   b.Axu != b.Ax ? b.Axu : nullptr, b.Ayu != b.Ay ? b.Ayu : nullptr,
                   b.Azu != b.Az ? b.Azu : nullptr};
@@ -351,7 +364,7 @@ void free_all(cams_handle* h) {
     if (p) cudaFree(p);
   const SingleBuffers& f = b.f32;
   void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
-                   f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz,
+                   f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz, f.Lc, f.Lr, f.cblk, f.cdinv,
                    f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
                    f.Azu != f.Az ? f.Azu : nullptr};
   for (void* p : fptrs)
@@ -392,11 +405,14 @@ int validate(const cams_grid* gr, const cams_fluid* fl, const cams_options* o) {
 
 void free_surrogate(cams_handle* h) {
   void* ptrs[] = {h->net, h->surr_org, h->surr_ent, h->surr_x, h->surr_h1, h->surr_h2, h->surr_y,
+                  h->surr_ta, h->surr_tb,
                   h->surr_ratio};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->net = nullptr; h->surr_org = h->surr_ent = nullptr;
   h->surr_x = h->surr_h1 = h->surr_h2 = h->surr_y = h->surr_ratio = nullptr;
+  h->surr_ta = h->surr_tb = nullptr;
+  h->surr_tc = false;
   h->surr_tol = 0.0; h->surr_n = 0; h->surr_chunk = 0;
 }
 
@@ -429,6 +445,15 @@ cudaError_t net_forward(cams_handle* h, int n, const float* x, float* y) {
   const float *w2 = b1 + kNetHid, *b2 = w2 + kNetHid * kNetHid * 27;
   const float *w3 = b2 + kNetHid, *b3 = w3 + kNetHid * kNetHid * 27;
   const float *w4 = b3 + kNetHid, *b4 = w4 + kNetOut * kNetHid * 27;
+  if (h->surr_tc) {
+    // tensor cores: BF16 activations, FP32 accumulation; the last layer writes FP32
+    cudaError_t e = launch_tc_pack(n, S, kNetIn, x, h->surr_ta, h->stream);
+    if (e == cudaSuccess) e = launch_conv_tc(n, S, kNetIn, kNetHid, h->surr_ta, w1, b1, 1, true, h->surr_tb, h->b.status, h->sms, h->stream);
+    if (e == cudaSuccess) e = launch_conv_tc(n, S, kNetHid, kNetHid, h->surr_tb, w2, b2, 1, true, h->surr_ta, h->b.status, h->sms, h->stream);
+    if (e == cudaSuccess) e = launch_conv_tc(n, S, kNetHid, kNetHid, h->surr_ta, w3, b3, 1, true, h->surr_tb, h->b.status, h->sms, h->stream);
+    if (e == cudaSuccess) e = launch_conv_tc(n, S, kNetHid, kNetOut, h->surr_tb, w4, b4, 0, false, y, h->b.status, h->sms, h->stream);
+    return e;
+  }
   cudaError_t e = launch_conv_fwd(n, S, kNetIn, kNetHid, x, w1, b1, 1, h->surr_h1, h->stream);
   if (e == cudaSuccess) e = launch_conv_fwd(n, S, kNetHid, kNetHid, h->surr_h1, w2, b2, 1, h->surr_h2, h->stream);
   if (e == cudaSuccess) e = launch_conv_fwd(n, S, kNetHid, kNetHid, h->surr_h2, w3, b3, 1, h->surr_h1, h->stream);
@@ -623,6 +648,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
       }
       CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
                              h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, h->single,
+                             h->lev_gbytes[lev],
                              h->lev_blocked[lev], b, h->stream));
     }
   }
@@ -666,6 +692,7 @@ int ilu_smooth(cams_handle* h) {
   LAUNCH(CAMS_PROF_ILU_RESID, launch_ilu_resid(h->g, h->b, s, h->stream));
   LAUNCH(CAMS_PROF_ILU_FWD, launch_ilu_sweep(h->g, h->b, false, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, s, h->stream));
   LAUNCH(CAMS_PROF_ILU_BWD, launch_ilu_sweep(h->g, h->b, true, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, s, h->stream));
+  LAUNCH(CAMS_PROF_ILU_APPLY, launch_ilu_apply(h->g, h->b, s, h->stream));
   return CAMS_OK;
 }
 
@@ -689,7 +716,8 @@ int cams_step_direct(cams_handle* h) {
       for (int lev = 1; lev <= 3; ++lev) {
         const int f = h->lev_first[lev];
         CK(launch_entity_cf(h->g, b.ents + f, h->lev_count[lev], h->lev_smem[lev],
-                            h->lev_grid[lev], h->lev_lstride[lev], s, h->lev_blocked[lev], b,
+                            h->lev_grid[lev], h->lev_lstride[lev], s, h->lev_blocked[lev],
+                            h->lev_gbytes[lev], b,
                             h->stream));
       }
     }
@@ -697,19 +725,19 @@ int cams_step_direct(cams_handle* h) {
       int rc = ilu_smooth(h);
       if (rc) return rc;
     }
-    if (s) LAUNCH(CAMS_PROF_ILU_BWD, launch_add_correction(h->g, b, h->stream));
+    if (s) LAUNCH(CAMS_PROF_UPDATE, launch_add_correction(h->g, b, h->stream));
     LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
   }
   const int fv = h->opt.restriction == 1;
   LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, fv, b.r, s, b, h->stream));
   LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv && !h->opt.jacobian,
-                                                   h->coarse_cluster, b, h->stream));
+                                                   h->coarse_cluster, s, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, s, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
     int rc = ilu_smooth(h);
     if (rc) return rc;
   }
-  if (s) LAUNCH(CAMS_PROF_ILU_BWD, launch_add_correction(h->g, b, h->stream));
+  if (s) LAUNCH(CAMS_PROF_UPDATE, launch_add_correction(h->g, b, h->stream));
   return CAMS_OK;
 }
 
@@ -747,6 +775,120 @@ int capture_step(cams_handle* h) {
   return CAMS_OK;
 }
 
+// Device side of the inner loop's stopping test (Sec. 4.1.1): scal[0] holds
+// ||f - A p||^2 of the current iterate (the residual kernel's sum),
+// scal[1] the same at the start of the linearisation, scal[2] the
+// iterations run.  The test is the host loop's, in the same FP64 operations:
+// continue while ||r|| >= lin_rtol ||r^0|| (and finite) and fewer than
+// max_cams iterations have run.
+__global__ void k_loop_begin(double* scal) {
+  scal[1] = scal[0];
+  scal[2] = 0.0;
+}
+__global__ void k_loop_ctrl(cudaGraphConditionalHandle cond, double* scal, int max_cams,
+                            double lin_rtol) {
+  const double its = scal[2] + 1.0;
+  scal[2] = its;
+  const double rn = sqrt(scal[0]), r0 = sqrt(scal[1]);
+  const bool more = its < (double)max_cams && isfinite(rn) && !(rn < lin_rtol * r0);
+  cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+// Capture the inner loop: a graph holding one conditional WHILE node whose
+// body is one C-AMS iteration, the residual norm and k_loop_ctrl (which
+// sets the node's condition).  Like the single-iteration graph it is
+// captured once (every pointer and size is fixed for the handle's life).
+int capture_loop(cams_handle* h) {
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  // (the parameter union has no default constructor: zeroed raw storage)
+  alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(h, CAMS_ECUDA, std::string("loop graph: ") + cudaGetErrorString(e));
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t own = h->stream;
+  e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return fail(h, CAMS_ECUDA, std::string("loop graph capture: ") + cudaGetErrorString(e));
+  }
+  h->stream = h->cap_stream;
+  const long long l0 = lc::mine;
+  int rc = cams_step_direct(h);
+  if (!rc) {
+    cudaError_t e2 = launch_residual(h->g, h->b, h->b.p, h->b.r, h->b.red, h->b.scal, h->stream);
+    if (e2 == cudaSuccess) {
+      k_loop_ctrl<<<1, 1, 0, h->stream>>>(cond, h->b.scal, h->opt.max_cams, h->opt.lin_rtol);
+      count_launches(1);
+      e2 = cudaGetLastError();
+    }
+    if (e2 != cudaSuccess) rc = fail(h, CAMS_ECUDA, std::string("loop graph body: ") + cudaGetErrorString(e2));
+  }
+  const long long l1 = lc::mine;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(h->cap_stream, &captured);
+  h->stream = own;
+  lc::total -= l1 - l0;                        // captured, not launched
+  lc::mine -= l1 - l0;
+  if (rc || e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc ? rc : fail(h, CAMS_ECUDA, std::string("loop graph capture: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&h->loop_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->loop_exec = nullptr;
+    cudaGetLastError();
+    return fail(h, CAMS_ECUDA, std::string("loop graph instantiation: ") + cudaGetErrorString(e));
+  }
+  h->loop_body_launches = l1 - l0;
+  return CAMS_OK;
+}
+
+// The inner loop of one linearisation on the device: from the residual of
+// the current iterate (residual_norm just computed it), C-AMS iterations
+// until ||r|| < lin_rtol ||r^0|| or max_cams.  *its and *rn receive the
+// count and the final ||r||.  Returns CAMS_EINVAL (nothing launched) when
+// the loop graph is unavailable, so the caller keeps its host loop.
+int inner_loop_graph(cams_handle* h, int* its, double* rn) {
+  if (h->prof || !h->graphs || !h->loop_graph) return CAMS_EINVAL;
+  if (!h->loop_exec) {
+    const int rc = capture_loop(h);
+    if (rc) {
+      h->loop_graph = false;                   // keep the host loop for this handle
+      return CAMS_EINVAL;
+    }
+  }
+  k_loop_begin<<<1, 1, 0, h->stream>>>(h->b.scal);
+  count_launches(1);
+  CK(cudaGetLastError());
+  CK(cudaGraphLaunch(h->loop_exec, h->stream));
+  double sc[3];
+  CK(cudaMemcpyAsync(sc, h->b.scal, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *its = (int)sc[2];
+  count_launches((long long)*its * h->loop_body_launches);
+  if (!std::isfinite(sc[0])) return fail(h, CAMS_ENAN, "non-finite residual norm");
+  *rn = std::sqrt(sc[0]);
+  return CAMS_OK;
+}
+
 // One C-AMS iteration: the captured graph, or direct launches while
 // per-kernel-class profiling is on (its events bracket every class).
 int cams_step(cams_handle* h) {
@@ -767,6 +909,42 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
   return ms;
+}
+
+// Workspace of the tensor-core network entry points: a status word, then
+// two BF16 activation buffers of 32 channels.
+long long tc_work_bytes(int B, int S) {
+  if (B < 1 || S < 1) return -1;
+  return 256 + 2 * ((2 * net_tc_act_elems(B, S, kNetHid) + 255) / 256 * 256);
+}
+
+// Shared driver of the two tensor-core entry points: zero the workspace,
+// run `body` on its two activation buffers, wait and read the status word.
+template <class F>
+int run_tc(int B, int S, void* work, long long work_bytes, cudaStream_t s, F body) {
+  const long long need = tc_work_bytes(B, S);
+  if (!work || work_bytes < need)
+    return fail(nullptr, CAMS_EINVAL, "tensor-core workspace missing or smaller than "
+                                      "cams_net_tc_work_bytes(B, S)");
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return fail(nullptr, CAMS_ECUDA, "no CUDA device available");
+  if (!net_tc_fits(S, (int)prop.sharedMemPerBlockOptin))
+    return fail(nullptr, CAMS_EINVAL, "the patch does not fit the tensor-core kernel's shared memory");
+  char* base = static_cast<char*>(work);
+  int* status = reinterpret_cast<int*>(base);
+  const long long half = (need - 256) / 2;
+  void* ta = base + 256;
+  void* tb = base + 256 + half;
+  cudaError_t e = cudaMemsetAsync(work, 0, (size_t)need, s);
+  if (e == cudaSuccess) e = body(ta, tb, status, prop.multiProcessorCount);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
+  if (st & kStatTimeout) return fail(nullptr, CAMS_ETIMEOUT, "a tensor-core barrier wait exceeded its limit");
+  return CAMS_OK;
 }
 
 }  // namespace
@@ -857,6 +1035,12 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     }
     h->lev_smem[lev] = sm;
     h->lev_lstride[lev] = ls;
+    if (h->lev_blocked[lev] && sm > (int)prop.sharedMemPerBlockOptin) {
+      // the blocked solver's window in global memory (the 15^3 interiors of
+      // 16^3 blocks): per CTA the same bytes, 256-byte aligned
+      h->lev_gbytes[lev] = ((long long)sm + 255) / 256 * 256;
+      continue;
+    }
     smem_max = std::max(smem_max, sm);
   }
   if (smem_max > (int)prop.sharedMemPerBlockOptin) {
@@ -868,9 +1052,11 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     return fail(nullptr, CAMS_ECUDA, "cudaFuncSetAttribute failed");
   }
   for (int lev = 1; lev <= 3; ++lev) {
-    const int per_sm = std::max(1, (int)(prop.sharedMemPerMultiprocessor / std::max(h->lev_smem[lev] + 1024, 1)));
+    const int per_sm = h->lev_gbytes[lev] ? 2 :
+        std::max(1, (int)(prop.sharedMemPerMultiprocessor / std::max(h->lev_smem[lev] + 1024, 1)));
     h->lev_grid[lev] = std::min(h->lev_count[lev], prop.multiProcessorCount * std::min(per_sm, 8));
     h->lscratch_len = std::max(h->lscratch_len, (long long)h->lev_grid[lev] * h->lev_lstride[lev]);
+    h->lwork_len = std::max(h->lwork_len, (long long)h->lev_grid[lev] * h->lev_gbytes[lev]);
   }
   // coarse ordering: fastest = fewest coarse cells
   int ordc[3] = {0, 1, 2};
@@ -898,6 +1084,8 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   {
     const char* gr = std::getenv("CAMS_GRAPHS");
     h->graphs = !(gr && gr[0] == '0');
+    const char* lg = std::getenv("CAMS_LOOP_GRAPH");
+    h->loop_graph = !(lg && lg[0] == '0');
     const char* lv = std::getenv("CAMS_ILU_LEVEL");
     h->ilu_pipelined = !(lv && lv[0] == '1');
     h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
@@ -1020,6 +1208,10 @@ int cams_set_schedule(cams_handle* h, int ilu_cta, int coarse_cluster) {
     CK(cudaGraphExecDestroy(h->step_exec));
     h->step_exec = nullptr;
   }
+  if (h->loop_exec) {
+    CK(cudaGraphExecDestroy(h->loop_exec));
+    h->loop_exec = nullptr;
+  }
   return CAMS_OK;
 }
 
@@ -1069,7 +1261,7 @@ int closing_msfv(cams_handle* h) {
   }
   LAUNCH(CAMS_PROF_RESIDUAL, launch_residual(h->g, b, b.p, b.r, b.red, b.scal, h->stream));
   LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, 1, b.r, h->single, b, h->stream));
-  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, 0, false, b, h->stream));
+  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, 0, false, false, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_to_p(h->g, h->c, h->single, b, h->stream));
   return check_status(h);
 }
@@ -1139,14 +1331,19 @@ int cams_solve(cams_handle* h, const double* p_n, double dt, const cams_bc* bc, 
     rc = residual_norm(h, &r0);
     if (rc) return rc;
     int its = 0;
-    while (its < o.max_cams) {
-      rc = cams_step(h);
-      if (rc) return rc;
-      ++its;
-      rc = residual_norm(h, &rn);
-      if (rc) return rc;
-      if (rn < o.lin_rtol * r0) break;
+    rc = inner_loop_graph(h, &its, &rn);
+    if (rc == CAMS_EINVAL) {                   // host-driven loop (profiling on, or no loop graph)
+      rc = CAMS_OK;
+      while (its < o.max_cams) {
+        rc = cams_step(h);
+        if (rc) return rc;
+        ++its;
+        rc = residual_norm(h, &rn);
+        if (rc) return rc;
+        if (rn < o.lin_rtol * r0) break;
+      }
     }
+    if (rc) return rc;
     cudaEventRecord(ev[3], h->stream);
     cudaEventSynchronize(ev[3]);
     t_it += elapsed(ev[2], ev[3]);
@@ -1253,10 +1450,29 @@ int cams_set_surrogate(cams_handle* h, const float* params, double gate_tol) {
   if (rc) { free_surrogate(h); return rc; }
   const long long S3 = (long long)(h->surr_b + 1) * (h->surr_b + 1) * (h->surr_b + 1);
   h->surr_chunk = std::max(1, std::min(h->surr_n, 1024));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, h->dev));
+  h->sms = prop.multiProcessorCount;
+  // the tensor-core network when a patch and the weights fit shared memory
+  const char* tcv = std::getenv("CAMS_NET_TC");
+  h->surr_tc = !(tcv && tcv[0] == '0') &&
+               net_tc_fits(h->surr_b + 1, (int)prop.sharedMemPerBlockOptin);
   rc = dalloc(h, &h->net, (size_t)kNetParams);
   if (!rc) rc = dalloc(h, &h->surr_x, (size_t)(h->surr_chunk * kNetIn * S3));
-  if (!rc) rc = dalloc(h, &h->surr_h1, (size_t)(h->surr_chunk * kNetHid * S3));
-  if (!rc) rc = dalloc(h, &h->surr_h2, (size_t)(h->surr_chunk * kNetHid * S3));
+  if (h->surr_tc) {
+    const size_t n = (size_t)net_tc_act_elems(h->surr_chunk, h->surr_b + 1, kNetHid);
+    unsigned short *ta = nullptr, *tb = nullptr;     // BF16 storage
+    if (!rc) rc = dalloc(h, &ta, n);
+    if (!rc) rc = dalloc(h, &tb, n);
+    h->surr_ta = ta;
+    h->surr_tb = tb;
+    // rows outside the output-tile range are never written: they hold the zero border
+    if (!rc && (cudaMemset(ta, 0, 2 * n) != cudaSuccess || cudaMemset(tb, 0, 2 * n) != cudaSuccess))
+      rc = fail(h, CAMS_ECUDA, "cudaMemset failed");
+  } else {
+    if (!rc) rc = dalloc(h, &h->surr_h1, (size_t)(h->surr_chunk * kNetHid * S3));
+    if (!rc) rc = dalloc(h, &h->surr_h2, (size_t)(h->surr_chunk * kNetHid * S3));
+  }
   if (!rc) rc = dalloc(h, &h->surr_y, (size_t)(h->surr_chunk * kNetOut * S3));
   if (!rc) rc = dalloc(h, &h->surr_ratio, (size_t)h->surr_n);
   if (rc) { free_surrogate(h); return rc; }
@@ -1309,6 +1525,41 @@ int cams_net_conv_backward(int B, int S, int ci, int co, const float* x, const f
                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return fail(nullptr, CAMS_ECUDA, cudaGetErrorString(e));
   return CAMS_OK;
+}
+
+long long cams_net_tc_work_bytes(int B, int S) { return tc_work_bytes(B, S); }
+
+int cams_net_conv_forward_tc(int B, int S, int ci, int co, const float* x, const float* w,
+                             const float* bias, int relu, float* y, void* work,
+                             long long work_bytes, void* stream) {
+  if (B < 0 || S < 1 || ci < 1 || ci > kNetHid || co < 1 || co > kNetHid || !x || !w || !bias || !y)
+    return fail(nullptr, CAMS_EINVAL, "bad convolution arguments");
+  if (B == 0) return CAMS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return run_tc(B, S, work, work_bytes, s, [&](void* ta, void*, int* status, int sms) {
+    cudaError_t e = launch_tc_pack(B, S, ci, x, ta, s);
+    if (e == cudaSuccess) e = launch_conv_tc(B, S, ci, co, ta, w, bias, relu, false, y, status, sms, s);
+    return e;
+  });
+}
+
+int cams_net_forward_tc(int B, int S, const float* x, const float* params, float* y, void* work,
+                        long long work_bytes, void* stream) {
+  if (B < 0 || S < 1 || !x || !params || !y) return fail(nullptr, CAMS_EINVAL, "bad network arguments");
+  if (B == 0) return CAMS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float *w1 = params, *b1 = w1 + kNetHid * kNetIn * 27;
+  const float *w2 = b1 + kNetHid, *b2 = w2 + kNetHid * kNetHid * 27;
+  const float *w3 = b2 + kNetHid, *b3 = w3 + kNetHid * kNetHid * 27;
+  const float *w4 = b3 + kNetHid, *b4 = w4 + kNetOut * kNetHid * 27;
+  return run_tc(B, S, work, work_bytes, s, [&](void* ta, void* tb, int* status, int sms) {
+    cudaError_t e = launch_tc_pack(B, S, kNetIn, x, ta, s);
+    if (e == cudaSuccess) e = launch_conv_tc(B, S, kNetIn, kNetHid, ta, w1, b1, 1, true, tb, status, sms, s);
+    if (e == cudaSuccess) e = launch_conv_tc(B, S, kNetHid, kNetHid, tb, w2, b2, 1, true, ta, status, sms, s);
+    if (e == cudaSuccess) e = launch_conv_tc(B, S, kNetHid, kNetHid, ta, w3, b3, 1, true, tb, status, sms, s);
+    if (e == cudaSuccess) e = launch_conv_tc(B, S, kNetHid, kNetOut, tb, w4, b4, 0, false, y, status, sms, s);
+    return e;
+  });
 }
 
 int cams_net_mse(long long n, const float* pred, const float* target, const float* mask,
@@ -1484,6 +1735,7 @@ void cams_destroy(cams_handle* h) {
   cudaStreamSynchronize(h->stream);
   free_surrogate(h);
   if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);

@@ -86,6 +86,8 @@ struct SingleBuffers {
   float* d = nullptr;                                     // the correction delta (N)
   float* P = nullptr;                                     // 8N, slot-major
   float* pc = nullptr;                                    // coarse solution (band order)
+  // FP32 copy of the symmetric coarse factor (the substitution's operands)
+  float *Lc = nullptr, *Lr = nullptr, *cblk = nullptr, *cdinv = nullptr;
 };
 
 // Device buffers, one allocation each, owned by the handle.
@@ -112,6 +114,7 @@ struct Buffers {
   Entity* ents = nullptr;                                 // all entities, level-sorted
   unsigned char* flag = nullptr;                          // per entity
   double* lscratch = nullptr;                             // local L factors, per resident CTA
+  unsigned char* lwork = nullptr;                         // local solver windows too large for shared memory
   double* loc = nullptr;                                  // FE local 8x8 blocks per dual block (64 each)
   double* Acs = nullptr;                                  // 27*Nc coarse stencil
   double* band = nullptr;                                 // coarse band (column-major)
@@ -121,6 +124,7 @@ struct Buffers {
   int* cabort = nullptr;                                  // abort flag of the cluster solve
   int* perm = nullptr;                                    // coarse natural -> band order
   double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
+  double* ywork = nullptr;                                // forward-solve vector of the global band solve
   double* dinv = nullptr;                                 // 1 / ILU(0) pivots
   // ILU(0) sweep vectors, skewed tile-major (ilu_skew_len elements each)
   double *Lx = nullptr, *Ly = nullptr, *Lz = nullptr;     // a_{i,i-e_d} / d_i
@@ -187,13 +191,16 @@ cudaError_t launch_count_flags(int count, const unsigned char* flag, double* out
 cudaError_t launch_vertices(const Geo& g, const CGeo& c, Buffers& b, bool single, cudaStream_t s);
 // blocked: panels of pivots with a register-tiled trailing update (large
 // local problems); otherwise one pivot at a time.
+// gbytes > 0: the blocked solver's window lives in b.lwork, gbytes per CTA
+// (entities whose window exceeds shared memory), else in shared memory
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                bool single, bool blocked, Buffers& b, cudaStream_t s);
+                                bool single, bool blocked, long long gbytes, Buffers& b,
+                                cudaStream_t s);
 int entity_smem_bytes(const Entity& E, bool single, bool blocked);
 cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int smem, int grid,
-                             long long lstride, bool single, bool blocked, Buffers& b,
-                             cudaStream_t s);
+                             long long lstride, bool single, bool blocked, long long gbytes,
+                             Buffers& b, cudaStream_t s);
 cudaError_t set_entity_smem(int smem);
 // nonsym: A is not symmetric (the full-Jacobian step)
 cudaError_t launch_galerkin_fe(const Geo& g, const CGeo& c, bool single, bool nonsym, Buffers& b,
@@ -204,7 +211,11 @@ cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStre
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, bool single,
                             Buffers& b, cudaStream_t s);
-cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, cudaStream_t s);
+// the coarse solution into b.pc; with single into b.f32.pc for the FP32
+// prolongation (the symmetric cluster solve then substitutes in FP32 with
+// the FP32 copy of the factor)
+cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, bool single, Buffers& b,
+                              cudaStream_t s);
 long long coarse_blocks_len(int Nc);
 bool coarse_cluster_ok(int Nc, int max_smem);
 // FP64: p += P p_c; single: delta = P p_c (FP32 P and delta)
@@ -223,6 +234,8 @@ cudaError_t launch_ilu_factor(const Geo& g, Buffers& b, bool pipelined, int sms,
 cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t s);
 cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipelined, int sms,
                              bool cta, bool single, cudaStream_t s);
+// x += z after the backward sweep (single: delta in FP32, else p)
+cudaError_t launch_ilu_apply(const Geo& g, Buffers& b, bool single, cudaStream_t s);
 bool ilu_cta_ok(const Geo& g, int max_smem);
 cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s);   // p += delta
 int ilu_ctrl_ints(const Geo& g);
@@ -250,6 +263,21 @@ cudaError_t launch_energy(int B, int S, int C, int cx, const float* p, const flo
                           const float* mask, const float* x, double count, float* grad, double* part,
                           double* loss, cudaStream_t s);
 int mse_partial_blocks();
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation) path of the
+// network (k_net_tc.cu).  Activations between layers are BF16 "chunked and
+// padded" (a zero border around the patch, channels in chunks of 8); a
+// buffer of net_tc_act_elems(B, S, C) BF16 values must start zeroed (only
+// rows inside the output-tile range are ever written).
+long long net_tc_act_elems(int B, int S, int C);
+bool net_tc_fits(int S, int max_smem);
+// FP32 [B][C][S^3] -> BF16 chunked-padded
+cudaError_t launch_tc_pack(int B, int S, int C, const float* x, void* out, cudaStream_t s);
+// one layer from a BF16 chunked-padded input: BF16 chunked-padded output
+// (out_bf16, the next layer's input) or FP32 [B][co][S^3]; status gets
+// kStatTimeout if an MMA barrier wait gives up
+cudaError_t launch_conv_tc(int B, int S, int ci, int co, const void* x, const float* w,
+                           const float* bias, int relu, bool out_bf16, void* y, int* status,
+                           int sms, cudaStream_t s);
 // patches of the full interior dual blocks: org = lower corner (x, y, z) per patch
 cudaError_t launch_patch_inputs(const Geo& g, int b, int n, const int* org, bool single,
                                 const Buffers& bf, float* x, float* target, float* mask,

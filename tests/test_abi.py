@@ -14,7 +14,7 @@ LIB = os.path.join(ROOT, "paper_1705_05783_gb300", "_lib", "libcams.so")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(cams_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(cams_\w+)\s*\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -123,6 +123,10 @@ def test_binding_constants_match_header():
     for name in defs:
         if name.startswith(("CAMS_Q_", "CAMS_PREC_", "CAMS_E", "CAMS_OK", "CAMS_HOST", "CAMS_DEVICE")):
             assert hasattr(cams, name), name
+    # the profile classes, in the header's order
+    assert len(cams.PROF_CLASSES) == int(defs["CAMS_PROF_CLASSES"])
+    for k, name in enumerate(cams.PROF_CLASSES):
+        assert int(defs["CAMS_PROF_" + name.upper()]) == k, name
 
 
 def test_variant_options_are_checked_before_the_gpu():

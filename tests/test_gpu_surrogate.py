@@ -68,6 +68,92 @@ def test_conv_forward_backward_match_oracle(env, relu):
     assert _rel(gb.cpu().numpy(), rb) < 1e-5
 
 
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), as the tensor-core
+    kernels round their operands; returned in float64."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _tc_work(torch, cams, B, S):
+    n = cams.cams_net_tc_work_bytes(B, S)
+    return torch.zeros(n, dtype=torch.uint8, device="cuda"), n
+
+
+@pytest.mark.parametrize("S,ci,co,relu", [(11, 12, 32, 1), (11, 32, 32, 1), (11, 32, 8, 0),
+                                          (6, 5, 13, 1), (4, 32, 16, 0)])
+def test_tensor_core_conv_matches_oracle(env, S, ci, co, relu):
+    """One 3x3x3 layer on the tensor cores (BF16 operands, FP32 accumulation
+    in tensor memory) against the oracle's convolution of the same
+    BF16-rounded input and weights: only the FP32 accumulation order differs,
+    so every output is within 1e-4 of the sum of the magnitudes of its (at
+    most 27 x 32 = 864) terms, the worst-case FP32 rounding of such a sum.
+    Ragged channel counts and small patches exercise the zero padding of
+    channels, tiles and borders."""
+    torch, cams, _ = env
+    rng = np.random.default_rng(11 + S + ci)
+    B = 5
+    x = rng.standard_normal((B, ci, S, S, S))
+    w = 0.3 * rng.standard_normal((co, ci, 27))
+    b = rng.standard_normal(co)
+    y = torch.full((B, co, S, S, S), float("nan"), device="cuda")
+    work, nbytes = _tc_work(torch, cams, B, S)
+    code = cams.cams_net_conv_forward_tc(B, S, ci, co, _dev(torch, x), _dev(torch, w), _dev(torch, b),
+                                         relu, y, work, nbytes)
+    assert code == cams.CAMS_OK, cams.cams_last_error()
+    yg = y.cpu().numpy().astype(np.float64)
+    xb, wb, br = bf16(x), bf16(w), b.astype(np.float32).astype(np.float64)
+    ref = conv_forward(xb, wb, br, bool(relu))
+    mag = conv_forward(np.abs(xb), np.abs(wb), np.abs(br), False)
+    assert np.all(np.isfinite(yg))
+    err = np.abs(yg - ref)
+    print(f"[tc conv S={S} {ci}->{co}] max |dy| / magnitude = {(err / mag).max():.2e}")
+    assert np.all(err <= 1e-4 * mag)
+
+
+def test_tensor_core_network_matches_oracle(env):
+    """The whole 4-layer network on the tensor cores against the oracle's
+    network with the kernels' precision applied between layers (input,
+    weights and every hidden activation rounded to BF16, FP32 output).  A
+    hidden value within FP32 rounding of a BF16 rounding boundary may round
+    the other way on the GPU, a one-ulp (2^-8 relative) change of one input
+    of the next layer, so the bar is 1e-3 of the output's magnitude sum."""
+    torch, cams, surrogate = env
+    rng = np.random.default_rng(12)
+    B, S = 4, 11
+    params = surrogate.init_params(5)
+    x = rng.standard_normal((B, cams.CAMS_NET_IN, S, S, S))
+    y = torch.full((B, cams.CAMS_NET_OUT, S, S, S), float("nan"), device="cuda")
+    work, nbytes = _tc_work(torch, cams, B, S)
+    code = cams.cams_net_forward_tc(B, S, _dev(torch, x), _dev(torch, params), y, work, nbytes)
+    assert code == cams.CAMS_OK, cams.cams_last_error()
+    a = bf16(x)
+    amag = np.abs(a)
+    L = surrogate.LAYERS
+    for k, ((ci, co), (ow, ob)) in enumerate(zip(L, surrogate.offsets())):
+        w = params[ow:ob].astype(np.float64).reshape(co, ci, 27)
+        b = params[ob:ob + co].astype(np.float64)
+        last = k == len(L) - 1
+        a = conv_forward(a, bf16(w), b, not last)
+        amag = conv_forward(amag, np.abs(bf16(w)), np.abs(b), False)
+        if not last:
+            a = bf16(a)
+    yg = y.cpu().numpy().astype(np.float64)
+    err = np.abs(yg - a)
+    print(f"[tc network] max |dy| / magnitude = {(err / amag).max():.2e}")
+    assert np.all(err <= 1e-3 * amag)
+
+
+def test_tensor_core_workspace_is_checked(env):
+    torch, cams, _ = env
+    work = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    x = torch.zeros((1, 4, 5, 5, 5), device="cuda")
+    code = cams.cams_net_conv_forward_tc(1, 5, 4, 4, x, torch.zeros(4 * 4 * 27, device="cuda"),
+                                         torch.zeros(4, device="cuda"), 0, x, work, 16)
+    assert code == cams.CAMS_EINVAL and "workspace" in cams.cams_last_error()
+
+
 def test_mse_and_adam_match_oracle(env):
     torch, cams, _ = env
     rng = np.random.default_rng(6)
