@@ -55,6 +55,42 @@ def tune(h, p_n, dt, bc, iters=3, repeats=2, candidates=CANDIDATES, clock=time.p
     return choice, times
 
 
+def tune_ensemble(handles, run, repeats=2, candidates=CANDIDATES, clock=time.perf_counter):
+    """Tune the schedule of an ensemble as it runs: under each candidate
+    (set on every handle that accepts it; the others keep theirs) time
+    `repeats` calls of run(), which runs the whole ensemble once, after one
+    untimed call (graph capture); keep the fastest candidate on every handle.
+    Members that run concurrently share the GPU, so a schedule timed on one
+    handle alone need not be the fastest among them.  Returns
+    (choice, {candidate: best seconds})."""
+    times = {}
+    for cand in candidates:
+        accepted = 0
+        for h in handles:
+            try:
+                cams.cams_set_schedule(h, *cand)
+                accepted += 1
+            except cams.CamsError:
+                pass
+        if accepted == 0:
+            continue
+        run()
+        best = float("inf")
+        for _ in range(repeats):
+            t0 = clock()
+            run()
+            best = min(best, clock() - t0)
+        times[cand] = best
+    choice = min(times, key=times.get) if times else None
+    if choice is not None:
+        for h in handles:
+            try:
+                cams.cams_set_schedule(h, *choice)
+            except cams.CamsError:
+                pass
+    return choice, times
+
+
 def shape_key(nx, ny, nz, coarse, precision, restriction):
     return (int(nx), int(ny), int(nz), tuple(int(b) for b in coarse), int(precision),
             int(restriction))

@@ -285,9 +285,12 @@ __global__ void __launch_bounds__(256) k_entity_solve_blk(
     int adaptive, const double* __restrict__ Abd, const double* __restrict__ Abx,
     const double* __restrict__ Aby, const double* __restrict__ Abz, T* P, double* snap,
     T* lscratch, long long lstride, int* status, const double* __restrict__ rin, T* psi,
-    double* padd) {
+    double* padd, unsigned char* gwork, long long gbytes) {
+  // the working window, right-hand sides and panel: dynamic shared memory,
+  // or this CTA's slice of gwork when an entity's window is too large for it
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sm = reinterpret_cast<T*>(sm_raw);
+  T* sm = gwork ? reinterpret_cast<T*>(gwork + (long long)blockIdx.x * gbytes)
+                : reinterpret_cast<T*>(sm_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
   T* Lg = lscratch + (long long)blockIdx.x * lstride;
   __shared__ T s_d[kKB], s_dinv[kKB];
@@ -607,24 +610,25 @@ int entity_smem_bytes(const Entity& E, bool single, bool blocked) {
 
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
-                                bool single, bool blocked, Buffers& b, cudaStream_t s) {
+                                bool single, bool blocked, long long gbytes, Buffers& b,
+                                cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (grid > count) grid = count;
   if (single) {
     float* ls = reinterpret_cast<float*>(b.lscratch);
     if (blocked)
-      k_entity_solve_blk<float, false><<<grid, 256, smem, s>>>(
+      k_entity_solve_blk<float, false><<<grid, 256, gbytes ? 0 : smem, s>>>(
           g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
-          b.status, nullptr, nullptr, nullptr);
+          b.status, nullptr, nullptr, nullptr, gbytes ? b.lwork : nullptr, gbytes);
     else
       k_entity_solve<float, false><<<grid, 256, smem, s>>>(
           g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, b.snap, ls, lstride,
           b.status, nullptr, nullptr, nullptr);
   } else {
     if (blocked)
-      k_entity_solve_blk<double, false><<<grid, 256, smem, s>>>(
+      k_entity_solve_blk<double, false><<<grid, 256, gbytes ? 0 : smem, s>>>(
           g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.P, b.snap, b.lscratch,
-          lstride, b.status, nullptr, nullptr, nullptr);
+          lstride, b.status, nullptr, nullptr, nullptr, gbytes ? b.lwork : nullptr, gbytes);
     else
       k_entity_solve<double, false><<<grid, 256, smem, s>>>(
           g, ents, count, flag, adaptive, b.Abd, b.Abx, b.Aby, b.Abz, b.P, b.snap, b.lscratch,
@@ -638,25 +642,25 @@ cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned
 // FP64 into b.cf with p += Psi; in mixed precision into the FP32 correction
 // b.f32.d (which the caller zeroed: its vertex values are Psi's).
 cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int smem, int grid,
-                             long long lstride, bool single, bool blocked, Buffers& b,
-                             cudaStream_t s) {
+                             long long lstride, bool single, bool blocked, long long gbytes,
+                             Buffers& b, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (grid > count) grid = count;
   if (single) {
     float* ls = reinterpret_cast<float*>(b.lscratch);
     if (blocked)
-      k_entity_solve_blk<float, true><<<grid, 256, smem, s>>>(
+      k_entity_solve_blk<float, true><<<grid, 256, gbytes ? 0 : smem, s>>>(
           g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, nullptr, ls, lstride,
-          b.status, b.r, b.f32.d, nullptr);
+          b.status, b.r, b.f32.d, nullptr, gbytes ? b.lwork : nullptr, gbytes);
     else
       k_entity_solve<float, true><<<grid, 256, smem, s>>>(
           g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.f32.P, nullptr, ls, lstride,
           b.status, b.r, b.f32.d, nullptr);
   } else {
     if (blocked)
-      k_entity_solve_blk<double, true><<<grid, 256, smem, s>>>(
+      k_entity_solve_blk<double, true><<<grid, 256, gbytes ? 0 : smem, s>>>(
           g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.P, nullptr, b.lscratch,
-          lstride, b.status, b.r, b.cf, b.p);
+          lstride, b.status, b.r, b.cf, b.p, gbytes ? b.lwork : nullptr, gbytes);
     else
       k_entity_solve<double, true><<<grid, 256, smem, s>>>(
           g, ents, count, nullptr, 0, b.Abd, b.Abx, b.Aby, b.Abz, b.P, nullptr, b.lscratch,

@@ -598,6 +598,7 @@ constexpr int kCB = 32;                      // rows per block
 constexpr int kCBlocks = 3;                  // per block: L_JJ^{-1}, M_J, M'_J
 constexpr int kCC = 8;                       // CTAs per cluster
 constexpr unsigned long long kCNotReady = 0x7FF4DEADBEEF0002ull;   // signalling NaN
+constexpr unsigned kCNotReady32 = 0x7FA5A5A2u;                      // signalling NaN (FP32)
 constexpr long long kCSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ double lower_at(const double* Lc, int N, int m, int r, int c) {
@@ -678,6 +679,15 @@ __device__ __forceinline__ void cl_broadcast(const double* local, double v) {
     asm volatile("st.relaxed.cluster.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
   }
 }
+__device__ __forceinline__ void cl_broadcast(const float* local, float v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+#pragma unroll
+  for (int rk = 0; rk < kCC; ++rk) {
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rk));
+    asm volatile("st.relaxed.cluster.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
+  }
+}
 __device__ __forceinline__ unsigned long long ld_cl(const double* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.cluster.shared::cta.b64 %0, [%1];"
@@ -686,6 +696,24 @@ __device__ __forceinline__ unsigned long long ld_cl(const double* p) {
                : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned ld_cl(const float* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.cluster.shared::cta.b32 %0, [%1];"
+               : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+// the "not yet written" pattern of each precision, and its value
+template <class T> struct CWord;
+template <> struct CWord<double> {
+  static constexpr unsigned long long kNR = kCNotReady;
+  static __device__ __forceinline__ double value(unsigned long long b) { return __longlong_as_double((long long)b); }
+};
+template <> struct CWord<float> {
+  static constexpr unsigned kNR = kCNotReady32;
+  static __device__ __forceinline__ float value(unsigned b) { return __uint_as_float(b); }
+};
 __device__ __forceinline__ int ld_abort(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -693,14 +721,15 @@ __device__ __forceinline__ int ld_abort(const int* p) {
 }
 
 // Waits until the 4 values at p are written; false after an abort or a timeout.
-__device__ __forceinline__ bool wait4(const double* p, double* v, int* abort_flag, int* status) {
+template <class T>
+__device__ __forceinline__ bool wait4(const T* p, T* v, int* abort_flag, int* status) {
   for (long long it = 0; it < kCSpinLimit; ++it) {
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const unsigned long long b = ld_cl(p + k);
-      v[k] = __longlong_as_double((long long)b);
-      ok &= b != kCNotReady;
+      const auto b = ld_cl(p + k);
+      v[k] = CWord<T>::value(b);
+      ok &= b != CWord<T>::kNR;
     }
     if (ok) return true;
     if ((it & 63) == 63) {
@@ -714,7 +743,8 @@ __device__ __forceinline__ bool wait4(const double* p, double* v, int* abort_fla
 }
 
 // sum over the 8 lanes of an aligned lane group (every lane gets the sum)
-__device__ __forceinline__ double sum8(double v) {
+template <class T>
+__device__ __forceinline__ T sum8(T v) {
   v += __shfl_xor_sync(0xffffffffu, v, 4);
   v += __shfl_xor_sync(0xffffffffu, v, 2);
   v += __shfl_xor_sync(0xffffffffu, v, 1);
@@ -722,49 +752,53 @@ __device__ __forceinline__ double sum8(double v) {
 }
 
 // 256 threads: thread (r = tid / 8, h = tid % 8) owns row r of a block and
-// the 4 columns 4h .. 4h+3 of every kCB x kCB product.
+// the 4 columns 4h .. 4h+3 of every kCB x kCB product.  T: the precision of
+// the substitution (the factor's blocks come in that precision; the
+// right-hand side is FP64, rounded to T).
+template <class T>
 __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
-    int N, int m, const double* __restrict__ Lc, const double* __restrict__ Lr,
-    const double* __restrict__ blk, const double* __restrict__ dinv,
-    const double* __restrict__ rc, double* pc, int* abort_flag, int* status) {
-  extern __shared__ double sm[];
-  __shared__ double uv[kCB];
+    int N, int m, const T* __restrict__ Lc, const T* __restrict__ Lr,
+    const T* __restrict__ blk, const T* __restrict__ dinv,
+    const double* __restrict__ rc, T* pc, int* abort_flag, int* status) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
+  __shared__ T uv[kCB];
   const int NB = (N + kCB - 1) / kCB, Np = NB * kCB;
-  double* y = sm;
-  double* x = sm + Np;
+  T* y = sm;
+  T* x = sm + Np;
   const int rank = (int)cl_rank();
   const int tid = threadIdx.x, r = tid >> 3, h = tid & 7;
   const int W = (m + kCB - 1) / kCB;           // blocks of the band left of a diagonal block
-  for (int i = tid; i < 2 * Np; i += blockDim.x) sm[i] = __longlong_as_double((long long)kCNotReady);
+  for (int i = tid; i < 2 * Np; i += blockDim.x) sm[i] = CWord<T>::value(CWord<T>::kNR);
   cl_sync();
   bool ok = true;
   // ---- forward: L y = b ----
   for (int J = rank; J < NB; J += kCC) {
     const int base = J * kCB, row = base + r;
-    double acc = (h == 0 && row < N) ? rc[row] : 0.0;
+    T acc = (h == 0 && row < N) ? T(rc[row]) : T(0);
     for (int I = J - W > 0 ? J - W : 0; I <= J - 2; ++I) {
-      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      T yv[4] = {0.0, 0.0, 0.0, 0.0};
       ok = ok && wait4(y + I * kCB + 4 * h, yv, abort_flag, status);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int c = I * kCB + 4 * h + k;
-        const double l = (row < N && row - c <= m) ? Lr[(long long)row * (m + 1) + (row - c)] : 0.0;
+        const T l = (row < N && row - c <= m) ? Lr[(long long)row * (m + 1) + (row - c)] : 0.0;
         acc -= l * yv[k];
       }
     }
     acc = sum8(acc);
     if (h == 0) uv[r] = acc;
     __syncthreads();
-    const double* Li = blk + (long long)J * kCBlocks * kCB * kCB;
-    double s = 0.0;
+    const T* Li = blk + (long long)J * kCBlocks * kCB * kCB;
+    T s = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += Li[r * kCB + 4 * h + k] * uv[4 * h + k];
     s = sum8(s);
     if (J > 0) {
-      const double* M = Li + kCB * kCB;
-      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      const T* M = Li + kCB * kCB;
+      T yv[4] = {0.0, 0.0, 0.0, 0.0};
       ok = ok && wait4(y + (J - 1) * kCB + 4 * h, yv, abort_flag, status);
-      double t = 0.0;
+      T t = 0.0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) t += M[r * kCB + 4 * h + k] * yv[k];
       s -= sum8(t);
@@ -776,35 +810,35 @@ __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
   const int lastJ = NB - 1 - ((NB - 1 - rank) % kCC + kCC) % kCC;
   for (int I = lastJ; I >= 0; I -= kCC) {
     const int base = I * kCB, col = base + r;
-    double acc = 0.0;
+    T acc = 0.0;
     if (h == 0) {
-      double yv[4] = {0.0, 0.0, 0.0, 0.0};
+      T yv[4] = {0.0, 0.0, 0.0, 0.0};
       ok = ok && wait4(y + base + (r & ~3), yv, abort_flag, status);
       acc = col < N ? yv[r & 3] * dinv[col] : 0.0;
     }
     for (int J = I + W < NB - 1 ? I + W : NB - 1; J >= I + 2; --J) {
-      double xv[4] = {0.0, 0.0, 0.0, 0.0};
+      T xv[4] = {0.0, 0.0, 0.0, 0.0};
       ok = ok && wait4(x + J * kCB + 4 * h, xv, abort_flag, status);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int rw = J * kCB + 4 * h + k;
-        const double l = (rw < N && col < N && rw - col <= m) ? Lc[(long long)col * (m + 1) + (rw - col)] : 0.0;
+        const T l = (rw < N && col < N && rw - col <= m) ? Lc[(long long)col * (m + 1) + (rw - col)] : 0.0;
         acc -= l * xv[k];
       }
     }
     acc = sum8(acc);
     if (h == 0) uv[r] = acc;
     __syncthreads();
-    const double* Li = blk + (long long)I * kCBlocks * kCB * kCB;
-    double s = 0.0;
+    const T* Li = blk + (long long)I * kCBlocks * kCB * kCB;
+    T s = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += Li[(4 * h + k) * kCB + r] * uv[4 * h + k];
     s = sum8(s);
     if (I + 1 < NB) {
-      const double* Mt = Li + 2 * kCB * kCB;
-      double xv[4] = {0.0, 0.0, 0.0, 0.0};
+      const T* Mt = Li + 2 * kCB * kCB;
+      T xv[4] = {0.0, 0.0, 0.0, 0.0};
       ok = ok && wait4(x + (I + 1) * kCB + 4 * h, xv, abort_flag, status);
-      double t = 0.0;
+      T t = 0.0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) t += Mt[r * kCB + 4 * h + k] * xv[k];
       s -= sum8(t);
@@ -816,6 +850,61 @@ __global__ void __launch_bounds__(256, 1) k_coarse_solve_cluster(
     }
   }
   cl_sync();   // no CTA leaves while others may still store into its shared memory
+}
+
+// Symmetric band solve for coarse grids whose vectors do not fit shared
+// memory (N_c of tens of thousands): the block recurrences of
+// k_coarse_solve_cluster, run by one CTA block after block, with y and x in
+// global memory (they stay in L2).  Per block of kCB rows: the band's part
+// from the solved blocks (four independent partial sums per thread, so the
+// FP64 additions overlap), then the kCB x kCB inverse of the diagonal block.
+__global__ void __launch_bounds__(256, 1) k_coarse_solve_global(
+    int N, int m, const double* __restrict__ Lc, const double* __restrict__ Lr,
+    const double* __restrict__ blk, const double* __restrict__ dinv,
+    const double* __restrict__ rc, double* y, double* pc) {
+  __shared__ double uv[kCB];
+  const int NB = (N + kCB - 1) / kCB;
+  const int tid = threadIdx.x, r = tid >> 3, h = tid & 7;
+  // ---- forward: L y = b ----
+  for (int J = 0; J < NB; ++J) {
+    const int base = J * kCB, row = base + r;
+    const int lo = row - m > 0 ? row - m : 0;
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (row < N)
+      for (int c = lo + h; c < base; c += 8)
+        a4[(c >> 3) & 3] -= Lr[(long long)row * (m + 1) + (row - c)] * y[c];
+    double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    acc = sum8(acc);
+    if (h == 0) uv[r] = (row < N ? rc[row] : 0.0) + acc;
+    __syncthreads();
+    const double* Li = blk + (long long)J * kCBlocks * kCB * kCB;
+    double sy = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sy += Li[r * kCB + 4 * h + k] * uv[4 * h + k];
+    sy = sum8(sy);
+    if (h == 0 && row < N) y[row] = sy;
+    __syncthreads();                           // y of this block is visible to the CTA
+  }
+  // ---- backward: L^T x = D^{-1} y ----
+  for (int I = NB - 1; I >= 0; --I) {
+    const int base = I * kCB, col = base + r;
+    const int hi = col + m < N - 1 ? col + m : N - 1;
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    if (col < N)
+      for (int rw = base + kCB + h; rw <= hi; rw += 8)
+        a4[(rw >> 3) & 3] -= Lc[(long long)col * (m + 1) + (rw - col)] * pc[rw];
+    double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    acc = sum8(acc);
+    if (h == 0) uv[r] = (col < N ? y[col] * dinv[col] : 0.0) + acc;
+    __syncthreads();
+    const double* Li = blk + (long long)I * kCBlocks * kCB * kCB;
+    double sx = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sx += Li[(4 * h + k) * kCB + r] * uv[4 * h + k];
+    sx = sum8(sx);
+    if (h == 0 && col < N) pc[col] = sx;
+    __syncthreads();
+  }
 }
 
 // ---- general coarse matrix (MSFV, or MSFE of a nonsymmetric A): band LU ----
@@ -1193,6 +1282,15 @@ cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t 
   k_ldlt_rows<<<(int)((n + 255) / 256), 256, 0, s>>>(Nc, m, b.Lc, b.Lr);
   k_coarse_prep<<<(Nc + kCB - 1) / kCB, 256, 0, s>>>(Nc, m, b.Lc, b.cblk, b.cdinv);
   count_launches(launches + 2);
+  if (b.f32.Lc) {
+    // FP32 copy of the factor for the mixed-precision substitution
+    const long long nb = coarse_blocks_len(Nc);
+    k_to_single<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, b.Lc, b.f32.Lc);
+    k_to_single<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, b.Lr, b.f32.Lr);
+    k_to_single<<<(int)((nb + 255) / 256), 256, 0, s>>>((int)nb, b.cblk, b.f32.cblk);
+    k_to_single<<<(Nc + 255) / 256, 256, 0, s>>>(Nc, b.cdinv, b.f32.cdinv);
+    count_launches(4);
+  }
   return cudaGetLastError();
 }
 
@@ -1214,14 +1312,24 @@ long long coarse_blocks_len(int Nc) {
   return (long long)((Nc + kCB - 1) / kCB) * kCBlocks * kCB * kCB;
 }
 
-static int coarse_cluster_smem(int Nc) {
-  return (int)sizeof(double) * 2 * ((Nc + kCB - 1) / kCB) * kCB;
+// the device's opt-in shared memory per CTA
+static int coarse_smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 48 * 1024;
+  return v;
+}
+
+static int coarse_cluster_smem(int Nc, int bytes = 8) {
+  return bytes * 2 * ((Nc + kCB - 1) / kCB) * kCB;
 }
 
 bool coarse_cluster_ok(int Nc, int max_smem) {
   const int smem = coarse_cluster_smem(Nc);
   if (smem > max_smem) return false;
-  if (raise_smem_limit(k_coarse_solve_cluster, smem) != cudaSuccess) {
+  if (raise_smem_limit(k_coarse_solve_cluster<double>, smem) != cudaSuccess ||
+      raise_smem_limit(k_coarse_solve_cluster<float>, coarse_cluster_smem(Nc, 4)) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -1237,19 +1345,20 @@ bool coarse_cluster_ok(int Nc, int max_smem) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_coarse_solve_cluster, &cfg) != cudaSuccess) n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_coarse_solve_cluster<double>, &cfg) != cudaSuccess) n = 0;
   cudaGetLastError();
   return n > 0;
 }
 
-cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, cudaStream_t s) {
+cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, bool single, Buffers& b,
+                              cudaStream_t s) {
   if (sym && cluster) {
     cudaError_t e = cudaMemsetAsync(b.cabort, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCC);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = (size_t)coarse_cluster_smem(Nc);
+    cfg.dynamicSmemBytes = (size_t)coarse_cluster_smem(Nc, single ? 4 : 8);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1258,17 +1367,32 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_coarse_solve_cluster, Nc, m, (const double*)b.Lc,
-                           (const double*)b.Lr, (const double*)b.cblk, (const double*)b.cdinv,
-                           (const double*)b.rc, b.pc, b.cabort, b.status);
+    if (single) {
+      // FP32 substitution with the FP64 factor's FP32 copy; the result goes
+      // straight to the FP32 prolongation
+      const SingleBuffers& f = b.f32;
+      e = cudaLaunchKernelEx(&cfg, k_coarse_solve_cluster<float>, Nc, m, (const float*)f.Lc,
+                             (const float*)f.Lr, (const float*)f.cblk, (const float*)f.cdinv,
+                             (const double*)b.rc, b.f32.pc, b.cabort, b.status);
+    } else {
+      e = cudaLaunchKernelEx(&cfg, k_coarse_solve_cluster<double>, Nc, m, (const double*)b.Lc,
+                             (const double*)b.Lr, (const double*)b.cblk, (const double*)b.cdinv,
+                             (const double*)b.rc, b.pc, b.cabort, b.status);
+    }
     count_launches(1);
     return e;
   }
   if (sym) {
     const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
-    cudaError_t e = raise_smem_limit(k_ldlt_solve, smem);
-    if (e != cudaSuccess) return e;
-    k_ldlt_solve<<<1, 256, smem, s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
+    if (smem <= coarse_smem_optin()) {
+      cudaError_t e = raise_smem_limit(k_ldlt_solve, smem);
+      if (e != cudaSuccess) return e;
+      k_ldlt_solve<<<1, 256, smem, s>>>(Nc, m, b.Lc, b.Lr, b.rc, b.pc);
+    } else {
+      // vectors in global memory (b.ywork holds y)
+      k_coarse_solve_global<<<1, 256, 0, s>>>(Nc, m, b.Lc, b.Lr, b.cblk, b.cdinv, b.rc, b.ywork,
+                                             b.pc);
+    }
   } else {
     const int smem = (int)sizeof(double) * (2 * kSC * (m + 1) + Nc);
     cudaError_t e = raise_smem_limit(k_band_lu_solve, smem);
@@ -1276,6 +1400,10 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, Buffers& b, 
     k_band_lu_solve<<<1, 256, smem, s>>>(Nc, m, b.Fc, b.rc, b.pc);
   }
   count_launches(1);
+  if (single) {
+    k_to_single<<<(Nc + 255) / 256, 256, 0, s>>>(Nc, b.pc, b.f32.pc);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -1283,10 +1411,9 @@ cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers
                                cudaStream_t s) {
   const int blocks = (int)(((long long)g.ny * g.nz + 7) / 8);   // one warp per x-row
   if (single) {
-    k_to_single<<<(c.Nc + 255) / 256, 256, 0, s>>>(c.Nc, b.pc, b.f32.pc);
+    // the coarse solution is already in b.f32.pc (launch_band_solve with single)
     k_prolong<float, float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm,
                                                               b.f32.d);
-    count_launches(1);
   } else {
     k_prolong<double, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
   }

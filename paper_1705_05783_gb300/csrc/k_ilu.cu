@@ -48,7 +48,7 @@
 //    four warps per SM keeps one sweeping warp per FP64 pipe.
 //  The backward sweep runs the same schedule on the mirrored grid; with the
 //  tiling fixed by the forward direction, its steps read the same records in
-//  reverse order.
+//  reverse order.  x += z follows as a separate coalesced pass (k_apply_z).
 #include "cams_internal.h"
 
 namespace cams {
@@ -931,10 +931,16 @@ cudaError_t sweep_impl(const Geo& g, Buffers& b, bool backward, bool pipelined, 
     count_launches(1);
     if (e != cudaSuccess) return e;
   }
-  if (backward) {
-    k_apply_z<T><<<transpose_grid(g, sk), 256, 0, s>>>(g, sk, v.z, xv);
-    count_launches(1);
-  }
+  (void)xv;
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t apply_impl(const Geo& g, Buffers& b, T* xv, cudaStream_t s) {
+  const Skew sk = make_skew(g);
+  const IluSet<T> v = set_of(b, (T*)nullptr);
+  k_apply_z<T><<<transpose_grid(g, sk), 256, 0, s>>>(g, sk, v.z, xv);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -1016,6 +1022,10 @@ cudaError_t launch_ilu_sweep(const Geo& g, Buffers& b, bool backward, bool pipel
                              bool cta, bool single, cudaStream_t s) {
   return single ? sweep_impl<float>(g, b, backward, pipelined, sms, cta, b.f32.d, s)
                 : sweep_impl<double>(g, b, backward, pipelined, sms, cta, b.p, s);
+}
+
+cudaError_t launch_ilu_apply(const Geo& g, Buffers& b, bool single, cudaStream_t s) {
+  return single ? apply_impl<float>(g, b, b.f32.d, s) : apply_impl<double>(g, b, b.p, s);
 }
 
 cudaError_t launch_add_correction(const Geo& g, Buffers& b, cudaStream_t s) {

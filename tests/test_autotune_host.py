@@ -65,3 +65,25 @@ def test_cache_tunes_each_shape_once(monkeypatch):
     assert cache.apply("b", key, None, 0.1, None, clock=eng.clock) == (0, 0)
     assert sum(1 for c in eng.calls if c[0] == "iterate") == n_iter   # not tuned again
     assert eng.schedule["b"] == (0, 0)
+
+
+def test_tune_ensemble_times_whole_runs(monkeypatch):
+    """Every candidate is set on every handle that accepts it and timed over
+    whole ensemble runs (after one untimed run); the fastest is kept on
+    all handles."""
+    eng = FakeEngine({(0, 0): 3.0, (0, 1): 1.0, (1, 0): 2.0, (1, 1): 5.0}, refused={(1, 1)})
+    eng.install(monkeypatch)
+    handles = ["a", "b", "c"]
+    runs = []
+
+    def run():
+        # an ensemble run costs the sum of its members under their schedules
+        runs.append(dict(eng.schedule))
+        eng.now += sum(eng.cost[eng.schedule[h]] for h in handles)
+
+    choice, times = autotune.tune_ensemble(handles, run, repeats=2, clock=eng.clock)
+    assert choice == (0, 1)
+    assert set(times) == {(0, 0), (0, 1), (1, 0)}
+    assert times[(0, 1)] == pytest.approx(3.0)
+    assert all(eng.schedule[h] == (0, 1) for h in handles)
+    assert len(runs) == 3 * 3                    # one untimed + two timed runs per candidate
