@@ -213,8 +213,46 @@ def evaluate(tr, x, t, m, kind="mse"):
     return tot / max(cnt, 1.0)
 
 
+def time_network(B, S=11, repeats=10):
+    """CUDA-event time of one forward pass of the network over B patches of
+    S^3 voxels: the tensor-core entry point (BF16 operands, FP32
+    accumulation) and the FP32 CUDA-core layer kernels, with random
+    parameters.  Returns {name: ms}."""
+    import torch
+    dev = torch.device("cuda", 0)
+    params = init_params(5)
+    p = torch.from_numpy(params).to(dev)
+    x = torch.randn(B, cams.CAMS_NET_IN, S ** 3, device=dev)
+    y = torch.zeros(B, cams.CAMS_NET_OUT, S ** 3, device=dev)
+    nb = cams.cams_net_tc_work_bytes(B, S)
+    work = torch.zeros(nb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def tc():
+        code = cams.cams_net_forward_tc(B, S, x, p, y, work, nb, stream)
+        if code != cams.CAMS_OK:
+            raise cams.CamsError(code, cams.cams_last_error())
+
+    tr = Trainer(params, B, S, dev)
+    out = {}
+    for name, fn, n in (("tensor_core", tc, repeats), ("fp32_cuda_core", lambda: tr.forward(x, B), 3)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / n
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time", type=int, default=0,
+                    help="only time one forward pass over this many patches and exit")
     ap.add_argument("--out", default=PARAMS_FILE)
     ap.add_argument("--fields", type=int, default=20)
     ap.add_argument("--steps", type=int, default=3000)
@@ -222,6 +260,13 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--loss", default="energy", choices=["energy", "mse"])
     a = ap.parse_args(argv)
+    if a.time > 0:
+        S = 11
+        flop = 2.0 * a.time * S ** 3 * 27 * sum(ci * co for ci, co in LAYERS)
+        for name, ms in time_network(a.time, S).items():
+            print(f"{name}: {ms:.3f} ms for {a.time} patches of {S}^3, "
+                  f"{flop / ms / 1e9:.1f} useful TFLOP/s", flush=True)
+        return
     import torch
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
