@@ -97,6 +97,9 @@ def parse():
                     help="the full-Jacobian Newton step (flux density differentiated)")
     ap.add_argument("--cf", action="store_true",
                     help="correction functions before every multiscale stage")
+    ap.add_argument("--oracle-newton-step", action="store_true",
+                    help="with --impl reference: time the oracle on the whole workload for "
+                         "its first Newton step, stage by stage (minutes to an hour)")
     ap.add_argument("--restriction", type=int, choices=[0, 1, 2], default=None,
                     help="override the workload's restriction: 0 MSFE, 1 MSFV, "
                          "2 MSFE then a closing MSFV correction")
@@ -512,6 +515,32 @@ def run_ensemble(args, rank, world, local_rank):
 
 # ---------------------------------------------------- oracle (CPU) legs --
 
+def _oracle_problem(w, inp, nx, ny, nz):
+    """The oracle's Problem and Options for the (nx, ny, nz) corner box of
+    workload w's seeded field (the whole field when the sizes are w's)."""
+    import oracle
+    kx = inp["kx"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    ky = inp["ky"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    kz = inp["kz"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
+    g = oracle.Grid(nx, ny, nz, inp["dx"], inp["dy"], inp["dz"])
+    if w.bc == "lines":
+        # the two prescribed columns at the box's own corners
+        fc, fv = line_columns(w.with_(nx=nx, ny=ny, nz=nz))
+        bc = oracle.BC(False, w.p_west, w.p_east, fix_cell=fc, fix_value=fv)
+    elif w.bc == "wells" and (nx, ny, nz) == (w.nx, w.ny, w.nz):
+        bc = oracle.BC(inp["dirichlet"], w.p_west, w.p_east, inp["src_cell"], inp["src_rate"],
+                       inp["fix_cell"], inp["fix_value"])
+    else:
+        bc = oracle.BC(True, w.p_west, w.p_east)
+    pb = oracle.Problem.build(g, oracle.Fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi),
+                              bc, kx, ky, kz)
+    opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
+                         n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
+                         adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams,
+                         full_jacobian=bool(VARIANT.get("jacobian")), cf=bool(VARIANT.get("cf")))
+    return pb, opt
+
+
 def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
     """A bounded sample of workload w for the CPU oracle: the (sub) corner
     box of the same seeded field, same coarsening, fluid, time step and
@@ -522,26 +551,62 @@ def oracle_sample(w, seed, sub=(60, 60, 40), inp=None):
     # each side a whole number of coarse blocks, within the grid
     nx, ny, nz = (min(n, max(2 * b, (s // b) * b))
                   for n, b, s in zip((w.nx, w.ny, w.nz), w.coarse, sub))
-    kx = inp["kx"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
-    ky = inp["ky"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
-    kz = inp["kz"].reshape(w.nz, w.ny, w.nx)[:nz, :ny, :nx].ravel().copy()
-    g = oracle.Grid(nx, ny, nz, inp["dx"], inp["dy"], inp["dz"])
-    if w.bc == "lines":
-        # the two prescribed columns at the sample box's own corners
-        fc, fv = line_columns(w.with_(nx=nx, ny=ny, nz=nz))
-        bc = oracle.BC(False, w.p_west, w.p_east, fix_cell=fc, fix_value=fv)
-    else:
-        bc = oracle.BC(True, w.p_west, w.p_east)
-    pb = oracle.Problem.build(g, oracle.Fluid(w.law, w.c_or_eta, w.rho0, w.mu, w.phi),
-                              bc, kx, ky, kz)
-    opt = oracle.Options(coarse=w.coarse, basis=w.basis, restriction=w.restriction,
-                         n_pre=w.n_pre, n_post=w.n_post, lin_rtol=w.lin_rtol, nl_tol=w.nl_tol,
-                         adapt_theta=w.adapt_theta, max_newton=w.max_newton, max_cams=w.max_cams,
-                         full_jacobian=bool(VARIANT.get("jacobian")), cf=bool(VARIANT.get("cf")))
+    pb, opt = _oracle_problem(w, inp, nx, ny, nz)
     t0 = time.perf_counter()
-    _, st = oracle.run(pb, opt, np.zeros(g.N), inp["dt"], 1)
+    _, st = oracle.run(pb, opt, np.zeros(pb.grid.N), inp["dt"], 1)
     dt = time.perf_counter() - t0
-    return g.N * st[0].cams_its / dt, dt, st[0], f"{nx}x{ny}x{nz} corner box of the {w.name} field"
+    return pb.grid.N * st[0].cams_its / dt, dt, st[0], f"{nx}x{ny}x{nz} corner box of the {w.name} field"
+
+
+def oracle_newton_step(w, seed):
+    """The oracle on the whole workload for its first Newton step, stage by
+    stage (Table 1: assembly, ILU(0) factors, basis, R A P and its factor,
+    then C-AMS iterations to the inner stopping test of Sec. 4.1.1); the
+    wall time of each stage on one host core."""
+    import oracle
+    from oracle.coarse import coarse_factor
+    inp = make_inputs(w, seed)
+    t_all = time.perf_counter()
+    pb, opt = _oracle_problem(w, inp, w.nx, w.ny, w.nz)
+    wb = oracle.build_wirebasket(pb.grid, opt.coarse)
+    state = oracle.BasisState(wb)
+    stages = {}
+
+    def timed(name, fn, *a):
+        t0 = time.perf_counter()
+        out = fn(*a)
+        stages[name] = stages.get(name, 0.0) + time.perf_counter() - t0
+        return out
+
+    p_n = pb.with_fixed(inp["p0"])
+    dt = inp["dts"][0]
+    lin = timed("assemble", oracle.assemble, pb, p_n, p_n, dt, opt.full_jacobian)
+    LU = timed("ilu_factor", oracle.ilu0, lin.A)
+    Ab = timed("basis", oracle.basis_operator, pb, opt.basis, lin.rho, lin.c, p_n, dt)
+    rebuilt = timed("basis", state.update, Ab, opt.adapt_theta)
+    P = timed("basis", state.matrix)
+    R = timed("coarse_factor", oracle.restriction,
+              0 if opt.restriction == 2 else opt.restriction, P, wb)
+    lu = timed("coarse_factor", lambda: coarse_factor(oracle.coarse_operator(R, lin.A, P)))
+    p = p_n.copy()
+    r0 = float(np.linalg.norm(lin.f - lin.A @ p))
+    its = 0
+    t0 = time.perf_counter()
+    while its < opt.max_cams:
+        p = oracle.cams_iteration(lin.A, lin.f, p, P, R, lu, LU, opt.n_pre, opt.n_post)
+        its += 1
+        if float(np.linalg.norm(lin.f - lin.A @ p)) < opt.lin_rtol * r0:
+            break
+    stages["cams_iterations"] = time.perf_counter() - t0
+    wall = time.perf_counter() - t_all
+    N = pb.grid.N
+    return {"workload": w.name, "cells": N, "newton_steps": 1, "cams_its": its,
+            "entities_built": int(rebuilt), "wall_s": wall,
+            "stage_s": {k: round(v, 3) for k, v in stages.items()},
+            "setup_s": round(wall - sum(stages.values()), 3),
+            "value": N * its / wall, "unit": UNIT,
+            "value_iterations_only": N * its / stages["cams_iterations"],
+            "cores": cpu_cores_used(), **host_cpu()}
 
 
 def cpu_cores_used():
@@ -621,7 +686,10 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    if args.impl == "reference":
+    if args.impl == "reference" and args.oracle_newton_step:
+        out = {"impl": "reference", "oracle_newton_step": oracle_newton_step(w, args.seed)} \
+            if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, w, rank, world)
     else:
         out = run_cams(args, w, rank, world, local_rank)

@@ -5,10 +5,11 @@ correlation lengths 0.2 / 0.2 / 0.02 of the domain, kz = 0.1 k), c dp = 0.2,
 an injector and a producer as vertical line wells in opposite corners
 (Reading R16), 10 implicit steps, 10 x 10 x 5 coarse blocks, the (B1) basis
 with adaptive updates at theta = 0.1 (Sec. 4.1.2), 5 ILU(0) post-smoothing
-steps, MSFE or MSFV restriction (Sec. 3, Eq. 7), relative stopping test 1e-5
-per step.  (The workload's 1e-6 is out of reach at full size: in the second
-step the oracle's linearisations stall near 1.5e-6 relative, its inner loops
-falling to 3 or 4 iterations, and 50 of them do not meet it.)
+steps, MSFE or MSFV restriction (Sec. 3, Eq. 7), relative stopping test
+NL_TOL per step.  (The workload's 1e-6 is out of reach at full size: in the
+second step the oracle's linearisations stall near 1.5e-6 relative, its
+inner loops falling to 3 or 4 iterations, and 50 of them do not meet it; at
+1e-5 the third step stalls the same way.)
 For every step the record holds the oracle's Newton and C-AMS counts (per
 linearisation), the number of local entities rebuilt, convergence, the 2-norm,
 maximum, minimum and sum of the pressure field, and the pressure at a fixed
@@ -40,11 +41,12 @@ from workloads import WORKLOADS, make_inputs  # noqa: E402
 WORKLOAD = "3d-100x100x50-wells"
 SEED = 0
 N_SAMPLE = 256
-NL_TOL = 1e-5
+NL_TOL = float(os.environ.get("GOLDEN_NL_TOL", "1e-4"))
 
 
 def golden_path(restriction: int) -> str:
-    return os.path.join(HERE, f"wells_100x100x50_seed{SEED}_{('msfe', 'msfv')[restriction]}.json")
+    return os.path.join(HERE, f"wells_100x100x50_seed{SEED}_{('msfe', 'msfv')[restriction]}"
+                              f"_tol{NL_TOL:g}.json")
 
 
 def sample_cells(w, inp) -> np.ndarray:
@@ -85,6 +87,7 @@ def make(restriction: int) -> dict:
             "cams_per_newton": list(st.cams_per_newton), "basis_rebuilt": st.basis_rebuilt,
             "converged": bool(st.converged),
             "eps_rel_final": float(st.eps_hist[-1] / st.eps_hist[0]),
+            "eps_hist": [float(v) for v in st.eps_hist],
             "p_norm2": float(np.linalg.norm(p)), "p_max": float(p.max()),
             "p_min": float(p.min()), "p_sum": float(p.sum()),
             "p_sample": [float(v) for v in p[cells]],
