@@ -59,6 +59,15 @@ BYTES_PER_CELL = {
     "ilu_factor": 88,          # A x4 -> 1/d, scaled couplings x6
     "basis_op": 64,
 }
+# Latency model of a wavefront sweep: its last cell is (nx + ny + nz - 3)
+# dependent steps after its first, so no schedule finishes before that many
+# steps of one tile's step loop.  T_STEP_US: a tile's time per step alone
+# (no neighbour to wait for), measured on this GPU with a lone 8 x 4-row
+# tile of 65,536 x-positions (one group of 4 steps: 0.30 us in FP32,
+# 0.78 us in FP64).
+T_STEP_US = {0: 0.78 / 4, 1: 0.30 / 4}
+SWEEP_CLASSES = ("ilu_fwd", "ilu_bwd")
+
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + write.sum) for
 # a kernel class on a workload, for the kernels as they stand; see profiles/.
 MEASURED_TRAFFIC = {}
@@ -183,6 +192,22 @@ def class_rooflines(prof, n_cells, precision, peak):
         avg_ms = ms_tot / n_l
         gbs = table[k] * n_cells / (avg_ms / 1e3) / 1e9
         out[k] = {"launches": int(n_l), "avg_ms": avg_ms, "gbs": gbs, "frac": gbs / peak}
+    return out
+
+
+def sweep_latency_bound(prof, w):
+    """The ILU(0) sweeps against their critical path: (nx + ny + nz - 3)
+    steps at a lone tile's step time (a bound no schedule of the exact
+    lexicographic recurrence beats at that step time)."""
+    steps = w.nx + w.ny + w.nz - 3
+    bound_us = steps * T_STEP_US[1 if w.precision else 0]
+    out = {"model": "(nx+ny+nz-3) dependent steps x t_step of a lone tile",
+           "t_step_us": T_STEP_US[1 if w.precision else 0], "steps": steps,
+           "bound_us": bound_us}
+    for k in SWEEP_CLASSES:
+        if k in prof and prof[k][0]:
+            avg_us = 1e3 * prof[k][1] / prof[k][0]
+            out[k] = {"avg_launch_us": avg_us, "frac": bound_us / avg_us}
     return out
 
 
@@ -403,6 +428,7 @@ def run_cams(args, w, rank, world, local_rank, e2e_leg=True, surrogate=None):
                      "timing": "CUDA events per kernel class on the handle's stream, in a "
                                "separate pass of the same steps after the timed region"},
         "kernel_roofline": class_rooflines(prof, N, w.precision, peak),
+        "latency_bound": sweep_latency_bound(prof, w),
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

@@ -122,9 +122,14 @@ typedef struct {
                           R A P, restriction and prolongation, ILU(0) factor and sweeps) runs
                           in FP32 on the correction equation A delta = r inside FP64 iterative
                           refinement (block sums of R A P and of R r in FP64); assembly, the
-                          residual r = f - A p, the update p += delta and the coarse
-                          factorisation and solve stay FP64.  Converges to the same fixed
-                          point (the FP64 residual decides the stopping tests). */
+                          residual r = f - A p and the update p += delta stay FP64.  The
+                          symmetric (MSFE) coarse system is factored in FP32 and solved as
+                          Z^T D^{-1} Z R r with Z = L^{-1} formed once per factorisation,
+                          where that costs at most 2e10 FMAs and 1 GiB (environment variable
+                          CAMS_COARSE_INV=0 at setup: FP64 factor, FP32 substitution with its
+                          copy); the MSFV coarse system is factored and solved in FP64.
+                          Converges to the same fixed point (the FP64 residual decides the
+                          stopping tests). */
   int cf;              /* 1: correction functions (Sec. 3; Table 1 step 4) open every C-AMS
                           iteration: p += Psi, Psi solving the basis stages' local problems
                           with the residual f - A p as the source (zero on the vertices),
@@ -185,18 +190,19 @@ typedef struct {
 #define CAMS_PROF_ADAPT         2   /* adaptive-update flags (a3) */
 #define CAMS_PROF_BASIS         3   /* vertex/edge/face/interior local solves (a4-a7) */
 #define CAMS_PROF_GALERKIN      4   /* R A P (a8) */
-#define CAMS_PROF_COARSE_FACTOR 5   /* band fill + LU of R A P (a9) */
+#define CAMS_PROF_COARSE_FACTOR 5   /* band fill + LDL^T / LU of R A P (a9) */
 #define CAMS_PROF_ILU_FACTOR    6   /* ILU(0) pivots (a10) */
 #define CAMS_PROF_RESIDUAL      7   /* r = f - A p with its norm */
 #define CAMS_PROF_RESTRICT      8   /* R r */
-#define CAMS_PROF_COARSE_SOLVE  9   /* band substitution */
+#define CAMS_PROF_COARSE_SOLVE  9   /* band substitution, or Z^T D^{-1} Z (mixed) */
 #define CAMS_PROF_PROLONG      10   /* p += P p_c (FP64), delta = P p_c (mixed precision) */
 #define CAMS_PROF_ILU_FWD      11   /* ILU(0) forward wavefront sweep */
 #define CAMS_PROF_ILU_BWD      12   /* ILU(0) backward wavefront sweep */
 #define CAMS_PROF_ILU_RESID    13   /* D^{-1}(f - A p) feeding the forward sweep */
 #define CAMS_PROF_UPDATE       14   /* p += delta (mixed precision) */
 #define CAMS_PROF_ILU_APPLY    15   /* x += z after the backward sweep */
-#define CAMS_PROF_CLASSES      16
+#define CAMS_PROF_COARSE_INV   16   /* Z = L^{-1} of the mixed coarse solve's FP32 factor */
+#define CAMS_PROF_CLASSES      17
 
 /* (a1) Set up a solver for one grid and permeability field.
  * kx, ky, kz: permeability per cell (> 0, finite); ky and kz may alias kx.

@@ -26,7 +26,7 @@ CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES, CAMS_Q_SURR_RATIO = 11, 12, 13, 1
 CAMS_Q_MATRIX_UPPER = 15
 PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
                 "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
-                "ilu_bwd", "ilu_resid", "update", "ilu_apply")
+                "ilu_bwd", "ilu_resid", "update", "ilu_apply", "coarse_inv")
 
 EXPORTS = ("cams_setup", "cams_set_permeability", "cams_profile", "cams_selftest_wait",
            "cams_set_stream", "cams_set_schedule", "cams_get_schedule",

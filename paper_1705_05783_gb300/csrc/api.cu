@@ -59,6 +59,7 @@ struct cams_handle {
   bool ilu_pipelined = true;    // false: level-scheduled sweeps (CAMS_ILU_LEVEL=1)
   bool ilu_cta = false;         // 2 x 2 tile blocks per CTA, else one tile per warp
   bool coarse_cluster = false;  // MSFE coarse solve across a cluster (CAMS_COARSE_CLUSTER=0: one CTA)
+  bool coarse_inv = false;      // mixed MSFE: FP32 factor and inverse factor (CAMS_COARSE_INV=0: off)
   int ilu_grid = 1;
   // learned surrogate of the interior basis stage (cams_set_surrogate)
   double surr_tol = 0.0;           // > 0: enabled
@@ -304,6 +305,12 @@ int alloc_all(cams_handle* h) {
     AL(f.P, 8 * N); AL(f.pc, h->c.Nc);
     AL(f.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(f.Lr, (size_t)h->c.Nc * (h->mc + 1));
     AL(f.cblk, coarse_blocks_len(h->c.Nc)); AL(f.cdinv, h->c.Nc);
+    if (h->coarse_inv) {
+      AL(f.band, (size_t)h->c.Nc * (h->mc + 1));
+      AL(f.Z, (size_t)h->c.Nc * (size_t)coarse_ldz(h->c.Nc));
+      AL(f.tc, coarse_ldz(h->c.Nc));
+      AL(f.zpart, coarse_part_len(h->c.Nc));
+    }
     AL(f.Lx, S); AL(f.Ly, S); AL(f.Lz, S); AL(f.Ux, S); AL(f.Uy, S); AL(f.Uz, S);
     AL(f.rds, S); AL(f.w, S); AL(f.z, S);
     // slots that hold no cell must read as zero (the sweeps run branch-free over them)
@@ -365,7 +372,7 @@ void free_all(cams_handle* h) {
   const SingleBuffers& f = b.f32;
   void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
                    f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz, f.Lc, f.Lr, f.cblk, f.cdinv,
-                   f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
+                   f.band, f.Z, f.tc, f.zpart, f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
                    f.Azu != f.Az ? f.Azu : nullptr};
   for (void* p : fptrs)
     if (p) cudaFree(p);
@@ -648,8 +655,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
       }
       CK(launch_entity_solve(h->g, b.ents + f, b.flag + f, h->lev_count[lev], h->lev_smem[lev],
                              h->lev_grid[lev], h->lev_lstride[lev], adaptive ? 1 : 0, h->single,
-                             h->lev_gbytes[lev],
-                             h->lev_blocked[lev], b, h->stream));
+                             h->lev_blocked[lev], h->lev_gbytes[lev], b, h->stream));
     }
   }
   h->built = true;
@@ -666,9 +672,14 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     // MSFE with a symmetric A: R A P = P^T A P is symmetric (LDL^T), else band LU
     const int sym = o.restriction != 1 && !nonsym;
-    CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
-    CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
+    if (h->coarse_inv) {
+      CK(launch_coarse_factor_f32(h->c, h->mc, b, h->stream));
+    } else {
+      CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
+      CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
+    }
   }
+  if (h->coarse_inv) LAUNCH(CAMS_PROF_COARSE_INV, launch_coarse_zinv(h->c.Nc, h->mc, b, h->stream));
   LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta,
                                                   h->single, nonsym, h->stream));
   return check_status(h);
@@ -730,8 +741,11 @@ int cams_step_direct(cams_handle* h) {
   }
   const int fv = h->opt.restriction == 1;
   LAUNCH(CAMS_PROF_RESTRICT, launch_restrict(h->g, h->c, fv, b.r, s, b, h->stream));
-  LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv && !h->opt.jacobian,
-                                                   h->coarse_cluster, s, b, h->stream));
+  if (h->coarse_inv)
+    LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_coarse_solve_f32(h->c.Nc, h->mc, b, h->stream));
+  else
+    LAUNCH(CAMS_PROF_COARSE_SOLVE, launch_band_solve(h->c.Nc, h->mc, !fv && !h->opt.jacobian,
+                                                     h->coarse_cluster, s, b, h->stream));
   LAUNCH(CAMS_PROF_PROLONG, launch_prolong_add(h->g, h->c, s, b, h->stream));
   for (int k = 0; k < h->opt.n_post; ++k) {
     int rc = ilu_smooth(h);
@@ -1072,6 +1086,13 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
     perm[I] = Ic[ordc[0]] + na * (Ic[ordc[1]] + nb * Ic[ordc[2]]);
   }
+  {
+    // the mixed preconditioner's symmetric (MSFE) coarse solve by the FP32
+    // inverse factor, where its work and memory stay small
+    const char* ci = std::getenv("CAMS_COARSE_INV");
+    h->coarse_inv = h->single && opt->restriction != 1 && !opt->jacobian &&
+                    !(ci && ci[0] == '0') && coarse_inverse_ok(c.Nc, h->mc);
+  }
   rc = alloc_all(h);
   if (rc) {
     const std::string msg = h->err;
@@ -1089,11 +1110,12 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
     const char* lv = std::getenv("CAMS_ILU_LEVEL");
     h->ilu_pipelined = !(lv && lv[0] == '1');
     h->ilu_grid = ilu_pipe_grid(h->g, prop.multiProcessorCount);
-    // 2 x 2 tile blocks per CTA pay off for the FP32 smoother (measured ~5%
-    // faster sweeps); the FP64 one is faster with one tile per warp.
-    // CAMS_ILU_CTA=1 / 0 forces either.
+    // One tile per warp for both precisions (with the cross-tile loads
+    // issued ahead of the operand copies it measured faster than 2 x 2 tile
+    // blocks per CTA: 143 against 161 us a 4M-cell FP32 sweep).
+    // CAMS_ILU_CTA=1 forces the tile blocks.
     const char* ct = std::getenv("CAMS_ILU_CTA");
-    const bool want = ct ? ct[0] == '1' : h->single;
+    const bool want = ct && ct[0] == '1';
     h->ilu_cta = want && ilu_cta_ok(h->g, (int)prop.sharedMemPerBlockOptin);
     const char* cc = std::getenv("CAMS_COARSE_CLUSTER");
     h->coarse_cluster = !(cc && cc[0] == '0') &&

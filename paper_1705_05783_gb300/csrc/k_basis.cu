@@ -608,11 +608,18 @@ int entity_smem_bytes(const Entity& E, bool single, bool blocked) {
   return elems * (int)(single ? sizeof(float) : sizeof(double));
 }
 
+// A window in global memory belongs to the blocked solver only, and each
+// CTA's slice must keep every element aligned (the slices are 256 bytes apart).
+static bool window_ok(bool blocked, long long gbytes, const Buffers& b) {
+  return gbytes == 0 || (blocked && gbytes % 256 == 0 && b.lwork != nullptr);
+}
+
 cudaError_t launch_entity_solve(const Geo& g, const Entity* ents, const unsigned char* flag,
                                 int count, int smem, int grid, long long lstride, int adaptive,
                                 bool single, bool blocked, long long gbytes, Buffers& b,
                                 cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (!window_ok(blocked, gbytes, b)) return cudaErrorInvalidValue;
   if (grid > count) grid = count;
   if (single) {
     float* ls = reinterpret_cast<float*>(b.lscratch);
@@ -645,6 +652,7 @@ cudaError_t launch_entity_cf(const Geo& g, const Entity* ents, int count, int sm
                              long long lstride, bool single, bool blocked, long long gbytes,
                              Buffers& b, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (!window_ok(blocked, gbytes, b)) return cudaErrorInvalidValue;
   if (grid > count) grid = count;
   if (single) {
     float* ls = reinterpret_cast<float*>(b.lscratch);

@@ -331,8 +331,9 @@ __global__ void __launch_bounds__(128) k_galerkin_fe_ns(
 // Natural-order 27-point stencil -> column-major band in the reordered
 // index.  General (MSFV): Bc[col*(2m+1) + (row - col + m)].  Symmetric
 // (MSFE): lower triangle only, W[col*(m+1) + (row - col)].
+template <class TB>
 __global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ Acs,
-                            const int* __restrict__ perm, double* band) {
+                            const int* __restrict__ perm, TB* band) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= 27LL * c.Nc) return;
   const int I = (int)(q / 27), t = (int)(q % 27);
@@ -347,9 +348,9 @@ __global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ A
   }
   const int row = perm[I], col = perm[J];
   if (sym) {
-    if (row >= col) band[(long long)col * (m + 1) + (row - col)] = Acs[q];
+    if (row >= col) band[(long long)col * (m + 1) + (row - col)] = (TB)Acs[q];
   } else {
-    band[(long long)col * (2 * m + 1) + (row - col + m)] = Acs[q];
+    band[(long long)col * (2 * m + 1) + (row - col + m)] = (TB)Acs[q];
   }
 }
 
@@ -372,18 +373,22 @@ __global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ A
 constexpr int kTB = 16;
 constexpr int kTri = kTB * (kTB + 1) / 2;   // lower-triangle elements of a diagonal block
 
-__device__ __forceinline__ double band_at(const double* W, int m, int r, int c) {
+template <class T>
+__device__ __forceinline__ T band_at(const T* W, int m, int r, int c) {
   // lower band, column-major; 0 outside the band
-  return (r - c <= m && r >= c) ? W[(long long)c * (m + 1) + (r - c)] : 0.0;
+  return (r - c <= m && r >= c) ? W[(long long)c * (m + 1) + (r - c)] : T(0);
 }
 
-__global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const double* __restrict__ Wr,
-                                                    double* W, double* Lc, int* status) {
-  __shared__ double A[kTB][kTB + 1];        // diagonal block; column q keeps d_q l_rq
-  __shared__ double L[kTB][kTB + 1];        // l_rq below the diagonal
-  __shared__ double rinv[kTB];              // 1 / d_q
-  __shared__ double V[2 * kTB][kTB + 1];    // panel rows: a_rq in, l_rq out
-  __shared__ double VD[2 * kTB][kTB + 1];   // d_q l_rq of the panel rows
+// T: the precision of the factorisation (FP64, or FP32 for the mixed
+// preconditioner's coarse solve)
+template <class T>
+__global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const T* __restrict__ Wr,
+                                                    T* W, T* Lc, int* status) {
+  __shared__ T A[kTB][kTB + 1];        // diagonal block; column q keeps d_q l_rq
+  __shared__ T L[kTB][kTB + 1];        // l_rq below the diagonal
+  __shared__ T rinv[kTB];              // 1 / d_q
+  __shared__ T V[2 * kTB][kTB + 1];    // panel rows: a_rq in, l_rq out
+  __shared__ T VD[2 * kTB][kTB + 1];   // d_q l_rq of the panel rows
   const int c1 = min(c0 + kTB, N) - 1;
   const int tb = c1 - c0 + 1;
   const int tid = threadIdx.x;
@@ -407,12 +412,12 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
   // --- stage the diagonal block and the 2 kTB panel rows ---
   {
     const int r = tid / kTB, q = tid % kTB;
-    A[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : 0.0;
+    A[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : T(0);
   }
   for (int e = tid; e < 2 * kTB * kTB; e += blockDim.x) {
     const int k = e / kTB, q = e % kTB;
     const int r = (k < kTB ? r0 + k : cc0 + k - kTB);
-    V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : 0.0;
+    V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : T(0);
   }
   // element of the lower triangle owned by this thread (row-major order)
   int er = 0, ec = -1;
@@ -423,25 +428,25 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
   }
   __syncthreads();
   if (tid == 0) {
-    double d = A[0][0];
-    if (!(d > 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
-    rinv[0] = 1.0 / d;
+    T d = A[0][0];
+    if (!(d > T(0)) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = T(1); }
+    rinv[0] = T(1) / d;
   }
   __syncthreads();
   // --- factor the diagonal block ---
   for (int q = 0; q < tb; ++q) {
     if (ec >= 0 && er < tb) {
-      const double rq = rinv[q];
+      const T rq = rinv[q];
       if (ec == q && er > q) {
         L[er][q] = A[er][q] * rq;
       } else if (ec > q) {
-        const double t = A[er][q] * rq;
-        const double v = fma(-t, A[ec][q], A[er][ec]);
+        const T t = A[er][q] * rq;
+        const T v = fma(-t, A[ec][q], A[er][ec]);
         A[er][ec] = v;
         if (er == q + 1 && ec == q + 1) {     // the next pivot is final
-          double d = v;
-          if (!(d > 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
-          rinv[q + 1] = 1.0 / d;
+          T d = v;
+          if (!(d > T(0)) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = T(1); }
+          rinv[q + 1] = T(1) / d;
         }
       }
     }
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
   // --- panel rows: l_rq = (a_rq - sum_{k<q} l_rk d_k l_qk) / d_q, four threads a row ---
   if (tid < 4 * 2 * kTB) {
     const int k = tid >> 2, t = tid & 3;
-    double v[kTB / 4];
+    T v[kTB / 4];
 #pragma unroll
     for (int j = 0; j < kTB / 4; ++j) v[j] = V[k][4 * j + t];
     const unsigned mask = 0xffffffffu;
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
 #pragma unroll
     for (int q = 0; q < kTB; ++q) {
       if (q < tb) {                              // uniform across the CTA
-        double l = 0.0;
+        T l = T(0);
         if (t == (q & 3)) {
           VD[k][q] = v[q >> 2];
           l = v[q >> 2] * rinv[q];
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
     const int a = tid / kTB, b = tid % kTB;
     const int r = r0 + a, cc = cc0 + b;
     if (r <= rhi && cc <= rhi && cc <= r && r - cc <= m) {
-      double s = 0.0;
+      T s = T(0);
       for (int q = 0; q < tb; ++q) s = fma(V[a][q], VD[kTB + b][q], s);
       W[(long long)cc * (m + 1) + (r - cc)] -= s;
     }
@@ -501,6 +506,220 @@ __global__ void k_ldlt_rows(int N, int m, const double* __restrict__ Lc, double*
   if (e >= (long long)N * (m + 1)) return;
   const int k = (int)(e / (m + 1)), a = (int)(e % (m + 1));
   Lr[e] = (a == 0) ? Lc[(long long)k * (m + 1)] : (k - a >= 0 ? Lc[(long long)(k - a) * (m + 1) + a] : 0.0);
+}
+
+// ---- the mixed preconditioner's coarse solve by the inverse factor ----
+// With the FP32 factor L D L^T of the coarse matrix, Z = L^{-1} (unit lower
+// triangular, dense below the diagonal) is formed once per factorisation,
+// and every solve is x = Z^T (D^{-1} (Z b)): two matrix-vector products over
+// the lower triangle of Z, which stream Z from memory, in place of a
+// substitution whose N forward and N backward steps depend on one another.
+// In exact arithmetic the result is the substitution's.
+//
+// Column j of Z solves L z = e_j: z_i = 0 (i < j), z_j = 1, and
+// z_i = -sum_{k=max(j,i-m)}^{i-1} l_ik z_k.  A CTA takes 32 consecutive
+// columns and walks their rows in blocks of 32, one row a lane.  For each
+// block it stages the band entries l_ik of its 32 rows (columns k from
+// max(first column, r0 - m) to r0 + 31) in shared memory, the next block's
+// while it works on this one.  Its 32 warps are 8 column groups (kZC
+// columns each) x 4 quarters of the k range: every warp adds its quarter
+// of the terms of the rows before the block (each column group's values of
+// the last m rows sit in a ring in shared memory, four columns per 16-byte
+// entry, written twice so that any window of m rows is contiguous); the
+// first quarter's warp adds the other three partial sums and finishes the
+// block's rows one after the other, each broadcast by shuffle to the rows
+// below it.  Z is column-major with leading dimension ldz (a multiple of
+// 128); rows i >= j of column j are written, the others are never read.
+constexpr int kZC = 4;    // columns of Z per column group (one 16-byte ring entry)
+constexpr int kZG = 8;    // column groups per CTA: 32 columns
+constexpr int kZQ = 4;    // quarters of the k range
+constexpr int kZT = 32 * kZG * kZQ;   // threads per CTA
+
+__device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kZT, 1) k_coarse_zinv(int N, int m, int ring,
+                                                      const float* __restrict__ Lc, float* Z,
+                                                      long long ldz) {
+  // [2][m + 32][32] band tiles, [kZQ - 1][kZG][32] float4 partial sums, then
+  // [kZG][2 ring] float4 rings (ring >= m + 32, a power of two)
+  extern __shared__ __align__(16) float zsm[];
+  const int tw = m + 32;                           // tile columns
+  float* tiles = zsm;
+  float4* part = reinterpret_cast<float4*>(zsm + 2 * tw * 32);
+  float4* rings = part + (kZQ - 1) * kZG * 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cg = warp % kZG, kq = warp / kZG;
+  const int J0 = blockIdx.x * 32;                  // the CTA's first column
+  const int j0 = J0 + cg * kZC;                    // the column group's first column
+  const bool active = j0 < N;
+  float4* R = rings + (size_t)cg * 2 * ring;
+  const int mask = ring - 1, mp = m + 1;
+  for (int t = tid; t < kZG * 2 * ring; t += kZT) rings[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // tile of block r0: Lt[(k - kb) * 32 + (i - r0)] = l_ik inside the band, else 0
+  auto load_tile = [&](int r0, float* Lt) {
+    const int kb = max(J0, r0 - m);
+    const int n = (r0 + 32 - kb) * 32;
+    for (int e = tid; e < n; e += kZT) {
+      const int k = kb + (e >> 5), i = r0 + (e & 31), d = i - k;
+      const bool v = i < N && d >= 1 && d <= m;
+      cp_async4_zfill(Lt + e, v ? Lc + (long long)k * mp + d : Lc, v);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  load_tile(J0, tiles);
+  int buf = 0;
+  for (int r0 = J0; r0 < N; r0 += 32, buf ^= 1) {
+    const float* Lt = tiles + buf * tw * 32;
+    if (r0 + 32 < N) {
+      load_tile(r0 + 32, tiles + (buf ^ 1) * tw * 32);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const int kb = max(J0, r0 - m);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) {
+      // my quarter of the rows before the block (every column is zero above
+      // its own j >= j0)
+      const int klo = max(j0, r0 - m), len = r0 - klo;
+      const int k0 = klo + (len * kq) / kZQ, k1 = klo + (len * (kq + 1)) / kZQ;
+      const float* lp = Lt + (k0 - kb) * 32 + lane;
+      const float4* yp = R + (k0 & mask);          // contiguous: the ring is written twice
+#pragma unroll 8
+      for (int t = 0; t < k1 - k0; ++t) {
+        const float l = lp[t * 32];
+        const float4 y = yp[t];
+        acc.x = fmaf(l, y.x, acc.x);
+        acc.y = fmaf(l, y.y, acc.y);
+        acc.z = fmaf(l, y.z, acc.z);
+        acc.w = fmaf(l, y.w, acc.w);
+      }
+      if (kq > 0) part[((kq - 1) * kZG + cg) * 32 + lane] = acc;
+    }
+    __syncthreads();
+    if (active && kq == 0) {
+#pragma unroll
+      for (int q = 0; q < kZQ - 1; ++q) {
+        const float4 p = part[(q * kZG + cg) * 32 + lane];
+        acc.x += p.x;
+        acc.y += p.y;
+        acc.z += p.z;
+        acc.w += p.w;
+      }
+      float a4[kZC] = {acc.x, acc.y, acc.z, acc.w};
+      // the block's rows, in order
+      float y[kZC];
+#pragma unroll
+      for (int c = 0; c < kZC; ++c) y[c] = 0.f;
+      for (int kk = 0; kk < 32 && r0 + kk < N; ++kk) {
+        const int k = r0 + kk;
+        if (lane == kk) {
+#pragma unroll
+          for (int c = 0; c < kZC; ++c) {
+            const int j = j0 + c;
+            y[c] = k == j ? 1.f : (k > j ? -a4[c] : 0.f);
+          }
+        }
+        const float l = Lt[(k - kb) * 32 + lane];   // 0 for rows at or above k
+#pragma unroll
+        for (int c = 0; c < kZC; ++c) a4[c] = fmaf(l, __shfl_sync(0xffffffffu, y[c], kk), a4[c]);
+      }
+      const int i = r0 + lane;
+      if (i < N) {
+        const float4 yv = make_float4(y[0], y[1], y[2], y[3]);
+        R[i & mask] = yv;
+        R[(i & mask) + ring] = yv;
+#pragma unroll
+        for (int c = 0; c < kZC; ++c) {
+          const int j = j0 + c;
+          if (j < N && i >= j) Z[(long long)j * ldz + i] = y[c];
+        }
+      }
+    }
+    __syncthreads();                               // ring written; the tile buffer is refilled next
+  }
+}
+
+// Partial sums of Z b: CTA (strip s, chunk c) adds, for the 128 rows
+// i0 = 128 s .. i0 + 127, the columns j of chunk c (256 columns) with
+// j <= i; each lane takes four consecutive rows (one 16-byte load per
+// column), each warp 32 columns, and the warps' sums meet in shared memory.
+// part[c * ldz + i].  b is the FP64 restricted residual, rounded to FP32.
+constexpr int kZS = 128;   // rows per strip
+constexpr int kZK = 256;   // columns per chunk
+__global__ void __launch_bounds__(256) k_coarse_zlower(int N, const float* __restrict__ Z,
+                                                       long long ldz, const double* __restrict__ rhs,
+                                                       float* part) {
+  __shared__ float4 red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * kZS, c = blockIdx.y, jc = c * kZK;
+  if (jc > i0 + kZS - 1 || jc >= N) return;        // the whole chunk lies above the strip
+  const int ib = i0 + 4 * lane;                    // my rows ib .. ib + 3
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int jlo = jc + warp * 32, jhi = min(min(jlo + 32, N), i0 + kZS);
+#pragma unroll 8
+  for (int j = jlo; j < jhi; ++j) {
+    const float4 z = *reinterpret_cast<const float4*>(Z + (long long)j * ldz + ib);
+    const float bj = (float)rhs[j];
+    // rows above the diagonal or past N hold no value of Z
+    acc.x += (ib + 0 >= j && ib + 0 < N) ? z.x * bj : 0.f;
+    acc.y += (ib + 1 >= j && ib + 1 < N) ? z.y * bj : 0.f;
+    acc.z += (ib + 2 >= j && ib + 2 < N) ? z.z * bj : 0.f;
+    acc.w += (ib + 3 >= j && ib + 3 < N) ? z.w * bj : 0.f;
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    float4 s = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) {
+      s.x += red[w][lane].x;
+      s.y += red[w][lane].y;
+      s.z += red[w][lane].z;
+      s.w += red[w][lane].w;
+    }
+    *reinterpret_cast<float4*>(part + (long long)c * ldz + ib) = s;
+  }
+}
+
+// t_i = (Z b)_i / d_i: the chunks' partial sums in chunk order.
+__global__ void k_coarse_tsum(int N, int m, const float* __restrict__ Lc,
+                              const float* __restrict__ part, long long ldz, float* t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float s = 0.f;
+  for (int c = 0; c * kZK <= i; ++c) s += part[(long long)c * ldz + i];
+  t[i] = s / Lc[(long long)i * (m + 1)];
+}
+
+// x = Z^T t: one warp per column j (its rows i >= j are contiguous), 16-byte
+// loads from the aligned row j & ~3 on.
+__global__ void __launch_bounds__(256) k_coarse_zupper(int N, const float* __restrict__ Z,
+                                                       long long ldz, const float* __restrict__ t,
+                                                       float* x) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (j >= N) return;
+  const float* col = Z + (long long)j * ldz;
+  float acc = 0.f;
+#pragma unroll 4
+  for (int i = (j & ~3) + 4 * lane; i < N; i += 128) {
+    const float4 z = *reinterpret_cast<const float4*>(col + i);
+    const float4 v = *reinterpret_cast<const float4*>(t + i);
+    acc += (i + 0 >= j) ? z.x * v.x : 0.f;
+    acc += (i + 1 >= j && i + 1 < N) ? z.y * v.y : 0.f;
+    acc += (i + 2 >= j && i + 2 < N) ? z.z * v.z : 0.f;
+    acc += (i + 3 >= j && i + 3 < N) ? z.w * v.w : 0.f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[j] = acc;
 }
 
 // L D L^T x = b, one CTA.  y lives in shared memory; the factor is streamed
@@ -1230,7 +1449,93 @@ cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStre
   const size_t len = sym ? (size_t)c.Nc * (m + 1) : (size_t)c.Nc * (2 * m + 1);
   cudaError_t e = cudaMemsetAsync(b.band, 0, sizeof(double) * len, s);
   if (e != cudaSuccess) return e;
-  k_band_fill<<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, m, sym, b.Acs, b.perm, b.band); count_launches(1);
+  k_band_fill<double><<<(27 * c.Nc + 255) / 256, 256, 0, s>>>(c, m, sym, b.Acs, b.perm, b.band);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// The symmetric band factorisation: one launch per block of kTB columns,
+// each allowed to start while the previous one drains (programmatic
+// dependent launch; the kernel waits for its predecessor).
+template <class T>
+static cudaError_t ldlt_launches(int Nc, int m, T* band, T* Lc, int* status, cudaStream_t s,
+                                 int& launches) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  for (int c0 = 0; c0 < Nc; c0 += kTB) {
+    const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
+    const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
+    const int nb = rhi > c1 ? (rhi - c1 - 1 + kTB) / kTB : 0;
+    const int grid = nb > 0 ? nb * (nb + 1) / 2 : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = c0 == 0 ? 0 : 1;      // the first block follows the band fill normally
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_ldlt_block<T>, Nc, m, c0, (const T*)band, band, Lc,
+                                       status);
+    if (e != cudaSuccess) return e;
+    ++launches;
+  }
+  return cudaSuccess;
+}
+
+long long coarse_ldz(int Nc) { return ((long long)Nc + kZS - 1) / kZS * kZS; }
+
+static int coarse_ring(int m) {
+  int r = 32;
+  while (r < m + 32) r *= 2;
+  return r;
+}
+
+static int zinv_smem(int m) {
+  return (int)sizeof(float) * 2 * (m + 32) * 32 +
+         (int)sizeof(float4) * ((kZQ - 1) * kZG * 32 + kZG * 2 * coarse_ring(m));
+}
+
+long long coarse_part_len(int Nc) { return ((long long)Nc + kZK - 1) / kZK * coarse_ldz(Nc); }
+
+bool coarse_inverse_ok(int Nc, int m) {
+  // forming Z costs about Nc^2 m / 2 FP32 FMAs and holds Nc x ldz floats
+  const double work = (double)Nc * (double)Nc * (double)m;
+  const double bytes = 4.0 * (double)Nc * (double)coarse_ldz(Nc);
+  return Nc > 0 && work <= 2e10 && bytes <= 1073741824.0 && zinv_smem(m) <= 200 * 1024;
+}
+
+cudaError_t launch_coarse_factor_f32(const CGeo& c, int m, Buffers& b, cudaStream_t s) {
+  const int Nc = c.Nc;
+  SingleBuffers& f = b.f32;
+  cudaError_t e = cudaMemsetAsync(f.band, 0, sizeof(float) * (size_t)Nc * (m + 1), s);
+  if (e != cudaSuccess) return e;
+  k_band_fill<float><<<(27 * Nc + 255) / 256, 256, 0, s>>>(c, m, 1, b.Acs, b.perm, f.band);
+  int launches = 1;
+  e = ldlt_launches<float>(Nc, m, f.band, f.Lc, b.status, s, launches);
+  count_launches(launches);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_zinv(int Nc, int m, Buffers& b, cudaStream_t s) {
+  const int smem = zinv_smem(m);
+  cudaError_t e = raise_smem_limit(k_coarse_zinv, smem);
+  if (e != cudaSuccess) return e;
+  k_coarse_zinv<<<(Nc + 31) / 32, kZT, smem, s>>>(Nc, m, coarse_ring(m), b.f32.Lc, b.f32.Z,
+                                                  coarse_ldz(Nc));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_f32(int Nc, int m, Buffers& b, cudaStream_t s) {
+  SingleBuffers& f = b.f32;
+  const long long ldz = coarse_ldz(Nc);
+  const dim3 grid((unsigned)((Nc + kZS - 1) / kZS), (unsigned)((Nc + kZK - 1) / kZK));
+  k_coarse_zlower<<<grid, 256, 0, s>>>(Nc, f.Z, ldz, b.rc, f.zpart);
+  k_coarse_tsum<<<(Nc + 255) / 256, 256, 0, s>>>(Nc, m, f.Lc, f.zpart, ldz, f.tc);
+  k_coarse_zupper<<<(Nc + 7) / 8, 256, 0, s>>>(Nc, f.Z, ldz, f.tc, f.pc);
+  count_launches(3);
   return cudaGetLastError();
 }
 
@@ -1261,23 +1566,8 @@ cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t 
     count_launches(launches);
     return cudaGetLastError();
   }
-  for (int c0 = 0; c0 < Nc; c0 += kTB) {
-    const int c1 = (c0 + kTB < Nc ? c0 + kTB : Nc) - 1;
-    const int rhi = (c1 + m < Nc - 1) ? c1 + m : Nc - 1;
-    const int nb = rhi > c1 ? (rhi - c1 - 1 + kTB) / kTB : 0;
-    const int grid = nb > 0 ? nb * (nb + 1) / 2 : 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = c0 == 0 ? 0 : 1;      // the first block follows the band fill normally
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_ldlt_block, Nc, m, c0, (const double*)b.band,
-                                       b.band, b.Lc, b.status);
-    if (e != cudaSuccess) return e;
-    ++launches;
-  }
+  cudaError_t e = ldlt_launches<double>(Nc, m, b.band, b.Lc, b.status, s, launches);
+  if (e != cudaSuccess) return e;
   const long long n = (long long)Nc * (m + 1);
   k_ldlt_rows<<<(int)((n + 255) / 256), 256, 0, s>>>(Nc, m, b.Lc, b.Lr);
   k_coarse_prep<<<(Nc + kCB - 1) / kCB, 256, 0, s>>>(Nc, m, b.Lc, b.cblk, b.cdinv);

@@ -34,7 +34,8 @@
 //    tile and steps through it; the values a row needs from rows y-1 and
 //    z-1 of its own tile were produced by the neighbouring lanes one step
 //    earlier and arrive by warp shuffle.  Operands are staged into a
-//    per-lane shared-memory ring by cp.async two groups ahead.  Values from
+//    shared-memory ring kG - 1 groups ahead by bulk copies (the TMA
+//    engine; one per operand and group of kU records).  Values from
 //    another tile are read from the sweep's output vector itself, which is
 //    pre-filled with a signalling-NaN sentinel that no arithmetic produces:
 //    a value is ready once it differs from the sentinel, so no flags or
@@ -50,6 +51,7 @@
 //  tiling fixed by the forward direction, its steps read the same records in
 //  reverse order.  x += z follows as a separate coalesced pass (k_apply_z).
 #include "cams_internal.h"
+#include "tc_ptx.h"
 
 namespace cams {
 
@@ -59,8 +61,11 @@ constexpr int kTY = kIluTY, kTZ = kIluTZ, kR = kIluR;
 static_assert(kR == 32, "a tile is one warp");
 constexpr int kWarps = 4;                    // tiles in flight per CTA (one per FP64 pipe)
 constexpr int kU = 4;                        // steps per group (straight-line code)
-constexpr int kG = 3;                        // operand groups in flight (staged 2 groups ahead)
-constexpr int kPad = kG * kU;                // spare records at both ends of a vector
+constexpr int kG = 3;                        // operand ring slots (groups staged kG - 1 ahead)
+constexpr int kPad = 3 * kU;                 // spare records at both ends of a vector
+constexpr bool kBulkStage = false;           // skewed operands staged by bulk copies
+constexpr int kL2Ahead = 0;                  // groups of skewed operands prefetched into L2 ahead
+constexpr bool kFetchFirst = true;           // cross-tile loads issued before the group's staging
 constexpr long long kSpinLimit = 1LL << 22;  // polls before a wait gives up (~ a second)
 constexpr int kFastPolls = 64;               // in-loop polls before a wait starts to sleep
 
@@ -501,11 +506,12 @@ __device__ __forceinline__ typename Word<T>::U wait_shared(const T* p, int* abor
 }
 
 // One tile of a sweep, run by one warp: the tile at (Ym, Zm) in the sweep
-// frame (mirrored for the backward sweep).  ring: this lane's operand ring.
+// frame (mirrored for the backward sweep).  ringw, bars, phase: this warp's
+// operand ring, its slot barriers and their phase bits (kept across tiles).
 // Values from other tiles are read from `out`.  Before its first step the
 // tile waits (lightly) for the upstream values of its first group; steps
 // then run in groups of kU: a group's prologue stages the operands of the
-// group two ahead (cp.async) and prefetches the next group's cross-tile
+// group kG - 1 ahead and prefetches the next group's cross-tile
 // values; values still unset are re-polled together; the kU steps
 // themselves are straight-line code.  Returns false after an abort or a
 // timeout (the warp's copies drained).
@@ -517,7 +523,8 @@ __device__ __forceinline__ typename Word<T>::U wait_shared(const T* p, int* abor
 template <class Op, bool kBackward, bool kCta = false>
 __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const Op& op,
                                            const typename Op::Scalar* out, int* abort_flag,
-                                           int* status, typename Op::Scalar* ring, int lane, int Ym,
+                                           int* status, typename Op::Scalar* ringw,
+                                           uint64_t* bars, uint32_t& phase, int lane, int Ym,
                                            int Zm, const typename Op::Scalar* ey = nullptr,
                                            const typename Op::Scalar* ez = nullptr,
                                            typename Op::Scalar* py = nullptr,
@@ -561,22 +568,75 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
   const long long od = Op::kSkewOut ? dj : di;
   const long long oy0 = o0 + (Op::kSkewOut ? offy_s : offy_n);
   const long long oz0 = o0 + (Op::kSkewOut ? offz_s : offz_n);
-  // operands of steps gs .. gs+kU-1 into ring group q.  Skewed operands
-  // are always in range (spare records); natural ones (the factorisation's)
-  // are clamped to my row (read, then discarded).
+  // Operands of steps gs .. gs+kU-1 into ring slot q, laid out
+  // [slot][operand][step][lane].  Skewed operands (the solves'): the group's
+  // kU records of one operand are contiguous, so one lane issues a bulk copy
+  // per operand (the TMA engine, completing on the slot's mbarrier; the
+  // backward sweep's records arrive in reverse step order).  Bulk copies do
+  // not queue in front of the cross-tile loads of the critical path the way
+  // per-lane copies do.  Groups past the tile are not staged (nor waited
+  // for).  Natural operands (the factorisation's): per-lane cp.async,
+  // clamped to my row (read, then discarded).
+  constexpr bool kBulk = Op::kSkewIn && kBulkStage;
+  T* const ring = ringw + lane;                    // where my cp.async copies land
+  const T* const ring_rd = ringw + (kBulk ? slot : lane);   // a bulk copy keeps record order
+  const long long jr0 = j0 - slot;                 // record of step 0
+  int issued = -1;                                 // last group staged (bulk)
   auto stage = [&](int gs, int q) {
+    if constexpr (kBulk) {
+      if (gs >= sk.ns) return;
+      __syncwarp();                                // the slot's previous reads are done
+      if (lane == 0) {
+        tc::mbar_arrive_expect_tx(bars + q, (uint32_t)(kN * kU * kR * sizeof(T)));
+        const long long rs = kBackward ? jr0 - (long long)(gs + kU - 1) * kR : jr0 + (long long)gs * kR;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      long long i = i0 + (gs + u) * di;
-      if (!Op::kSkewIn) {
+        for (int a = 0; a < kN; ++a)
+          tc::bulk_g2s(ringw + (q * kN + a) * kU * kR, op.src(a, 0, rs),
+                       (uint32_t)(kU * kR * sizeof(T)), bars + q);
+      }
+      issued = gs / kU;
+    } else {
+      if (gs >= sk.ns) {                           // past the tile: an empty group
+        cp_async_commit();
+        return;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        long long i = i0 + (gs + u) * di;
         i = i < row ? row : i;
         i = i > row + g.nx - 1 ? row + g.nx - 1 : i;
-      }
-      const long long j = j0 + (gs + u) * dj;
+        const long long j = j0 + (gs + u) * dj;
 #pragma unroll
-      for (int a = 0; a < kN; ++a) cp_async(ring + ((q * kU + u) * kN + a) * kR, op.src(a, i, j));
+        for (int a = 0; a < kN; ++a) cp_async(ring + ((q * kN + a) * kU + u) * kR, op.src(a, i, j));
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
+  };
+  // the operands of group gq (slot gq % kG) have landed; false after a timeout
+  auto landed = [&](int gq) -> bool {
+    if constexpr (kBulk) {
+      const int q = gq % kG;
+      if (!tc::mbar_wait(bars + q, (phase >> q) & 1u, kSpinLimit)) {
+        if (lane == 0) {
+          atomicOr(status, kStatTimeout);
+          atomicExch(abort_flag, 1);
+        }
+        return false;
+      }
+      phase ^= 1u << q;
+    } else {
+      cp_async_wait<kG - 1>();
+    }
+    return true;
+  };
+  // before leaving early: wait (bounded) for the copies still in flight
+  auto drain = [&](int next) {
+    if constexpr (kBulk) {
+      for (int gq = next; gq <= issued; ++gq)
+        if (!landed(gq)) break;
+    } else {
+      cp_async_wait<0>();
+    }
   };
   // values of steps gs .. gs+kU-1 read from `out` (0 where none is needed)
   auto fetch = [&](int gs, U* cy, U* cz) {
@@ -588,10 +648,25 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
       cz[u] = ld_relaxed_if(gz && in_row, out + oz0 + (gs + u) * od);
     }
   };
-  // the operands of the first two groups do not depend on other tiles:
+  // skewed operands of the group at step gs into L2 (the TMA engine; no
+  // completion to wait for)
+  auto l2_prefetch = [&](int gs) {
+    if (gs >= sk.ns || lane != 0) return;
+    const long long rs = kBackward ? jr0 - (long long)(gs + kU - 1) * kR : jr0 + (long long)gs * kR;
+#pragma unroll
+    for (int a = 0; a < kN; ++a)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(op.src(a, 0, rs)),
+                   "r"((uint32_t)(kU * kR * sizeof(T)))
+                   : "memory");
+  };
+  if constexpr (kL2Ahead > 0 && Op::kSkewIn) {
+#pragma unroll 1
+    for (int gq = kG - 1; gq < kL2Ahead; ++gq) l2_prefetch(gq * kU);
+  }
+  // the operands of the first kG - 1 groups do not depend on other tiles:
   // their copies overlap the first wait
-  stage(0, 0);
-  stage(kU, 1);
+#pragma unroll 1
+  for (int gq = 0; gq < kG - 1; ++gq) stage(gq * kU, gq);
   {
     // The first group's upstream values (the first wait is the long one).
     // A tile publishes in step order, and among my edge lanes the one with
@@ -612,7 +687,7 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
     if (kCta && sy && in_row && last_y) ok &= wait_shared(ey + xq, abort_flag, status) != kNR;
     if (kCta && sz && in_row && last_z) ok &= wait_shared(ez + xq, abort_flag, status) != kNR;
     if (__any_sync(kAll, !ok)) {
-      cp_async_wait<0>();
+      drain(0);
       return false;
     }
   }
@@ -621,9 +696,11 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
   T vprev = T(0), from_y = T(0), from_z = T(0);
   int q = 0;
   for (int s0 = 0; s0 < sk.ns; s0 += kU) {
-    stage(s0 + 2 * kU, q == 0 ? 2 : q - 1);
     U ny_[kU], nz_[kU];
-    fetch(s0 + kU, ny_, nz_);
+    if constexpr (kFetchFirst) fetch(s0 + kU, ny_, nz_);
+    if constexpr (kL2Ahead > 0 && Op::kSkewIn) l2_prefetch(s0 + kL2Ahead * kU);
+    stage(s0 + (kG - 1) * kU, q == 0 ? kG - 1 : q - 1);
+    if constexpr (!kFetchFirst) fetch(s0 + kU, ny_, nz_);
     if (kCta && (sy || sz)) {   // edge values of this group from my CTA's shared memory
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
@@ -665,16 +742,24 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
         }
       }
       if (__any_sync(kAll, fail)) {
-        cp_async_wait<0>();
+        drain(s0 / kU);
         return false;
       }
     }
-    cp_async_wait<2>();
+    if constexpr (kBulk) {
+      if (!__all_sync(kAll, landed(s0 / kU))) {
+        drain(s0 / kU + 1);
+        return false;
+      }
+    } else {
+      cp_async_wait<kG - 1>();
+    }
     T in[kU][kN];
 #pragma unroll
     for (int u = 0; u < kU; ++u)
 #pragma unroll
-      for (int a = 0; a < kN; ++a) in[u][a] = ring[((q * kU + u) * kN + a) * kR];
+      for (int a = 0; a < kN; ++a)
+        in[u][a] = ring_rd[((q * kN + a) * kU + (kBulk && kBackward ? kU - 1 - u : u)) * kR];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int s = s0 + u;
@@ -700,13 +785,34 @@ __device__ __forceinline__ bool sweep_tile(const Geo& g, const Skew& sk, const O
     }
     q = q == kG - 1 ? 0 : q + 1;
   }
-  cp_async_wait<0>();
+  if constexpr (!kBulk) cp_async_wait<0>();   // (every bulk group staged was waited for)
   return true;
 }
 
+// Shared memory of the sweep kernels: the warps' operand rings
+// [kWarps][kG][Op::kN][kU][32], then one mbarrier per ring slot
+// [kWarps][kG] (then, in k_sweep_cta, the edge buffers).
+template <class Op>
+constexpr int ring_bytes() {
+  return (int)sizeof(typename Op::Scalar) * kWarps * kG * Op::kN * kU * kR;
+}
+constexpr int bar_bytes() { return (int)sizeof(uint64_t) * kWarps * kG; }
+
+// This warp's ring and slot barriers (initialised: one arrival each).
+template <class Op>
+__device__ __forceinline__ void warp_ring(unsigned char* smem_raw, int warp, int lane,
+                                          typename Op::Scalar*& ringw, uint64_t*& bars) {
+  ringw = reinterpret_cast<typename Op::Scalar*>(smem_raw) + warp * (kG * Op::kN * kU * kR);
+  bars = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes<Op>()) + warp * kG;
+  if (lane == 0) {
+    for (int q = 0; q < kG; ++q) tc::mbar_init(bars + q, 1);
+    tc::fence_proxy_async();
+  }
+  __syncwarp();
+}
+
 // ctrl: [0] ticket, [1] abort flag.  `out` is the vector the operator
-// publishes into (pre-filled with the sentinel on every cell).  Shared
-// memory: per warp, the operand ring [kG][kU][Op::kN][32].  Each warp
+// publishes into (pre-filled with the sentinel on every cell).  Each warp
 // claims tiles on its own.
 template <class Op, bool kBackward>
 __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, Op op,
@@ -714,9 +820,11 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
                                                                 int* ctrl, int* status) {
   using T = typename Op::Scalar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
+  T* ringw;
+  uint64_t* bars;
+  warp_ring<Op>(smem_raw, warp, lane, ringw, bars);
+  uint32_t phase = 0;
   const int ntiles = sk.nty * sk.ntz;
   for (;;) {
     int t = 0;
@@ -725,7 +833,9 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_warp(Geo g, Skew sk, O
     if (t >= ntiles) return;
     int Ym, Zm;
     tile_of_ticket(t, sk.nty, sk.ntz, Ym, Zm);
-    if (!sweep_tile<Op, kBackward>(g, sk, op, out, ctrl + 1, status, ring, lane, Ym, Zm)) return;
+    if (!sweep_tile<Op, kBackward>(g, sk, op, out, ctrl + 1, status, ringw, bars, phase, lane, Ym,
+                                   Zm))
+      return;
   }
 }
 
@@ -744,13 +854,15 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_cta(Geo g, Skew sk, Op
   static_assert(kWarps == 4, "a CTA block is 2 x 2 tiles");
   using T = typename Op::Scalar;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
   __shared__ int s_ticket;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tym = lane % kTY, tzm = lane / kTY;
   const int wy = warp & 1, wz = warp >> 1;
-  T* ring = smem + warp * (kG * kU * Op::kN * kR) + lane;
-  T* edges = smem + kWarps * (kG * kU * Op::kN * kR);
+  T* ringw;
+  uint64_t* bars;
+  warp_ring<Op>(smem_raw, warp, lane, ringw, bars);
+  uint32_t phase = 0;
+  T* edges = reinterpret_cast<T*>(smem_raw + ring_bytes<Op>() + bar_bytes());
   const long long nx = g.nx;
   T* ey_row = edges + (wz * kTZ + tzm) * nx;                  // y-edge of block column wz, row tz
   T* ez_row = edges + 2 * kTZ * nx + (wy * kTY + tym) * nx;    // z-edge of block row wy, row ty
@@ -775,8 +887,8 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_sweep_cta(Geo g, Skew sk, Op
     tile_of_ticket(t, ncy, ncz, CY, CZ);
     const int Ym = 2 * CY + wy, Zm = 2 * CZ + wz;
     if (Ym < sk.nty && Zm < sk.ntz)
-      sweep_tile<Op, kBackward, true>(g, sk, op, out, ctrl + 1, status, ring, lane, Ym, Zm, ey,
-                                      ez, py, pz);
+      sweep_tile<Op, kBackward, true>(g, sk, op, out, ctrl + 1, status, ringw, bars, phase, lane,
+                                      Ym, Zm, ey, ez, py, pz);
     // a warp that failed falls through: the others see the abort flag in
     // their waits, and the next claim ends the CTA
     __syncthreads();
@@ -803,7 +915,7 @@ inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 template <class Op>
 constexpr int warp_smem() {
-  return (int)sizeof(typename Op::Scalar) * kWarps * kG * kU * Op::kN * kR;
+  return ring_bytes<Op>() + bar_bytes();
 }
 
 template <class Op>

@@ -2,7 +2,8 @@
 // sm_100-family GPUs: tensor-memory allocation, shared-memory matrix
 // descriptors, the BF16 MMA with FP32 accumulation in tensor memory, its
 // completion through an mbarrier, and the tensor-memory loads of the
-// epilogue.  Device code only; every wait is bounded by its caller.
+// epilogue; also mbarrier-tracked bulk copies (global -> shared through the
+// TMA engine).  Device code only; every wait is bounded by its caller.
 #pragma once
 
 #include <cstdint>
@@ -62,6 +63,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     if (it > 64) __nanosleep(64);
   }
   return false;
+}
+
+// The arrive of the one thread that issues a barrier's copies, announcing the
+// bytes they will deliver (the phase completes once all have landed).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// ---- bulk copies (the TMA engine; no tensor map) ----
+// Contiguous global -> shared copy of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned), completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ---- descriptors ----

@@ -6,10 +6,12 @@ an injector and a producer as vertical line wells in opposite corners
 (Reading R16), 10 implicit steps, 10 x 10 x 5 coarse blocks, the (B1) basis
 with adaptive updates at theta = 0.1 (Sec. 4.1.2), 5 ILU(0) post-smoothing
 steps, MSFE or MSFV restriction (Sec. 3, Eq. 7), relative stopping test
-NL_TOL per step.  (The workload's 1e-6 is out of reach at full size: in the
-second step the oracle's linearisations stall near 1.5e-6 relative, its
-inner loops falling to 3 or 4 iterations, and 50 of them do not meet it; at
-1e-5 the third step stalls the same way.)
+NL_TOL per step (1e-5 unless GOLDEN_NL_TOL says otherwise).  (The
+workload's 1e-6 is out of reach at full size: in the second step the
+oracle's lagged-density linearisations stall near 1.5e-6 relative, its inner
+loops falling to 3 or 4 iterations, and 50 of them do not meet it; in the
+third step they stall above 1e-4.  The record keeps the converged steps and
+the first one that does not converge.)
 For every step the record holds the oracle's Newton and C-AMS counts (per
 linearisation), the number of local entities rebuilt, convergence, the 2-norm,
 maximum, minimum and sum of the pressure field, and the pressure at a fixed
@@ -41,7 +43,7 @@ from workloads import WORKLOADS, make_inputs  # noqa: E402
 WORKLOAD = "3d-100x100x50-wells"
 SEED = 0
 N_SAMPLE = 256
-NL_TOL = float(os.environ.get("GOLDEN_NL_TOL", "1e-4"))
+NL_TOL = float(os.environ.get("GOLDEN_NL_TOL", "1e-5"))
 
 
 def golden_path(restriction: int) -> str:

@@ -1,7 +1,8 @@
 """Mixed precision (CAMS_PREC_MIXED): the multiscale preconditioner (basis
-solves and P, restriction/prolongation, ILU(0) factor and sweeps) in FP32
-inside FP64 iterative refinement; assembly, the residual, the update and
-the coarse factorisation stay FP64.  The iteration's fixed point is the
+solves and P, restriction/prolongation, the coarse factor and solve (by
+the inverse factor where it is small enough), ILU(0) factor and sweeps) in
+FP32 inside FP64 iterative refinement; assembly, the Galerkin sums, the
+residual and the update stay FP64.  The iteration's fixed point is the
 FP64 one, so the converged pressure is held to the FP64 oracle: within
 1e-6 relative L-infinity at a 1e-8 relative nonlinear tolerance (and much
 closer in practice), with the Newton count of the oracle to within one.
