@@ -70,7 +70,13 @@ SWEEP_CLASSES = ("ilu_fwd", "ilu_bwd")
 
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + write.sum) for
 # a kernel class on a workload, for the kernels as they stand; see profiles/.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/launch_list_3d-200x200x100-mixed.md (the kernels as of the fetch-first sweeps)
+    ("3d-200x200x100-mixed", "ilu_fwd"): 73.4e6,
+    ("3d-200x200x100-mixed", "ilu_bwd"): 70.8e6,
+    ("3d-200x200x100-mixed", "ilu_resid"): 142.1e6,
+    ("3d-200x200x100-mixed", "ilu_apply"): 32.8e6,
+}
 
 # the same classes with the FP32 preconditioner (4-byte operands; r and p stay FP64)
 BYTES_PER_CELL_MIXED = dict(BYTES_PER_CELL, **{
