@@ -518,21 +518,24 @@ __global__ void k_ldlt_rows(int N, int m, const double* __restrict__ Lc, double*
 //
 // Column j of Z solves L z = e_j: z_i = 0 (i < j), z_j = 1, and
 // z_i = -sum_{k=max(j,i-m)}^{i-1} l_ik z_k.  A CTA takes 32 consecutive
-// columns and walks their rows in blocks of 32, one row a lane.  For each
-// block it stages the band entries l_ik of its 32 rows (columns k from
-// max(first column, r0 - m) to r0 + 31) in shared memory, the next block's
-// while it works on this one.  Its 32 warps are 8 column groups (kZC
-// columns each) x 4 quarters of the k range: every warp adds its quarter
-// of the terms of the rows before the block (each column group's values of
-// the last m rows sit in a ring in shared memory, four columns per 16-byte
-// entry, written twice so that any window of m rows is contiguous); the
-// first quarter's warp adds the other three partial sums and finishes the
-// block's rows one after the other, each broadcast by shuffle to the rows
-// below it.  Z is column-major with leading dimension ldz (a multiple of
-// 128); rows i >= j of column j are written, the others are never read.
+// columns and walks their rows in blocks of 32, one row a lane; its 32 warps
+// are 8 column groups (kZC columns each, one 16-byte ring entry) x 4
+// quarters.  The band entries l_ik of a block's 32 rows (columns k from
+// max(first column, r0 - m) to r0 + 31) are staged in shared memory two
+// blocks ahead (cp.async with zero fill; three tile buffers).  Each column
+// group keeps its values of the last m + 32 rows in a ring in shared memory,
+// written twice so that any window of them is contiguous.  The sum over
+// the rows before a block is split into a far part (rows of the blocks
+// before the previous one) and a near part (the previous block's rows):
+// while the first-quarter warp of each group finishes block b's rows one
+// after the other (each broadcast by shuffle to the rows below it), the
+// other three warps already sum the far part of block b + 1; the near part
+// is then shared by all four.  Z is column-major with leading dimension ldz
+// (a multiple of 128); rows i >= j of column j are written, the others are
+// never read.
 constexpr int kZC = 4;    // columns of Z per column group (one 16-byte ring entry)
 constexpr int kZG = 8;    // column groups per CTA: 32 columns
-constexpr int kZQ = 4;    // quarters of the k range
+constexpr int kZQ = 4;    // warps per column group
 constexpr int kZT = 32 * kZG * kZQ;   // threads per CTA
 
 __device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool valid) {
@@ -542,16 +545,41 @@ __device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bo
                : "memory");
 }
 
+__device__ __forceinline__ void add4(float4& a, const float4& b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
+}
+
+// acc += sum over rows k in [k0, k1) of l_ik y_k (lane = row i - r0), with
+// Lt the tile whose first column is kb and R the column group's ring
+__device__ __forceinline__ void zband(float4& acc, const float* Lt, int kb, const float4* R,
+                                      int mask, int k0, int k1, int lane) {
+  const float* lp = Lt + (k0 - kb) * 32 + lane;
+  const float4* yp = R + (k0 & mask);              // contiguous: the ring is written twice
+#pragma unroll 8
+  for (int t = 0; t < k1 - k0; ++t) {
+    const float l = lp[t * 32];
+    const float4 y = yp[t];
+    acc.x = fmaf(l, y.x, acc.x);
+    acc.y = fmaf(l, y.y, acc.y);
+    acc.z = fmaf(l, y.z, acc.z);
+    acc.w = fmaf(l, y.w, acc.w);
+  }
+}
+
 __global__ void __launch_bounds__(kZT, 1) k_coarse_zinv(int N, int m, int ring,
                                                       const float* __restrict__ Lc, float* Z,
                                                       long long ldz) {
-  // [2][m + 32][32] band tiles, [kZQ - 1][kZG][32] float4 partial sums, then
-  // [kZG][2 ring] float4 rings (ring >= m + 32, a power of two)
+  // [3][m + 32][32] band tiles, [2][kZQ - 1][kZG][32] float4 far sums,
+  // [kZQ - 1][kZG][32] float4 near sums, [kZG][2 ring] float4 rings
   extern __shared__ __align__(16) float zsm[];
   const int tw = m + 32;                           // tile columns
   float* tiles = zsm;
-  float4* part = reinterpret_cast<float4*>(zsm + 2 * tw * 32);
-  float4* rings = part + (kZQ - 1) * kZG * 32;
+  float4* farp = reinterpret_cast<float4*>(zsm + 3 * tw * 32);
+  float4* nearp = farp + 2 * (kZQ - 1) * kZG * 32;
+  float4* rings = nearp + (kZQ - 1) * kZG * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cg = warp % kZG, kq = warp / kZG;
   const int J0 = blockIdx.x * 32;                  // the CTA's first column
@@ -559,7 +587,9 @@ __global__ void __launch_bounds__(kZT, 1) k_coarse_zinv(int N, int m, int ring,
   const bool active = j0 < N;
   float4* R = rings + (size_t)cg * 2 * ring;
   const int mask = ring - 1, mp = m + 1;
-  for (int t = tid; t < kZG * 2 * ring; t += kZT) rings[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int t = tid; t < kZG * 2 * ring; t += kZT) rings[t] = zero4;
+  for (int t = tid; t < 3 * (kZQ - 1) * kZG * 32; t += kZT) farp[t] = zero4;   // far and near sums
   // tile of block r0: Lt[(k - kb) * 32 + (i - r0)] = l_ik inside the band, else 0
   auto load_tile = [&](int r0, float* Lt) {
     const int kb = max(J0, r0 - m);
@@ -571,46 +601,34 @@ __global__ void __launch_bounds__(kZT, 1) k_coarse_zinv(int N, int m, int ring,
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
+  const int nblk = (N - J0 + 31) / 32;
   load_tile(J0, tiles);
-  int buf = 0;
-  for (int r0 = J0; r0 < N; r0 += 32, buf ^= 1) {
-    const float* Lt = tiles + buf * tw * 32;
-    if (r0 + 32 < N) {
-      load_tile(r0 + 32, tiles + (buf ^ 1) * tw * 32);
+  if (nblk > 1) load_tile(J0 + 32, tiles + tw * 32);
+  for (int b = 0; b < nblk; ++b) {
+    const int r0 = J0 + 32 * b;
+    const float* Lt = tiles + (b % 3) * tw * 32;
+    const float* Ln = tiles + ((b + 1) % 3) * tw * 32;
+    if (b + 2 < nblk) {
+      load_tile(r0 + 64, tiles + ((b + 2) % 3) * tw * 32);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
     } else {
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    __syncthreads();
+    __syncthreads();                               // tiles b, b+1 in; rows < r0 in the rings
     const int kb = max(J0, r0 - m);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // near part of block b: the previous block's rows, a quarter per warp
+    float4 acc = zero4;
     if (active) {
-      // my quarter of the rows before the block (every column is zero above
-      // its own j >= j0)
-      const int klo = max(j0, r0 - m), len = r0 - klo;
-      const int k0 = klo + (len * kq) / kZQ, k1 = klo + (len * (kq + 1)) / kZQ;
-      const float* lp = Lt + (k0 - kb) * 32 + lane;
-      const float4* yp = R + (k0 & mask);          // contiguous: the ring is written twice
-#pragma unroll 8
-      for (int t = 0; t < k1 - k0; ++t) {
-        const float l = lp[t * 32];
-        const float4 y = yp[t];
-        acc.x = fmaf(l, y.x, acc.x);
-        acc.y = fmaf(l, y.y, acc.y);
-        acc.z = fmaf(l, y.z, acc.z);
-        acc.w = fmaf(l, y.w, acc.w);
-      }
-      if (kq > 0) part[((kq - 1) * kZG + cg) * 32 + lane] = acc;
+      const int nlo = max(max(j0, r0 - m), r0 - 32), n = r0 - nlo;
+      if (n > 0) zband(acc, Lt, kb, R, mask, nlo + (n * kq) / kZQ, nlo + (n * (kq + 1)) / kZQ, lane);
+      if (kq > 0) nearp[((kq - 1) * kZG + cg) * 32 + lane] = acc;
     }
     __syncthreads();
     if (active && kq == 0) {
 #pragma unroll
       for (int q = 0; q < kZQ - 1; ++q) {
-        const float4 p = part[(q * kZG + cg) * 32 + lane];
-        acc.x += p.x;
-        acc.y += p.y;
-        acc.z += p.z;
-        acc.w += p.w;
+        add4(acc, nearp[(q * kZG + cg) * 32 + lane]);
+        add4(acc, farp[(((b & 1) * (kZQ - 1) + q) * kZG + cg) * 32 + lane]);
       }
       float a4[kZC] = {acc.x, acc.y, acc.z, acc.w};
       // the block's rows, in order
@@ -641,8 +659,18 @@ __global__ void __launch_bounds__(kZT, 1) k_coarse_zinv(int N, int m, int ring,
           if (j < N && i >= j) Z[(long long)j * ldz + i] = y[c];
         }
       }
+    } else if (active && b + 1 < nblk) {
+      // far part of block b + 1 (rows of the blocks before b), a third per warp
+      const int r1 = r0 + 32, kb1 = max(J0, r1 - m);
+      const int flo = max(j0, r1 - m), n = r0 - flo;
+      float4 f = zero4;
+      if (n > 0) {
+        const int w = kq - 1;
+        zband(f, Ln, kb1, R, mask, flo + (n * w) / (kZQ - 1), flo + (n * (w + 1)) / (kZQ - 1), lane);
+      }
+      farp[((((b + 1) & 1) * (kZQ - 1) + (kq - 1)) * kZG + cg) * 32 + lane] = f;
     }
-    __syncthreads();                               // ring written; the tile buffer is refilled next
+    __syncthreads();                               // ring written; tile b is refilled next
   }
 }
 
@@ -1492,8 +1520,8 @@ static int coarse_ring(int m) {
 }
 
 static int zinv_smem(int m) {
-  return (int)sizeof(float) * 2 * (m + 32) * 32 +
-         (int)sizeof(float4) * ((kZQ - 1) * kZG * 32 + kZG * 2 * coarse_ring(m));
+  return (int)sizeof(float) * 3 * (m + 32) * 32 +
+         (int)sizeof(float4) * (3 * (kZQ - 1) * kZG * 32 + kZG * 2 * coarse_ring(m));
 }
 
 long long coarse_part_len(int Nc) { return ((long long)Nc + kZK - 1) / kZK * coarse_ldz(Nc); }
