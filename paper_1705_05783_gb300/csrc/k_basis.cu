@@ -313,75 +313,162 @@ __global__ void __launch_bounds__(256) k_entity_solve_blk(
       const int k_slot = k % R;                    // ring slot of row k
       const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
       for (int t = tid; t < (m + kKB) * kLPS; t += nt) Lp[t] = T(0);
-      if (tid == 0) {
-        T d = W[k_slot * mp];
-        if (!(d > T(0)) || !isfinite(d)) { atomicOr(status, kStatSingular); d = T(1); }
-        s_d[0] = d;
-        s_dinv[0] = T(1) / d;
-        for (int q = kb; q < kKB; ++q) { s_d[q] = T(0); s_dinv[q] = T(0); }
-      }
-      __syncthreads();
-      {  // scale column k: l_{i,k} = a_{i,k} / d_k
-        const int rmax = min(m, n - 1 - k);
-        const T dinv = s_dinv[0];
-        for (int a = 1 + tid; a <= rmax; a += nt) {
-          int sl = k_slot + a;
-          if (sl >= R) sl -= R;
-          T* w = W + sl * mp + a;
-          const T l = *w * dinv;
-          *w = l;
-          Lp[a * kLPS] = l;
+      if constexpr (sizeof(T) == 4) {
+        // FP32: the panel's diagonal block by one warp, then its rows below
+        // by one thread a row (three barriers a panel)
+        __syncthreads();
+        // --- the panel's kb x kb diagonal block, by warp 0: lane r holds row
+        // k+r (x[c] = a_{k+r,k+c}, c <= r); after pivot c, lanes r > c hold
+        // l_{k+r,k+c} and have updated their later entries.  Then the
+        // right-hand sides of the panel's rows, lane r' < nr one column. ---
+        if (warp == 0) {
+          T x[kKB];
+          int rs = k_slot + lane;                    // slot of row k+lane
+          if (rs >= R) rs -= R;
+  #pragma unroll
+          for (int c = 0; c < kKB; ++c)
+            x[c] = (lane < kb && c <= lane && lane - c <= m) ? W[rs * mp + (lane - c)] : T(0);
+  #pragma unroll
+          for (int c = 0; c < kKB; ++c) {
+            if (c < kb) {                            // uniform
+              T d = __shfl_sync(0xffffffffu, x[c], c);
+              if (!(d > T(0)) || !isfinite(d)) {
+                if (lane == 0) atomicOr(status, kStatSingular);
+                d = T(1);
+              }
+              const T dinv = T(1) / d;
+              if (lane == c) { s_d[c] = d; s_dinv[c] = dinv; }
+              if (lane > c && lane < kb) x[c] *= dinv;
+              // x[c'] -= l_{r,c} d_c l_{c',c} for c < c' <= r (the diagonal too)
+  #pragma unroll
+              for (int cp = c + 1; cp < kKB; ++cp) {
+                const T lcp = __shfl_sync(0xffffffffu, x[c], cp);
+                if (cp <= lane && lane < kb) x[cp] -= x[c] * d * lcp;
+              }
+            }
+          }
+          if (lane < kb) {
+  #pragma unroll
+            for (int c = 0; c < kKB; ++c) {
+              if (c < lane) {
+                if (lane - c <= m) W[rs * mp + (lane - c)] = x[c];
+                Lp[lane * kLPS + c] = x[c];
+              }
+            }
+          }
+          if (lane == 0)
+            for (int q = kb; q < kKB; ++q) { s_d[q] = T(0); s_dinv[q] = T(0); }
+          // forward substitution of the panel's rows in the right-hand sides
+  #pragma unroll
+          for (int r = 1; r < kKB; ++r) {
+  #pragma unroll
+            for (int c = 0; c < kKB; ++c) {
+              if (c < r) {
+                const T l = __shfl_sync(0xffffffffu, x[c], r);
+                if (r < kb && lane < nr) Y[(k + r) * nr + lane] -= l * Y[(k + c) * nr + lane];
+              }
+            }
+          }
         }
-      }
-      __syncthreads();
-      // --- the panel's pivots, eliminating within the panel only.  Warp c
-      // updates column k+q+1+c; warp 0 then also forms pivot q+1 and scales
-      // its column, so one barrier per pivot suffices. ---
-      for (int q = 0; q < kb; ++q) {
-        const int kq = k + q;
-        const int rmax = min(m, n - 1 - kq);       // rows kq+1 .. kq+rmax hold column kq
-        const T dq = s_d[q];
-        const int ncol = kb - 1 - q;
-        for (int c = warp; c < ncol; c += nwarp) {
-          //   a_{i,k+q'} -= l_{i,kq} d_q l_{k+q',kq},  rows k+q' .. kq+rmax
-          const int qp = q + 1 + c;
-          const T u = Lp[qp * kLPS + q] * dq;
-          int base = k_slot + qp;                  // slot of row k+q'
-          if (base >= R) base -= R;
-          for (int a = lane; a < rmax - c; a += 32) {
-            int sl = base + a;
+        __syncthreads();
+        // --- the panel's rows below the block, one thread a row:
+        // l_{i,k+c} = (a_{i,k+c} - sum_{c'<c} t_{c'} l_{k+c,k+c'}) / d_c, with
+        // t_{c'} = l_{i,k+c'} d_{c'} (the entries outside the band are zero) ---
+        {
+          const int amax = min(kb + m - 1, n - 1 - k);   // rows k+kb .. k+amax
+          for (int a = kb + tid; a <= amax; a += nt) {
+            int sl = k_slot + a;
+            if (sl >= R) sl -= R;
+            T* wrow = W + sl * mp;
+            T t[kKB];
+  #pragma unroll
+            for (int c = 0; c < kKB; ++c) {
+              T v = (c < kb && a - c <= m) ? wrow[a - c] : T(0);
+  #pragma unroll
+              for (int cp = 0; cp < c; ++cp) v -= t[cp] * Lp[c * kLPS + cp];
+              t[c] = v;
+              const T l = v * s_dinv[c];
+              if (c < kb && a - c <= m) {
+                wrow[a - c] = l;
+                Lp[a * kLPS + c] = l;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      } else {
+        // FP64: pivot by pivot across the CTA (one barrier a pivot), the
+        // order of operations the FP64 parity bar was established with
+        if (tid == 0) {
+          T d = W[k_slot * mp];
+          if (!(d > T(0)) || !isfinite(d)) { atomicOr(status, kStatSingular); d = T(1); }
+          s_d[0] = d;
+          s_dinv[0] = T(1) / d;
+          for (int q = kb; q < kKB; ++q) { s_d[q] = T(0); s_dinv[q] = T(0); }
+        }
+        __syncthreads();
+        {  // scale column k: l_{i,k} = a_{i,k} / d_k
+          const int rmax = min(m, n - 1 - k);
+          const T dinv = s_dinv[0];
+          for (int a = 1 + tid; a <= rmax; a += nt) {
+            int sl = k_slot + a;
             if (sl >= R) sl -= R;
             T* w = W + sl * mp + a;
-            *w -= Lp[(qp + a) * kLPS + q] * u;
+            const T l = *w * dinv;
+            *w = l;
+            Lp[a * kLPS] = l;
           }
-          if (c == 0) {
-            // column k+q+1 is final: its pivot, then l_{i,k+q+1} for rows
-            // k+q+2 .. k+q+1+rmax1
-            __syncwarp();
-            T d = W[base * mp];
-            if (!(d > T(0)) || !isfinite(d)) {
-              if (lane == 0) atomicOr(status, kStatSingular);
-              d = T(1);
-            }
-            const T dinv = T(1) / d;
-            if (lane == 0) { s_d[q + 1] = d; s_dinv[q + 1] = dinv; }
-            const int rmax1 = min(m, n - 1 - (kq + 1));
-            for (int a = 1 + lane; a <= rmax1; a += 32) {
+        }
+        __syncthreads();
+        // --- the panel's pivots, eliminating within the panel only.  Warp c
+        // updates column k+q+1+c; warp 0 then also forms pivot q+1 and scales
+        // its column, so one barrier per pivot suffices. ---
+        for (int q = 0; q < kb; ++q) {
+          const int kq = k + q;
+          const int rmax = min(m, n - 1 - kq);       // rows kq+1 .. kq+rmax hold column kq
+          const T dq = s_d[q];
+          const int ncol = kb - 1 - q;
+          for (int c = warp; c < ncol; c += nwarp) {
+            //   a_{i,k+q'} -= l_{i,kq} d_q l_{k+q',kq},  rows k+q' .. kq+rmax
+            const int qp = q + 1 + c;
+            const T u = Lp[qp * kLPS + q] * dq;
+            int base = k_slot + qp;                  // slot of row k+q'
+            if (base >= R) base -= R;
+            for (int a = lane; a < rmax - c; a += 32) {
               int sl = base + a;
               if (sl >= R) sl -= R;
               T* w = W + sl * mp + a;
-              const T l = *w * dinv;
-              *w = l;
-              Lp[(qp + a) * kLPS + qp] = l;
+              *w -= Lp[(qp + a) * kLPS + q] * u;
+            }
+            if (c == 0) {
+              // column k+q+1 is final: its pivot, then l_{i,k+q+1} for rows
+              // k+q+2 .. k+q+1+rmax1
+              __syncwarp();
+              T d = W[base * mp];
+              if (!(d > T(0)) || !isfinite(d)) {
+                if (lane == 0) atomicOr(status, kStatSingular);
+                d = T(1);
+              }
+              const T dinv = T(1) / d;
+              if (lane == 0) { s_d[q + 1] = d; s_dinv[q + 1] = dinv; }
+              const int rmax1 = min(m, n - 1 - (kq + 1));
+              for (int a = 1 + lane; a <= rmax1; a += 32) {
+                int sl = base + a;
+                if (sl >= R) sl -= R;
+                T* w = W + sl * mp + a;
+                const T l = *w * dinv;
+                *w = l;
+                Lp[(qp + a) * kLPS + qp] = l;
+              }
             }
           }
+          // right-hand sides of the panel's later rows
+          for (int t = tid; t < (ncol << lnr); t += nt) {
+            const int i = kq + 1 + (t >> lnr), r = t & (nr - 1);
+            Y[i * nr + r] -= Lp[(i - k) * kLPS + q] * Y[kq * nr + r];
+          }
+          __syncthreads();
         }
-        // right-hand sides of the panel's later rows
-        for (int t = tid; t < (ncol << lnr); t += nt) {
-          const int i = kq + 1 + (t >> lnr), r = t & (nr - 1);
-          Y[i * nr + r] -= Lp[(i - k) * kLPS + q] * Y[kq * nr + r];
-        }
-        __syncthreads();
       }
       // --- rank-kb update of the trailing window and of the right-hand sides ---
       const int me = min(m, n - (k + kb));        // trailing rows k+kb .. k+kb+me-1
