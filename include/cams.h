@@ -122,12 +122,13 @@ typedef struct {
                           R A P, restriction and prolongation, ILU(0) factor and sweeps) runs
                           in FP32 on the correction equation A delta = r inside FP64 iterative
                           refinement (block sums of R A P and of R r in FP64); assembly, the
-                          residual r = f - A p and the update p += delta stay FP64.  The
-                          symmetric (MSFE) coarse system is factored in FP32 and solved as
-                          Z^T D^{-1} Z R r with Z = L^{-1} formed once per factorisation,
-                          where that costs at most 2e10 FMAs and 1 GiB (environment variable
-                          CAMS_COARSE_INV=0 at setup: FP64 factor, FP32 substitution with its
-                          copy); the MSFV coarse system is factored and solved in FP64.
+                          residual r = f - A p, the update p += delta and the coarse-system
+                          factorisation stay FP64.  The symmetric (MSFE) coarse system is then
+                          solved in FP32 as Z^T D^{-1} Z R r, Z = L^{-1} of the factor's FP32
+                          copy formed once per factorisation, where that costs at most 2e10
+                          FMAs and 1 GiB (environment variable CAMS_COARSE_INV=0 at setup: FP32
+                          substitution with the factor's copy); the MSFV coarse system is
+                          factored and solved in FP64.
                           Converges to the same fixed point (the FP64 residual decides the
                           stopping tests). */
   int cf;              /* 1: correction functions (Sec. 3; Table 1 step 4) open every C-AMS

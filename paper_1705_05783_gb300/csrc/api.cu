@@ -76,6 +76,8 @@ struct cams_handle {
   bool graphs = true;               // CAMS_GRAPHS=0 launches every kernel directly
   cudaGraphExec_t step_exec = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;   // the ILU(0) factorisation beside the coarse one
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long step_launches = 0;
   // the whole inner loop of a linearisation as one graph: a conditional WHILE
   // node around one iteration, the residual norm and the stopping test
@@ -306,7 +308,6 @@ int alloc_all(cams_handle* h) {
     AL(f.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(f.Lr, (size_t)h->c.Nc * (h->mc + 1));
     AL(f.cblk, coarse_blocks_len(h->c.Nc)); AL(f.cdinv, h->c.Nc);
     if (h->coarse_inv) {
-      AL(f.band, (size_t)h->c.Nc * (h->mc + 1));
       AL(f.Z, (size_t)h->c.Nc * (size_t)coarse_ldz(h->c.Nc));
       AL(f.tc, coarse_ldz(h->c.Nc));
       AL(f.zpart, coarse_part_len(h->c.Nc));
@@ -372,7 +373,7 @@ void free_all(cams_handle* h) {
   const SingleBuffers& f = b.f32;
   void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
                    f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz, f.Lc, f.Lr, f.cblk, f.cdinv,
-                   f.band, f.Z, f.tc, f.zpart, f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
+                   f.Z, f.tc, f.zpart, f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
                    f.Azu != f.Az ? f.Azu : nullptr};
   for (void* p : fptrs)
     if (p) cudaFree(p);
@@ -619,6 +620,25 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   Buffers& b = h->b;
   const cams_options& o = h->opt;
   const int ne = (int)h->ents.size();
+  const bool nonsym = o.jacobian != 0;
+  // The ILU(0) factorisation needs only A: it runs on a second stream while
+  // the basis, R A P and the coarse factorisation (latency-bound chains that
+  // leave most SMs idle) run on the handle's stream, and the handle's stream
+  // waits for it at the end.  With per-class profiling on, everything stays
+  // on one stream so that each class is timed alone.
+  const bool overlap = !h->prof;
+  if (overlap) {
+    if (!h->aux_stream) {
+      CK(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+    CK(launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta, h->single, nonsym,
+                         h->aux_stream));
+    CK(cudaEventRecord(h->ev_join, h->aux_stream));
+  }
   LAUNCH(CAMS_PROF_BASIS_OP, launch_basis_operator(h->g, h->fl, o.basis, h->dt,
                                                      h->have_fix ? b.fixm : nullptr, b, h->stream));
   const bool adaptive = o.basis != 4;
@@ -663,7 +683,6 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
   if (n_rebuilt) *n_rebuilt = rebuilt;
   // Galerkin coarse operator and its factorisation
   // restriction 2 iterates with MSFE (its MSFV correction closes the step)
-  const bool nonsym = o.jacobian != 0;
   if (o.restriction != 1)
     LAUNCH(CAMS_PROF_GALERKIN, launch_galerkin_fe(h->g, h->c, h->single, nonsym, b, h->stream));
   else
@@ -673,15 +692,18 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
     // MSFE with a symmetric A: R A P = P^T A P is symmetric (LDL^T), else band LU
     const int sym = o.restriction != 1 && !nonsym;
     if (h->coarse_inv) {
-      CK(launch_coarse_factor_f32(h->c, h->mc, b, h->stream));
+      CK(launch_coarse_factor_inv(h->c, h->mc, b, h->stream));
     } else {
       CK(launch_band_fill(h->c, h->mc, sym, b, h->stream));
       CK(launch_band_factor(h->c.Nc, h->mc, sym, b, h->stream));
     }
   }
   if (h->coarse_inv) LAUNCH(CAMS_PROF_COARSE_INV, launch_coarse_zinv(h->c.Nc, h->mc, b, h->stream));
-  LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid, h->ilu_cta,
-                                                  h->single, nonsym, h->stream));
+  if (overlap)
+    CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  else
+    LAUNCH(CAMS_PROF_ILU_FACTOR, launch_ilu_factor(h->g, b, h->ilu_pipelined, h->ilu_grid,
+                                                    h->ilu_cta, h->single, nonsym, h->stream));
   return check_status(h);
 }
 
@@ -1755,10 +1777,14 @@ const char* cams_last_error(cams_handle* h) {
 void cams_destroy(cams_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->aux_stream) cudaStreamSynchronize(h->aux_stream);
   free_surrogate(h);
   if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
   if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   prof_flush(h);

@@ -88,9 +88,10 @@ struct SingleBuffers {
   float* pc = nullptr;                                    // coarse solution (band order)
   // FP32 copy of the symmetric coarse factor (the substitution's operands)
   float *Lc = nullptr, *Lr = nullptr, *cblk = nullptr, *cdinv = nullptr;
-  // the inverse-factor coarse solve: FP32 band (factored in place into Lc),
-  // Z = L^{-1} (Nc x coarse_ldz(Nc), column-major) and t = D^{-1} Z b
-  float *band = nullptr, *Z = nullptr, *tc = nullptr, *zpart = nullptr;
+  // the inverse-factor coarse solve: Z = L^{-1} of the FP32 copy Lc of the
+  // FP64 factor (Nc x coarse_ldz(Nc), column-major), the partial sums of
+  // Z b and t = D^{-1} Z b
+  float *Z = nullptr, *tc = nullptr, *zpart = nullptr;
 };
 
 // Device buffers, one allocation each, owned by the handle.
@@ -213,12 +214,13 @@ cudaError_t launch_galerkin_fv(const Geo& g, const CGeo& c, bool single, bool no
 cudaError_t launch_band_fill(const CGeo& c, int m, int sym, Buffers& b, cudaStream_t s);
 cudaError_t launch_band_factor(int Nc, int m, int sym, Buffers& b, cudaStream_t s);
 // The mixed preconditioner's symmetric coarse solve by the explicit inverse
-// factor: FP32 band LDL^T of the Galerkin matrix and Z = L^{-1}, then per
-// solve f32.pc = Z^T D^{-1} Z rc.  coarse_inverse_ok bounds its work and memory.
+// factor: the FP64 band LDL^T of the Galerkin matrix, its FP32 copy and
+// Z = L^{-1} of that copy, then per solve f32.pc = Z^T D^{-1} Z rc.
+// coarse_inverse_ok bounds its work and memory.
 bool coarse_inverse_ok(int Nc, int m);
 long long coarse_ldz(int Nc);        // leading dimension of Z (and length of t)
 long long coarse_part_len(int Nc);   // partial sums of Z b
-cudaError_t launch_coarse_factor_f32(const CGeo& c, int m, Buffers& b, cudaStream_t s);
+cudaError_t launch_coarse_factor_inv(const CGeo& c, int m, Buffers& b, cudaStream_t s);
 cudaError_t launch_coarse_zinv(int Nc, int m, Buffers& b, cudaStream_t s);
 cudaError_t launch_coarse_solve_f32(int Nc, int m, Buffers& b, cudaStream_t s);
 cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double* r, bool single,

@@ -1535,16 +1535,18 @@ bool coarse_inverse_ok(int Nc, int m) {
   return Nc > 0 && work <= 2e10 && bytes <= 1073741824.0 && zinv_smem(m) <= 200 * 1024;
 }
 
-cudaError_t launch_coarse_factor_f32(const CGeo& c, int m, Buffers& b, cudaStream_t s) {
+cudaError_t launch_coarse_factor_inv(const CGeo& c, int m, Buffers& b, cudaStream_t s) {
+  // the FP64 band L D L^T (the coarse-system factorisation stays FP64), then
+  // its FP32 copy, from which k_coarse_zinv forms Z
   const int Nc = c.Nc;
-  SingleBuffers& f = b.f32;
-  cudaError_t e = cudaMemsetAsync(f.band, 0, sizeof(float) * (size_t)Nc * (m + 1), s);
+  cudaError_t e = launch_band_fill(c, m, 1, b, s);
   if (e != cudaSuccess) return e;
-  k_band_fill<float><<<(27 * Nc + 255) / 256, 256, 0, s>>>(c, m, 1, b.Acs, b.perm, f.band);
-  int launches = 1;
-  e = ldlt_launches<float>(Nc, m, f.band, f.Lc, b.status, s, launches);
-  count_launches(launches);
+  int launches = 0;
+  e = ldlt_launches<double>(Nc, m, b.band, b.Lc, b.status, s, launches);
   if (e != cudaSuccess) return e;
+  const long long n = (long long)Nc * (m + 1);
+  k_to_single<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, b.Lc, b.f32.Lc);
+  count_launches(launches + 1);
   return cudaGetLastError();
 }
 
