@@ -184,6 +184,13 @@ typedef struct {
 #define CAMS_Q_MATRIX_UPPER 15  /* double 3N: the transposed couplings a_{i-1,i}, a_{i-nx,i},
                                 a_{i-nx*ny,i} stored at cell i (0 when absent); equal to the
                                 couplings of CAMS_Q_MATRIX when jacobian = 0 */
+#define CAMS_Q_COARSE_FACTOR 16 /* double Nc*(m+1): the FP64 L D L^T of R A P (Sec. 3) in the
+                                band order of CAMS_Q_COARSE_ORDER, column-major band: column q at
+                                q*(m+1) holds d_q, then l_{q+1,q} .. l_{q+m,q} (rows past Nc-1 are
+                                not defined); CAMS_EINVAL unless the last update factored R A P
+                                by L D L^T (MSFE of a symmetric A) */
+#define CAMS_Q_COARSE_ORDER  17 /* int Nc+1 (cams_get_int): the band half-width m, then the band
+                                position of each natural coarse index I (x fastest) */
 
 /* kernel classes of CAMS_Q_PROFILE */
 #define CAMS_PROF_ASSEMBLE      0   /* density + linear-system population (a2) */

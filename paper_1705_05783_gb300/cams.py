@@ -24,6 +24,7 @@ CAMS_Q_TRANS, CAMS_Q_MATRIX, CAMS_Q_RHS, CAMS_Q_EPS, CAMS_Q_PRESSURE = 1, 2, 3, 
 CAMS_Q_PROLONG, CAMS_Q_PROLONG_J, CAMS_Q_COARSE, CAMS_Q_ILU_DIAG, CAMS_Q_RESIDUAL = 6, 7, 8, 9, 10
 CAMS_Q_SIZES, CAMS_Q_PROFILE, CAMS_Q_LAUNCHES, CAMS_Q_SURR_RATIO = 11, 12, 13, 14
 CAMS_Q_MATRIX_UPPER = 15
+CAMS_Q_COARSE_FACTOR, CAMS_Q_COARSE_ORDER = 16, 17
 PROF_CLASSES = ("assemble", "basis_op", "adapt", "basis", "galerkin", "coarse_factor",
                 "ilu_factor", "residual", "restrict", "coarse_solve", "prolong", "ilu_fwd",
                 "ilu_bwd", "ilu_resid", "update", "ilu_apply", "coarse_inv")

@@ -44,6 +44,8 @@ struct cams_handle {
   int n_dual = 0;
   // coarse band
   int mc = 0;
+  std::vector<int> perm;        // band position of each natural coarse index
+  bool coarse_ldlt = false;     // b.Lc holds the L D L^T of the current R A P
   // state
   bool built = false;
   bool assembled = false;
@@ -691,6 +693,7 @@ int update_operators(cams_handle* h, int force, int* n_rebuilt) {
     ProfScope ps_(h, CAMS_PROF_COARSE_FACTOR);
     // MSFE with a symmetric A: R A P = P^T A P is symmetric (LDL^T), else band LU
     const int sym = o.restriction != 1 && !nonsym;
+    h->coarse_ldlt = sym != 0;
     if (h->coarse_inv) {
       CK(launch_coarse_factor_inv(h->c, h->mc, b, h->stream));
     } else {
@@ -1148,6 +1151,7 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   cudaMemcpyAsync(h->b.ents, h->ents.data(), sizeof(Entity) * h->ents.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->b.ent_of_cell, eoc.data(), sizeof(int) * g.N, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->b.perm, perm.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, s);
+  h->perm = perm;
   cudaMemsetAsync(h->b.status, 0, sizeof(int), s);
   cudaMemsetAsync(h->b.Tbw, 0, sizeof(double) * g.ny * g.nz, s);
   cudaMemsetAsync(h->b.Tbe, 0, sizeof(double) * g.ny * g.nz, s);
@@ -1679,6 +1683,10 @@ int cams_get(cams_handle* h, int what, double* dst) {
       break;
     }
     case CAMS_Q_COARSE: CK(cudaMemcpyAsync(dst, b.Acs, sizeof(double) * 27 * h->c.Nc, k, s)); break;
+    case CAMS_Q_COARSE_FACTOR:
+      if (!h->coarse_ldlt) return fail(h, CAMS_EINVAL, "the coarse matrix was not factored by L D L^T");
+      CK(cudaMemcpyAsync(dst, b.Lc, sizeof(double) * h->c.Nc * (h->mc + 1), k, s));
+      break;
     case CAMS_Q_ILU_DIAG: {
       // d_i = 1 / dinv_i, formed in the residual work vector
       std::vector<double> tmp(N);
@@ -1738,6 +1746,15 @@ int cams_get_int(cams_handle* h, int what, int* dst) {
   if (what == CAMS_Q_SIZES) {
     dst[0] = (int)N; dst[1] = h->c.Nc; dst[2] = h->c.nc[0]; dst[3] = h->c.nc[1]; dst[4] = h->c.nc[2];
     dst[5] = (int)h->ents.size(); dst[6] = h->last_rebuilt; dst[7] = h->surr_accepted;
+    return CAMS_OK;
+  }
+  if (what == CAMS_Q_COARSE_ORDER) {
+    std::vector<int> v(h->c.Nc + 1);
+    v[0] = h->mc;
+    std::copy(h->perm.begin(), h->perm.end(), v.begin() + 1);
+    CK(cudaMemcpyAsync(dst, v.data(), sizeof(int) * v.size(),
+                       h->opt.memspace == CAMS_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return CAMS_OK;
   }
   if (what != CAMS_Q_PROLONG_J) return fail(h, CAMS_EINVAL, "unknown integer quantity");

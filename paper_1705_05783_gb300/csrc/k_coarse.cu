@@ -14,6 +14,7 @@
 // block tree, and every sum over blocks runs in a fixed block order, so the
 // MSFE matrix is bitwise symmetric.
 #include "cams_internal.h"
+#include "rcp64.h"
 
 namespace cams {
 
@@ -364,14 +365,35 @@ __global__ void k_band_fill(CGeo c, int m, int sym, const double* __restrict__ A
 // working band W is only read in the block columns and only written right of
 // them, so CTAs of one launch never race.
 //
-// FP64 instructions occupy a sub-partition's FP64 pipe for many cycles, so
-// the kernel keeps their count and their dependent chains short: one thread
-// per element of the diagonal block's lower triangle, the reciprocal of the
-// next pivot formed by its owner as soon as that pivot is final, the panel
-// rows solved by four threads per row (one warp per sub-partition), and the
-// products d_q l_cq kept from the elimination instead of recomputed.
+// On this GPU an FP64 warp instruction holds its sub-partition's FP64 unit
+// for about 64 cycles whatever the number of active lanes, and a dependent
+// FP64 instruction waits as long, so the factorisation's time is the number
+// of FP64 warp instructions on its pivot chain.  The kernel keeps that
+// number small: one thread per element of the diagonal block's lower
+// triangle, the elements right of column 0 in warps 0-3 (at most one warp
+// per sub-partition issues at each pivot: one product and one FMA), the
+// reciprocal of the next pivot formed by its owner as soon as that pivot is
+// final, from the hardware estimate and one Halley step instead of a
+// division, the pivot tests on the bit pattern instead of FP64 compares, the
+// panel rows solved by four threads per row (one warp per sub-partition),
+// and the products d_q l_cq kept from the elimination instead of recomputed.
 constexpr int kTB = 16;
 constexpr int kTri = kTB * (kTB + 1) / 2;   // lower-triangle elements of a diagonal block
+
+// 1/d of a pivot (rcp64.h), and whether d is positive and finite, tested on
+// its bit pattern instead of by FP64 compares; a non-positive or non-finite
+// pivot is replaced by 1 and reported.
+__device__ __forceinline__ double pivot_rcp(double d, bool& bad) {
+  const long long b = __double_as_longlong(d);
+  bad = !(b > 0 && b < 0x7FF0000000000000LL);
+  return rcp_halley(bad ? 1.0 : d);
+}
+// the same for a pivot of either sign (band LU): nonzero and finite
+__device__ __forceinline__ double pivot_rcp_signed(double d, bool& bad) {
+  const long long a = __double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFLL;
+  bad = !(a > 0 && a < 0x7FF0000000000000LL);
+  return rcp_halley(bad ? 1.0 : d);
+}
 
 template <class T>
 __device__ __forceinline__ T band_at(const T* W, int m, int r, int c) {
@@ -419,34 +441,40 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
     const int r = (k < kTB ? r0 + k : cc0 + k - kTB);
     V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : T(0);
   }
-  // element of the lower triangle owned by this thread (row-major order)
+  // element of the lower triangle owned by this thread: those right of
+  // column 0 row by row in threads 0..119 (warps 0-3), column 0 in threads
+  // 128..143 (it is only scaled, at the first pivot)
   int er = 0, ec = -1;
-  if (tid < kTri) {
-    int t = tid;
-    while (t > er) { t -= er + 1; ++er; }
-    ec = t;
+  if (tid < kTri - kTB) {
+    int t = tid, r = 1;
+    while (t >= r) { t -= r; ++r; }
+    er = r;
+    ec = t + 1;
+  } else if (tid >= 128 && tid < 128 + kTB) {
+    er = tid - 128;
+    ec = 0;
   }
   __syncthreads();
   if (tid == 0) {
-    T d = A[0][0];
-    if (!(d > T(0)) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = T(1); }
-    rinv[0] = T(1) / d;
+    bool bad;
+    rinv[0] = pivot_rcp(A[0][0], bad);
+    if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
   }
   __syncthreads();
-  // --- factor the diagonal block ---
+  // --- factor the diagonal block: at pivot q, column q is scaled and the
+  // trailing triangle updated, a_rc -= (a_rq / d_q) a_cq ---
   for (int q = 0; q < tb; ++q) {
-    if (ec >= 0 && er < tb) {
-      const T rq = rinv[q];
-      if (ec == q && er > q) {
-        L[er][q] = A[er][q] * rq;
-      } else if (ec > q) {
-        const T t = A[er][q] * rq;
+    if (ec >= q && er > q && er < tb) {
+      const T t = A[er][q] * rinv[q];
+      if (ec == q) {
+        L[er][q] = t;
+      } else {
         const T v = fma(-t, A[ec][q], A[er][ec]);
         A[er][ec] = v;
         if (er == q + 1 && ec == q + 1) {     // the next pivot is final
-          T d = v;
-          if (!(d > T(0)) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = T(1); }
-          rinv[q + 1] = T(1) / d;
+          bool bad;
+          rinv[q + 1] = pivot_rcp(v, bad);
+          if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
         }
       }
     }
@@ -1197,9 +1225,9 @@ __global__ void __launch_bounds__(256) k_lu_block(int N, int m, int c0, const do
   }
   __syncthreads();
   if (tid == 0) {
-    double d = D[0][0];
-    if (!(d != 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
-    dinv[0] = 1.0 / d;
+    bool bad;
+    dinv[0] = pivot_rcp_signed(D[0][0], bad);
+    if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
   }
   __syncthreads();
   // --- D = L_D U_D, one element a thread ---
@@ -1213,15 +1241,16 @@ __global__ void __launch_bounds__(256) k_lu_block(int N, int m, int c0, const do
         const double v = fma(-t, D[q][ec], D[er][ec]);
         D[er][ec] = v;
         if (er == q + 1 && ec == q + 1) {     // the next pivot is final
-          double d = v;
-          if (!(d != 0.0) || !isfinite(d)) { if (blockIdx.x == 0) atomicOr(status, kStatSingular); d = 1.0; }
-          dinv[q + 1] = 1.0 / d;
+          bool bad;
+          dinv[q + 1] = pivot_rcp_signed(v, bad);
+          if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
         }
       }
     }
     __syncthreads();
   }
-  // --- panels: row k of V by thread k, column k of H by thread kTB + k ---
+  // --- panels: row k of V by thread k of warp 0, column k of H by thread k
+  // of warp 1 (two sub-partitions: their FP64 chains run side by side) ---
   if (tid < kTB) {
     const int k = tid;
     for (int q = 0; q < tb; ++q) {
@@ -1229,8 +1258,8 @@ __global__ void __launch_bounds__(256) k_lu_block(int N, int m, int c0, const do
       for (int j = 0; j < q; ++j) s = fma(-V[k][j], D[j][q], s);
       V[k][q] = s * dinv[q];
     }
-  } else if (tid < 2 * kTB) {
-    const int k = tid - kTB;
+  } else if (tid >= 32 && tid < 32 + kTB) {
+    const int k = tid - 32;
     for (int q = 0; q < tb; ++q) {
       double s = H[q][k];
       for (int j = 0; j < q; ++j) s = fma(-L[q][j], H[j][k], s);
