@@ -71,18 +71,19 @@ SWEEP_CLASSES = ("ilu_fwd", "ilu_bwd")
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + write.sum) for
 # a kernel class on a workload, for the kernels as they stand; see profiles/.
 MEASURED_TRAFFIC = {
-    # profiles/launch_list_3d-200x200x100-mixed.md (the kernels as of the fetch-first sweeps)
-    ("3d-200x200x100-mixed", "ilu_fwd"): 73.4e6,
-    ("3d-200x200x100-mixed", "ilu_bwd"): 70.8e6,
-    ("3d-200x200x100-mixed", "ilu_resid"): 142.1e6,
+    # profiles/launch_list_3d-200x200x100-mixed.md (the kernels as of the FP32 residual copy)
+    ("3d-200x200x100-mixed", "ilu_fwd"): 73.9e6,
+    ("3d-200x200x100-mixed", "ilu_bwd"): 70.1e6,
+    ("3d-200x200x100-mixed", "ilu_resid"): 121.9e6,
     ("3d-200x200x100-mixed", "ilu_apply"): 32.8e6,
 }
 
 # the same classes with the FP32 preconditioner (4-byte operands; r and p stay FP64)
 BYTES_PER_CELL_MIXED = dict(BYTES_PER_CELL, **{
-    "restrict": 40,            # P x8 (FP32), r
+    "residual": 60,            # A x4, f, p -> r (FP64) and its FP32 copy
+    "restrict": 36,            # P x8, r (FP32)
     "prolong": 36,             # P x8 -> delta (FP32)
-    "ilu_resid": 36,           # A x4, delta, 1/d (FP32), r (FP64) -> D^{-1}(r - A delta)
+    "ilu_resid": 32,           # A x4, delta, 1/d, r (FP32) -> D^{-1}(r - A delta)
     "ilu_fwd": 20,             # FP32 forward sweep
     "ilu_bwd": 20,             # FP32 backward sweep
     "ilu_apply": 12,           # delta += z (FP32)

@@ -300,7 +300,7 @@ int alloc_all(cams_handle* h) {
   if (h->single) {
     SingleBuffers& f = b.f32;
     const long long S = ilu_skew_len(h->g);
-    AL(f.Ad, N); AL(f.Ax, N); AL(f.Ay, N); AL(f.Az, N); AL(f.dinv, N); AL(f.d, N);
+    AL(f.Ad, N); AL(f.Ax, N); AL(f.Ay, N); AL(f.Az, N); AL(f.dinv, N); AL(f.d, N); AL(f.r, N);
     if (h->opt.jacobian) {
       AL(f.Axu, N); AL(f.Ayu, N); AL(f.Azu, N); AL(f.Qx, N); AL(f.Qy, N); AL(f.Qz, N);
     } else {
@@ -333,6 +333,7 @@ int alloc_all(cams_handle* h) {
   AL(b.Lc, (size_t)h->c.Nc * (h->mc + 1)); AL(b.Lr, (size_t)h->c.Nc * (h->mc + 1));
   AL(b.cblk, coarse_blocks_len(h->c.Nc)); AL(b.cdinv, h->c.Nc); AL(b.cabort, 1);
   AL(b.perm, h->c.Nc);
+  AL(b.jxt, 2LL * h->g.nx);
   AL(b.rc, h->c.Nc); AL(b.pc, h->c.Nc); AL(b.ywork, h->c.Nc);
   AL(b.dinv, N);
   {
@@ -363,7 +364,7 @@ void free_all(cams_handle* h) {
   Buffers& b = h->b;
   void* ptrs[] = {b.Tx, b.Ty, b.Tz, b.Tbw, b.Tbe, b.p, b.pn, b.rho, b.rhon, b.Ad, b.Ax, b.Ay,
                   b.Az, b.Cacc, b.f, b.eps, b.src, b.Abd, b.Abx, b.Aby, b.Abz, b.snap, b.P,
-                  b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.rc,
+                  b.ent_of_cell, b.ents, b.flag, b.lscratch, b.loc, b.Acs, b.band, b.perm, b.jxt, b.rc,
                   b.pc, b.dinv, b.r, b.rds, b.w, b.z, b.red, b.scal, b.status, b.Lx, b.Ly, b.Lz,
                   b.Ux, b.Uy, b.Uz, b.ctrl, b.Lc, b.Lr, b.cblk, b.cdinv, b.cabort, b.fixm,
                   b.fixc, b.fixv, b.cf, b.Qx, b.Qy, b.Qz, b.Fc, b.ywork, b.lwork,
@@ -374,7 +375,7 @@ void free_all(cams_handle* h) {
     if (p) cudaFree(p);
   const SingleBuffers& f = b.f32;
   void* fptrs[] = {f.Ad, f.Ax, f.Ay, f.Az, f.dinv, f.Lx, f.Ly, f.Lz, f.Ux, f.Uy, f.Uz,
-                   f.rds, f.w, f.z, f.d, f.P, f.pc, f.Qx, f.Qy, f.Qz, f.Lc, f.Lr, f.cblk, f.cdinv,
+                   f.rds, f.w, f.z, f.d, f.r, f.P, f.pc, f.Qx, f.Qy, f.Qz, f.Lc, f.Lr, f.cblk, f.cdinv,
                    f.Z, f.tc, f.zpart, f.Axu != f.Ax ? f.Axu : nullptr, f.Ayu != f.Ay ? f.Ayu : nullptr,
                    f.Azu != f.Az ? f.Azu : nullptr};
   for (void* p : fptrs)
@@ -1151,6 +1152,24 @@ int cams_setup(const cams_grid* grid, const cams_fluid* fluid, const cams_option
   cudaMemcpyAsync(h->b.ents, h->ents.data(), sizeof(Entity) * h->ents.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->b.ent_of_cell, eoc.data(), sizeof(int) * g.N, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(h->b.perm, perm.data(), sizeof(int) * c.Nc, cudaMemcpyHostToDevice, s);
+  {
+    // the two coarse x-corners of every x (the prolongation's per-x table):
+    // on a vertex plane the lower one only, else the nodes either side
+    std::vector<int> jxt(2 * (size_t)g.nx);
+    for (int x = 0; x < g.nx; ++x)
+      for (int bit = 0; bit < 2; ++bit) {
+        const int sft = x - c.o[0];
+        int J;
+        if (sft >= 0 && sft % c.b[0] == 0) J = bit ? -1 : sft / c.b[0];
+        else {
+          const int j = sft >= 0 ? sft / c.b[0] + 1 : 0;
+          J = bit ? j : j - 1;
+        }
+        jxt[2 * x + bit] = (J >= 0 && J < c.nc[0]) ? J : -1;
+      }
+    cudaMemcpyAsync(h->b.jxt, jxt.data(), sizeof(int) * jxt.size(), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
   h->perm = perm;
   cudaMemsetAsync(h->b.status, 0, sizeof(int), s);
   cudaMemsetAsync(h->b.Tbw, 0, sizeof(double) * g.ny * g.nz, s);

@@ -84,6 +84,7 @@ struct SingleBuffers {
   float *Ux = nullptr, *Uy = nullptr, *Uz = nullptr;
   float *rds = nullptr, *w = nullptr, *z = nullptr;       // smoother vectors, skewed
   float* d = nullptr;                                     // the correction delta (N)
+  float* r = nullptr;                                     // the outer residual rounded to FP32 (N)
   float* P = nullptr;                                     // 8N, slot-major
   float* pc = nullptr;                                    // coarse solution (band order)
   // FP32 copy of the symmetric coarse factor (the substitution's operands)
@@ -127,6 +128,7 @@ struct Buffers {
   double *cblk = nullptr, *cdinv = nullptr;               // block inverses / products, 1/d
   int* cabort = nullptr;                                  // abort flag of the cluster solve
   int* perm = nullptr;                                    // coarse natural -> band order
+  int* jxt = nullptr;                                     // per x: the two coarse x-corners (-1: none)
   double *rc = nullptr, *pc = nullptr;                    // coarse vectors (band order)
   double* ywork = nullptr;                                // forward-solve vector of the global band solve
   double* dinv = nullptr;                                 // 1 / ILU(0) pivots

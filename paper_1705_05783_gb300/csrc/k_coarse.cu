@@ -48,11 +48,31 @@ __device__ __forceinline__ void dual_range(const CGeo& c, const Geo& g, int d, i
 template <int K, class TA>
 __device__ void block_sum_k(TA (&v)[K], double* sh /* K*32 */, double* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (sizeof(TA) == 4) {
+    // FP32 sums: lane k % 32 collects sum k, so that each warp converts its
+    // sums to FP64 in ceil(K / 32) instructions instead of K (a conversion is
+    // an FP64-unit instruction, as slow with one active lane as with 32)
+    constexpr int kW = (K + 31) / 32;
+    TA mine[kW];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    TA t = v[k];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) sh[k * 32 + wid] = (double)t;
+    for (int w = 0; w < kW; ++w) mine[w] = TA(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      TA t = v[k];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (lane == k % 32) mine[k / 32] = t;
+    }
+#pragma unroll
+    for (int w = 0; w < kW; ++w)
+      if (32 * w + lane < K) sh[(32 * w + lane) * 32 + wid] = (double)mine[w];
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      TA t = v[k];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) sh[k * 32 + wid] = (double)t;
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -432,12 +452,14 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // --- stage the diagonal block and the 2 kTB panel rows ---
+  // (consecutive threads take consecutive rows of one band column: the
+  // column is contiguous in the band)
   {
-    const int r = tid / kTB, q = tid % kTB;
+    const int r = tid % kTB, q = tid / kTB;
     A[r][q] = (r < tb && q <= r) ? band_at(Wr, m, c0 + r, c0 + q) : T(0);
   }
   for (int e = tid; e < 2 * kTB * kTB; e += blockDim.x) {
-    const int k = e / kTB, q = e % kTB;
+    const int k = e % (2 * kTB), q = e / (2 * kTB);
     const int r = (k < kTB ? r0 + k : cc0 + k - kTB);
     V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : T(0);
   }
@@ -715,16 +737,21 @@ __global__ void __launch_bounds__(256) k_coarse_zlower(int N, const float* __res
                                                        long long ldz, const double* __restrict__ rhs,
                                                        float* part) {
   __shared__ float4 red[8][32];
+  __shared__ float bs[kZK];                        // the chunk's b, rounded to FP32 once
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * kZS, c = blockIdx.y, jc = c * kZK;
   if (jc > i0 + kZS - 1 || jc >= N) return;        // the whole chunk lies above the strip
+  // (an FP64 -> FP32 conversion is an FP64-unit instruction: one per
+  // element here, not one per element and warp in the loop below)
+  for (int e = threadIdx.x; e < kZK; e += blockDim.x) bs[e] = jc + e < N ? (float)rhs[jc + e] : 0.f;
+  __syncthreads();
   const int ib = i0 + 4 * lane;                    // my rows ib .. ib + 3
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   const int jlo = jc + warp * 32, jhi = min(min(jlo + 32, N), i0 + kZS);
 #pragma unroll 8
   for (int j = jlo; j < jhi; ++j) {
     const float4 z = *reinterpret_cast<const float4*>(Z + (long long)j * ldz + ib);
-    const float bj = (float)rhs[j];
+    const float bj = bs[j - jc];
     // rows above the diagonal or past N hold no value of Z
     acc.x += (ib + 0 >= j && ib + 0 < N) ? z.x * bj : 0.f;
     acc.y += (ib + 1 >= j && ib + 1 < N) ? z.y * bj : 0.f;
@@ -1373,9 +1400,9 @@ __global__ void __launch_bounds__(256) k_band_lu_solve(int N, int m, const doubl
 }
 
 // MSFE restriction, part 1: per dual block the 8 sums  sum_i P_i[s] r_i.
-template <class TP>
+template <class TP, class TR>
 __global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const TP* __restrict__ P,
-                                                           const double* __restrict__ r, double* part) {
+                                                           const TR* __restrict__ r, double* part) {
   __shared__ double sh[8 * 32];
   const int ndx = c.nc[0] + 1, ndy = c.nc[1] + 1;
   const int D = blockIdx.x;
@@ -1387,11 +1414,24 @@ __global__ void __launch_bounds__(256) k_restrict_fe_local(Geo g, CGeo c, const 
   // products, each thread's and each warp's sums in P's precision, the sum
   // over the block's warps in FP64
   TP tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int l = threadIdx.x; l < ncell; l += blockDim.x) {
-    const long long i = (lo[0] + l % ex) + g.sy * (lo[1] + (l / ex) % ey) + g.sz * (lo[2] + l / (ex * ey));
-    const TP ri = (TP)r[i];
+  if (threadIdx.x < ncell) {
+    // thread t takes cells t, t + blockDim.x, ... of the block in x-fastest
+    // order; the cell's coordinates advance by a fixed mixed-radix step
+    // instead of being divided out of l
+    const int st = blockDim.x;
+    const int sx = st % ex, sy = (st / ex) % ey, sz = st / (ex * ey);
+    int x = threadIdx.x % ex, y = (threadIdx.x / ex) % ey, z = threadIdx.x / (ex * ey);
+    for (int l = threadIdx.x; l < ncell; l += st) {
+      const long long i = (lo[0] + x) + g.sy * (lo[1] + y) + g.sz * (lo[2] + z);
+      const TP ri = (TP)r[i];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) tacc[s] += P[(long long)s * g.N + i] * ri;
+      for (int s = 0; s < 8; ++s) tacc[s] += P[(long long)s * g.N + i] * ri;
+      x += sx;
+      y += sy;
+      z += sz;
+      if (x >= ex) { x -= ex; ++y; }
+      if (y >= ey) { y -= ey; ++z; }
+    }
   }
   block_sum_k<8>(tacc, sh, part + (long long)D * 8);
 }
@@ -1424,8 +1464,21 @@ __global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double
   const int Ic[3] = {I % c.nc[0], (I / c.nc[0]) % c.nc[1], I / (c.nc[0] * c.nc[1])};
   const int bx = c.b[0], by = c.b[1], bz = c.b[2];
   double acc[1] = {0.0};
-  for (int l = threadIdx.x; l < bx * by * bz; l += blockDim.x)
-    acc[0] += r[(Ic[0] * bx + l % bx) + g.sy * (Ic[1] * by + (l / bx) % by) + g.sz * (Ic[2] * bz + l / (bx * by))];
+  if ((int)threadIdx.x < bx * by * bz) {
+    // cells t, t + blockDim.x, ... in x-fastest order, coordinates advanced
+    // by a fixed mixed-radix step (as in k_restrict_fe_local)
+    const int st = blockDim.x;
+    const int sx = st % bx, sy = (st / bx) % by, sz = st / (bx * by);
+    int x = threadIdx.x % bx, y = (threadIdx.x / bx) % by, z = threadIdx.x / (bx * by);
+    for (int l = threadIdx.x; l < bx * by * bz; l += st) {
+      acc[0] += r[(Ic[0] * bx + x) + g.sy * (Ic[1] * by + y) + g.sz * (Ic[2] * bz + z)];
+      x += sx;
+      y += sy;
+      z += sz;
+      if (x >= bx) { x -= bx; ++y; }
+      if (y >= by) { y -= by; ++z; }
+    }
+  }
   double out;
   block_sum_k<1>(acc, sh, &out);
   // block_sum_k writes through thread 0 only when K == 1
@@ -1433,27 +1486,44 @@ __global__ void __launch_bounds__(256) k_restrict_fv(Geo g, CGeo c, const double
 }
 
 // p += P p_c (FP64), or delta = P p_c (the mixed-precision preconditioner:
-// P, p_c and delta in FP32); the sum is formed in p_c's precision
+// P, p_c and delta in FP32); the sum is formed in p_c's precision.  Warps
+// take whole x-rows.  A row's y and z corners are fixed, so its coarse
+// values (4 corner pairs x the coarse x-nodes) are staged in the warp's
+// shared memory once per row, and each cell's two x-corners come from the
+// per-x table jxt: a cell costs its 8 P loads and 8 shared reads, with no
+// index division and no gather through the permutation.
 template <class TP, class TC, class TO, bool kSet>
 __global__ void k_prolong(Geo g, CGeo c, const TP* __restrict__ P, const TC* __restrict__ pc,
-                          const int* __restrict__ perm, TO* p) {
-  // warps take whole x-rows: the y and z corners are per row, only x's per cell
+                          const int* __restrict__ perm, const int* __restrict__ jxt, TO* p) {
+  extern __shared__ __align__(16) unsigned char prolong_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ncx = c.nc[0];
+  TC* cv = reinterpret_cast<TC*>(prolong_smem) + (size_t)warp * 4 * ncx;
   const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
   for (unsigned row = blockIdx.x * nw + warp; row < rows; row += gridDim.x * nw) {
     const int y = (int)(row % (unsigned)g.ny), z = (int)(row / (unsigned)g.ny);
     const int Jy[2] = {corner_d(c, 1, y, 0), corner_d(c, 1, y, 1)};
     const int Jz[2] = {corner_d(c, 2, z, 0), corner_d(c, 2, z, 1)};
+    // corner pair k = (y bit, z bit) = (k & 1, k >> 1), the slot's bits 1 and 2
+    unsigned ok = 0;
+    __syncwarp();                                // the previous row's reads are done
+    for (int k = 0; k < 4; ++k) {
+      const int jy = Jy[k & 1], jz = Jz[k >> 1];
+      if (jy < 0 || jz < 0) continue;            // uniform across the warp
+      ok |= 1u << k;
+      for (int jx = lane; jx < ncx; jx += 32) cv[k * ncx + jx] = pc[perm[jx + ncx * (jy + c.nc[1] * jz)]];
+    }
+    __syncwarp();
     const long long base = g.sy * y + g.sz * z;
     for (int x = lane; x < g.nx; x += 32) {
       const long long i = base + x;
-      const int Jx[2] = {corner_d(c, 0, x, 0), corner_d(c, 0, x, 1)};
+      const int Jx[2] = {jxt[2 * x], jxt[2 * x + 1]};
       TC s = TC(0);
 #pragma unroll
       for (int sl = 0; sl < 8; ++sl) {
-        const int jx = Jx[sl & 1], jy = Jy[(sl >> 1) & 1], jz = Jz[(sl >> 2) & 1];
-        if (jx < 0 || jy < 0 || jz < 0) continue;
-        s += (TC)P[(long long)sl * g.N + i] * pc[perm[jx + c.nc[0] * (jy + c.nc[1] * jz)]];
+        const int jx = Jx[sl & 1], k = (sl >> 1) & 3;
+        if (jx < 0 || !((ok >> k) & 1u)) continue;
+        s += (TC)P[(long long)sl * g.N + i] * cv[k * ncx + jx];
       }
       if (kSet) p[i] = (TO)s;
       else p[i] += (TO)s;
@@ -1649,8 +1719,10 @@ cudaError_t launch_restrict(const Geo& g, const CGeo& c, int kind, const double*
                             Buffers& b, cudaStream_t s) {
   if (kind == 0) {
     const int nd = (c.nc[0] + 1) * (c.nc[1] + 1) * (c.nc[2] + 1);
-    if (single) k_restrict_fe_local<float><<<nd, 256, 0, s>>>(g, c, b.f32.P, r, b.loc);
-    else k_restrict_fe_local<double><<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc);
+    // mixed precision: the FP32 copy of the handle's residual (written with it)
+    if (single && r == b.r) k_restrict_fe_local<float, float><<<nd, 256, 0, s>>>(g, c, b.f32.P, b.f32.r, b.loc);
+    else if (single) k_restrict_fe_local<float, double><<<nd, 256, 0, s>>>(g, c, b.f32.P, r, b.loc);
+    else k_restrict_fe_local<double, double><<<nd, 256, 0, s>>>(g, c, b.P, r, b.loc);
     count_launches(1);
     k_restrict_fe_gather<<<(c.Nc + 127) / 128, 128, 0, s>>>(c, b.loc, b.perm, b.rc); count_launches(1);
   } else {
@@ -1758,29 +1830,41 @@ cudaError_t launch_band_solve(int Nc, int m, int sym, bool cluster, bool single,
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
-                               cudaStream_t s) {
-  const int blocks = (int)(((long long)g.ny * g.nz + 7) / 8);   // one warp per x-row
-  if (single) {
-    // the coarse solution is already in b.f32.pc (launch_band_solve with single)
-    k_prolong<float, float, float, true><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.f32.pc, b.perm,
-                                                              b.f32.d);
-  } else {
-    k_prolong<double, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
+// warps a CTA for k_prolong: 8, fewer when the staged coarse values of 8
+// warps would not fit in 48 KB of shared memory
+static int prolong_warps(const CGeo& c, int elem) {
+  const int per = 4 * c.nc[0] * elem;
+  int w = 8;
+  while (w > 1 && w * per > 48 * 1024) --w;
+  return w;
+}
+
+template <class TP, class TC, class TO, bool kSet>
+static cudaError_t prolong(const Geo& g, const CGeo& c, const TP* P, const TC* pc, Buffers& b, TO* p,
+                           cudaStream_t s) {
+  const int w = prolong_warps(c, (int)sizeof(TC));
+  const int smem = w * 4 * c.nc[0] * (int)sizeof(TC);
+  if (smem > 48 * 1024) {
+    cudaError_t e = raise_smem_limit(k_prolong<TP, TC, TO, kSet>, smem);
+    if (e != cudaSuccess) return e;
   }
+  const int blocks = (int)(((long long)g.ny * g.nz + w - 1) / w);   // one warp per x-row
+  k_prolong<TP, TC, TO, kSet><<<blocks, 32 * w, smem, s>>>(g, c, P, pc, b.perm, b.jxt, p);
   count_launches(1);
   return cudaGetLastError();
 }
 
+cudaError_t launch_prolong_add(const Geo& g, const CGeo& c, bool single, Buffers& b,
+                               cudaStream_t s) {
+  // the coarse solution of the mixed preconditioner is already in b.f32.pc
+  if (single) return prolong<float, float, float, true>(g, c, b.f32.P, b.f32.pc, b, b.f32.d, s);
+  return prolong<double, double, double, false>(g, c, b.P, b.pc, b, b.p, s);
+}
+
 cudaError_t launch_prolong_to_p(const Geo& g, const CGeo& c, bool single, Buffers& b,
                                 cudaStream_t s) {
-  const int blocks = (int)(((long long)g.ny * g.nz + 7) / 8);   // one warp per x-row
-  if (single)
-    k_prolong<float, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.f32.P, b.pc, b.perm, b.p);
-  else
-    k_prolong<double, double, double, false><<<blocks, 256, 0, s>>>(g, c, b.P, b.pc, b.perm, b.p);
-  count_launches(1);
-  return cudaGetLastError();
+  if (single) return prolong<float, double, double, false>(g, c, b.f32.P, b.pc, b, b.p, s);
+  return prolong<double, double, double, false>(g, c, b.P, b.pc, b, b.p, s);
 }
 
 }  // namespace cams

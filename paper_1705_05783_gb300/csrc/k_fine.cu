@@ -227,13 +227,15 @@ __global__ void k_finish_sum(const double* __restrict__ red, int n, double* out)
 // r = f - A p and per-block sums of r^2 (kNS: Axu.. hold the couplings to
 // the upper neighbours; otherwise A is symmetric and Ax.. serve both).  Warps take whole
 // x-rows (lanes along x, coalesced), so the cell coordinates cost one
-// division per row.
+// division per row.  r32 (null unless wanted): r rounded to FP32 once, for
+// the mixed preconditioner's restriction and smoothing steps, which would
+// otherwise each round it again (an FP64-unit conversion per cell).
 template <bool kNS>
 __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* __restrict__ Ax,
                            const double* __restrict__ Ay, const double* __restrict__ Az,
                            const double* __restrict__ Axu, const double* __restrict__ Ayu,
                            const double* __restrict__ Azu, const double* __restrict__ f,
-                           const double* __restrict__ p, double* r, double* red) {
+                           const double* __restrict__ p, double* r, float* r32, double* red) {
   double s2 = 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const unsigned rows = (unsigned)g.ny * (unsigned)g.nz;
@@ -250,6 +252,7 @@ __global__ void k_residual(Geo g, const double* __restrict__ Ad, const double* _
       if (z > 0) a -= Az[i] * p[i - g.sz];
       if (z < g.nz - 1) a -= (kNS ? Azu : Az)[i + g.sz] * p[i + g.sz];
       if (r) r[i] = a;
+      if (r32) r32[i] = (float)a;
       s2 += a * a;
     }
   }
@@ -354,12 +357,14 @@ cudaError_t launch_sumsq(const double* x, long long N, double* red, double* out,
 
 cudaError_t launch_residual(const Geo& g, const Buffers& b, const double* p, double* r,
                             double* red, double* out, cudaStream_t s) {
+  // the FP32 copy goes with the handle's own residual vector (mixed precision)
+  float* r32 = (r && r == b.r) ? b.f32.r : nullptr;
   if (b.Axu != b.Ax)
     k_residual<true><<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu,
-                                                        b.Azu, b.f, p, r, red);
+                                                        b.Azu, b.f, p, r, r32, red);
   else
     k_residual<false><<<kRedBlocks, kRedThreads, 0, s>>>(g, b.Ad, b.Ax, b.Ay, b.Az, b.Axu, b.Ayu,
-                                                         b.Azu, b.f, p, r, red);
+                                                         b.Azu, b.f, p, r, r32, red);
   count_launches(1);
   k_finish_sum<<<1, 1024, 0, s>>>(red, kRedBlocks, out); count_launches(1);
   return cudaGetLastError();

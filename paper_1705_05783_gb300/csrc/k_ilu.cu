@@ -194,6 +194,7 @@ __global__ void k_ilu_scale(Geo g, Skew sk, const T* __restrict__ Ax, const T* _
 // whose lanes are the tile's 32 rows (one 128- or 256-byte record each);
 // shared memory holds the kR x kXC block in between.
 constexpr int kXC = 64;
+static_assert(kR % 8 == 0 && kXC % 32 == 0, "the transposes take 8 warps of 32 lanes");
 
 // rd = D^{-1} (b - A x), stored skewed; b is read in its own precision and
 // rounded to T.  kNS: Axu.. hold the couplings to the upper neighbours (A
@@ -213,21 +214,27 @@ __global__ void __launch_bounds__(256) k_resid_scaled(Geo g, Skew sk, const T* _
   const int tile = blockIdx.x, x0 = blockIdx.y * kXC;
   const int Y = tile % sk.nty, Z = tile / sk.nty;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-  for (int r = warp; r < kR; r += nwarp) {
+  // (both loops unrolled, with predicates instead of early exits, so that a
+  // thread's loads of all its cells are in flight together; 256 threads)
+#pragma unroll
+  for (int rr = 0; rr < kR / 8; ++rr) {
+    const int r = warp + rr * 8;
     const int y = Y * kTY + r % kTY, z = Z * kTZ + r / kTY;
-    if (y >= g.ny || z >= g.nz) continue;
-    for (int h = lane; h < kXC; h += 32) {
+#pragma unroll
+    for (int hh = 0; hh < kXC / 32; ++hh) {
+      const int h = lane + 32 * hh;
       const int x = x0 + h;
-      if (x >= g.nx) break;
-      const long long i = x + g.sy * y + g.sz * z;
-      T a = T(bv[i]) - Ad[i] * xv[i];
-      if (x > 0) a -= Ax[i] * xv[i - 1];
-      if (x < g.nx - 1) a -= (kNS ? Axu : Ax)[i + 1] * xv[i + 1];
-      if (y > 0) a -= Ay[i] * xv[i - g.sy];
-      if (y < g.ny - 1) a -= (kNS ? Ayu : Ay)[i + g.sy] * xv[i + g.sy];
-      if (z > 0) a -= Az[i] * xv[i - g.sz];
-      if (z < g.nz - 1) a -= (kNS ? Azu : Az)[i + g.sz] * xv[i + g.sz];
-      blk[r][h] = a * dinv[i];
+      if (y < g.ny && z < g.nz && x < g.nx) {
+        const long long i = x + g.sy * y + g.sz * z;
+        T a = T(bv[i]) - Ad[i] * xv[i];
+        if (x > 0) a -= Ax[i] * xv[i - 1];
+        if (x < g.nx - 1) a -= (kNS ? Axu : Ax)[i + 1] * xv[i + 1];
+        if (y > 0) a -= Ay[i] * xv[i - g.sy];
+        if (y < g.ny - 1) a -= (kNS ? Ayu : Ay)[i + g.sy] * xv[i + g.sy];
+        if (z > 0) a -= Az[i] * xv[i - g.sz];
+        if (z < g.nz - 1) a -= (kNS ? Azu : Az)[i + g.sz] * xv[i + g.sz];
+        blk[r][h] = a * dinv[i];
+      }
     }
   }
   __syncthreads();
@@ -256,13 +263,28 @@ __global__ void __launch_bounds__(256) k_apply_z(Geo g, Skew sk, const T* __rest
       blk[lane][x - x0] = zs[((long long)tile * sk.ns + q + kPad) * kR + lane];
   }
   __syncthreads();
-  for (int r = warp; r < kR; r += nwarp) {
+  // all of a thread's x values are loaded before any is written back (the
+  // stores through xv would otherwise order every later load after them);
+  // 256 threads
+  T xo[kR / 8][kXC / 32];
+#pragma unroll
+  for (int rr = 0; rr < kR / 8; ++rr) {
+    const int r = warp + rr * 8;
     const int y = Y * kTY + r % kTY, z = Z * kTZ + r / kTY;
-    if (y >= g.ny || z >= g.nz) continue;
-    for (int h = lane; h < kXC; h += 32) {
-      const int x = x0 + h;
-      if (x >= g.nx) break;
-      xv[x + g.sy * y + g.sz * z] += blk[r][h];
+#pragma unroll
+    for (int hh = 0; hh < kXC / 32; ++hh) {
+      const int x = x0 + lane + 32 * hh;
+      xo[rr][hh] = (y < g.ny && z < g.nz && x < g.nx) ? xv[x + g.sy * y + g.sz * z] : T(0);
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < kR / 8; ++rr) {
+    const int r = warp + rr * 8;
+    const int y = Y * kTY + r % kTY, z = Z * kTZ + r / kTY;
+#pragma unroll
+    for (int hh = 0; hh < kXC / 32; ++hh) {
+      const int h = lane + 32 * hh, x = x0 + h;
+      if (y < g.ny && z < g.nz && x < g.nx) xv[x + g.sy * y + g.sz * z] = xo[rr][hh] + blk[r][h];
     }
   }
 }
@@ -1112,12 +1134,13 @@ cudaError_t launch_ilu_resid(const Geo& g, Buffers& b, bool single, cudaStream_t
   const Skew sk = make_skew(g);
   if (single) {
     const SingleBuffers& f = b.f32;
+    // b = the outer residual's FP32 copy (written with it by launch_residual)
     if (f.Axu != f.Ax)
-      k_resid_scaled<double, float, true><<<transpose_grid(g, sk), 256, 0, s>>>(
-          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, b.r, f.d, f.dinv, f.rds);
+      k_resid_scaled<float, float, true><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, f.r, f.d, f.dinv, f.rds);
     else
-      k_resid_scaled<double, float, false><<<transpose_grid(g, sk), 256, 0, s>>>(
-          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, b.r, f.d, f.dinv, f.rds);
+      k_resid_scaled<float, float, false><<<transpose_grid(g, sk), 256, 0, s>>>(
+          g, sk, f.Ad, f.Ax, f.Ay, f.Az, f.Axu, f.Ayu, f.Azu, f.r, f.d, f.dinv, f.rds);
   } else {
     if (b.Axu != b.Ax)
       k_resid_scaled<double, double, true><<<transpose_grid(g, sk), 256, 0, s>>>(
