@@ -463,18 +463,16 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
     const int r = (k < kTB ? r0 + k : cc0 + k - kTB);
     V[k][q] = (have_tile && r <= rhi && q < tb) ? band_at(Wr, m, r, c0 + q) : T(0);
   }
-  // element of the lower triangle owned by this thread: those right of
-  // column 0 row by row in threads 0..119 (warps 0-3), column 0 in threads
-  // 128..143 (it is only scaled, at the first pivot)
+  // element of the diagonal block's lower triangle owned by this thread:
+  // those right of column 0, row by row in threads 0..119 (warps 0-3).
+  // Column 0 is scaled at the first pivot by the threads of column 1, which
+  // form the same products.
   int er = 0, ec = -1;
   if (tid < kTri - kTB) {
     int t = tid, r = 1;
     while (t >= r) { t -= r; ++r; }
     er = r;
     ec = t + 1;
-  } else if (tid >= 128 && tid < 128 + kTB) {
-    er = tid - 128;
-    ec = 0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -482,51 +480,58 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
     rinv[0] = pivot_rcp(A[0][0], bad);
     if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
   }
-  __syncthreads();
-  // --- factor the diagonal block: at pivot q, column q is scaled and the
-  // trailing triangle updated, a_rc -= (a_rq / d_q) a_cq ---
-  for (int q = 0; q < tb; ++q) {
-    if (ec >= q && er > q && er < tb) {
-      const T t = A[er][q] * rinv[q];
-      if (ec == q) {
-        L[er][q] = t;
-      } else {
-        const T v = fma(-t, A[ec][q], A[er][ec]);
-        A[er][ec] = v;
-        if (er == q + 1 && ec == q + 1) {     // the next pivot is final
-          bool bad;
-          rinv[q + 1] = pivot_rcp(v, bad);
-          if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
-        }
-      }
-    }
-    __syncthreads();
+  // panel rows, four threads a row in warps 4-7
+  const int pk = (tid - 128) >> 2, pt = tid & 3;
+  const int src0 = (threadIdx.x & 31) & ~3;
+  T v[kTB / 4];
+  if (tid >= 128) {
+#pragma unroll
+    for (int j = 0; j < kTB / 4; ++j) v[j] = V[pk][4 * j + pt];
   }
-  // --- panel rows: l_rq = (a_rq - sum_{k<q} l_rk d_k l_qk) / d_q, four threads a row ---
-  if (tid < 4 * 2 * kTB) {
-    const int k = tid >> 2, t = tid & 3;
-    T v[kTB / 4];
+  __syncthreads();
+  // --- factor the diagonal block (warps 0-3): at pivot q, column q is
+  // scaled and the trailing triangle updated, a_rc -= (a_rq / d_q) a_cq.
+  // Beside it (warps 4-7), step q of the panel rows: l_rq = (a_rq -
+  // sum_{k<q} l_rk d_k l_qk) / d_q, which needs only column q and 1/d_q,
+  // final once pivot q-1 is done, so the panel runs one pivot behind the
+  // factorisation under the same barriers instead of after it ---
 #pragma unroll
-    for (int j = 0; j < kTB / 4; ++j) v[j] = V[k][4 * j + t];
-    const unsigned mask = 0xffffffffu;
-    const int src0 = (threadIdx.x & 31) & ~3;
-#pragma unroll
-    for (int q = 0; q < kTB; ++q) {
-      if (q < tb) {                              // uniform across the CTA
+  for (int q = 0; q < kTB; ++q) {
+    if (q < tb) {                                // uniform across the CTA
+      if (tid < 128) {
+        if (ec >= q && er > q && er < tb) {
+          const T t = A[er][q] * rinv[q];
+          if (ec == q) {
+            L[er][q] = t;
+          } else {
+            if (q == 0 && ec == 1) L[er][0] = t;
+            const T vv = fma(-t, A[ec][q], A[er][ec]);
+            A[er][ec] = vv;
+            if (er == q + 1 && ec == q + 1) {   // the next pivot is final
+              bool bad;
+              rinv[q + 1] = pivot_rcp(vv, bad);
+              if (bad && blockIdx.x == 0) atomicOr(status, kStatSingular);
+            }
+          }
+        }
+      } else {
         T l = T(0);
-        if (t == (q & 3)) {
-          VD[k][q] = v[q >> 2];
+        if (pt == (q & 3)) {
+          VD[pk][q] = v[q >> 2];
           l = v[q >> 2] * rinv[q];
           v[q >> 2] = l;
         }
-        l = __shfl_sync(mask, l, src0 | (q & 3));
+        l = __shfl_sync(0xffffffffu, l, src0 | (q & 3));
 #pragma unroll
         for (int j = 0; j < kTB / 4; ++j)
-          if (4 * j + 3 > q && 4 * j + t > q) v[j] = fma(-l, A[4 * j + t][q], v[j]);
+          if (4 * j + 3 > q && 4 * j + pt > q) v[j] = fma(-l, A[4 * j + pt][q], v[j]);
       }
+      __syncthreads();
     }
+  }
+  if (tid >= 128) {
 #pragma unroll
-    for (int j = 0; j < kTB / 4; ++j) V[k][4 * j + t] = v[j];
+    for (int j = 0; j < kTB / 4; ++j) V[pk][4 * j + pt] = v[j];
   }
   __syncthreads();
   if (have_tile) {
@@ -548,6 +553,8 @@ __global__ void __launch_bounds__(256) k_ldlt_block(int N, int m, int c0, const 
   // the first CTA publishes the diagonal block: l below, d_q on the diagonal
   if (blockIdx.x == 0 && ec >= 0 && er < tb && er - ec <= m)
     Lc[(long long)(c0 + ec) * (m + 1) + (er - ec)] = er == ec ? A[er][er] : L[er][ec];
+  if (blockIdx.x == 0 && tid < tb && tid <= m)   // column 0
+    Lc[(long long)c0 * (m + 1) + tid] = tid == 0 ? A[0][0] : L[tid][0];
 }
 
 // Row-major copy of L for the backward substitution: Lr[k*(m+1) + a] = l_{k,k-a}.
