@@ -66,8 +66,9 @@ def test_global_window_local_solver_matches_oracle(cams, precision):
 
 
 def test_large_blocks_step_matches_oracle(cams):
-    """One step of the 32^3 field with 16^3 blocks in FP64 at 1e-10: the
-    spec bar (pressure 1e-9, Newton and C-AMS counts within one)."""
+    """One step of the 32^3 field with 16^3 blocks in FP64 at 1e-10, held to
+    the FP64 parity bar: pressure within 1e-9, Newton and C-AMS counts
+    within one."""
     case = make_case("3d-64x64x64-set1", nx=32, ny=32, nz=32, coarse=(16, 16, 16), nl_tol=1e-10)
     h, bc, keep = gpu_handle(case)
     try:

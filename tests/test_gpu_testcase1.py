@@ -5,7 +5,7 @@ the paper's three steps to t* = 0.4, 1 and 2 (non-uniform steps), FP64 and
 mixed precision.
 
 Tolerances: FP64 stops at a relative ||eps|| of 1e-10 and is held to the
-spec bar at every step: pressure within 1e-9 relative L_inf, the
+FP64 parity bar at every step: pressure within 1e-9 relative L_inf, the
 Newton count and the step's C-AMS count each within one.  Mixed precision
 stops at 1e-8 and is held to the FP64 oracle's pressure within 1e-6 relative
 L_inf with the Newton count within one."""
