@@ -209,7 +209,7 @@ typedef struct {
 #define CAMS_PROF_ILU_RESID    13   /* D^{-1}(f - A p) feeding the forward sweep */
 #define CAMS_PROF_UPDATE       14   /* p += delta (mixed precision) */
 #define CAMS_PROF_ILU_APPLY    15   /* x += z after the backward sweep */
-#define CAMS_PROF_COARSE_INV   16   /* Z = L^{-1} of the mixed coarse solve's FP32 factor */
+#define CAMS_PROF_COARSE_INV   16   /* Z = L^{-1} of the FP32 copy of the FP64 coarse factor (mixed) */
 #define CAMS_PROF_CLASSES      17
 
 /* (a1) Set up a solver for one grid and permeability field.
