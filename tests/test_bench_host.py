@@ -64,3 +64,25 @@ def test_restriction_override_reaches_the_oracle_leg(bench):
     w = bench.WORKLOADS["2d-40x40"].with_(restriction=2)
     out = bench.run_reference(Args, w, 0, 1)
     assert out["config"]["restriction"] == "MSFE+closing MSFV"
+
+
+def test_measured_traffic_matches_the_launch_list_profile(bench):
+    """The DRAM traffic the bench line reports for the mixed 4M-cell
+    smoother classes is the committed launch list's read + write per launch
+    (profiles/launch_list_3d-200x200x100-mixed.md), to the 0.1 MB the table
+    prints."""
+    import re
+    path = os.path.join(ROOT, "profiles", "launch_list_3d-200x200x100-mixed.md")
+    rows = {}
+    for line in open(path):
+        m = re.match(r"\| (k_\S+(?:\\<[^|]*)?) \| (\d+) \| [\d.]+ \| [\d.]+% \| ([\d.]+) MB \| ([\d.]+) MB \|", line)
+        if m:
+            rows[m.group(1).replace("\\<", "<").strip()] = float(m.group(3)) + float(m.group(4))
+    kernels = {"ilu_fwd": "k_sweep_warp<FwdSolve<float>, 0>",
+               "ilu_bwd": "k_sweep_warp<BwdSolve<float>, 1>",
+               "ilu_resid": "k_resid_scaled<float, float, 0>",
+               "ilu_apply": "k_apply_z<float>"}
+    for cls, kern in kernels.items():
+        assert kern in rows, kern
+        got = bench.MEASURED_TRAFFIC[("3d-200x200x100-mixed", cls)] / 1e6
+        assert abs(got - rows[kern]) <= 0.15, (cls, got, rows[kern])
